@@ -1,0 +1,341 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these tests compares the oracle with itself: every expected value comes
+from a closed form, a finite difference, a theorem of the paper's Sec. 3, a
+textbook special case, brute force, or a published known-answer vector.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import gmm_knn_graph, planted_dense, uniform_init
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def _rand_nonneg(g, n, r, scale=1.0):
+    return g.random((n, r)) * scale
+
+
+def _small_problem(n=24, r=3, seed=7):
+    A, _ = planted_dense(n, r, 0.01, seed=seed)
+    W = uniform_init(n, r, math.sqrt(A.mean() / r), seed=seed + 1)
+    return A, W
+
+
+# ---------------------------------------------------------------------------
+# Philox (published known-answer vectors; Box-Muller moments)
+# ---------------------------------------------------------------------------
+
+def test_philox_known_answers(repo_root):
+    path = os.path.join(repo_root, "tests", "golden", "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for row in rows:
+        vals = [int(x, 16) for x in row]
+        out = O.philox4x32(*[np.uint64(v) for v in vals[:6]])
+        assert [int(x) for x in out] == vals[6:]
+
+
+def test_philox_streams_moments():
+    Z = O.philox_gaussian(300, 401, seed=12345)  # odd column count: pairs span rows
+    N = Z.size
+    assert abs(Z.mean()) < 5.0 / math.sqrt(N)
+    assert abs(Z.var() - 1.0) < 5.0 * math.sqrt(2.0 / N)
+    U = O.philox_uniform(300, 400, seed=99)
+    assert U.min() > 0.0 and U.max() < 1.0
+    assert abs(U.mean() - 0.5) < 5.0 / math.sqrt(12.0 * U.size)
+    # distinct seeds give distinct streams
+    assert not np.array_equal(O.philox_gaussian(4, 4, 1), O.philox_gaussian(4, 4, 2))
+
+
+# ---------------------------------------------------------------------------
+# Objectives: definition vs Frobenius expansion
+# ---------------------------------------------------------------------------
+
+def test_closed_form_objectives_match_definition():
+    g = np.random.default_rng(1)
+    A, W = _small_problem(30, 4, seed=3)
+    Ht = _rand_nonneg(g, 30, 4)
+    L = O.paper_laplacian(A)
+    for gamma in (0.0, 0.3):
+        fe = O.direct_objective(A, W, gamma, L, "explicit")
+        fc = O.direct_objective(A, W, gamma, L, "closed")
+        assert abs(fe - fc) <= 1e-12 * abs(fe)
+        pe = O.penalty_objective(A, W, Ht, 0.7, gamma, L, "explicit")
+        pc = O.penalty_objective(A, W, Ht, 0.7, gamma, L, "closed")
+        assert abs(pe - pc) <= 1e-12 * abs(pe)
+    # LAI operator: ||U E U^T||^2 = sum lam^2 enters the closed form
+    U, _ = np.linalg.qr(g.normal(size=(30, 5)))
+    op = O.LaiOperator(U, g.normal(size=5) * 10)
+    fe = O.penalty_objective(op, W, Ht, 0.2, 0.0, None, "explicit")
+    fc = O.penalty_objective(op, W, Ht, 0.2, 0.0, None, "closed")
+    assert abs(fe - fc) <= 1e-12 * abs(fe)
+
+
+def test_direct_objective_brute_sum():
+    """1/4 sum_ij (V_ij - sum_c W_ic W_jc)^2 written with scalar loops."""
+    A, W = _small_problem(6, 2, seed=11)
+    s = 0.0
+    for i in range(6):
+        for j in range(6):
+            s += (A[i, j] - sum(W[i, c] * W[j, c] for c in range(2))) ** 2
+    assert abs(O.direct_objective(A, W) - 0.25 * s) <= 1e-13 * s
+
+
+# ---------------------------------------------------------------------------
+# Gradients: central finite differences
+# ---------------------------------------------------------------------------
+
+def _fd_check(f, grad, X, h=1e-6, tol=1e-6):
+    G = grad(X)
+    g = np.random.default_rng(5)
+    for _ in range(6):
+        E = g.normal(size=X.shape)
+        d = (f(X + h * E) - f(X - h * E)) / (2 * h)
+        a = float(np.sum(G * E))
+        assert abs(d - a) <= tol * max(1.0, abs(a)), (d, a)
+
+
+def test_gradients_finite_differences():
+    g = np.random.default_rng(2)
+    A, W = _small_problem(12, 3, seed=5)
+    Ht = _rand_nonneg(g, 12, 3)
+    Ldense = O.paper_laplacian(A)
+    lam, gam = 0.4, 0.25
+    _fd_check(lambda X: O.direct_objective(A, X), lambda X: O.direct_gradient(A, X), W)
+    _fd_check(lambda X: O.direct_objective(A, X, gam, Ldense),
+              lambda X: O.direct_gradient(A, X, gam, Ldense), W)
+    _fd_check(lambda X: O.penalty_objective(A, X, Ht, lam),
+              lambda X: O.penalty_grad_W(A, X, Ht, lam), W)
+    _fd_check(lambda X: O.penalty_objective(A, W, X, lam, gam, Ldense),
+              lambda X: O.penalty_grad_Ht(A, W, X, lam, gam, Ldense), Ht)
+    U, _ = np.linalg.qr(g.normal(size=(12, 4)))
+    op = O.LaiOperator(U, g.normal(size=4) * 3)
+    _fd_check(lambda X: O.penalty_objective(op, X, Ht, lam),
+              lambda X: O.penalty_grad_W(op, X, Ht, lam), W)
+    _fd_check(lambda X: O.direct_objective(op, X), lambda X: O.direct_gradient(op, X), W)
+
+
+# ---------------------------------------------------------------------------
+# rho_0 and the Lipschitz bounds (Sec. 3.1-3.2)
+# ---------------------------------------------------------------------------
+
+def test_spectral_norm_against_eigensolver():
+    g = np.random.default_rng(4)
+    for (n, r) in [(50, 8), (200, 16), (30, 1), (64, 32)]:
+        X = _rand_nonneg(g, n, r)
+        G = X.T @ X
+        ref = float(np.linalg.eigvalsh(G)[-1])
+        assert abs(O.spectral_norm(G, 50) - ref) <= 1e-12 * ref
+    assert O.spectral_norm(np.zeros((3, 3))) == 0.0
+
+
+def test_lipschitz_bounds_random_pairs():
+    g = np.random.default_rng(8)
+    A, _ = _small_problem(20, 3, seed=9)
+    Ht = _rand_nonneg(g, 20, 3)
+    W = _rand_nonneg(g, 20, 3)
+    lam, gam = 0.5, 0.3
+    L = O.paper_laplacian(A)
+    Lw = np.linalg.eigvalsh(Ht.T @ Ht)[-1] + lam
+    Lh = np.linalg.eigvalsh(W.T @ W)[-1] + lam + gam * np.linalg.eigvalsh(L)[-1]
+    for _ in range(20):
+        X1, X2 = g.normal(size=(20, 3)), g.normal(size=(20, 3))
+        d = np.linalg.norm(O.penalty_grad_W(A, X1, Ht, lam) - O.penalty_grad_W(A, X2, Ht, lam))
+        assert d <= Lw * np.linalg.norm(X1 - X2) * (1 + 1e-12)
+        d = np.linalg.norm(O.penalty_grad_Ht(A, W, X1, lam, gam, L) - O.penalty_grad_Ht(A, W, X2, lam, gam, L))
+        assert d <= Lh * np.linalg.norm(X1 - X2) * (1 + 1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 invariants (Sec. 3.1 restatement of Li et al.)
+# ---------------------------------------------------------------------------
+
+def test_descent_lemma_and_reference_monotonicity():
+    A, W = _small_problem(40, 4, seed=21)
+    opts = O.Options(formulation="penalty", phi=1.0, memory=0, max_iter=15, tol=0.0)
+    _, _, info = O.snmpbb_penalty(A, W, W, opts)
+    nsteps = 0
+    for rec in info["trace"]:
+        for tr in (rec["w_trace"], rec["h_trace"]):
+            prevF = math.inf
+            for s in tr:
+                # <grad f(Z), D_alpha(Z)> <= -(1/alpha) ||D_alpha(Z)||^2
+                assert s["gd"] <= -s["dd"] / s["alpha"] + 1e-9 * max(1.0, abs(s["gd"]))
+                # f(W_k) <= F_k <= F_{k-1}
+                assert s["f"] <= s["F"] * (1 + 1e-13) + 1e-12
+                assert s["F"] <= prevF * (1 + 1e-13) + 1e-12
+                prevF = s["F"]
+                assert s["beta"] > 0.0  # finite backtracking
+                nsteps += 1
+    assert nsteps == 15 * 2 * opts.inner_iters
+
+
+def test_bb_step_within_block_curvature():
+    """In a block, Y = S (H H^T + lambda I) (Sec. 3.3), so BB1 lies in
+    [1/lambda_max, 1/lambda_min] of H H^T + lambda I unless clamped."""
+    A, W = _small_problem(40, 4, seed=31)
+    lam = 0.5
+    opts = O.Options(formulation="penalty", lambda_sym=lam, max_iter=4, tol=0.0)
+    Ht = W.copy()
+    ev = np.linalg.eigvalsh(Ht.T @ Ht + lam * np.eye(4))
+    _, _, info = O.nmpbb(lambda X: O.penalty_objective(A, X, Ht, lam),
+                         lambda X: O.penalty_grad_W(A, X, Ht, lam), W,
+                         lambda X: O.spectral_norm(Ht.T @ Ht), 8, opts)
+    for s in info["trace"][1:]:
+        assert 1.0 / ev[-1] * (1 - 1e-10) <= s["alpha"] <= 1.0 / ev[0] * (1 + 1e-10)
+
+
+def test_max_memory_reference():
+    A, W = _small_problem(30, 3, seed=41)
+    opts = O.Options(formulation="direct", memory=3, max_iter=12, tol=0.0)
+    _, info = O.snmpbb_direct(A, W, opts)
+    fs = [info["trace"][0]["f"]] + [s["f_next"] for s in info["trace"]]
+    for k, s in enumerate(info["trace"]):
+        if k > 0:
+            assert s["F"] == max(fs[max(0, k - 2):k + 1])
+
+
+# ---------------------------------------------------------------------------
+# End-to-end special cases
+# ---------------------------------------------------------------------------
+
+def test_planted_exact_recovery_and_kkt():
+    g = np.random.default_rng(51)
+    W0 = g.random((40, 3))
+    A = W0 @ W0.T
+    Winit = uniform_init(40, 3, math.sqrt(A.mean() / 3), seed=52)
+    opts = O.Options(formulation="direct", memory=10, max_iter=6000, tol=1e-10)
+    W, info = O.snmpbb_direct(A, Winit, opts)
+    assert info["residual"] <= 1e-6
+    kkt = np.linalg.norm(np.minimum(W, O.direct_gradient(A, W)))
+    assert kkt <= 1e-8 * info["pg0"]
+    opts = O.Options(formulation="penalty", lambda_sym=1.0, max_iter=3000, tol=1e-10, objective="closed")
+    W, Ht, info = O.snmpbb_penalty(A, Winit, Winit, opts)
+    assert info["residual"] <= 1e-6
+    assert np.linalg.norm(W - Ht) <= 1e-5 * np.linalg.norm(W)
+
+
+def test_rank_one_perron_closed_form():
+    """r = 1 and V entrywise positive: the minimiser of 1/4 ||V - w w^T||^2 over
+    w >= 0 is sqrt(lambda_1) v_1 (Perron-Frobenius, Eckart-Young)."""
+    g = np.random.default_rng(61)
+    B = g.random((25, 25)) + 0.1
+    V = B + B.T
+    lam, vec = np.linalg.eigh(V)
+    v1 = np.abs(vec[:, -1])
+    w_star = math.sqrt(lam[-1]) * v1
+    w0 = uniform_init(25, 1, 1.0, seed=62)
+    opts = O.Options(formulation="direct", memory=10, max_iter=3000, tol=1e-12)
+    w, info = O.snmpbb_direct(V, w0, opts)
+    assert np.linalg.norm(w[:, 0] - w_star) <= 1e-7 * np.linalg.norm(w_star)
+
+
+def test_brute_force_tiny_grid():
+    """n = 4, r = 1: the converged objective is no worse than the minimum over a
+    uniform grid of w >= 0, and the grid minimum is within its spacing."""
+    g = np.random.default_rng(71)
+    B = g.random((4, 4))
+    V = B @ B.T + 0.05
+    h = 0.025
+    axis = np.arange(0.0, 2.0 + h / 2, h)
+    best = math.inf
+    for w0 in axis:
+        w = np.stack(np.meshgrid(np.array([w0]), axis, axis, axis, indexing="ij"), -1).reshape(-1, 4)
+        outer = w[:, :, None] * w[:, None, :]
+        f = 0.25 * np.sum((V[None] - outer) ** 2, axis=(1, 2))
+        best = min(best, float(f.min()))
+    for seed in (72, 73):
+        # start drawn as the configs draw it: U[0, sqrt(mean(V)/r)]
+        w0 = uniform_init(4, 1, math.sqrt(V.mean()), seed)
+        w, info = O.snmpbb_direct(V, w0, O.Options(formulation="direct", max_iter=2000, tol=1e-12))
+        fconv = O.direct_objective(V, w)
+        assert fconv <= best + 1e-12
+        assert best - fconv <= 50 * h  # grid within a Lipschitz-times-spacing margin
+
+
+def test_objective_modes_give_same_iterates():
+    A, W = _small_problem(30, 3, seed=81)
+    o1 = O.Options(formulation="penalty", max_iter=8, tol=0.0, objective="explicit")
+    o2 = O.Options(formulation="penalty", max_iter=8, tol=0.0, objective="closed")
+    W1, H1, _ = O.snmpbb_penalty(A, W, W, o1)
+    W2, H2, _ = O.snmpbb_penalty(A, W, W, o2)
+    assert np.linalg.norm(W1 - W2) <= 1e-10 * np.linalg.norm(W1)
+    assert np.linalg.norm(H1 - H2) <= 1e-10 * np.linalg.norm(H1)
+
+
+# ---------------------------------------------------------------------------
+# Graph-SNMPBB (Sec. 2.2)
+# ---------------------------------------------------------------------------
+
+def test_graph_laplacian_properties_and_gamma_zero():
+    A_hat, Lcsr, labels, S = gmm_knn_graph(n=300, d=8, comps=3, k=10, seed=91)
+    Sd = S.to_dense()
+    assert np.allclose(Sd, Sd.T)
+    L = O.paper_laplacian(Sd)
+    ev = np.linalg.eigvalsh(L)
+    assert ev[0] >= -1e-12 and ev[-1] <= 2.0 + 1e-12
+    Ld = Lcsr.to_dense()
+    assert np.allclose(Ld, np.diag(Sd.sum(1)) - Sd)
+    assert np.allclose(A_hat.to_dense(), Sd / np.sqrt(np.outer(Sd.sum(1), Sd.sum(1))))
+    X = uniform_init(300, 3, 1.0, 92)
+    assert O.inner(X, Ld @ X) >= 0.0
+    Ad = A_hat.to_dense()
+    W = uniform_init(300, 3, math.sqrt(Ad.mean() / 3), 93)
+    a = O.snmpbb_penalty(Ad, W, W, O.Options(max_iter=5, tol=0.0, gamma=0.0), L=Ld)
+    b = O.snmpbb_penalty(Ad, W, W, O.Options(max_iter=5, tol=0.0))
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# ---------------------------------------------------------------------------
+# LAI-SNMPBB (Sec. 2.3, Sec. 3.3)
+# ---------------------------------------------------------------------------
+
+def test_lai_full_sketch_equals_exact():
+    A, W = _small_problem(20, 3, seed=101)
+    U, lam = O.lai_sketch(lambda X: A @ X, 20, 20, 0, 0, seed=102)
+    op = O.LaiOperator(U, lam)
+    assert np.linalg.norm(O.dense_of(op) - A) <= 1e-12 * np.linalg.norm(A)
+    opts = O.Options(max_iter=6, tol=0.0)
+    W1, H1, _ = O.snmpbb_penalty(A, W, W, opts)
+    W2, H2, _ = O.snmpbb_penalty(op, W, W, opts)
+    assert np.linalg.norm(W1 - W2) <= 1e-9 * np.linalg.norm(W1)
+
+
+def test_lai_exact_low_rank_and_eigenvalues():
+    g = np.random.default_rng(111)
+    Q, _ = np.linalg.qr(g.normal(size=(60, 6)))
+    ev = np.array([50.0, -20.0, 9.0, 4.0, -2.0, 1.0])
+    V = (Q * ev) @ Q.T
+    U, lam = O.lai_sketch(lambda X: V @ X, 60, 6, 4, 2, seed=112)
+    assert np.allclose(np.sort(lam), np.sort(ev), rtol=1e-10, atol=1e-10)
+    assert np.linalg.norm((U * lam) @ U.T - V) <= 1e-10 * np.linalg.norm(V)
+    assert np.allclose(U.T @ U, np.eye(6), atol=1e-12)
+
+
+def test_lai_bb_invariance_and_bias_bound():
+    A, W = _small_problem(40, 3, seed=121)
+    U, lam = O.lai_sketch(lambda X: A @ X, 40, 4, 2, 1, seed=122)
+    op = O.LaiOperator(U, lam)
+    mu = np.linalg.norm(A - O.dense_of(op))
+    g = np.random.default_rng(123)
+    Ht = g.random((40, 3))
+    lmb = 0.3
+    W1, W2 = g.random((40, 3)), g.random((40, 3))
+    y_lai = O.penalty_grad_W(op, W1, Ht, lmb) - O.penalty_grad_W(op, W2, Ht, lmb)
+    y_true = O.penalty_grad_W(A, W1, Ht, lmb) - O.penalty_grad_W(A, W2, Ht, lmb)
+    assert np.linalg.norm(y_lai - y_true) <= 1e-12 * np.linalg.norm(y_true)
+    assert np.allclose(y_true, (W1 - W2) @ (Ht.T @ Ht + lmb * np.eye(3)), rtol=1e-12, atol=1e-12)
+    bias = np.linalg.norm(O.penalty_grad_W(op, W1, Ht, lmb) - O.penalty_grad_W(A, W1, Ht, lmb))
+    assert bias <= mu * np.linalg.norm(Ht) * (1 + 1e-12)
+
+
+def test_lambda_default_rule():
+    A, _ = _small_problem(10, 2, seed=131)
+    assert O.resolve_lambda(A, O.Options()) == pytest.approx(0.01 * np.linalg.norm(A), rel=1e-15)
+    assert O.resolve_lambda(A, O.Options(lambda_sym=2.5)) == 2.5
