@@ -1,0 +1,230 @@
+/*
+ * snmf.h -- C ABI of the GB300 library for symmetric nonnegative matrix
+ * factorization by the nonmonotone projected Barzilai-Borwein method (SNMPBB)
+ * of Swart and Brust, "A Nonmonotone Gradient-Based Algorithm for Symmetric
+ * Nonnegative Matrix Factorization and Graph Clustering".
+ *
+ * Problem (Sec. 1.2, Eq. (2)):    min_{W >= 0} || A - W W^T ||_F^2,  A symmetric n x n.
+ * Penalty form (Sec. 2.1, Eq. (3)): f(W,H) = 1/2 ||A - W H||^2 + lambda/2 ||W - H^T||^2,
+ *   solved by alternating Algorithm 1 (NMPBB) over W and H; Graph-SNMPBB (Sec. 2.2,
+ *   Eq. (5)) adds gamma/2 tr(H L H^T); LAI-SNMPBB (Sec. 2.3, Eq. (8)) replaces A by a
+ *   randomized eigen-sketch U E U^T.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are row-major.  The factors W and Ht (= H^T) are n x (r * batch):
+ *     restart j occupies columns [j r, (j+1) r).
+ *   - Element type of W and Ht: double in SNMF_F64 precision, float otherwise.
+ *   - Pointers marked "device" must be CUDA device (or managed) memory of the
+ *     current device; "host" pointers are ordinary host memory.
+ *   - The library never takes ownership of caller memory.  A is borrowed (must
+ *     outlive the handle) when it lives on the device and its dtype equals the
+ *     working precision; otherwise snmf_create makes an owned device copy.
+ *   - All device work is issued on the CUDA stream given to snmf_create (NULL =
+ *     legacy default stream).  Calls are synchronous with respect to the host on
+ *     return.  A handle is not thread-safe.
+ *   - No exceptions cross the ABI.  Every call returns an snmf_status; on error a
+ *     message is available from snmf_last_error(handle).  Invalid arguments are
+ *     rejected with SNMF_ERR_ARG before any kernel is launched.
+ *   - There is no CPU fallback: a call that needs the GPU fails with
+ *     SNMF_ERR_CUDA when no usable device is present.
+ */
+#ifndef SNMF_H
+#define SNMF_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SNMF_API __attribute__((visibility("default")))
+#else
+#define SNMF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct snmf_ctx* snmf_handle;
+
+typedef enum {
+  SNMF_OK = 0,
+  SNMF_NOT_CONVERGED = 1,   /* max_iter reached before the tolerance */
+  SNMF_ERR_ARG = -1,        /* invalid argument, rejected before any launch */
+  SNMF_ERR_CUDA = -2,       /* CUDA runtime error or no device */
+  SNMF_ERR_OOM = -3,        /* device allocation failed */
+  SNMF_ERR_NUMERIC = -4,    /* NaN/Inf met in the FP64 scalar state */
+  SNMF_ERR_TIMEOUT = -5,    /* a bounded device wait ran out */
+  SNMF_ERR_STATE = -6       /* call out of order (e.g. solve on a destroyed handle) */
+} snmf_status;
+
+/* matrix kinds */
+enum { SNMF_DENSE = 0, SNMF_CSR = 1 };
+/* element types (matrix dtype) and working precisions */
+enum { SNMF_F64 = 0, SNMF_F32 = 1, SNMF_BF16 = 2, SNMF_FP8 = 3 };
+/* where a matrix passed to snmf_create lives */
+enum { SNMF_ON_DEVICE = 0, SNMF_ON_HOST = 1 };
+/* formulations */
+enum { SNMF_PENALTY = 0, SNMF_DIRECT = 1 };
+/* BB step variants */
+enum { SNMF_BB1 = 0, SNMF_BB2 = 1 };
+
+/*
+ * Symmetric input matrix A (Sec. 1.2: V in the paper).
+ *   dense: values is n x n row-major with leading dimension ld >= n (elements).
+ *   CSR:   rowptr[n+1], colidx[nnz] (int32, each row's columns in [0, n)),
+ *          values[nnz]; both triangles stored.
+ * dtype is SNMF_F64 or SNMF_F32.  location says whether the three arrays are
+ * device or host memory.
+ */
+typedef struct {
+  int32_t kind;
+  int32_t dtype;
+  int32_t location;
+  int32_t reserved;
+  int64_t n;
+  int64_t nnz;
+  int64_t ld;
+  const void* values;
+  const int32_t* rowptr;
+  const int32_t* colidx;
+} snmf_matrix;
+
+/*
+ * Solver options.  snmf_default_options fills the documented defaults.
+ */
+typedef struct {
+  int32_t formulation;     /* SNMF_PENALTY (Sec. 2.1, default) | SNMF_DIRECT (Eq. (2))       */
+  int32_t precision;       /* SNMF_F64 | SNMF_F32 (default) | SNMF_BF16 | SNMF_FP8: storage of A
+                              for the A*X products; accumulation is FP32 (FP64 in SNMF_F64) and
+                              objective, line search and BB inner products are FP64 throughout */
+  int32_t batch;           /* b random restarts sharing A (columns r*b), default 1            */
+  int32_t nonmonotone_M;   /* 0: eta averaging of Alg. 1 line 4; M > 0: max of the last M
+                              objective values (M <= 64).  Default 10                          */
+  int32_t bb_variant;      /* SNMF_BB1 <S,S>/<S,Y> (Alg. 1 line 3, default) | SNMF_BB2        */
+  int32_t max_ls;          /* line-search trials per step, default 20 (Sec. 4.1 (5))           */
+  int32_t inner_iters;     /* Algorithm 1 steps per block (penalty), default 5                */
+  int32_t max_iter;        /* outer iterations (penalty) or steps (direct), default 500        */
+  int32_t power_iters;     /* power iterations for rho = ||G||_2 (Eq. (2.11)), default 50      */
+  int32_t step_controller; /* 0: plain BB; 1: learned step multiplier (needs mlp_weights)     */
+  double lambda_sym;       /* penalty weight lambda (Eq. (3)); < 0 -> 0.01 ||A||_F (Sec. 4.1 (1)) */
+  double theta;            /* Armijo parameter, default 1e-3 (Sec. 2.4)                        */
+  double phi;              /* relaxation factor, default 1.7 (Sec. 2.4)                        */
+  double eta;              /* averaging weight for nonmonotone_M == 0, default 0.85            */
+  double alpha_min;        /* BB clamp, default 1e-10                                          */
+  double alpha_max;        /* BB clamp, default 1e10                                           */
+  double beta_shrink;      /* backtracking factor, default 0.5                                 */
+  double tol;              /* relative projected-gradient tolerance, default 1e-4              */
+  double direct_rho_factor;/* direct form: rho_k = factor ||W^T W||_2, default 3               */
+  double init_scale;       /* W == NULL init: U[0,1] * init_scale * sqrt(mean(A)/r), default 2
+                              (Sec. 4.1 (4))                                                   */
+  uint64_t seed;           /* Philox seed of the default initialisation                         */
+  const float* mlp_weights;/* host, SNMF_MLP_NPARAMS floats (layout in snmf_mlp_*), or NULL   */
+  int64_t timeout_cycles;  /* bound on device-side waits (clock64 cycles), 0 = default        */
+} snmf_options;
+
+/* Per-solve statistics (best restart = lowest objective). */
+typedef struct {
+  int32_t iters;           /* outer iterations (penalty) / steps (direct) performed          */
+  int32_t converged;       /* 1 when every restart met the tolerance                          */
+  int32_t ls_fail;         /* line searches with no accepted trial (beta set to 0)           */
+  int32_t clipped_steps;   /* direct: steps whose relaxed update had clipped entries          */
+  int32_t best_restart;
+  int32_t ax_products;     /* A*X products issued (dense GEMM / SpMM / LAI pair)             */
+  double f;                /* objective of the best restart at the returned point            */
+  double residual;         /* ||A - W Ht^T||_F / ||A||_F (direct: Ht = W), FP64               */
+  double pg_rel;           /* relative projected gradient of the best restart                 */
+  double seconds;          /* device time of the solve (CUDA events)                          */
+} snmf_stats;
+
+#define SNMF_MLP_IN 5
+#define SNMF_MLP_HIDDEN 64
+#define SNMF_MLP_NPARAMS (SNMF_MLP_IN * SNMF_MLP_HIDDEN + SNMF_MLP_HIDDEN + SNMF_MLP_HIDDEN + 1)
+
+/* Fill *opt with the defaults listed above.  Never fails. */
+SNMF_API void snmf_default_options(snmf_options* opt);
+
+/*
+ * Create a solver for the symmetric matrix *A and rank r (Sec. 1.2).
+ *   h      out: new handle (NULL on failure)
+ *   A      input matrix; dense (any precision) or CSR (SNMF_F32/SNMF_F64 precision)
+ *   r      rank, 1 <= r <= min(n, 256)
+ *   opt    options or NULL for the defaults; copied
+ *   stream cudaStream_t (as void*) for all device work of this handle
+ * Errors: SNMF_ERR_ARG for r out of range, batch < 1, r*batch > 4096, non-square or
+ * negative sizes, ld < n, CSR with nnz mismatch, unknown enum values; SNMF_ERR_OOM,
+ * SNMF_ERR_CUDA.  ||A||_F^2 of the stored (possibly quantized) A is computed here.
+ */
+SNMF_API snmf_status snmf_create(snmf_handle* h, const snmf_matrix* A, int r,
+                        const snmf_options* opt, void* stream);
+
+/*
+ * Graph-SNMPBB (Sec. 2.2, Eq. (5)): add gamma/2 tr(H L H^T) to the objective.
+ *   L      NULL: L = I - D^-1/2 A D^-1/2 with D = diag(A e) (the paper's Laplacian);
+ *          otherwise an explicit symmetric n x n CSR matrix (SNMF_F32 or SNMF_F64 values,
+ *          device or host), copied into library memory.
+ *   gamma  >= 0; 0 removes the term.
+ * Penalty form: the term enters the H block only (Sec. 2.2); direct form:
+ * gamma/2 tr(W^T L W).  Errors: SNMF_ERR_ARG (size mismatch, gamma < 0, dense L).
+ */
+SNMF_API snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma);
+
+/*
+ * LAI-SNMPBB (Sec. 2.3, Eq. (8)): build the randomized eigen-sketch A ~ U E U^T and
+ * use it for every later A*X product of this handle.
+ *   k           kept eigenpairs (largest |eigenvalue|), 1 <= k
+ *   oversample  extra sketch columns p; l = k + p <= min(n, 128)
+ *   power_iters subspace iterations Q <- orth(A Q) before Q^T A Q is formed
+ *   seed        Philox seed of the Gaussian sketch matrix
+ * ||A||^2 in the objective becomes sum(E^2).  Errors: SNMF_ERR_ARG.
+ */
+SNMF_API snmf_status snmf_lai_sketch(snmf_handle h, int k, int oversample, int power_iters,
+                            uint64_t seed);
+
+/*
+ * Run the solver (Algorithm 1 per block, Sec. 2) from the given start.
+ *   W   device, n x (r*batch), in/out.  NULL: the default initialisation
+ *       init_scale * sqrt(mean(A)/r) * U[0,1] (Philox, opt.seed) is used and the
+ *       result is kept inside the handle (read it with snmf_get_factors).
+ *   Ht  device, n x (r*batch), in/out, penalty form only; NULL: Ht_0 = W_0 (Sec. 4.1 (4)).
+ *   out optional statistics.
+ * Returns SNMF_OK when every restart met the tolerance, SNMF_NOT_CONVERGED when
+ * max_iter was reached first, or an error.
+ */
+SNMF_API snmf_status snmf_solve(snmf_handle h, void* W, void* Ht, snmf_stats* out);
+
+/*
+ * As snmf_solve, with W and Ht in HOST memory (same shapes and element types):
+ * the start is copied to the device and the result back, inside the call.
+ * W must not be NULL; Ht may be NULL (Ht_0 = W_0, result not returned).
+ */
+SNMF_API snmf_status snmf_solve_host(snmf_handle h, void* W, void* Ht, snmf_stats* out);
+
+/*
+ * Per-restart results of the last solve (host arrays of length batch; any may be NULL):
+ * objective, relative residual, relative projected gradient, iterations.
+ */
+SNMF_API snmf_status snmf_restart_stats(snmf_handle h, double* f, double* residual,
+                               double* pg_rel, int32_t* iters);
+
+/* Copy the factors held inside the handle (after a solve with W == NULL) to device
+ * buffers W / Ht (n x r*batch; either may be NULL). */
+SNMF_API snmf_status snmf_get_factors(snmf_handle h, void* W, void* Ht);
+
+/*
+ * Single product through the library's A*X kernels: Y = A X (X, Y device,
+ * n x cols of the handle's factor element type, cols <= r*batch).  Also returns
+ * <X, A X> in *xax (host, may be NULL).  Uses the LAI sketch when one is set.
+ */
+SNMF_API snmf_status snmf_apply(snmf_handle h, const void* X, void* Y, int cols, double* xax);
+
+/* Release every resource of the handle.  NULL is accepted. */
+SNMF_API snmf_status snmf_destroy(snmf_handle h);
+
+/* Message of the last error on this handle (or of the last failed create when
+ * h is NULL).  Never NULL; valid until the next call on the handle. */
+SNMF_API const char* snmf_last_error(snmf_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNMF_H */

@@ -1,0 +1,852 @@
+// C ABI of the SNMPBB library (declarations and argument contract in include/snmf.h).
+//
+// Host orchestration: every step of an iteration is a kernel on the handle's internal
+// stream; one outer iteration (penalty form: W block then H block, Sec. 2.1) or one step
+// (direct form) is captured once into a CUDA graph and replayed.  The per-restart FP64
+// state of Algorithm 1 lives on the device (snmf::Ctl); the host reads one flag every
+// few replays to stop when every restart has converged.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/snmf.h"
+#include "common.cuh"
+#include "lai.cuh"
+#include "rowops.cuh"
+
+using namespace snmf;
+
+namespace {
+
+enum BufId {
+  B_W = 0, B_HT, B_B, B_G, B_Z, B_D, B_GZ, B_XN,  // penalty
+  B_AZ, B_AD, B_AWN, B_GN,                        // direct extras (B_B = AW, B_XN = Wn)
+  B_LX, B_LZ, B_LD,                               // graph products
+  NBUF
+};
+
+std::string g_create_err;
+
+}  // namespace
+
+struct snmf_ctx {
+  int kind = 0, prec = SNMF_F32, tdtype = 1;
+  int64_t n = 0;
+  int r = 0, b = 1, N = 0;
+  size_t esz = 4;
+  snmf_options opt{};
+  cudaStream_t user = nullptr, s = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evsync = nullptr;
+  AxArgs A{};
+  void* A_owned = nullptr;
+  int32_t* rowptr_owned = nullptr;
+  int32_t* colidx_owned = nullptr;
+  void* vals_owned = nullptr;
+  double normA2 = 0.0, sumA = 0.0, lam = 0.0;
+  // graph regulariser
+  bool graph = false;
+  double gamma = 0.0;
+  AxArgs L{};
+  int32_t* L_rowptr = nullptr;
+  int32_t* L_colidx = nullptr;
+  void* L_vals = nullptr;
+  // LAI sketch
+  bool lai = false;
+  LaiOp lai_op{};
+  // workspaces
+  void* buf[NBUF] = {};
+  void* ws = nullptr;
+  size_t ws_elems = 0;
+  double *prow = nullptr, *pax = nullptr, *pax2 = nullptr, *pax3 = nullptr, *pax4 = nullptr,
+         *pclip = nullptr;
+  int nrow = 0, nax = 0;
+  double* gpart = nullptr;
+  int nchunks = 1;
+  double *G64fix = nullptr, *G64p = nullptr;  // G64p: 3 pairs [pair][b][r*r]
+  void* GT = nullptr;
+  Ctl* ctl = nullptr;
+  int* run = nullptr;
+  int* recompute = nullptr;
+  double* dsc = nullptr;   // device scratch doubles
+  int* h_flag = nullptr;   // pinned
+  std::vector<Ctl> h_ctl;
+  // captured iteration
+  cudaGraphExec_t exec = nullptr;
+  int exec_form = -1;
+  int per_iter = 0;
+  bool have_result = false;
+  int ax_count = 0;
+  std::string err;
+};
+
+namespace {
+
+snmf_status fail(snmf_ctx* h, snmf_status st, const std::string& msg) {
+  if (h) h->err = msg; else g_create_err = msg;
+  return st;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? SNMF_ERR_OOM : SNMF_ERR_CUDA,  \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                \
+  } while (0)
+
+Params make_params(const snmf_ctx* h) {
+  Params P{};
+  P.formulation = h->opt.formulation;
+  P.memory = h->opt.nonmonotone_M;
+  P.bb = h->opt.bb_variant;
+  P.max_ls = h->opt.max_ls;
+  P.max_iter = h->opt.max_iter;
+  P.power_iters = h->opt.power_iters;
+  P.controller = h->opt.step_controller;
+  P.theta = h->opt.theta;
+  P.phi = h->opt.phi;
+  P.eta = h->opt.eta;
+  P.alpha_min = h->opt.alpha_min;
+  P.alpha_max = h->opt.alpha_max;
+  P.beta_shrink = h->opt.beta_shrink;
+  P.tol = h->opt.tol;
+  P.rho_factor = h->opt.direct_rho_factor;
+  P.normA2 = h->lai ? h->lai_op.normA2 : h->normA2;
+  P.gamma = h->graph ? h->gamma : 0.0;
+  return P;
+}
+
+Dims dims(const snmf_ctx* h) {
+  Dims d;
+  d.n = h->n; d.r = h->r; d.b = h->b; d.N = h->N; d.ld = h->N;
+  return d;
+}
+
+// Y = op X (+ c X2), dots <P1, op X> -> part q0, <P2, op X> -> q0+1; returns slot count.
+int ax_apply(snmf_ctx* h, const AxArgs& op, bool use_lai, const void* X, void* Y, double c,
+             const void* X2, const void* P1, const void* P2, double* part, const int* run) {
+  Dims d = dims(h);
+  h->ax_count++;
+  if (use_lai) {
+    return lai_apply(h->lai_op, h->tdtype, d, X, Y, c, X2, P1, P2, part, run, h->s);
+  }
+  int splits = launch_ax(op, h->tdtype, h->n, h->N, h->N, X, Y, h->ws, h->ws_elems, run, h->s);
+  return launch_ax_finish_impl(h->tdtype, d, Y, h->ws, splits, c, X2, P1, P2, part, 0, run, h->s);
+}
+
+int ax_A(snmf_ctx* h, const void* X, void* Y, double c, const void* X2, const void* P1,
+         const void* P2, double* part, const int* run) {
+  return ax_apply(h, h->A, h->lai, X, Y, c, X2, P1, P2, part, run);
+}
+
+int ax_L(snmf_ctx* h, const void* X, void* Y, const void* P1, const void* P2, double* part,
+         const int* run) {
+  return ax_apply(h, h->L, false, X, Y, 0.0, nullptr, P1, P2, part, run);
+}
+
+int choose_chunks(int64_t n, int b, int r) {
+  const int ntile = (r + 63) / 64;
+  const int64_t per = (int64_t)b * ntile * ntile;
+  int64_t c = (304 + per - 1) / per;
+  c = std::max<int64_t>(1, std::min<int64_t>(c, (n + 127) / 128));
+  return (int)c;
+}
+
+void gram1(snmf_ctx* h, const void* X, const void* Y, int pair, int npairs, const Ctl* ctl) {
+  launch_gram(h->tdtype, X, Y, dims(h), pair, npairs, h->gpart, h->nchunks, ctl, h->run, h->s);
+}
+
+RowArgs row_base(snmf_ctx* h) {
+  RowArgs a{};
+  a.n = h->n; a.r = h->r; a.b = h->b; a.ld = h->N;
+  a.G = h->GT;
+  a.ctl = h->ctl;
+  a.run = h->run;
+  a.gamma = h->graph ? h->gamma : 0.0;
+  a.part = h->prow;
+  return a;
+}
+
+// ----------------------------------------------------------------------------
+// penalty form (Sec. 2.1-2.2): one block of Algorithm 1 over Xvar with Xfix fixed
+// ----------------------------------------------------------------------------
+void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
+  const Dims d = dims(h);
+  const int td = h->tdtype;
+  void* X = h->buf[xv];
+  void* Xf = h->buf[xf];
+  const bool gr = h->graph && !is_w;
+  // B = A Xfix + lambda Xfix (Eq. (2.1)/(2.2))
+  ax_A(h, Xf, h->buf[B_B], h->lam, Xf, nullptr, nullptr, h->pax, h->run);
+  // G = Xfix^T Xfix (+ lambda I in the factor-type copy); rho_0 = ||Xfix^T Xfix||_2
+  gram1(h, Xf, Xf, 0, 1, h->ctl);
+  launch_gram_reduce(td, h->gpart, h->nchunks, 1, d, h->G64fix, h->GT, 0, h->lam, h->s);
+  launch_rho(td, h->G64fix, d, h->opt.power_iters, 1.0, h->ctl, 0, h->s);
+  if (gr) ax_L(h, X, h->buf[B_LX], nullptr, nullptr, h->pax2, h->run);
+  {
+    RowArgs a = row_base(h);
+    a.X = X; a.B = h->buf[B_B]; a.LX = gr ? h->buf[B_LX] : nullptr;
+    a.gout = h->buf[B_G];
+    launch_rowgemm(td, OP_LOAD, EPI_GRAD, a, h->s);
+  }
+  launch_ctl_pen_start(h->ctl, h->prow, h->nrow, h->b, P, is_w ? 1 : 0, 0, h->s);
+  launch_any_active(h->ctl, h->b, h->run, nullptr, h->s);
+  const int K = h->opt.inner_iters;
+  for (int k = 0; k < K; ++k) {
+    // Z = Proj[X - g / rho_0], D = Proj[Z - alpha g(Z)] - Z   (Alg. 1 lines 2-3)
+    {
+      RowArgs a = row_base(h);
+      a.B = h->buf[B_B];
+      a.Dout = h->buf[B_D]; a.gZout = h->buf[B_GZ];
+      a.Wcur = X; a.gWcur = h->buf[B_G];
+      if (gr) {
+        launch_zstep(td, d, X, h->buf[B_G], h->buf[B_Z], h->ctl, h->s);
+        ax_L(h, h->buf[B_Z], h->buf[B_LZ], nullptr, nullptr, h->pax2, h->run);
+        a.X = h->buf[B_Z]; a.LX = h->buf[B_LZ];
+        launch_rowgemm(td, OP_LOAD, EPI_DIR, a, h->s);
+      } else {
+        a.X = X; a.g_in = h->buf[B_G]; a.Xout = h->buf[B_Z];
+        launch_rowgemm(td, OP_ZSTEP, EPI_DIR, a, h->s);
+      }
+    }
+    // curvature of the line-search quadratic: D^T D (and <D, L D>)
+    gram1(h, h->buf[B_D], h->buf[B_D], 0, 1, h->ctl);
+    launch_gram_reduce(td, h->gpart, h->nchunks, 1, d, h->G64p, nullptr, -1, 0.0, h->s);
+    int nl = 0;
+    if (gr) nl = ax_L(h, h->buf[B_D], h->buf[B_LD], h->buf[B_D], nullptr, h->pax3, h->run);
+    launch_ctl_pen_ls(h->ctl, h->prow, h->nrow, h->pax3, gr ? nl : 0, h->b, h->r, h->G64fix,
+                      h->G64p, P, gr ? 1 : 0, h->s);
+    // X' = Proj[Z + phi beta D], gradient, BB inner products   (Alg. 1 line 4)
+    {
+      RowArgs a = row_base(h);
+      a.B = h->buf[B_B];
+      a.gout = h->buf[B_G];
+      a.Xold = X; a.gold = h->buf[B_G];
+      a.Zold = h->buf[B_Z]; a.gZold = h->buf[B_GZ];
+      a.Xout = X;
+      if (gr) {
+        launch_xupd(td, d, h->buf[B_Z], h->buf[B_D], h->buf[B_XN], nullptr, nullptr, nullptr,
+                    h->ctl, h->pclip, h->s);
+        ax_L(h, h->buf[B_XN], h->buf[B_LX], nullptr, nullptr, h->pax2, h->run);
+        a.X = h->buf[B_XN]; a.LX = h->buf[B_LX];
+        launch_rowgemm(td, OP_LOAD, EPI_GRAD, a, h->s);
+      } else {
+        a.Zin = h->buf[B_Z]; a.Din = h->buf[B_D];
+        launch_rowgemm(td, OP_UPD, EPI_GRAD, a, h->s);
+      }
+    }
+    launch_ctl_pen_upd(h->ctl, h->prow, h->nrow, h->b, P, is_w ? 0 : 1, k == K - 1 ? 1 : 0, h->s);
+  }
+}
+
+// H gradient at the start point (enters the first joint projected gradient).
+void pen_init(snmf_ctx* h, const Params& P) {
+  const Dims d = dims(h);
+  const int td = h->tdtype;
+  launch_any_active(h->ctl, h->b, h->run, nullptr, h->s);
+  ax_A(h, h->buf[B_W], h->buf[B_B], h->lam, h->buf[B_W], nullptr, nullptr, h->pax, h->run);
+  gram1(h, h->buf[B_W], h->buf[B_W], 0, 1, h->ctl);
+  launch_gram_reduce(td, h->gpart, h->nchunks, 1, d, h->G64fix, h->GT, 0, h->lam, h->s);
+  if (h->graph) ax_L(h, h->buf[B_HT], h->buf[B_LX], nullptr, nullptr, h->pax2, h->run);
+  RowArgs a = row_base(h);
+  a.X = h->buf[B_HT]; a.B = h->buf[B_B]; a.LX = h->graph ? h->buf[B_LX] : nullptr;
+  a.gout = h->buf[B_G];
+  launch_rowgemm(td, OP_LOAD, EPI_GRAD, a, h->s);
+  launch_ctl_pen_start(h->ctl, h->prow, h->nrow, h->b, P, 0, 1, h->s);
+}
+
+void pen_iteration(snmf_ctx* h, const Params& P) {
+  pen_block(h, B_W, B_HT, true, P);
+  pen_block(h, B_HT, B_W, false, P);
+  launch_any_active(h->ctl, h->b, h->run, nullptr, h->s);
+}
+
+void pen_final(snmf_ctx* h, const Params& P) {
+  const Dims d = dims(h);
+  const int td = h->tdtype;
+  // every restart contributes to the final evaluation
+  int nax = ax_apply(h, h->A, h->lai, h->buf[B_HT], h->buf[B_B], h->lam, h->buf[B_HT],
+                     h->buf[B_W], nullptr, h->pax, nullptr);
+  gram1(h, h->buf[B_W], h->buf[B_W], 0, 3, nullptr);
+  gram1(h, h->buf[B_HT], h->buf[B_HT], 1, 3, nullptr);
+  gram1(h, h->buf[B_W], h->buf[B_HT], 2, 3, nullptr);
+  launch_gram_reduce(td, h->gpart, h->nchunks, 3, d, h->G64p, h->GT, 1, h->lam, h->s);
+  // W gradient at the final point (projected-gradient statistic); uses a temporary
+  // "all active" view: the row kernel is run with ctl entries forced live by the host.
+  RowArgs a = row_base(h);
+  a.X = h->buf[B_W]; a.B = h->buf[B_B];
+  a.gout = h->buf[B_G];
+  a.run = nullptr;
+  a.ctl = h->ctl + h->b;  // second Ctl array: all active (set by the host)
+  launch_rowgemm(td, OP_LOAD, EPI_GRAD, a, h->s);
+  const int64_t rr = (int64_t)h->r * h->r * h->b;
+  launch_ctl_final_pen(h->ctl, h->pax, nax, h->prow, h->nrow, h->G64p, h->G64p + rr,
+                       h->G64p + 2 * rr, h->b, h->r, P, h->s);
+}
+
+// ----------------------------------------------------------------------------
+// direct form (Eq. (2) with 1/4 scaling): one step of Algorithm 1
+// ----------------------------------------------------------------------------
+void dir_init(snmf_ctx* h, const Params& P) {
+  const Dims d = dims(h);
+  const int td = h->tdtype;
+  int nax = ax_apply(h, h->A, h->lai, h->buf[B_W], h->buf[B_B], 0.0, nullptr, h->buf[B_W], nullptr,
+                     h->pax, nullptr);
+  int nlx = 0;
+  if (h->graph)
+    nlx = ax_apply(h, h->L, false, h->buf[B_W], h->buf[B_LX], 0.0, nullptr, h->buf[B_W], nullptr,
+                   h->pax2, nullptr);
+  gram1(h, h->buf[B_W], h->buf[B_W], 0, 1, nullptr);
+  launch_gram_reduce(td, h->gpart, h->nchunks, 1, d, h->G64fix, h->GT, 0, 0.0, h->s);
+  RowArgs a = row_base(h);
+  a.X = h->buf[B_W]; a.B = h->buf[B_B]; a.LX = h->graph ? h->buf[B_LX] : nullptr;
+  a.gout = h->buf[B_G];
+  a.run = nullptr;
+  a.ctl = h->ctl + h->b;  // all live
+  launch_rowgemm(td, OP_LOAD, EPI_GRAD, a, h->s);
+  launch_ctl_dir_init(h->ctl, h->pax, nax, h->prow, h->nrow, h->graph ? h->pax2 : nullptr, nlx,
+                      h->G64fix, h->b, h->r, P, h->s);
+  launch_any_active(h->ctl, h->b, h->run, h->recompute, h->s);
+}
+
+void dir_iteration(snmf_ctx* h, const Params& P) {
+  const Dims d = dims(h);
+  const int td = h->tdtype;
+  const int64_t rr = (int64_t)h->r * h->r * h->b;
+  void *W = h->buf[B_W], *AW = h->buf[B_B], *g = h->buf[B_G];
+  void *Z = h->buf[B_Z], *AZ = h->buf[B_AZ], *D = h->buf[B_D], *AD = h->buf[B_AD];
+  void *Wn = h->buf[B_XN], *AWn = h->buf[B_AWN], *gn = h->buf[B_GN];
+  // rho_k = factor ||W^T W||_2 and alpha_k
+  launch_rho(td, h->G64fix, d, h->opt.power_iters, h->opt.direct_rho_factor, h->ctl, 0, h->s);
+  launch_ctl_dir_alpha(h->ctl, h->b, P, h->s);
+  launch_zstep(td, d, W, g, Z, h->ctl, h->s);
+  int nz = ax_A(h, Z, AZ, 0.0, nullptr, Z, nullptr, h->pax, h->run);
+  if (h->graph) ax_L(h, Z, h->buf[B_LZ], Z, nullptr, h->pax3, h->run);
+  gram1(h, Z, Z, 0, 1, h->ctl);
+  launch_gram_reduce(td, h->gpart, h->nchunks, 1, d, h->G64p, h->GT, 0, 0.0, h->s);
+  {
+    RowArgs a = row_base(h);
+    a.X = Z; a.B = AZ; a.LX = h->graph ? h->buf[B_LZ] : nullptr;
+    a.Dout = D;
+    launch_rowgemm(td, OP_LOAD, EPI_DIR, a, h->s);
+  }
+  int nd = ax_A(h, D, AD, 0.0, nullptr, Z, D, h->pax2, h->run);
+  if (h->graph) ax_L(h, D, h->buf[B_LD], D, nullptr, h->pax4, h->run);
+  gram1(h, Z, D, 0, 2, h->ctl);
+  gram1(h, D, D, 1, 2, h->ctl);
+  launch_gram_reduce(td, h->gpart, h->nchunks, 2, d, h->G64p + rr, nullptr, -1, 0.0, h->s);
+  launch_ctl_dir_ls(h->ctl, h->pax, nz, h->prow, h->nrow, h->pax2, nd, h->G64p, h->G64p + rr,
+                    h->G64p + 2 * rr, h->graph ? h->pax3 : nullptr, h->graph ? h->pax4 : nullptr,
+                    h->b, h->r, P, h->s);
+  int ncl = launch_xupd(td, d, Z, D, Wn, AZ, AD, AWn, h->ctl, h->pclip, h->s);
+  launch_ctl_dir_clip(h->ctl, h->pclip, ncl, h->b, h->recompute, h->s);
+  int nre = ax_A(h, Wn, AWn, 0.0, nullptr, Wn, nullptr, h->pax, h->recompute);
+  int nlx = 0;
+  if (h->graph) nlx = ax_L(h, Wn, h->buf[B_LX], Wn, nullptr, h->pax3, h->run);
+  gram1(h, Wn, Wn, 0, 1, h->ctl);
+  launch_gram_reduce(td, h->gpart, h->nchunks, 1, d, h->G64fix, h->GT, 0, 0.0, h->s);
+  {
+    RowArgs a = row_base(h);
+    a.X = Wn; a.B = AWn; a.LX = h->graph ? h->buf[B_LX] : nullptr;
+    a.gout = gn; a.Xold = W; a.gold = g;
+    launch_rowgemm(td, OP_LOAD, EPI_GRAD, a, h->s);
+  }
+  launch_ctl_dir_upd(h->ctl, h->prow, h->nrow, h->pax, nre, h->graph ? h->pax3 : nullptr, nlx,
+                     h->G64fix, h->recompute, h->b, h->r, P, h->s);
+  launch_copy_live(td, d, Wn, W, h->ctl, h->s);
+  launch_copy_live(td, d, AWn, AW, h->ctl, h->s);
+  launch_copy_live(td, d, gn, g, h->ctl, h->s);
+  launch_any_active(h->ctl, h->b, h->run, h->recompute, h->s);
+}
+
+void dir_final(snmf_ctx* h, const Params& P) {
+  launch_ctl_final_dir(h->ctl, h->G64fix, h->b, h->r, P, h->s);
+}
+
+snmf_status alloc_buffers(snmf_ctx* h) {
+  const size_t fe = (size_t)h->n * h->N;
+  for (int i = 0; i < NBUF; ++i) {
+    CK(cudaMalloc(&h->buf[i], fe * h->esz));
+    CK(cudaMemsetAsync(h->buf[i], 0, fe * h->esz, h->s));
+  }
+  h->ws_elems = (h->kind == AX_DENSE) ? 8 * fe : 0;
+  if (h->ws_elems) CK(cudaMalloc(&h->ws, h->ws_elems * h->esz));
+  const Dims d = dims(h);
+  h->nrow = rowgemm_slots(d);
+  h->nax = (int)((h->n + kRowTile - 1) / kRowTile);
+  const size_t prec_n = (size_t)std::max(h->nrow, h->nax) * h->b * kNQ;
+  double** parts[] = {&h->prow, &h->pax, &h->pax2, &h->pax3, &h->pax4, &h->pclip};
+  for (double** p : parts) {
+    CK(cudaMalloc(p, prec_n * sizeof(double)));
+    CK(cudaMemsetAsync(*p, 0, prec_n * sizeof(double), h->s));
+  }
+  h->nchunks = choose_chunks(h->n, h->b, h->r);
+  const size_t rr = (size_t)h->r * h->r * h->b;
+  CK(cudaMalloc(&h->gpart, (size_t)h->nchunks * 3 * rr * sizeof(double)));
+  CK(cudaMalloc(&h->G64fix, rr * sizeof(double)));
+  CK(cudaMalloc(&h->G64p, 3 * rr * sizeof(double)));
+  CK(cudaMalloc(&h->GT, rr * h->esz));
+  CK(cudaMalloc(&h->ctl, 2 * h->b * sizeof(Ctl)));
+  CK(cudaMalloc(&h->run, sizeof(int)));
+  CK(cudaMalloc(&h->recompute, sizeof(int)));
+  CK(cudaMalloc(&h->dsc, 4096 * sizeof(double)));
+  CK(cudaMallocHost(&h->h_flag, sizeof(int)));
+  return SNMF_OK;
+}
+
+bool valid_enum(int v, int lo, int hi) { return v >= lo && v <= hi; }
+
+snmf_status validate_options(const snmf_options& o) {
+  if (!valid_enum(o.formulation, 0, 1) || !valid_enum(o.precision, 0, 3) ||
+      !valid_enum(o.bb_variant, 0, 1))
+    return SNMF_ERR_ARG;
+  if (o.batch < 1 || o.nonmonotone_M < 0 || o.nonmonotone_M > kMaxHist || o.max_ls < 1 ||
+      o.inner_iters < 1 || o.max_iter < 0 || o.power_iters < 1)
+    return SNMF_ERR_ARG;
+  if (!(o.theta > 0.0 && o.theta < 1.0) || !(o.phi > 0.0) || !(o.eta >= 0.0 && o.eta < 1.0) ||
+      !(o.alpha_min > 0.0 && o.alpha_min < o.alpha_max) || !(o.beta_shrink > 0.0 && o.beta_shrink < 1.0) ||
+      !(o.tol >= 0.0) || !(o.direct_rho_factor > 0.0))
+    return SNMF_ERR_ARG;
+  if (o.step_controller && !o.mlp_weights) return SNMF_ERR_ARG;
+  return SNMF_OK;
+}
+
+snmf_status sync_user(snmf_ctx* h) {
+  CK(cudaEventRecord(h->evsync, h->user));
+  CK(cudaStreamWaitEvent(h->s, h->evsync, 0));
+  return SNMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void snmf_default_options(snmf_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->formulation = SNMF_PENALTY;
+  o->precision = SNMF_F32;
+  o->batch = 1;
+  o->nonmonotone_M = 10;
+  o->bb_variant = SNMF_BB1;
+  o->max_ls = 20;
+  o->inner_iters = 5;
+  o->max_iter = 500;
+  o->power_iters = 50;
+  o->step_controller = 0;
+  o->lambda_sym = -1.0;
+  o->theta = 1e-3;
+  o->phi = 1.7;
+  o->eta = 0.85;
+  o->alpha_min = 1e-10;
+  o->alpha_max = 1e10;
+  o->beta_shrink = 0.5;
+  o->tol = 1e-4;
+  o->direct_rho_factor = 3.0;
+  o->init_scale = 2.0;
+  o->seed = 0;
+  o->mlp_weights = nullptr;
+  o->timeout_cycles = 0;
+}
+
+snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const snmf_options* opt,
+                        void* stream) {
+  snmf_ctx* h = nullptr;
+  if (!out) return fail(nullptr, SNMF_ERR_ARG, "h is NULL");
+  *out = nullptr;
+  if (!Am) return fail(nullptr, SNMF_ERR_ARG, "A is NULL");
+  snmf_options o;
+  if (opt) o = *opt; else snmf_default_options(&o);
+  if (validate_options(o) != SNMF_OK) return fail(nullptr, SNMF_ERR_ARG, "invalid options");
+  if (Am->kind != SNMF_DENSE && Am->kind != SNMF_CSR) return fail(nullptr, SNMF_ERR_ARG, "unknown matrix kind");
+  if (Am->dtype != SNMF_F64 && Am->dtype != SNMF_F32) return fail(nullptr, SNMF_ERR_ARG, "A dtype must be F64 or F32");
+  if (Am->location != SNMF_ON_DEVICE && Am->location != SNMF_ON_HOST) return fail(nullptr, SNMF_ERR_ARG, "bad location");
+  if (Am->n <= 0 || !Am->values) return fail(nullptr, SNMF_ERR_ARG, "n must be positive and values non-NULL");
+  if (r < 1 || r > kMaxR || r > Am->n) return fail(nullptr, SNMF_ERR_ARG, "r out of range [1, min(n,256)]");
+  if ((int64_t)r * o.batch > 4096) return fail(nullptr, SNMF_ERR_ARG, "r*batch > 4096");
+  if (Am->kind == SNMF_DENSE && Am->ld < Am->n) return fail(nullptr, SNMF_ERR_ARG, "ld < n");
+  if (Am->kind == SNMF_CSR) {
+    if (!Am->rowptr || !Am->colidx || Am->nnz < 0) return fail(nullptr, SNMF_ERR_ARG, "CSR arrays missing");
+    if (o.precision == SNMF_BF16 || o.precision == SNMF_FP8)
+      return fail(nullptr, SNMF_ERR_ARG, "CSR supports F64/F32 precision");
+  }
+  if (o.precision == SNMF_BF16 || o.precision == SNMF_FP8)
+    return fail(nullptr, SNMF_ERR_ARG, "BF16/FP8 precision not available in this build");
+  if (o.formulation == SNMF_PENALTY && o.step_controller)
+    return fail(nullptr, SNMF_ERR_ARG, "learned step controller not available in this build");
+
+  h = new snmf_ctx();
+  h->opt = o;
+  h->kind = Am->kind == SNMF_DENSE ? AX_DENSE : AX_CSR;
+  h->prec = o.precision;
+  h->tdtype = (o.precision == SNMF_F64) ? 0 : 1;
+  h->esz = h->tdtype == 0 ? 8 : 4;
+  h->n = Am->n;
+  h->r = r;
+  h->b = o.batch;
+  h->N = r * o.batch;
+  h->user = (cudaStream_t)stream;
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
+    delete h;
+    return fail(nullptr, SNMF_ERR_CUDA, "no CUDA device");
+  }
+  auto bail = [&](snmf_status st) {
+    g_create_err = h->err;
+    snmf_destroy(h);
+    return st;
+  };
+#define CKC(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                         \
+      return bail(e_ == cudaErrorMemoryAllocation ? SNMF_ERR_OOM : SNMF_ERR_CUDA);         \
+    }                                                                                      \
+  } while (0)
+  init_kernel_attributes();
+  CKC(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
+  CKC(cudaEventCreate(&h->ev0));
+  CKC(cudaEventCreate(&h->ev1));
+  CKC(cudaEventCreateWithFlags(&h->evsync, cudaEventDisableTiming));
+  if (sync_user(h) != SNMF_OK) return bail(SNMF_ERR_CUDA);
+  const int src_dt = Am->dtype == SNMF_F64 ? 0 : 1;
+  const int64_t n = h->n;
+  if (h->kind == AX_DENSE) {
+    // working copy of A in the factor type unless it can be borrowed
+    const bool borrow = Am->location == SNMF_ON_DEVICE && src_dt == h->tdtype;
+    if (borrow) {
+      h->A.A = Am->values;
+      h->A.lda = Am->ld;
+    } else {
+      const void* src = Am->values;
+      void* staging = nullptr;
+      const size_t sbytes = (size_t)n * Am->ld * (src_dt == 0 ? 8 : 4);
+      if (Am->location == SNMF_ON_HOST) {
+        CKC(cudaMalloc(&staging, sbytes));
+        CKC(cudaMemcpyAsync(staging, src, sbytes, cudaMemcpyHostToDevice, h->s));
+        src = staging;
+      }
+      if (src_dt == h->tdtype) {
+        h->A_owned = staging;
+        h->A.A = staging;
+        h->A.lda = Am->ld;
+      } else {
+        CKC(cudaMalloc(&h->A_owned, (size_t)n * n * h->esz));
+        launch_convert(src_dt, h->tdtype, src, n, n, Am->ld, h->A_owned, n, h->s);
+        h->A.A = h->A_owned;
+        h->A.lda = n;
+        if (staging) {
+          CKC(cudaStreamSynchronize(h->s));
+          cudaFree(staging);
+        }
+      }
+    }
+    h->A.a_dtype = h->tdtype;
+    h->A.kind = AX_DENSE;
+  } else {
+    const int64_t nnz = Am->nnz;
+    if (Am->location == SNMF_ON_HOST) {
+      const int32_t* rp = Am->rowptr;
+      if (rp[0] != 0 || rp[n] != nnz) {
+        h->err = "CSR rowptr inconsistent with nnz";
+        return bail(SNMF_ERR_ARG);
+      }
+      for (int64_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) { h->err = "CSR rowptr not monotone"; return bail(SNMF_ERR_ARG); }
+      for (int64_t e = 0; e < nnz; ++e)
+        if (Am->colidx[e] < 0 || Am->colidx[e] >= n) { h->err = "CSR column index out of range"; return bail(SNMF_ERR_ARG); }
+      CKC(cudaMalloc(&h->rowptr_owned, (n + 1) * sizeof(int32_t)));
+      CKC(cudaMalloc(&h->colidx_owned, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+      CKC(cudaMalloc(&h->vals_owned, std::max<int64_t>(nnz, 1) * (src_dt == 0 ? 8 : 4)));
+      CKC(cudaMemcpyAsync(h->rowptr_owned, rp, (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, h->s));
+      if (nnz) {
+        CKC(cudaMemcpyAsync(h->colidx_owned, Am->colidx, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, h->s));
+        CKC(cudaMemcpyAsync(h->vals_owned, Am->values, nnz * (src_dt == 0 ? 8 : 4), cudaMemcpyHostToDevice, h->s));
+      }
+      h->A.rowptr = h->rowptr_owned;
+      h->A.colidx = h->colidx_owned;
+      h->A.vals = h->vals_owned;
+    } else {
+      int32_t ends[2] = {0, 0};
+      CKC(cudaMemcpyAsync(&ends[0], Am->rowptr, sizeof(int32_t), cudaMemcpyDeviceToHost, h->s));
+      CKC(cudaMemcpyAsync(&ends[1], Am->rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, h->s));
+      CKC(cudaStreamSynchronize(h->s));
+      if (ends[0] != 0 || ends[1] != nnz) { h->err = "CSR rowptr inconsistent with nnz"; return bail(SNMF_ERR_ARG); }
+      h->A.rowptr = Am->rowptr;
+      h->A.colidx = Am->colidx;
+      h->A.vals = Am->values;
+    }
+    h->A.v_dtype = src_dt;
+    h->A.kind = AX_CSR;
+    h->A.lda = nnz;
+  }
+  snmf_status st = alloc_buffers(h);
+  if (st != SNMF_OK) return bail(st);
+  // ||A||_F^2 and mean(A) of the stored operator
+  if (h->kind == AX_DENSE)
+    launch_matrix_sums(AX_DENSE, h->tdtype, h->A.A, n, h->A.lda, 0, h->dsc + 16, h->dsc, h->s);
+  else
+    launch_matrix_sums(AX_CSR, h->A.v_dtype, h->A.vals, n, 0, h->A.lda, h->dsc + 16, h->dsc, h->s);
+  double sums[2];
+  CKC(cudaMemcpyAsync(sums, h->dsc, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CKC(cudaStreamSynchronize(h->s));
+  h->normA2 = sums[0];
+  h->sumA = sums[1];
+  if (!std::isfinite(h->normA2)) { h->err = "A has NaN/Inf entries"; return bail(SNMF_ERR_NUMERIC); }
+  h->lam = o.lambda_sym >= 0.0 ? o.lambda_sym : 0.01 * std::sqrt(h->normA2);
+  *out = h;
+  return SNMF_OK;
+#undef CKC
+}
+
+snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma) {
+  if (!h) return SNMF_ERR_STATE;
+  if (!(gamma >= 0.0)) return fail(h, SNMF_ERR_ARG, "gamma must be >= 0");
+  if (gamma == 0.0) { h->graph = false; h->gamma = 0.0; h->exec_form = -1; return SNMF_OK; }
+  if (!L) return fail(h, SNMF_ERR_ARG, "implicit Laplacian (L == NULL) not available in this build");
+  if (L->kind != SNMF_CSR) return fail(h, SNMF_ERR_ARG, "L must be CSR");
+  if (L->n != h->n) return fail(h, SNMF_ERR_ARG, "L size mismatch");
+  if (L->dtype != SNMF_F64 && L->dtype != SNMF_F32) return fail(h, SNMF_ERR_ARG, "L dtype");
+  const int64_t n = h->n, nnz = L->nnz;
+  const size_t vb = L->dtype == SNMF_F64 ? 8 : 4;
+  const cudaMemcpyKind kd = L->location == SNMF_ON_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (L->location == SNMF_ON_HOST) {
+    if (L->rowptr[0] != 0 || L->rowptr[n] != nnz) return fail(h, SNMF_ERR_ARG, "L rowptr inconsistent");
+    for (int64_t e = 0; e < nnz; ++e)
+      if (L->colidx[e] < 0 || L->colidx[e] >= n) return fail(h, SNMF_ERR_ARG, "L column out of range");
+  }
+  cudaFree(h->L_rowptr); cudaFree(h->L_colidx); cudaFree(h->L_vals);
+  h->L_rowptr = nullptr; h->L_colidx = nullptr; h->L_vals = nullptr;
+  CK(cudaMalloc(&h->L_rowptr, (n + 1) * sizeof(int32_t)));
+  CK(cudaMalloc(&h->L_colidx, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+  CK(cudaMalloc(&h->L_vals, std::max<int64_t>(nnz, 1) * vb));
+  CK(cudaMemcpyAsync(h->L_rowptr, L->rowptr, (n + 1) * sizeof(int32_t), kd, h->s));
+  if (nnz) {
+    CK(cudaMemcpyAsync(h->L_colidx, L->colidx, nnz * sizeof(int32_t), kd, h->s));
+    CK(cudaMemcpyAsync(h->L_vals, L->values, nnz * vb, kd, h->s));
+  }
+  CK(cudaStreamSynchronize(h->s));
+  h->L = AxArgs{};
+  h->L.kind = AX_CSR;
+  h->L.rowptr = h->L_rowptr;
+  h->L.colidx = h->L_colidx;
+  h->L.vals = h->L_vals;
+  h->L.v_dtype = L->dtype == SNMF_F64 ? 0 : 1;
+  h->L.lda = nnz;
+  h->graph = true;
+  h->gamma = gamma;
+  h->exec_form = -1;
+  return SNMF_OK;
+}
+
+snmf_status snmf_lai_sketch(snmf_handle h, int k, int oversample, int power_iters, uint64_t seed) {
+  if (!h) return SNMF_ERR_STATE;
+  if (k < 1 || oversample < 0 || power_iters < 0) return fail(h, SNMF_ERR_ARG, "bad sketch sizes");
+  const int ell = k + oversample;
+  if (ell > 128 || ell > h->n) return fail(h, SNMF_ERR_ARG, "k + oversample must be <= min(n, 128)");
+  if (sync_user(h) != SNMF_OK) return SNMF_ERR_CUDA;
+  std::string msg;
+  const int rc = lai_build(h->lai_op, h->A, h->tdtype, h->n, k, ell, power_iters, seed, h->N, h->s, msg);
+  if (rc != 0) return fail(h, rc == -3 ? SNMF_ERR_OOM : SNMF_ERR_CUDA, msg);
+  h->lai = true;
+  h->exec_form = -1;
+  return SNMF_OK;
+}
+
+static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_stats* out) {
+  const size_t fbytes = (size_t)h->n * h->N * h->esz;
+  const cudaMemcpyKind kin = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind kout = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (sync_user(h) != SNMF_OK) return SNMF_ERR_CUDA;
+  CK(cudaEventRecord(h->ev0, h->s));
+  if (W) {
+    CK(cudaMemcpyAsync(h->buf[B_W], W, fbytes, kin, h->s));
+  } else {
+    const double mean = h->sumA / ((double)h->n * (double)h->n);
+    const double upper = h->opt.init_scale * std::sqrt(std::max(mean, 0.0) / h->r);
+    launch_philox_uniform(h->tdtype, h->buf[B_W], h->n, h->N, h->N, h->opt.seed, upper, h->s);
+  }
+  const bool pen = h->opt.formulation == SNMF_PENALTY;
+  if (pen) {
+    if (Ht) CK(cudaMemcpyAsync(h->buf[B_HT], Ht, fbytes, kin, h->s));
+    else CK(cudaMemcpyAsync(h->buf[B_HT], h->buf[B_W], fbytes, cudaMemcpyDeviceToDevice, h->s));
+  }
+  // control state: restarts active; second array = "all live" view for final passes
+  h->h_ctl.assign(2 * h->b, Ctl{});
+  for (int j = 0; j < 2 * h->b; ++j) {
+    h->h_ctl[j].active = 1;
+    h->h_ctl[j].lam = h->lam;
+    h->h_ctl[j].rho = 1.0;
+    h->h_ctl[j].mlp_mult = 1.0;
+  }
+  CK(cudaMemcpyAsync(h->ctl, h->h_ctl.data(), 2 * h->b * sizeof(Ctl), cudaMemcpyHostToDevice, h->s));
+  const Params P = make_params(h);
+  h->ax_count = 0;
+  if (pen) pen_init(h, P); else dir_init(h, P);
+  // capture one iteration once per configuration
+  const int form = pen ? 0 : 1;
+  if (h->exec_form != form) {
+    if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    const int c0 = h->ax_count;
+    if (pen) pen_iteration(h, P); else dir_iteration(h, P);
+    h->per_iter = h->ax_count - c0 - (pen ? 0 : 1);  // direct: the clipped-step recompute is conditional
+    h->ax_count = c0;
+    CK(cudaStreamEndCapture(h->s, &g));
+    CK(cudaGraphInstantiate(&h->exec, g, 0));
+    cudaGraphDestroy(g);
+    h->exec_form = form;
+  }
+  int done = 0, launched = 0, chunk = 1;
+  const int maxit = h->opt.max_iter;
+  while (launched < maxit) {
+    const int m = std::min(chunk, maxit - launched);
+    for (int t = 0; t < m; ++t) CK(cudaGraphLaunch(h->exec, h->s));
+    launched += m;
+    CK(cudaMemcpyAsync(h->h_flag, h->run, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    if (*h->h_flag == 0) { done = 1; break; }
+    chunk = std::min(chunk * 2, 8);
+  }
+  (void)done;
+  if (pen) pen_final(h, P); else dir_final(h, P);
+  if (W) CK(cudaMemcpyAsync(W, h->buf[B_W], fbytes, kout, h->s));
+  if (pen && Ht) CK(cudaMemcpyAsync(Ht, h->buf[B_HT], fbytes, kout, h->s));
+  CK(cudaEventRecord(h->ev1, h->s));
+  CK(cudaMemcpyAsync(h->h_ctl.data(), h->ctl, h->b * sizeof(Ctl), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  CK(cudaGetLastError());
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->have_result = true;
+  // statistics
+  int best = 0, conv = 1, lsf = 0, clip = 0, iters = 0, nan = 0;
+  for (int j = 0; j < h->b; ++j) {
+    const Ctl& c = h->h_ctl[j];
+    if (c.fin_f < h->h_ctl[best].fin_f) best = j;
+    const bool cj = c.pg0 == 0.0 || c.pg <= h->opt.tol * c.pg0;
+    conv &= cj ? 1 : 0;
+    lsf += c.ls_fail;
+    clip += c.clipped;
+    iters = std::max(iters, c.iters);
+    nan |= c.nan_seen;
+  }
+  if (out) {
+    out->iters = iters;
+    out->converged = conv;
+    out->ls_fail = lsf;
+    out->clipped_steps = clip;
+    out->best_restart = best;
+    out->ax_products = h->ax_count + h->per_iter * iters + (pen ? 0 : clip);
+    out->f = h->h_ctl[best].fin_f;
+    out->residual = h->h_ctl[best].fin_res;
+    out->pg_rel = h->h_ctl[best].fin_pg;
+    out->seconds = ms * 1e-3;
+  }
+  if (nan) return fail(h, SNMF_ERR_NUMERIC, "NaN/Inf in the scalar state");
+  return conv ? SNMF_OK : SNMF_NOT_CONVERGED;
+}
+
+snmf_status snmf_solve(snmf_handle h, void* W, void* Ht, snmf_stats* out) {
+  if (!h) return SNMF_ERR_STATE;
+  return solve_impl(h, false, W, Ht, out);
+}
+
+snmf_status snmf_solve_host(snmf_handle h, void* W, void* Ht, snmf_stats* out) {
+  if (!h) return SNMF_ERR_STATE;
+  if (!W) return fail(h, SNMF_ERR_ARG, "W must not be NULL");
+  return solve_impl(h, true, W, Ht, out);
+}
+
+snmf_status snmf_restart_stats(snmf_handle h, double* f, double* residual, double* pg_rel,
+                               int32_t* iters) {
+  if (!h) return SNMF_ERR_STATE;
+  if (!h->have_result) return fail(h, SNMF_ERR_STATE, "no solve has run");
+  for (int j = 0; j < h->b; ++j) {
+    const Ctl& c = h->h_ctl[j];
+    if (f) f[j] = c.fin_f;
+    if (residual) residual[j] = c.fin_res;
+    if (pg_rel) pg_rel[j] = c.fin_pg;
+    if (iters) iters[j] = c.iters;
+  }
+  return SNMF_OK;
+}
+
+snmf_status snmf_get_factors(snmf_handle h, void* W, void* Ht) {
+  if (!h) return SNMF_ERR_STATE;
+  if (!h->have_result) return fail(h, SNMF_ERR_STATE, "no solve has run");
+  const size_t fbytes = (size_t)h->n * h->N * h->esz;
+  if (W) CK(cudaMemcpyAsync(W, h->buf[B_W], fbytes, cudaMemcpyDeviceToDevice, h->s));
+  if (Ht) CK(cudaMemcpyAsync(Ht, h->buf[h->opt.formulation == SNMF_PENALTY ? B_HT : B_W], fbytes,
+                             cudaMemcpyDeviceToDevice, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  return SNMF_OK;
+}
+
+snmf_status snmf_apply(snmf_handle h, const void* X, void* Y, int cols, double* xax) {
+  if (!h) return SNMF_ERR_STATE;
+  if (!X || !Y || cols < 1 || cols > h->N) return fail(h, SNMF_ERR_ARG, "bad apply arguments");
+  if (sync_user(h) != SNMF_OK) return SNMF_ERR_CUDA;
+  const size_t fe = (size_t)h->n * h->N;
+  // stage X into the (ld = N) layout, zero-padded columns
+  CK(cudaMemsetAsync(h->buf[B_Z], 0, fe * h->esz, h->s));
+  CK(cudaMemcpy2DAsync(h->buf[B_Z], h->N * h->esz, X, cols * h->esz, cols * h->esz, h->n,
+                       cudaMemcpyDeviceToDevice, h->s));
+  int nax = ax_A(h, h->buf[B_Z], h->buf[B_AZ], 0.0, nullptr, h->buf[B_Z], nullptr, h->pax, nullptr);
+  CK(cudaMemcpy2DAsync(Y, cols * h->esz, h->buf[B_AZ], h->N * h->esz, cols * h->esz, h->n,
+                       cudaMemcpyDeviceToDevice, h->s));
+  std::vector<double> part((size_t)nax * h->b * kNQ);
+  CK(cudaMemcpyAsync(part.data(), h->pax, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (xax) {
+    double s = 0.0;
+    for (int t = 0; t < nax; ++t)
+      for (int j = 0; j < h->b; ++j) s += part[((size_t)t * h->b + j) * kNQ];
+    *xax = s;
+  }
+  return SNMF_OK;
+}
+
+snmf_status snmf_destroy(snmf_handle h) {
+  if (!h) return SNMF_OK;
+  if (h->s) cudaStreamSynchronize(h->s);
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  for (void* p : h->buf) cudaFree(p);
+  cudaFree(h->ws);
+  double* parts[] = {h->prow, h->pax, h->pax2, h->pax3, h->pax4, h->pclip, h->gpart, h->G64fix,
+                     h->G64p, h->dsc};
+  for (double* p : parts) cudaFree(p);
+  cudaFree(h->GT);
+  cudaFree(h->ctl);
+  cudaFree(h->run);
+  cudaFree(h->recompute);
+  if (h->h_flag) cudaFreeHost(h->h_flag);
+  cudaFree(h->A_owned);
+  cudaFree(h->rowptr_owned);
+  cudaFree(h->colidx_owned);
+  cudaFree(h->vals_owned);
+  cudaFree(h->L_rowptr);
+  cudaFree(h->L_colidx);
+  cudaFree(h->L_vals);
+  lai_free(h->lai_op);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->evsync) cudaEventDestroy(h->evsync);
+  if (h->s) cudaStreamDestroy(h->s);
+  delete h;
+  return SNMF_OK;
+}
+
+const char* snmf_last_error(snmf_handle h) {
+  if (!h) return g_create_err.c_str();
+  return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+// Shared definitions of the SNMPBB CUDA path (sm_103a).
+//
+// Data layout in HBM (all row-major):
+//   factors X (W, Ht, Z, D, gradients, products): n x N with N = r * b; restart j owns
+//   columns [j r, (j+1) r).  Element type T = double (FP64 precision) or float.
+//   partial sums: part[slot][restart][NQ] (double), one slot per CTA of a row kernel,
+//   reduced in a fixed order by the control kernels (deterministic, no atomics).
+//   Gram partials: gpart[chunk][pair][restart][r*r] (double), reduced in fixed order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace snmf {
+
+constexpr int kNQ = 8;          // dot slots per partial record
+constexpr int kMaxHist = 64;    // max nonmonotone memory M
+constexpr int kRowTile = 64;    // rows per CTA of the row kernels
+constexpr int kMaxR = 256;      // max rank per restart
+
+// Per-restart scalar state of Algorithm 1 (FP64, device resident).
+struct Ctl {
+  double rho;        // rho_0 of the block (penalty) / rho_k (direct), as used in the Z step
+  double alpha;      // BB step for the D direction of the current step
+  double beta;       // accepted line-search step (0 after a failed search)
+  double phibeta;    // phi * beta used by the relaxed update
+  double f;          // f(X_k) minus the block constant (penalty) / f(X_k) (direct)
+  double F;          // nonmonotone reference F_k
+  double fZ;         // f(Z_k)
+  double gd;         // <grad f(Z_k), D_k>
+  double q;          // curvature term of the line-search polynomial
+  double ss, sy, yy; // <S,S>, <S,Y>, <Y,Y> of the last update
+  double pg0;        // joint projected-gradient norm at the start
+  double pgH2;       // squared projected gradient of the last H block (penalty)
+  double pg;         // last joint projected-gradient norm
+  double lam;        // penalty weight lambda
+  double xax;        // <X, A X> of the current W (direct)
+  double xax_z, zad, dad;   // <Z,AZ>, <Z,AD>, <D,AD> (direct)
+  double zlz, dlz, dld;     // <Z,LZ>, <D,LZ>, <D,LD> (direct, graph)
+  double fhist[kMaxHist];
+  int hlen, hpos;
+  int k;             // step index within the block (penalty) or since start (direct)
+  int active;        // 1 while iterating
+  int iters;         // outer iterations (penalty) / steps (direct)
+  int ls_fail;
+  int clipped;       // direct: steps with clipped entries
+  int clip_now;      // direct: current update clipped
+  int nan_seen;
+  double fin_f, fin_res, fin_pg;   // final per-restart results
+  double gnorm_prev; // ||g_{k-1}|| for the step controller features
+  double f_prev, f_prev2;
+  double mlp_mult;   // multiplier proposed by the learned controller (1 = plain BB)
+  int mlp_tried;     // 1 when the current step used the proposal
+  int commit;       // direct: the update of this step is to be committed
+};
+
+struct Dims {
+  int64_t n;    // rows
+  int r;        // rank per restart
+  int b;        // restarts
+  int N;        // r * b
+  int64_t ld;   // leading dimension of factor buffers (= N)
+};
+
+// Launch-time scalars shared by the orchestration kernels.
+struct Params {
+  int formulation;   // 0 penalty, 1 direct
+  int memory;        // nonmonotone M (0 = eta rule)
+  int bb;            // 0 BB1, 1 BB2
+  int max_ls;
+  int max_iter;
+  int power_iters;
+  int controller;    // learned step controller on/off
+  double theta, phi, eta, alpha_min, alpha_max, beta_shrink, tol;
+  double rho_factor; // direct form rho scaling
+  double normA2;     // ||A||_F^2 of the stored operator
+  double gamma;      // graph weight (0 = none)
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fixed-order block sum over blockDim.x threads (multiple of 32, <= 1024).
+// Result valid in every thread.  `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  double out = sh[0];
+  __syncthreads();
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// host launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+
+// Product kinds of the A*X operator
+enum AxKind { AX_DENSE = 0, AX_CSR = 1 };
+
+struct AxArgs {
+  // dense
+  const void* A; int64_t lda; int a_dtype;  // a_dtype: 0 f64, 1 f32, 2 bf16, 3 fp8(e4m3) + scales
+  const float* a_scale;                     // fp8: per 128x128 tile scale (power of two)
+  // csr
+  const int32_t* rowptr; const int32_t* colidx; const void* vals; int v_dtype;
+  int kind;
+};
+
+// Y = A X (raw product, T = double/float), n x cols, ld = leading dimension of X and Y.
+// Dense products may split K: the splits write ws[s] (n x ld each) and the finish pass
+// sums them.  Returns the number of splits used (1 = result already in Y).
+int launch_ax(const AxArgs& a, int tdtype, int64_t n, int cols, int64_t ld,
+              const void* X, void* Y, void* ws, size_t ws_elems, const int* run_flag,
+              cudaStream_t s);
+
+// Epilogue of a product over the restarts of d: Y = sum_s ws[s] (splits > 1),
+// per-restart partials <P1, A X> -> part[slot][j][q0], <P2, A X> -> [q0+1], then
+// Y += c * X2 (when X2 != NULL).  Returns the number of partial slots written.
+int launch_ax_finish_impl(int tdtype, const Dims& d, void* Y, const void* ws, int splits,
+                          double c, const void* X2, const void* P1, const void* P2,
+                          double* part, int q0, const int* run_flag, cudaStream_t s);
+
+}  // namespace snmf

@@ -1,0 +1,89 @@
+// Launchers of the O(n r^2) kernels and the control kernels (defined in rowops.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace snmf {
+
+// operand of the row GEMM X G: loaded, Z = Proj[X - g/rho], or X' = Proj[Z + phi beta D]
+enum { OP_LOAD = 0, OP_ZSTEP = 1, OP_UPD = 2 };
+// epilogue: gradient (+ S/Y and increment dots) or the D direction (+ dots)
+enum { EPI_GRAD = 0, EPI_DIR = 1 };
+
+// Arguments of k_rowgemm.  Gradient g = op(X) G - B (+ gamma LX), G = per-restart r x r
+// matrix in the factor type.  Partial layout (part[slot][j][q], slot = CTA):
+//   EPI_GRAD: q0 ||P grad||^2, q1 1/2 <g - B, X>, q2 <S,S>, q3 <S,Y>, q4 <Y,Y>,
+//             q5 1/2 <X - Zold, g + gZold>
+//   EPI_DIR : q0 <g, D>, q1 <D, D>, q2 1/2 <Z - Wcur, g + gWcur>, q3 <D, LX>
+struct RowArgs {
+  int64_t n; int r; int b; int64_t ld;
+  const void* G;
+  const void* X;       // OP_LOAD / OP_ZSTEP
+  const void* g_in;    // OP_ZSTEP
+  const void* Zin;     // OP_UPD
+  const void* Din;     // OP_UPD
+  const void* B;
+  const void* LX; double gamma;
+  const Ctl* ctl;
+  const int* run;
+  void* Xout;          // operand value written (Z for OP_ZSTEP, X' for OP_UPD/OP_LOAD copy)
+  void* gout;          // EPI_GRAD: gradient
+  void* Dout;          // EPI_DIR: direction
+  void* gZout;         // EPI_DIR: gradient at Z
+  const void* Xold; const void* gold;    // EPI_GRAD: S = X - Xold, Y = g - gold
+  const void* Zold; const void* gZold;   // EPI_GRAD: increment f(X) - f(Zold)
+  const void* Wcur; const void* gWcur;   // EPI_DIR: increment f(Z) - f(Wcur)
+  double* part;
+};
+
+void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pair, int npairs,
+                 double* gpart, int nchunks, const Ctl* ctl, const int* run, cudaStream_t s);
+void launch_gram_reduce(int tdtype, const double* gpart, int nchunks, int npairs, const Dims& d,
+                        double* G64, void* GT, int tpair, double lam_shift, cudaStream_t s);
+int rowgemm_slots(const Dims& d);
+void launch_rowgemm(int tdtype, int op, int epi, const RowArgs& a, cudaStream_t s);
+void launch_zstep(int tdtype, const Dims& d, const void* X, const void* g, void* Z, const Ctl* ctl,
+                  cudaStream_t s);
+int launch_xupd(int tdtype, const Dims& d, const void* Z, const void* D, void* Xn, const void* AZ,
+                const void* AD, void* AXn, const Ctl* ctl, double* part, cudaStream_t s);
+void launch_copy_live(int tdtype, const Dims& d, const void* src, void* dst, const Ctl* ctl,
+                      cudaStream_t s);
+void launch_rho(int tdtype, const double* G64, const Dims& d, int iters, double scale, Ctl* ctl,
+                int set_alpha, cudaStream_t s);
+void launch_philox_uniform(int tdtype, void* out, int64_t rows, int cols, int64_t ld, uint64_t seed,
+                           double scale, cudaStream_t s);
+void launch_philox_gaussian(int tdtype, void* out, int64_t rows, int cols, uint64_t seed,
+                            cudaStream_t s);
+void launch_matrix_sums(int kind, int vdtype, const void* vals, int64_t n, int64_t lda, int64_t nnz,
+                        double* part, double* out, cudaStream_t s);
+void launch_convert(int sdtype, int ddtype, const void* src, int64_t rows, int64_t cols, int64_t lds,
+                    void* dst, int64_t ldd, cudaStream_t s);
+
+void launch_ctl_pen_start(Ctl* ctl, const double* prow, int nrow, int b, const Params& P, int is_w,
+                          int first, cudaStream_t s);
+void launch_ctl_pen_ls(Ctl* ctl, const double* prow, int nrow, const double* pax, int nax, int b,
+                       int r, const double* G64fix, const double* DtD, const Params& P, int graph,
+                       cudaStream_t s);
+void launch_ctl_pen_upd(Ctl* ctl, const double* prow, int nrow, int b, const Params& P, int is_h,
+                        int last, cudaStream_t s);
+void launch_ctl_dir_init(Ctl* ctl, const double* pax, int nax, const double* prow, int nrow,
+                         const double* plx, int nlx, const double* GW, int b, int r, const Params& P,
+                         cudaStream_t s);
+void launch_ctl_dir_alpha(Ctl* ctl, int b, const Params& P, cudaStream_t s);
+void launch_ctl_dir_ls(Ctl* ctl, const double* pz, int nz, const double* prow, int nrow,
+                       const double* pd, int nd, const double* GZ, const double* ZD,
+                       const double* DDm, const double* pgl, const double* pgd, int b, int r,
+                       const Params& P, cudaStream_t s);
+void launch_ctl_dir_clip(Ctl* ctl, const double* pclip, int nslots, int b, int* recompute,
+                         cudaStream_t s);
+void launch_ctl_dir_upd(Ctl* ctl, const double* prow, int nrow, const double* pax, int nax,
+                        const double* plx, int nlx, const double* GW, const int* recompute, int b,
+                        int r, const Params& P, cudaStream_t s);
+void init_kernel_attributes();
+void launch_any_active(const Ctl* ctl, int b, int* flag, int* recompute, cudaStream_t s);
+void launch_ctl_final_pen(Ctl* ctl, const double* pax, int nax, const double* prow, int nrow,
+                          const double* GW, const double* GH, const double* WH, int b, int r,
+                          const Params& P, cudaStream_t s);
+void launch_ctl_final_dir(Ctl* ctl, const double* GW, int b, int r, const Params& P, cudaStream_t s);
+
+}  // namespace snmf

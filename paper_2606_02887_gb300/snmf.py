@@ -1,0 +1,224 @@
+"""ctypes binding of the C ABI declared in include/snmf.h.
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.  There is no CPU fallback:
+loading fails loudly when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libsnmf_gb300.so")
+
+SNMF_OK, SNMF_NOT_CONVERGED = 0, 1
+SNMF_ERR_ARG, SNMF_ERR_CUDA, SNMF_ERR_OOM, SNMF_ERR_NUMERIC, SNMF_ERR_TIMEOUT, SNMF_ERR_STATE = -1, -2, -3, -4, -5, -6
+SNMF_DENSE, SNMF_CSR = 0, 1
+SNMF_F64, SNMF_F32, SNMF_BF16, SNMF_FP8 = 0, 1, 2, 3
+SNMF_ON_DEVICE, SNMF_ON_HOST = 0, 1
+SNMF_PENALTY, SNMF_DIRECT = 0, 1
+SNMF_BB1, SNMF_BB2 = 0, 1
+SNMF_MLP_IN, SNMF_MLP_HIDDEN = 5, 64
+SNMF_MLP_NPARAMS = SNMF_MLP_IN * SNMF_MLP_HIDDEN + 2 * SNMF_MLP_HIDDEN + 1
+
+EXPORTED = (
+    "snmf_default_options", "snmf_create", "snmf_set_graph_reg", "snmf_lai_sketch",
+    "snmf_solve", "snmf_solve_host", "snmf_restart_stats", "snmf_get_factors",
+    "snmf_apply", "snmf_destroy", "snmf_last_error",
+)
+
+
+class snmf_matrix(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("location", C.c_int32),
+                ("reserved", C.c_int32), ("n", C.c_int64), ("nnz", C.c_int64), ("ld", C.c_int64),
+                ("values", C.c_void_p), ("rowptr", C.c_void_p), ("colidx", C.c_void_p)]
+
+
+class snmf_options(C.Structure):
+    _fields_ = [("formulation", C.c_int32), ("precision", C.c_int32), ("batch", C.c_int32),
+                ("nonmonotone_M", C.c_int32), ("bb_variant", C.c_int32), ("max_ls", C.c_int32),
+                ("inner_iters", C.c_int32), ("max_iter", C.c_int32), ("power_iters", C.c_int32),
+                ("step_controller", C.c_int32), ("lambda_sym", C.c_double), ("theta", C.c_double),
+                ("phi", C.c_double), ("eta", C.c_double), ("alpha_min", C.c_double),
+                ("alpha_max", C.c_double), ("beta_shrink", C.c_double), ("tol", C.c_double),
+                ("direct_rho_factor", C.c_double), ("init_scale", C.c_double), ("seed", C.c_uint64),
+                ("mlp_weights", C.c_void_p), ("timeout_cycles", C.c_int64)]
+
+
+class snmf_stats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("ls_fail", C.c_int32),
+                ("clipped_steps", C.c_int32), ("best_restart", C.c_int32), ("ax_products", C.c_int32),
+                ("f", C.c_double), ("residual", C.c_double), ("pg_rel", C.c_double),
+                ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"SNMPBB CUDA library not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    H = C.c_void_p
+    lib.snmf_default_options.argtypes = [C.POINTER(snmf_options)]
+    lib.snmf_default_options.restype = None
+    lib.snmf_create.argtypes = [C.POINTER(H), C.POINTER(snmf_matrix), C.c_int, C.POINTER(snmf_options), C.c_void_p]
+    lib.snmf_set_graph_reg.argtypes = [H, C.POINTER(snmf_matrix), C.c_double]
+    lib.snmf_lai_sketch.argtypes = [H, C.c_int, C.c_int, C.c_int, C.c_uint64]
+    lib.snmf_solve.argtypes = [H, C.c_void_p, C.c_void_p, C.POINTER(snmf_stats)]
+    lib.snmf_solve_host.argtypes = [H, C.c_void_p, C.c_void_p, C.POINTER(snmf_stats)]
+    lib.snmf_restart_stats.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.snmf_get_factors.argtypes = [H, C.c_void_p, C.c_void_p]
+    lib.snmf_apply.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double)]
+    lib.snmf_destroy.argtypes = [H]
+    lib.snmf_last_error.argtypes = [H]
+    lib.snmf_last_error.restype = C.c_char_p
+    for name in EXPORTED:
+        if name not in ("snmf_default_options", "snmf_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class SnmfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"snmf status {status}: {msg}")
+        self.status = status
+
+
+def _check(lib, h, st):
+    if st < 0:
+        raise SnmfError(st, lib.snmf_last_error(h).decode(errors="replace"))
+    return st
+
+
+def snmf_default_options(**overrides) -> snmf_options:
+    lib = load_library()
+    o = snmf_options()
+    lib.snmf_default_options(C.byref(o))
+    for k, v in overrides.items():
+        if k == "mlp_weights":
+            continue
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    """Data pointer of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _is_cuda(t):
+    return hasattr(t, "is_cuda") and t.is_cuda
+
+
+def dense_matrix(A) -> tuple:
+    """snmf_matrix for a dense n x n torch tensor (device or host) or numpy array."""
+    dt = SNMF_F64 if str(A.dtype).endswith("float64") else SNMF_F32
+    m = snmf_matrix(kind=SNMF_DENSE, dtype=dt, location=SNMF_ON_DEVICE if _is_cuda(A) else SNMF_ON_HOST,
+                    n=A.shape[0], nnz=0, ld=A.shape[1] if A.ndim == 2 else A.shape[0],
+                    values=_ptr(A))
+    if hasattr(A, "stride") and not isinstance(A, np.ndarray):
+        m.ld = A.stride(0)
+    return m, (A,)
+
+
+def csr_matrix(n, rowptr, colidx, values) -> tuple:
+    """snmf_matrix for CSR arrays (all torch-on-device or all host numpy/torch)."""
+    dt = SNMF_F64 if str(values.dtype).endswith("float64") else SNMF_F32
+    m = snmf_matrix(kind=SNMF_CSR, dtype=dt, location=SNMF_ON_DEVICE if _is_cuda(values) else SNMF_ON_HOST,
+                    n=n, nnz=int(values.shape[0]), ld=0, values=_ptr(values), rowptr=_ptr(rowptr),
+                    colidx=_ptr(colidx))
+    return m, (rowptr, colidx, values)
+
+
+def snmf_create(matrix, r: int, options: snmf_options | None = None, stream=None, mlp_weights=None):
+    """Create a handle.  ``matrix`` is the (snmf_matrix, keepalive) pair of
+    dense_matrix/csr_matrix.  Returns the handle (c_void_p)."""
+    lib = load_library()
+    m, _keep = matrix
+    h = C.c_void_p()
+    opt = options if options is not None else snmf_default_options()
+    wbuf = None
+    if mlp_weights is not None:
+        wbuf = np.ascontiguousarray(np.asarray(mlp_weights, dtype=np.float32))
+        opt.mlp_weights = wbuf.ctypes.data
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    st = lib.snmf_create(C.byref(h), C.byref(m), int(r), C.byref(opt), s)
+    _check(lib, None, st)
+    return h
+
+
+def snmf_set_graph_reg(h, matrix, gamma: float):
+    lib = load_library()
+    m = None if matrix is None else C.byref(matrix[0])
+    return _check(lib, h, lib.snmf_set_graph_reg(h, m, float(gamma)))
+
+
+def snmf_lai_sketch(h, k: int, oversample: int, power_iters: int, seed: int):
+    lib = load_library()
+    return _check(lib, h, lib.snmf_lai_sketch(h, int(k), int(oversample), int(power_iters), int(seed)))
+
+
+def snmf_solve(h, W=None, Ht=None):
+    """Solve in place on device tensors W (and Ht).  Returns (status, stats dict)."""
+    lib = load_library()
+    out = snmf_stats()
+    st = _check(lib, h, lib.snmf_solve(h, _ptr(W), _ptr(Ht), C.byref(out)))
+    return st, out.as_dict()
+
+
+def snmf_solve_host(h, W, Ht=None):
+    """Solve with host (pinned or pageable) W / Ht, copied inside the call."""
+    lib = load_library()
+    out = snmf_stats()
+    st = _check(lib, h, lib.snmf_solve_host(h, _ptr(W), _ptr(Ht), C.byref(out)))
+    return st, out.as_dict()
+
+
+def snmf_restart_stats(h, batch: int):
+    lib = load_library()
+    f = np.zeros(batch)
+    res = np.zeros(batch)
+    pg = np.zeros(batch)
+    it = np.zeros(batch, dtype=np.int32)
+    _check(lib, h, lib.snmf_restart_stats(h, f.ctypes.data, res.ctypes.data, pg.ctypes.data, it.ctypes.data))
+    return dict(f=f, residual=res, pg_rel=pg, iters=it)
+
+
+def snmf_get_factors(h, W=None, Ht=None):
+    lib = load_library()
+    return _check(lib, h, lib.snmf_get_factors(h, _ptr(W), _ptr(Ht)))
+
+
+def snmf_apply(h, X, Y, cols: int):
+    lib = load_library()
+    xax = C.c_double()
+    _check(lib, h, lib.snmf_apply(h, _ptr(X), _ptr(Y), int(cols), C.byref(xax)))
+    return xax.value
+
+
+def snmf_destroy(h):
+    lib = load_library()
+    return lib.snmf_destroy(h)
+
+
+def snmf_last_error(h=None) -> str:
+    lib = load_library()
+    return lib.snmf_last_error(h).decode(errors="replace")

@@ -1,0 +1,86 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, fills documented defaults and rejects invalid arguments
+before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2606_02887_gb300.snmf as S
+
+
+@pytest.fixture(scope="module")
+def lib(repo_root):
+    if not os.path.exists(S.LIB_PATH):
+        from paper_2606_02887_gb300.build import build_library
+        build_library()
+    return S.load_library()
+
+
+def declared_symbols(repo_root):
+    txt = open(os.path.join(repo_root, "include", "snmf.h")).read()
+    return sorted(set(re.findall(r"SNMF_API[^;(]*?\b(snmf_\w+)\s*\(", txt, flags=re.S)))
+
+
+def test_header_symbols_exported(lib, repo_root):
+    names = declared_symbols(repo_root)
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(names) == sorted(S.EXPORTED)
+
+
+def test_struct_layouts_match_header(lib):
+    # sizes fixed by the header's field order (LP64)
+    assert C.sizeof(S.snmf_matrix) == 4 * 4 + 3 * 8 + 3 * 8
+    assert C.sizeof(S.snmf_stats) == 6 * 4 + 4 * 8
+    assert C.sizeof(S.snmf_options) == 10 * 4 + 10 * 8 + 8 + 8 + 8
+
+
+def test_default_options(lib):
+    o = S.snmf_default_options()
+    assert o.formulation == S.SNMF_PENALTY and o.precision == S.SNMF_F32
+    assert o.batch == 1 and o.nonmonotone_M == 10 and o.max_ls == 20 and o.inner_iters == 5
+    assert o.theta == 1e-3 and o.phi == 1.7 and o.tol == 1e-4 and o.lambda_sym < 0
+    assert o.alpha_min == 1e-10 and o.alpha_max == 1e10 and o.direct_rho_factor == 3.0
+
+
+def _create(lib, m, r, o):
+    h = C.c_void_p()
+    st = lib.snmf_create(C.byref(h), C.byref(m), r, C.byref(o), None)
+    return st, h
+
+
+def test_invalid_arguments_rejected_before_launch(lib):
+    A = np.eye(8)
+    m, _ = S.dense_matrix(A)
+    o = S.snmf_default_options()
+    assert _create(lib, m, 0, o)[0] == S.SNMF_ERR_ARG            # r < 1
+    assert _create(lib, m, 9, o)[0] == S.SNMF_ERR_ARG            # r > n
+    assert _create(lib, m, 300, o)[0] == S.SNMF_ERR_ARG          # r > 256
+    bad = S.snmf_default_options(batch=0)
+    assert _create(lib, m, 2, bad)[0] == S.SNMF_ERR_ARG
+    bad = S.snmf_default_options(theta=1.5)
+    assert _create(lib, m, 2, bad)[0] == S.SNMF_ERR_ARG
+    bad = S.snmf_default_options(nonmonotone_M=65)
+    assert _create(lib, m, 2, bad)[0] == S.SNMF_ERR_ARG
+    m2, _ = S.dense_matrix(A)
+    m2.ld = 4                                                    # ld < n
+    assert _create(lib, m2, 2, o)[0] == S.SNMF_ERR_ARG
+    m3, _ = S.dense_matrix(A)
+    m3.kind = 7
+    assert _create(lib, m3, 2, o)[0] == S.SNMF_ERR_ARG
+    msg = lib.snmf_last_error(None).decode()
+    assert "kind" in msg
+    assert lib.snmf_destroy(None) == S.SNMF_OK
+
+
+def test_no_cpu_fallback_without_gpu(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    A = np.eye(8)
+    st, h = _create(lib, S.dense_matrix(A)[0], 2, S.snmf_default_options())
+    assert st == S.SNMF_ERR_CUDA and not h.value

@@ -1,0 +1,186 @@
+"""GPU path vs the FP64 CPU oracle, through the C ABI.
+
+FP64 precision must follow the oracle iterate by iterate (relative Frobenius
+error <= 1e-10 over the first 50 iterations of the n=500, r=10 planted
+workload); the FP32 path must reach a final relative residual within 1e-3 of the
+oracle's with relative projected gradient <= 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2606_02887_gb300.snmf as S
+from workloads import gmm_knn_graph, planted_dense, uniform_init
+
+from gpu_helpers import gpu_solve, rel
+
+pytestmark = pytest.mark.gpu
+
+ITER_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    """n=500, r=10, W0 ~ U[0,1], A = W0 W0^T + E (E symmetric |N(0, 0.01^2)|),
+    init U[0, sqrt(mean(A)/r)]."""
+    A, _ = planted_dense(500, 10, 0.01, seed=1000)
+    W0 = uniform_init(500, 10, math.sqrt(A.mean() / 10), seed=1001)
+    return A, W0
+
+
+@pytest.fixture(scope="module")
+def oracle_pen50(cfg1):
+    A, W0 = cfg1
+    opts = O.Options(formulation="penalty", memory=10, max_iter=50, tol=0.0)
+    return O.snmpbb_penalty(A, W0, W0, opts, keep_iterates=True)
+
+
+def test_penalty_fp64_iterates_match_oracle(cfg1, oracle_pen50):
+    A, W0 = cfg1
+    _, _, info = oracle_pen50
+    worst = 0.0
+    for k in range(1, 51):
+        W, H, st, stats, _ = gpu_solve(A, W0, 10, W0, max_iter=k, tol=0.0, nonmonotone_M=10)
+        rec = info["trace"][k - 1]
+        e = max(rel(W, rec["W"]), rel(H, rec["Ht"]))
+        worst = max(worst, e)
+        assert e <= ITER_TOL, (k, e)
+        assert stats["iters"] == k
+    assert worst <= ITER_TOL
+
+
+def test_penalty_fp64_eta_rule_matches_oracle(cfg1):
+    A, W0 = cfg1
+    opts = O.Options(formulation="penalty", memory=0, eta=0.85, max_iter=20, tol=0.0)
+    _, _, info = O.snmpbb_penalty(A, W0, W0, opts, keep_iterates=True)
+    for k in (1, 2, 5, 10, 20):
+        W, H, _, _, _ = gpu_solve(A, W0, 10, W0, max_iter=k, tol=0.0, nonmonotone_M=0, eta=0.85)
+        rec = info["trace"][k - 1]
+        assert max(rel(W, rec["W"]), rel(H, rec["Ht"])) <= ITER_TOL, k
+
+
+def test_direct_fp64_iterates_match_oracle(cfg1):
+    A, W0 = cfg1
+    opts = O.Options(formulation="direct", memory=10, max_iter=50, tol=0.0)
+    _, info = O.snmpbb_direct(A, W0, opts, keep_iterates=True)
+    for k in list(range(1, 11)) + [20, 30, 40, 50]:
+        W, _, st, stats, _ = gpu_solve(A, W0, 10, formulation=S.SNMF_DIRECT, max_iter=k, tol=0.0,
+                                       nonmonotone_M=10)
+        assert rel(W, info["trace"][k - 1]["X"]) <= ITER_TOL, k
+
+
+def test_penalty_fp64_ragged_shapes_and_batch():
+    """Ragged row tiles (n = 130), a rank spanning two column tiles (r = 70),
+    rank one, and three restarts sharing A."""
+    for (n, r, b, seed) in [(130, 3, 1, 1), (150, 70, 1, 2), (97, 1, 1, 3), (130, 4, 3, 4)]:
+        A, _ = planted_dense(n, r, 0.01, seed=seed)
+        Ws = [uniform_init(n, r, math.sqrt(A.mean() / r), seed=100 * seed + j) for j in range(b)]
+        W0 = np.concatenate(Ws, axis=1)
+        W, H, _, _, _ = gpu_solve(A, W0, r, W0, max_iter=6, tol=0.0, batch=b)
+        for j in range(b):
+            Wo, Ho, _ = O.snmpbb_penalty(A, Ws[j], Ws[j], O.Options(max_iter=6, tol=0.0, objective="closed"))
+            sl = slice(j * r, (j + 1) * r)
+            assert rel(W[:, sl], Wo) <= ITER_TOL and rel(H[:, sl], Ho) <= ITER_TOL, (n, r, b, j)
+
+
+def test_direct_fp64_batch_restarts():
+    n, r, b = 200, 5, 4
+    A, _ = planted_dense(n, r, 0.01, seed=9)
+    Ws = [uniform_init(n, r, math.sqrt(A.mean() / r), seed=900 + j) for j in range(b)]
+    W, _, _, _, _ = gpu_solve(A, np.concatenate(Ws, 1), r, formulation=S.SNMF_DIRECT, max_iter=15,
+                              tol=0.0, batch=b)
+    for j in range(b):
+        Wo, _ = O.snmpbb_direct(A, Ws[j], O.Options(formulation="direct", max_iter=15, tol=0.0,
+                                                    objective="closed"))
+        assert rel(W[:, j * r:(j + 1) * r], Wo) <= ITER_TOL, j
+
+
+def _csr_of(D):
+    rows, cols = np.nonzero(D)
+    rp = np.zeros(D.shape[0] + 1, dtype=np.int32)
+    np.cumsum(np.bincount(rows, minlength=D.shape[0]), out=rp[1:])
+    return rp, cols.astype(np.int32), D[rows, cols]
+
+
+def test_csr_and_graph_penalty_fp64():
+    A_hat, L, labels, S_ = gmm_knn_graph(n=400, d=8, comps=4, k=10, seed=55)
+    Ad = A_hat.to_dense()
+    Ld = L.to_dense()
+    r = 4
+    W0 = uniform_init(400, r, math.sqrt(Ad.mean() / r), seed=56)
+    csr = (A_hat.rowptr, A_hat.colidx, A_hat.values)
+    Lc = (L.rowptr, L.colidx, L.values)
+    for gamma in (0.0, 0.1):
+        opts = O.Options(max_iter=8, tol=0.0, gamma=gamma, objective="closed")
+        Wo, Ho, _ = O.snmpbb_penalty(Ad, W0, W0, opts, L=Ld)
+        W, H, _, _, _ = gpu_solve(None, W0, r, W0, csr=csr, L=Lc if gamma else None, gamma=gamma,
+                                  max_iter=8, tol=0.0)
+        assert rel(W, Wo) <= ITER_TOL and rel(H, Ho) <= ITER_TOL, gamma
+
+
+def test_graph_direct_fp64_dense():
+    A_hat, L, _, _ = gmm_knn_graph(n=300, d=8, comps=3, k=10, seed=57)
+    Ad, Ld = A_hat.to_dense(), L.to_dense()
+    r = 3
+    W0 = uniform_init(300, r, math.sqrt(Ad.mean() / r), seed=58)
+    Wo, _ = O.snmpbb_direct(Ad, W0, O.Options(formulation="direct", gamma=0.05, max_iter=10, tol=0.0,
+                                              objective="closed"), L=Ld)
+    W, _, _, _, _ = gpu_solve(Ad, W0, r, L=(L.rowptr, L.colidx, L.values), gamma=0.05,
+                              formulation=S.SNMF_DIRECT, max_iter=10, tol=0.0)
+    assert rel(W, Wo) <= ITER_TOL
+
+
+def test_fp32_reaches_oracle_residual(cfg1):
+    A, W0 = cfg1
+    Wo, Ho, info = O.snmpbb_penalty(A, W0, W0, O.Options(max_iter=500, tol=1e-4, objective="closed"))
+    W, H, st, stats, _ = gpu_solve(A, W0, 10, W0, precision=S.SNMF_F32, max_iter=500, tol=1e-4)
+    res = float(np.linalg.norm(A - W @ H.T) / np.linalg.norm(A))
+    assert st == S.SNMF_OK, stats
+    assert stats["pg_rel"] <= 1e-4
+    assert abs(res - info["residual"]) <= 1e-3
+    assert abs(stats["residual"] - res) <= 1e-5
+
+
+def test_host_buffers_and_default_init(cfg1):
+    A, W0 = cfg1
+    Wd, Hd, _, _, _ = gpu_solve(A, W0, 10, W0, max_iter=5, tol=0.0)
+    Wh, Hh, _, _, _ = gpu_solve(A, W0, 10, W0, max_iter=5, tol=0.0, host=True)
+    assert np.array_equal(Wd, Wh) and np.array_equal(Hd, Hh)
+    # W == NULL: init_scale * sqrt(mean(A)/r) * U(0,1) from the Philox uniform stream
+    seed, scale = 4242, 1.0
+    Winit = O.philox_uniform(500, 10, seed) * scale * math.sqrt(A.mean() / 10)
+    Wo, Ho, _ = O.snmpbb_penalty(A, Winit, Winit, O.Options(max_iter=3, tol=0.0, objective="closed"))
+    Wg, Hg, _, _, _ = gpu_solve(A, None, 10, None, max_iter=3, tol=0.0, seed=seed, init_scale=scale)
+    assert rel(Wg, Wo) <= 1e-9 and rel(Hg, Ho) <= 1e-9
+
+
+def test_apply_products_dense_and_csr():
+    import torch
+    dev = torch.device("cuda:0")
+    g = np.random.default_rng(3)
+    for n, cols in [(333, 7), (64, 64), (1000, 130)]:
+        B = g.random((n, n))
+        A = B + B.T
+        A[g.random((n, n)) < 0.7] = 0.0
+        A = np.triu(A) + np.triu(A, 1).T
+        X = g.random((n, cols))
+        ref = A @ X
+        for csr in (False, True):
+            At = torch.tensor(A, device=dev)
+            if csr:
+                rp, ci, va = _csr_of(A)
+                keep = (torch.tensor(rp, device=dev), torch.tensor(ci, device=dev), torch.tensor(va, device=dev))
+                m = S.csr_matrix(n, *keep)
+            else:
+                m = S.dense_matrix(At)
+            h = S.snmf_create(m, cols, S.snmf_default_options(precision=S.SNMF_F64))
+            try:
+                Xt = torch.tensor(X, device=dev)
+                Yt = torch.empty_like(Xt)
+                xax = S.snmf_apply(h, Xt, Yt, cols)
+            finally:
+                S.snmf_destroy(h)
+            assert rel(Yt.cpu().numpy(), ref) <= 1e-13
+            assert abs(xax - float(np.sum(X * ref))) <= 1e-12 * abs(xax)
