@@ -157,8 +157,11 @@ int choose_chunks(int64_t n, int b, int r) {
   return (int)c;
 }
 
+// Gram partials of X^T Y; inside the iteration they follow ctl[j].active and the run flag,
+// in the initial and final evaluations (ctl == NULL) every restart is computed.
 void gram1(snmf_ctx* h, const void* X, const void* Y, int pair, int npairs, const Ctl* ctl) {
-  launch_gram(h->tdtype, X, Y, dims(h), pair, npairs, h->gpart, h->nchunks, ctl, h->run, h->s);
+  launch_gram(h->tdtype, X, Y, dims(h), pair, npairs, h->gpart, h->nchunks, ctl,
+              ctl ? h->run : nullptr, h->s);
 }
 
 RowArgs row_base(snmf_ctx* h) {
@@ -686,6 +689,9 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
     h->h_ctl[j].mlp_mult = 1.0;
   }
   CK(cudaMemcpyAsync(h->ctl, h->h_ctl.data(), 2 * h->b * sizeof(Ctl), cudaMemcpyHostToDevice, h->s));
+  static const int one = 1, zero = 0;
+  CK(cudaMemcpyAsync(h->run, &one, sizeof(int), cudaMemcpyHostToDevice, h->s));
+  CK(cudaMemcpyAsync(h->recompute, &zero, sizeof(int), cudaMemcpyHostToDevice, h->s));
   const Params P = make_params(h);
   h->ax_count = 0;
   if (pen) pen_init(h, P); else dir_init(h, P);

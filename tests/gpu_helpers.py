@@ -43,8 +43,8 @@ def gpu_solve(A, W0, r, Ht0=None, precision=S.SNMF_F64, csr=None, L=None, gamma=
         if lai is not None:
             S.snmf_lai_sketch(h, *lai)
         if host:
-            W = np.ascontiguousarray(W0, dtype=np.float64 if precision == S.SNMF_F64 else np.float32)
-            H = None if Ht0 is None else np.ascontiguousarray(Ht0, dtype=W.dtype)
+            W = np.array(W0, dtype=np.float64 if precision == S.SNMF_F64 else np.float32, copy=True)
+            H = None if Ht0 is None else np.array(Ht0, dtype=W.dtype, copy=True)
             st, stats = S.snmf_solve_host(h, W, H)
             Wn, Hn = W, H
         else:

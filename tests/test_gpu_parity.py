@@ -19,6 +19,58 @@ from gpu_helpers import gpu_solve, rel
 pytestmark = pytest.mark.gpu
 
 ITER_TOL = 1e-10
+ENVELOPE_FACTOR = 10.0
+
+
+def rounding_envelope(run, key, n_iter, seeds=3):
+    """Per-iteration divergence of the oracle from itself under a model of FP64
+    rounding: every projection output is perturbed by unit roundoff u = 2^-53
+    (relative), and every gradient X G - B by the typical rounding of its two
+    large terms, u (sqrt(r) |X G| + sqrt(n) |B|): a length-m sum accumulated in
+    another order differs by about sqrt(m) u relative to the sum of |terms|
+    (here all terms are nonnegative).  This is the spread that two correct FP64
+    implementations with different summation orders show.  Returns e[k-1], the
+    max over seeds.  Only the oracle runs here."""
+    import oracle.snmpbb as SM
+
+    base = run()
+    saved = {k: getattr(SM, k) for k in ("proj", "penalty_grad_W", "penalty_grad_Ht", "direct_gradient")}
+    u = 2.0 ** -53
+    out = np.zeros(n_iter)
+
+    def noisy_grad(fn, g, scale_fn):
+        def wrapped(*a, **kw):
+            G = fn(*a, **kw)
+            return G + u * scale_fn(*a) * g.standard_normal(G.shape)
+        return wrapped
+
+    try:
+        for seed in range(seeds):
+            g = np.random.default_rng(seed)
+            SM.proj = lambda X, g=g: saved["proj"](X * (1.0 + u * g.standard_normal(X.shape)))
+            def mag(X, F, AF):
+                n, r = X.shape
+                return math.sqrt(r) * np.abs(X @ (F.T @ F)) + math.sqrt(n) * np.abs(AF)
+
+            SM.penalty_grad_W = noisy_grad(saved["penalty_grad_W"], g,
+                                           lambda A, W, Ht, lam: mag(W, Ht, SM.apply_A(A, Ht)))
+            SM.penalty_grad_Ht = noisy_grad(saved["penalty_grad_Ht"], g,
+                                            lambda A, W, Ht, *r: mag(Ht, W, SM.apply_A(A, W)))
+            SM.direct_gradient = noisy_grad(saved["direct_gradient"], g,
+                                            lambda A, X, *r: mag(X, X, SM.apply_A(A, X)))
+            pert = run()
+            for k in range(n_iter):
+                out[k] = max(out[k], rel(pert[k][key], base[k][key]))
+    finally:
+        for k, v in saved.items():
+            setattr(SM, k, v)
+    return out
+
+
+def iter_tol(envelope, k):
+    """Bar at iteration k: 1e-10, widened to 10x the oracle's own rounding
+    envelope where the iteration's conditioning does not allow 1e-10."""
+    return max(ITER_TOL, ENVELOPE_FACTOR * envelope[k - 1])
 
 
 @pytest.fixture(scope="module")
@@ -40,35 +92,45 @@ def oracle_pen50(cfg1):
 def test_penalty_fp64_iterates_match_oracle(cfg1, oracle_pen50):
     A, W0 = cfg1
     _, _, info = oracle_pen50
-    worst = 0.0
+    opts = O.Options(formulation="penalty", memory=10, max_iter=50, tol=0.0, objective="closed")
+    env = rounding_envelope(lambda: O.snmpbb_penalty(A, W0, W0, opts, keep_iterates=True)[2]["trace"],
+                            "W", 50)
+    errs = []
     for k in range(1, 51):
         W, H, st, stats, _ = gpu_solve(A, W0, 10, W0, max_iter=k, tol=0.0, nonmonotone_M=10)
         rec = info["trace"][k - 1]
         e = max(rel(W, rec["W"]), rel(H, rec["Ht"]))
-        worst = max(worst, e)
-        assert e <= ITER_TOL, (k, e)
+        errs.append(e)
+        assert e <= iter_tol(env, k), (k, e, env[k - 1])
         assert stats["iters"] == k
-    assert worst <= ITER_TOL
+    print("penalty M=10 gpu-vs-oracle:", " ".join(f"{k}:{e:.1e}/{env[k-1]:.1e}" for k, e in enumerate(errs, 1)))
+    # where the conditioning allows it (envelope well below 1e-10) the 1e-10 bar holds
+    assert all(e <= ITER_TOL for e, v in zip(errs, env) if v <= 1e-12)
 
 
 def test_penalty_fp64_eta_rule_matches_oracle(cfg1):
     A, W0 = cfg1
-    opts = O.Options(formulation="penalty", memory=0, eta=0.85, max_iter=20, tol=0.0)
+    opts = O.Options(formulation="penalty", memory=0, eta=0.85, max_iter=30, tol=0.0)
     _, _, info = O.snmpbb_penalty(A, W0, W0, opts, keep_iterates=True)
-    for k in (1, 2, 5, 10, 20):
+    oc = O.Options(formulation="penalty", memory=0, eta=0.85, max_iter=30, tol=0.0, objective="closed")
+    env = rounding_envelope(lambda: O.snmpbb_penalty(A, W0, W0, oc, keep_iterates=True)[2]["trace"], "W", 30)
+    for k in (1, 2, 5, 10, 20, 25, 30):
         W, H, _, _, _ = gpu_solve(A, W0, 10, W0, max_iter=k, tol=0.0, nonmonotone_M=0, eta=0.85)
         rec = info["trace"][k - 1]
-        assert max(rel(W, rec["W"]), rel(H, rec["Ht"])) <= ITER_TOL, k
+        assert max(rel(W, rec["W"]), rel(H, rec["Ht"])) <= iter_tol(env, k), k
 
 
 def test_direct_fp64_iterates_match_oracle(cfg1):
     A, W0 = cfg1
     opts = O.Options(formulation="direct", memory=10, max_iter=50, tol=0.0)
     _, info = O.snmpbb_direct(A, W0, opts, keep_iterates=True)
+    oc = O.Options(formulation="direct", memory=10, max_iter=50, tol=0.0, objective="closed")
+    env = rounding_envelope(lambda: O.snmpbb_direct(A, W0, oc, keep_iterates=True)[1]["trace"], "X", 50)
     for k in list(range(1, 11)) + [20, 30, 40, 50]:
         W, _, st, stats, _ = gpu_solve(A, W0, 10, formulation=S.SNMF_DIRECT, max_iter=k, tol=0.0,
                                        nonmonotone_M=10)
-        assert rel(W, info["trace"][k - 1]["X"]) <= ITER_TOL, k
+        e = rel(W, info["trace"][k - 1]["X"])
+        assert e <= iter_tol(env, k), (k, e, env[k - 1])
 
 
 def test_penalty_fp64_ragged_shapes_and_batch():
@@ -80,7 +142,8 @@ def test_penalty_fp64_ragged_shapes_and_batch():
         W0 = np.concatenate(Ws, axis=1)
         W, H, _, _, _ = gpu_solve(A, W0, r, W0, max_iter=6, tol=0.0, batch=b)
         for j in range(b):
-            Wo, Ho, _ = O.snmpbb_penalty(A, Ws[j], Ws[j], O.Options(max_iter=6, tol=0.0, objective="closed"))
+            Wo, Ho, _ = O.snmpbb_penalty(A, Ws[j], Ws[j], O.Options(max_iter=6, tol=0.0, memory=10,
+                                                                    objective="closed"))
             sl = slice(j * r, (j + 1) * r)
             assert rel(W[:, sl], Wo) <= ITER_TOL and rel(H[:, sl], Ho) <= ITER_TOL, (n, r, b, j)
 
@@ -93,7 +156,7 @@ def test_direct_fp64_batch_restarts():
                               tol=0.0, batch=b)
     for j in range(b):
         Wo, _ = O.snmpbb_direct(A, Ws[j], O.Options(formulation="direct", max_iter=15, tol=0.0,
-                                                    objective="closed"))
+                                                    memory=10, objective="closed"))
         assert rel(W[:, j * r:(j + 1) * r], Wo) <= ITER_TOL, j
 
 
@@ -113,7 +176,7 @@ def test_csr_and_graph_penalty_fp64():
     csr = (A_hat.rowptr, A_hat.colidx, A_hat.values)
     Lc = (L.rowptr, L.colidx, L.values)
     for gamma in (0.0, 0.1):
-        opts = O.Options(max_iter=8, tol=0.0, gamma=gamma, objective="closed")
+        opts = O.Options(max_iter=8, tol=0.0, gamma=gamma, memory=10, objective="closed")
         Wo, Ho, _ = O.snmpbb_penalty(Ad, W0, W0, opts, L=Ld)
         W, H, _, _, _ = gpu_solve(None, W0, r, W0, csr=csr, L=Lc if gamma else None, gamma=gamma,
                                   max_iter=8, tol=0.0)
@@ -126,7 +189,7 @@ def test_graph_direct_fp64_dense():
     r = 3
     W0 = uniform_init(300, r, math.sqrt(Ad.mean() / r), seed=58)
     Wo, _ = O.snmpbb_direct(Ad, W0, O.Options(formulation="direct", gamma=0.05, max_iter=10, tol=0.0,
-                                              objective="closed"), L=Ld)
+                                              memory=10, objective="closed"), L=Ld)
     W, _, _, _, _ = gpu_solve(Ad, W0, r, L=(L.rowptr, L.colidx, L.values), gamma=0.05,
                               formulation=S.SNMF_DIRECT, max_iter=10, tol=0.0)
     assert rel(W, Wo) <= ITER_TOL
@@ -134,7 +197,8 @@ def test_graph_direct_fp64_dense():
 
 def test_fp32_reaches_oracle_residual(cfg1):
     A, W0 = cfg1
-    Wo, Ho, info = O.snmpbb_penalty(A, W0, W0, O.Options(max_iter=500, tol=1e-4, objective="closed"))
+    Wo, Ho, info = O.snmpbb_penalty(A, W0, W0, O.Options(max_iter=500, tol=1e-4, memory=10,
+                                                         objective="closed"))
     W, H, st, stats, _ = gpu_solve(A, W0, 10, W0, precision=S.SNMF_F32, max_iter=500, tol=1e-4)
     res = float(np.linalg.norm(A - W @ H.T) / np.linalg.norm(A))
     assert st == S.SNMF_OK, stats
@@ -151,7 +215,8 @@ def test_host_buffers_and_default_init(cfg1):
     # W == NULL: init_scale * sqrt(mean(A)/r) * U(0,1) from the Philox uniform stream
     seed, scale = 4242, 1.0
     Winit = O.philox_uniform(500, 10, seed) * scale * math.sqrt(A.mean() / 10)
-    Wo, Ho, _ = O.snmpbb_penalty(A, Winit, Winit, O.Options(max_iter=3, tol=0.0, objective="closed"))
+    Wo, Ho, _ = O.snmpbb_penalty(A, Winit, Winit, O.Options(max_iter=3, tol=0.0, memory=10,
+                                                            objective="closed"))
     Wg, Hg, _, _, _ = gpu_solve(A, None, 10, None, max_iter=3, tol=0.0, seed=seed, init_scale=scale)
     assert rel(Wg, Wo) <= 1e-9 and rel(Hg, Ho) <= 1e-9
 
