@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark of the SNMPBB solve on one GB300 (or N replicas under torchrun).
+
+Metric: time to reach relative projected gradient 1e-4 (seconds per solve, lower
+is better) on the dense planted n = 8192 workload, with the achieved A*W product
+bandwidth / arithmetic rate of the dominant kernel beside it.  A "step" is one
+full solve from the seeded start to the tolerance (penalty form, Sec. 2.1).
+
+  python bench.py [--gpus N --steps K --warmup W] [--r 64 --batch 1 --precision f32]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time to proj-grad 1e-4 (s) & AW GB/s: BF16+learned+batched vs plain FP32"
+L2_BYTES = 129 * 1024 * 1024
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=8192)
+    p.add_argument("--r", type=int, default=64)
+    p.add_argument("--batch", type=int, default=1)
+    p.add_argument("--precision", default="f32", choices=["f64", "f32"])
+    p.add_argument("--formulation", default="penalty", choices=["penalty", "direct"])
+    p.add_argument("--max-iter", type=int, default=500)
+    p.add_argument("--tol", type=float, default=1e-4)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        for ln in open(self.tmp.name):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows),
+                   power_w_max=max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                   if any(r[3].replace(".", "").isdigit() for r in rows) else None)
+        return out
+
+
+def cpu_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((i.get("num_threads", 0) for i in threadpool_info()), default=0)
+        if n:
+            return n
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def oracle_seconds_per_iter(A, W0, r, iters, formulation):
+    """FP64 CPU oracle, as it stands, timed over `iters` outer iterations."""
+    import oracle as O
+
+    opts = O.Options(formulation=formulation, memory=10, max_iter=iters, tol=0.0, objective="closed")
+    t = time.perf_counter()
+    if formulation == "penalty":
+        O.snmpbb_penalty(A, W0, W0, opts)
+    else:
+        O.snmpbb_direct(A, W0, opts)
+    return (time.perf_counter() - t) / iters
+
+
+def workload_name(args):
+    return (f"dense planted n={args.n} r={args.r} (W0~U[0,1], A=W0W0^T+|N(0,0.05^2)| sym noise), "
+            f"{args.batch} restart(s), {args.formulation} form, tol {args.tol:g} relative proj-grad")
+
+
+def run_reference(args):
+    """The FP64 CPU oracle timed on the host cores: each step one outer iteration on the
+    same workload, extrapolated by the oracle's own iteration count to the tolerance."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from workloads.configs import dense_planted_8192
+
+    A, starts = dense_planted_8192(args.r, 1, n=args.n)
+    gold = os.path.join(ROOT, "tests", "golden", "oracle_iters_dense8192.json")
+    data = json.load(open(gold)) if os.path.exists(gold) else {}
+    rec = data.get(str(args.r))
+    iters_to_tol = rec["iters"] if rec else args.max_iter
+    for _ in range(args.warmup):
+        oracle_seconds_per_iter(A, starts[0], args.r, 1, args.formulation)
+    per = [oracle_seconds_per_iter(A, starts[0], args.r, 1, args.formulation) for _ in range(args.steps)]
+    spi = statistics.mean(per)
+    value = spi * iters_to_tol * args.batch
+    sample = (f"{args.steps} single outer iterations of the oracle (closed-form objective mode) on the "
+              f"n={args.n} r={args.r} workload, x {iters_to_tol} iterations to tolerance "
+              f"({'oracle count, tests/golden' if rec else 'max_iter'}) x {args.batch} restart(s)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args), "n": args.n, "r": args.r, "batch": args.batch,
+                       "formulation": args.formulation, "tol": args.tol},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2606_02887_gb300.snmf as S
+    from workloads.configs import dense_planted_8192
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    S.load_library()
+
+    prec = {"f64": S.SNMF_F64, "f32": S.SNMF_F32}[args.precision]
+    tdt = torch.float64 if args.precision == "f64" else torch.float32
+    A_np, starts = dense_planted_8192(args.r, args.batch + rank * args.batch, n=args.n)
+    starts = starts[rank * args.batch:(rank + 1) * args.batch]  # replicas: own restarts per rank
+    W0_np = np.concatenate(starts, axis=1)
+    A = torch.tensor(A_np, dtype=tdt, device=dev)
+    W0 = torch.tensor(W0_np, dtype=tdt, device=dev)
+    W = torch.empty_like(W0)
+    H = torch.empty_like(W0)
+    form = S.SNMF_PENALTY if args.formulation == "penalty" else S.SNMF_DIRECT
+    opts = S.snmf_default_options(precision=prec, formulation=form, batch=args.batch, max_iter=args.max_iter,
+                                  tol=args.tol, nonmonotone_M=10)
+    stream = torch.cuda.current_stream(dev)
+    h = S.snmf_create(S.dense_matrix(A), args.r, opts, stream=stream)
+    a_bytes = A.numel() * A.element_size()
+    flush = None if a_bytes > 2 * L2_BYTES else torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        W.copy_(W0)
+        H.copy_(W0)
+        return S.snmf_solve(h, W, H if form == S.SNMF_PENALTY else None)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    launches = 0
+    stats_list = []
+    for k in range(args.steps):
+        if flush is not None:
+            flush.zero_()
+        ev[k][0].record(stream)
+        st, stats = step()
+        ev[k][1].record(stream)
+        launches += stats["kernel_launches"]
+        stats_list.append((st, stats))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(times)
+    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    st, stats = stats_list[-1]
+
+    # dominant kernel: the A*X product, timed alone on the library's stream (CUDA events)
+    ms_prod, ms_kern = S.snmf_profile_ax(h, 20)
+    n, N = args.n, args.r * args.batch
+    esz = 8 if args.precision == "f64" else 4
+    alg_bytes = n * n * esz + 2 * n * N * esz
+    flops = 2.0 * n * n * N
+    peaks, peak_kind = measured_peaks()
+    sm_mhz = clk.get("sm_mhz") or SM_MAX_MHZ_NOMINAL
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12  # TFLOP/s at max clock
+    achieved_tflops = flops / (ms_kern * 1e-3) / 1e12 if ms_kern > 0 else None
+    aw_gbs = alg_bytes / (ms_kern * 1e-3) / 1e9 if ms_kern > 0 else None
+    if args.precision == "f32":
+        roof = {"bound": "alu", "kernel": "k_gemm_dense<float> (CUDA-core FFMA)", "achieved": achieved_tflops,
+                "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak if achieved_tflops else None,
+                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "aw_gbs": aw_gbs, "aw_hbm_frac": aw_gbs / peaks["hbm_gbs"] if aw_gbs else None,
+                "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_kind,
+                "alg_bytes_per_launch": alg_bytes, "flops_per_launch": flops,
+                "ms_per_launch": ms_kern, "ms_per_product_with_epilogue": ms_prod}
+    else:
+        roof = {"bound": "alu", "kernel": "k_gemm_dense<double>", "achieved": achieved_tflops, "peak": None,
+                "unit": "TFLOP/s", "frac": None, "traffic": None, "aw_gbs": aw_gbs,
+                "ms_per_launch": ms_kern}
+
+    # end to end through the C ABI with host buffers (inputs and result cross PCIe/C2C)
+    e2e = None
+    if not args.no_e2e:
+        A_host = A.cpu().pin_memory()
+        W_host = torch.empty_like(W0, device="cpu").pin_memory()
+        H_host = torch.empty_like(W0, device="cpu").pin_memory()
+        W0_host = W0.cpu()
+        e_times = []
+        for k in range(args.e2e_steps + 1):
+            W_host.copy_(W0_host)
+            H_host.copy_(W0_host)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            he = S.snmf_create(S.dense_matrix(A_host), args.r, opts, stream=stream)
+            S.snmf_solve_host(he, W_host, H_host if form == S.SNMF_PENALTY else None)
+            S.snmf_destroy(he)
+            torch.cuda.synchronize()
+            if k > 0:
+                e_times.append(time.perf_counter() - t0)
+        fb = W0.numel() * W0.element_size()
+        nf = 2 if form == S.SNMF_PENALTY else 1
+        e2e = {"value": statistics.mean(e_times), "unit": "s", "h2d_bytes_per_step": a_bytes + nf * fb,
+               "d2h_bytes_per_step": nf * fb,
+               "path": "snmf_create(host A) + snmf_solve_host + snmf_destroy, wall clock"}
+    S.snmf_destroy(h)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        iters_s = 2
+        spi = oracle_seconds_per_iter(A_np, starts[0], args.r, iters_s, args.formulation)
+        est = spi * stats["iters"] * args.batch
+        cpu = {"value": est, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{iters_s} outer iterations of the FP64 oracle (closed-form objective) on restart 0 of "
+                         f"this workload ({spi:.3f} s/iteration), x {stats['iters']} iterations to tolerance "
+                         f"x {args.batch} restart(s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": workload_name(args), "n": args.n, "r": args.r, "batch": args.batch,
+                           "precision": args.precision, "formulation": args.formulation, "tol": args.tol,
+                           "max_iter": args.max_iter,
+                           "l2": ("inputs larger than L2 (A = %.0f MB)" % (a_bytes / 2**20)) if flush is None
+                           else "L2 flushed between timed steps (256 MB write)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk,
+                "solve": {"status": st, "iters": stats["iters"], "residual": stats["residual"],
+                          "pg_rel": stats["pg_rel"], "ls_fail": stats["ls_fail"],
+                          "ax_products": stats["ax_products"], "graph_replays": stats["graph_replays"],
+                          "ms_per_step_all": times}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -133,6 +133,9 @@ typedef struct {
   double residual;         /* ||A - W Ht^T||_F / ||A||_F (direct: Ht = W), FP64               */
   double pg_rel;           /* relative projected gradient of the best restart                 */
   double seconds;          /* device time of the solve (CUDA events)                          */
+  int64_t kernel_launches; /* library kernels executed by the solve                          */
+  int32_t graph_replays;   /* replays of the captured iteration                              */
+  int32_t reserved;
 } snmf_stats;
 
 #define SNMF_MLP_IN 5
@@ -215,6 +218,16 @@ SNMF_API snmf_status snmf_get_factors(snmf_handle h, void* W, void* Ht);
  * <X, A X> in *xax (host, may be NULL).  Uses the LAI sketch when one is set.
  */
 SNMF_API snmf_status snmf_apply(snmf_handle h, const void* X, void* Y, int cols, double* xax);
+
+/*
+ * Measurement utility (no counterpart in the paper): time `iters` back-to-back
+ * A*X products of the handle's factor shape (n x r*batch) on the handle's stream
+ * with CUDA events.  *ms_product: mean time of the whole product (kernel and
+ * epilogue); *ms_kernel: mean time of the product kernel alone (0 for LAI).
+ * Either pointer may be NULL.  Overwrites internal work buffers only.
+ */
+SNMF_API snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_product,
+                                     double* ms_kernel);
 
 /* Release every resource of the handle.  NULL is accepted. */
 SNMF_API snmf_status snmf_destroy(snmf_handle h);

@@ -75,10 +75,12 @@ struct snmf_ctx {
   double* dsc = nullptr;   // device scratch doubles
   int* h_flag = nullptr;   // pinned
   std::vector<Ctl> h_ctl;
-  // captured iteration
-  cudaGraphExec_t exec = nullptr;
+  // captured solve phases: 0 init, 1 one iteration, 2 final evaluation
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+  int nodes[3] = {0, 0, 0};
+  int axn[3] = {0, 0, 0};
   int exec_form = -1;
-  int per_iter = 0;
+  cudaEvent_t evdone = nullptr;
   bool have_result = false;
   int ax_count = 0;
   std::string err;
@@ -517,6 +519,7 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   CKC(cudaEventCreate(&h->ev0));
   CKC(cudaEventCreate(&h->ev1));
   CKC(cudaEventCreateWithFlags(&h->evsync, cudaEventDisableTiming));
+  CKC(cudaEventCreateWithFlags(&h->evdone, cudaEventDisableTiming));
   if (sync_user(h) != SNMF_OK) return bail(SNMF_ERR_CUDA);
   const int src_dt = Am->dtype == SNMF_F64 ? 0 : 1;
   const int64_t n = h->n;
@@ -693,28 +696,35 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
   CK(cudaMemcpyAsync(h->run, &one, sizeof(int), cudaMemcpyHostToDevice, h->s));
   CK(cudaMemcpyAsync(h->recompute, &zero, sizeof(int), cudaMemcpyHostToDevice, h->s));
   const Params P = make_params(h);
-  h->ax_count = 0;
-  if (pen) pen_init(h, P); else dir_init(h, P);
-  // capture one iteration once per configuration
+  // capture init / iteration / final once per configuration (buffers are fixed)
   const int form = pen ? 0 : 1;
   if (h->exec_form != form) {
-    if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
-    cudaGraph_t g;
-    CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
-    const int c0 = h->ax_count;
-    if (pen) pen_iteration(h, P); else dir_iteration(h, P);
-    h->per_iter = h->ax_count - c0 - (pen ? 0 : 1);  // direct: the clipped-step recompute is conditional
-    h->ax_count = c0;
-    CK(cudaStreamEndCapture(h->s, &g));
-    CK(cudaGraphInstantiate(&h->exec, g, 0));
-    cudaGraphDestroy(g);
+    for (int g = 0; g < 3; ++g) {
+      if (h->exec[g]) { cudaGraphExecDestroy(h->exec[g]); h->exec[g] = nullptr; }
+      cudaGraph_t gr;
+      CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+      h->ax_count = 0;
+      if (g == 0) { if (pen) pen_init(h, P); else dir_init(h, P); }
+      else if (g == 1) { if (pen) pen_iteration(h, P); else dir_iteration(h, P); }
+      else { if (pen) pen_final(h, P); else dir_final(h, P); }
+      CK(cudaStreamEndCapture(h->s, &gr));
+      size_t nn = 0;
+      CK(cudaGraphGetNodes(gr, nullptr, &nn));
+      h->nodes[g] = (int)nn;
+      h->axn[g] = h->ax_count - ((!pen && g == 1) ? 1 : 0);  // direct: clipped recompute is conditional
+      CK(cudaGraphInstantiate(&h->exec[g], gr, 0));
+      cudaGraphDestroy(gr);
+    }
     h->exec_form = form;
   }
+  int64_t launches = W ? 0 : 1;
+  CK(cudaGraphLaunch(h->exec[0], h->s));
+  launches += h->nodes[0];
   int done = 0, launched = 0, chunk = 1;
   const int maxit = h->opt.max_iter;
   while (launched < maxit) {
     const int m = std::min(chunk, maxit - launched);
-    for (int t = 0; t < m; ++t) CK(cudaGraphLaunch(h->exec, h->s));
+    for (int t = 0; t < m; ++t) CK(cudaGraphLaunch(h->exec[1], h->s));
     launched += m;
     CK(cudaMemcpyAsync(h->h_flag, h->run, sizeof(int), cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
@@ -722,11 +732,15 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
     chunk = std::min(chunk * 2, 8);
   }
   (void)done;
-  if (pen) pen_final(h, P); else dir_final(h, P);
+  launches += (int64_t)h->nodes[1] * launched;
+  CK(cudaGraphLaunch(h->exec[2], h->s));
+  launches += h->nodes[2];
   if (W) CK(cudaMemcpyAsync(W, h->buf[B_W], fbytes, kout, h->s));
   if (pen && Ht) CK(cudaMemcpyAsync(Ht, h->buf[B_HT], fbytes, kout, h->s));
   CK(cudaEventRecord(h->ev1, h->s));
   CK(cudaMemcpyAsync(h->h_ctl.data(), h->ctl, h->b * sizeof(Ctl), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaEventRecord(h->evdone, h->s));
+  CK(cudaStreamWaitEvent(h->user, h->evdone, 0));
   CK(cudaStreamSynchronize(h->s));
   CK(cudaGetLastError());
   float ms = 0.f;
@@ -750,7 +764,9 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
     out->ls_fail = lsf;
     out->clipped_steps = clip;
     out->best_restart = best;
-    out->ax_products = h->ax_count + h->per_iter * iters + (pen ? 0 : clip);
+    out->ax_products = h->axn[0] + h->axn[1] * launched + h->axn[2] + (pen ? 0 : clip);
+    out->kernel_launches = launches;
+    out->graph_replays = launched;
     out->f = h->h_ctl[best].fin_f;
     out->residual = h->h_ctl[best].fin_res;
     out->pg_rel = h->h_ctl[best].fin_pg;
@@ -820,10 +836,44 @@ snmf_status snmf_apply(snmf_handle h, const void* X, void* Y, int cols, double* 
   return SNMF_OK;
 }
 
+snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_product, double* ms_kernel) {
+  if (!h) return SNMF_ERR_STATE;
+  if (iters < 1) return fail(h, SNMF_ERR_ARG, "iters must be >= 1");
+  if (sync_user(h) != SNMF_OK) return SNMF_ERR_CUDA;
+  const Dims d = dims(h);
+  cudaEvent_t e[4];
+  for (auto& x : e) CK(cudaEventCreate(&x));
+  // warm-up, then the full product (kernel + epilogue) and the product kernel alone
+  ax_A(h, h->buf[B_W], h->buf[B_AZ], 0.0, nullptr, h->buf[B_W], nullptr, h->pax, nullptr);
+  CK(cudaEventRecord(e[0], h->s));
+  for (int t = 0; t < iters; ++t)
+    ax_A(h, h->buf[B_W], h->buf[B_AZ], 0.0, nullptr, h->buf[B_W], nullptr, h->pax, nullptr);
+  CK(cudaEventRecord(e[1], h->s));
+  float m1 = 0.f, m2 = 0.f;
+  if (!h->lai) {
+    CK(cudaEventRecord(e[2], h->s));
+    for (int t = 0; t < iters; ++t)
+      launch_ax(h->A, h->tdtype, h->n, h->N, h->N, h->buf[B_W], h->buf[B_AZ], h->ws, h->ws_elems,
+                nullptr, h->s);
+    CK(cudaEventRecord(e[3], h->s));
+  }
+  CK(cudaStreamSynchronize(h->s));
+  CK(cudaGetLastError());
+  cudaEventElapsedTime(&m1, e[0], e[1]);
+  if (!h->lai) cudaEventElapsedTime(&m2, e[2], e[3]);
+  for (auto& x : e) cudaEventDestroy(x);
+  (void)d;
+  if (ms_product) *ms_product = m1 / iters;
+  if (ms_kernel) *ms_kernel = h->lai ? 0.0 : m2 / iters;
+  return SNMF_OK;
+}
+
 snmf_status snmf_destroy(snmf_handle h) {
   if (!h) return SNMF_OK;
   if (h->s) cudaStreamSynchronize(h->s);
-  if (h->exec) cudaGraphExecDestroy(h->exec);
+  for (auto& e : h->exec)
+    if (e) cudaGraphExecDestroy(e);
+  if (h->evdone) cudaEventDestroy(h->evdone);
   for (void* p : h->buf) cudaFree(p);
   cudaFree(h->ws);
   double* parts[] = {h->prow, h->pax, h->pax2, h->pax3, h->pax4, h->pclip, h->gpart, h->G64fix,

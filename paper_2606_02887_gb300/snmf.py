@@ -27,7 +27,7 @@ SNMF_MLP_NPARAMS = SNMF_MLP_IN * SNMF_MLP_HIDDEN + 2 * SNMF_MLP_HIDDEN + 1
 EXPORTED = (
     "snmf_default_options", "snmf_create", "snmf_set_graph_reg", "snmf_lai_sketch",
     "snmf_solve", "snmf_solve_host", "snmf_restart_stats", "snmf_get_factors",
-    "snmf_apply", "snmf_destroy", "snmf_last_error",
+    "snmf_apply", "snmf_profile_ax", "snmf_destroy", "snmf_last_error",
 )
 
 
@@ -52,7 +52,8 @@ class snmf_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("ls_fail", C.c_int32),
                 ("clipped_steps", C.c_int32), ("best_restart", C.c_int32), ("ax_products", C.c_int32),
                 ("f", C.c_double), ("residual", C.c_double), ("pg_rel", C.c_double),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("kernel_launches", C.c_int64), ("graph_replays", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -80,6 +81,7 @@ def load_library(path: str = LIB_PATH):
     lib.snmf_restart_stats.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.snmf_get_factors.argtypes = [H, C.c_void_p, C.c_void_p]
     lib.snmf_apply.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double)]
+    lib.snmf_profile_ax.argtypes = [H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.snmf_destroy.argtypes = [H]
     lib.snmf_last_error.argtypes = [H]
     lib.snmf_last_error.restype = C.c_char_p
@@ -212,6 +214,14 @@ def snmf_apply(h, X, Y, cols: int):
     xax = C.c_double()
     _check(lib, h, lib.snmf_apply(h, _ptr(X), _ptr(Y), int(cols), C.byref(xax)))
     return xax.value
+
+
+def snmf_profile_ax(h, iters: int = 20):
+    """Mean ms of one A*X product (kernel + epilogue) and of the product kernel alone."""
+    lib = load_library()
+    a, b = C.c_double(), C.c_double()
+    _check(lib, h, lib.snmf_profile_ax(h, int(iters), C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def snmf_destroy(h):
