@@ -229,6 +229,36 @@ SNMF_API snmf_status snmf_apply(snmf_handle h, const void* X, void* Y, int cols,
 SNMF_API snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_product,
                                      double* ms_kernel);
 
+/*
+ * Allocation-free dense product (the paper has no counterpart; this is a service of
+ * the library).  Y = A X and <X, A X> for a dense FP32 or FP64 A, computed with the
+ * same kernels as snmf_apply, for callers that must not allocate device memory after
+ * start-up: programs that size and reserve every buffer once (cudaMalloc and cudaFree
+ * can synchronize the device and stall other streams), programs whose device memory
+ * is owned by another allocator such as a framework's caching pool, and programs
+ * running at the device-memory limit.  It makes no handle and calls no cudaMalloc,
+ * cudaFree or other allocating routine, on the device or on the host.
+ *   A      device, n x n row-major, leading dimension lda >= n, element type dtype
+ *   dtype  SNMF_F32 or SNMF_F64 (A, X and Y share it)
+ *   X, Y   device, n x cols row-major (leading dimension cols); Y is overwritten
+ *   xax    host, receives <X, A X> (may be NULL)
+ *   stream cudaStream_t as void*; the call returns after the stream has finished it
+ * Scratch: the split-K slices and FP64 partial sums live in one file-scope device
+ * array of SNMF_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until
+ * the process exits.  It is shared by all calls and keeps the last call's contents
+ * (every word a call reads was written by that call, so nothing needs clearing);
+ * calls that overlap on the GPU race on it, so issue them one at a time.
+ * Set-up: the first call on a device resolves the array's device address on the
+ * current device.  Limits: n <= 1048320 and 2 * n * cols * sizeof(element) <=
+ * SNMF_NOALLOC_MAX_SLICE_PAIR_BYTES; larger sizes, NULL pointers, lda < n or another
+ * dtype return SNMF_ERR_ARG before any launch.  CUDA failures return SNMF_ERR_CUDA.
+ */
+#define SNMF_NOALLOC_SCRATCH_BYTES (64ull << 20)
+#define SNMF_NOALLOC_MAX_SLICE_PAIR_BYTES (SNMF_NOALLOC_SCRATCH_BYTES - (1ull << 20))
+SNMF_API snmf_status snmf_apply_dense_noalloc(const void* A, int dtype, int64_t n, int64_t lda,
+                                              const void* X, void* Y, int cols, double* xax,
+                                              void* stream);
+
 /* Release every resource of the handle.  NULL is accepted. */
 SNMF_API snmf_status snmf_destroy(snmf_handle h);
 

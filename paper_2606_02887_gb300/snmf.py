@@ -27,8 +27,11 @@ SNMF_MLP_NPARAMS = SNMF_MLP_IN * SNMF_MLP_HIDDEN + 2 * SNMF_MLP_HIDDEN + 1
 EXPORTED = (
     "snmf_default_options", "snmf_create", "snmf_set_graph_reg", "snmf_lai_sketch",
     "snmf_solve", "snmf_solve_host", "snmf_restart_stats", "snmf_get_factors",
-    "snmf_apply", "snmf_profile_ax", "snmf_destroy", "snmf_last_error",
+    "snmf_apply", "snmf_profile_ax", "snmf_apply_dense_noalloc", "snmf_destroy", "snmf_last_error",
 )
+NOALLOC_SCRATCH_BYTES = 64 << 20
+NOALLOC_MAX_SLICE_PAIR_BYTES = NOALLOC_SCRATCH_BYTES - (1 << 20)
+NOALLOC_MAX_ROWS = 1048320
 
 
 class snmf_matrix(C.Structure):
@@ -82,6 +85,8 @@ def load_library(path: str = LIB_PATH):
     lib.snmf_get_factors.argtypes = [H, C.c_void_p, C.c_void_p]
     lib.snmf_apply.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double)]
     lib.snmf_profile_ax.argtypes = [H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.snmf_apply_dense_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                                             C.c_int, C.POINTER(C.c_double), C.c_void_p]
     lib.snmf_destroy.argtypes = [H]
     lib.snmf_last_error.argtypes = [H]
     lib.snmf_last_error.restype = C.c_char_p
@@ -222,6 +227,24 @@ def snmf_profile_ax(h, iters: int = 20):
     a, b = C.c_double(), C.c_double()
     _check(lib, h, lib.snmf_profile_ax(h, int(iters), C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def snmf_apply_dense_noalloc(A, X, Y, stream=None):
+    """Y = A X and <X, A X> without any device allocation (see include/snmf.h).
+    A: n x n device tensor (float32/float64), X, Y: n x cols device tensors."""
+    lib = load_library()
+    dt = SNMF_F64 if str(A.dtype).endswith("float64") else SNMF_F32
+    n, cols = X.shape
+    xax = C.c_double()
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    st = lib.snmf_apply_dense_noalloc(_ptr(A), dt, n, A.stride(0), _ptr(X), _ptr(Y), cols, C.byref(xax), s)
+    if st == SNMF_ERR_ARG:
+        raise SnmfError(st, "rejected: needs n <= %d and 2*n*cols*element size <= %d bytes, lda >= n, "
+                            "float32/float64" % (NOALLOC_MAX_ROWS, NOALLOC_MAX_SLICE_PAIR_BYTES))
+    _check(lib, None, st)
+    return xax.value
 
 
 def snmf_destroy(h):
