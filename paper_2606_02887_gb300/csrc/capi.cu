@@ -72,6 +72,7 @@ struct snmf_ctx {
   Ctl* ctl = nullptr;
   int* run = nullptr;
   int* recompute = nullptr;
+  unsigned* counters = nullptr;  // arrival counters of the fused Gram reduction
   double* dsc = nullptr;   // device scratch doubles
   int* h_flag = nullptr;   // pinned
   std::vector<Ctl> h_ctl;
@@ -155,15 +156,17 @@ int choose_chunks(int64_t n, int b, int r) {
   const int ntile = (r + 63) / 64;
   const int64_t per = (int64_t)b * ntile * ntile;
   int64_t c = (304 + per - 1) / per;
-  c = std::max<int64_t>(1, std::min<int64_t>(c, (n + 127) / 128));
+  c = std::max<int64_t>(1, std::min<int64_t>(c, n / 256));
   return (int)c;
 }
 
-// Gram partials of X^T Y; inside the iteration they follow ctl[j].active and the run flag,
-// in the initial and final evaluations (ctl == NULL) every restart is computed.
-void gram1(snmf_ctx* h, const void* X, const void* Y, int pair, int npairs, const Ctl* ctl) {
+// Gram X^T Y per restart into G64 (+ factor-type copy GT with lam I when pair == tpair);
+// inside the iteration it follows ctl[j].active and the run flag, in the initial and
+// final evaluations (ctl == NULL) every restart is computed.
+void gram1(snmf_ctx* h, const void* X, const void* Y, int pair, int npairs, const Ctl* ctl,
+           double* G64, void* GT, int tpair, double lam) {
   launch_gram(h->tdtype, X, Y, dims(h), pair, npairs, h->gpart, h->nchunks, ctl,
-              ctl ? h->run : nullptr, h->s);
+              ctl ? h->run : nullptr, G64, GT, tpair, lam, h->counters, h->s);
 }
 
 RowArgs row_base(snmf_ctx* h) {
@@ -189,8 +192,7 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
   // B = A Xfix + lambda Xfix (Eq. (2.1)/(2.2))
   ax_A(h, Xf, h->buf[B_B], h->lam, Xf, nullptr, nullptr, h->pax, h->run);
   // G = Xfix^T Xfix (+ lambda I in the factor-type copy); rho_0 = ||Xfix^T Xfix||_2
-  gram1(h, Xf, Xf, 0, 1, h->ctl);
-  launch_gram_reduce(td, h->gpart, h->nchunks, 1, d, h->G64fix, h->GT, 0, h->lam, h->s);
+  gram1(h, Xf, Xf, 0, 1, h->ctl, h->G64fix, h->GT, 0, h->lam);
   launch_rho(td, h->G64fix, d, h->opt.power_iters, 1.0, h->ctl, 0, h->s);
   if (gr) ax_L(h, X, h->buf[B_LX], nullptr, nullptr, h->pax2, h->run);
   {
@@ -202,6 +204,7 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
   launch_ctl_pen_start(h->ctl, h->prow, h->nrow, h->b, P, is_w ? 1 : 0, 0, h->s);
   launch_any_active(h->ctl, h->b, h->run, nullptr, h->s);
   const int K = h->opt.inner_iters;
+  const bool fused_q = h->r <= 64 && !gr;
   for (int k = 0; k < K; ++k) {
     // Z = Proj[X - g / rho_0], D = Proj[Z - alpha g(Z)] - Z   (Alg. 1 lines 2-3)
     {
@@ -216,16 +219,17 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
         launch_rowgemm(td, OP_LOAD, EPI_DIR, a, h->s);
       } else {
         a.X = X; a.g_in = h->buf[B_G]; a.Xout = h->buf[B_Z];
+        a.want_q = fused_q ? 1 : 0;
         launch_rowgemm(td, OP_ZSTEP, EPI_DIR, a, h->s);
       }
     }
-    // curvature of the line-search quadratic: D^T D (and <D, L D>)
-    gram1(h, h->buf[B_D], h->buf[B_D], 0, 1, h->ctl);
-    launch_gram_reduce(td, h->gpart, h->nchunks, 1, d, h->G64p, nullptr, -1, 0.0, h->s);
+    // curvature of the line-search quadratic: <D G, D> from the D kernel (one column
+    // tile) or from the Gram D^T D; graph term <D, L D>
+    if (!fused_q) gram1(h, h->buf[B_D], h->buf[B_D], 0, 1, h->ctl, h->G64p, nullptr, -1, 0.0);
     int nl = 0;
     if (gr) nl = ax_L(h, h->buf[B_D], h->buf[B_LD], h->buf[B_D], nullptr, h->pax3, h->run);
     launch_ctl_pen_ls(h->ctl, h->prow, h->nrow, h->pax3, gr ? nl : 0, h->b, h->r, h->G64fix,
-                      h->G64p, P, gr ? 1 : 0, h->s);
+                      fused_q ? nullptr : h->G64p, P, gr ? 1 : 0, h->s);
     // X' = Proj[Z + phi beta D], gradient, BB inner products   (Alg. 1 line 4)
     {
       RowArgs a = row_base(h);
@@ -255,8 +259,7 @@ void pen_init(snmf_ctx* h, const Params& P) {
   const int td = h->tdtype;
   launch_any_active(h->ctl, h->b, h->run, nullptr, h->s);
   ax_A(h, h->buf[B_W], h->buf[B_B], h->lam, h->buf[B_W], nullptr, nullptr, h->pax, h->run);
-  gram1(h, h->buf[B_W], h->buf[B_W], 0, 1, h->ctl);
-  launch_gram_reduce(td, h->gpart, h->nchunks, 1, d, h->G64fix, h->GT, 0, h->lam, h->s);
+  gram1(h, h->buf[B_W], h->buf[B_W], 0, 1, h->ctl, h->G64fix, h->GT, 0, h->lam);
   if (h->graph) ax_L(h, h->buf[B_HT], h->buf[B_LX], nullptr, nullptr, h->pax2, h->run);
   RowArgs a = row_base(h);
   a.X = h->buf[B_HT]; a.B = h->buf[B_B]; a.LX = h->graph ? h->buf[B_LX] : nullptr;
@@ -277,10 +280,9 @@ void pen_final(snmf_ctx* h, const Params& P) {
   // every restart contributes to the final evaluation
   int nax = ax_apply(h, h->A, h->lai, h->buf[B_HT], h->buf[B_B], h->lam, h->buf[B_HT],
                      h->buf[B_W], nullptr, h->pax, nullptr);
-  gram1(h, h->buf[B_W], h->buf[B_W], 0, 3, nullptr);
-  gram1(h, h->buf[B_HT], h->buf[B_HT], 1, 3, nullptr);
-  gram1(h, h->buf[B_W], h->buf[B_HT], 2, 3, nullptr);
-  launch_gram_reduce(td, h->gpart, h->nchunks, 3, d, h->G64p, h->GT, 1, h->lam, h->s);
+  gram1(h, h->buf[B_W], h->buf[B_W], 0, 3, nullptr, h->G64p, h->GT, 1, h->lam);
+  gram1(h, h->buf[B_HT], h->buf[B_HT], 1, 3, nullptr, h->G64p, h->GT, 1, h->lam);
+  gram1(h, h->buf[B_W], h->buf[B_HT], 2, 3, nullptr, h->G64p, h->GT, 1, h->lam);
   // W gradient at the final point (projected-gradient statistic); uses a temporary
   // "all active" view: the row kernel is run with ctl entries forced live by the host.
   RowArgs a = row_base(h);
@@ -306,8 +308,7 @@ void dir_init(snmf_ctx* h, const Params& P) {
   if (h->graph)
     nlx = ax_apply(h, h->L, false, h->buf[B_W], h->buf[B_LX], 0.0, nullptr, h->buf[B_W], nullptr,
                    h->pax2, nullptr);
-  gram1(h, h->buf[B_W], h->buf[B_W], 0, 1, nullptr);
-  launch_gram_reduce(td, h->gpart, h->nchunks, 1, d, h->G64fix, h->GT, 0, 0.0, h->s);
+  gram1(h, h->buf[B_W], h->buf[B_W], 0, 1, nullptr, h->G64fix, h->GT, 0, 0.0);
   RowArgs a = row_base(h);
   a.X = h->buf[B_W]; a.B = h->buf[B_B]; a.LX = h->graph ? h->buf[B_LX] : nullptr;
   a.gout = h->buf[B_G];
@@ -332,8 +333,7 @@ void dir_iteration(snmf_ctx* h, const Params& P) {
   launch_zstep(td, d, W, g, Z, h->ctl, h->s);
   int nz = ax_A(h, Z, AZ, 0.0, nullptr, Z, nullptr, h->pax, h->run);
   if (h->graph) ax_L(h, Z, h->buf[B_LZ], Z, nullptr, h->pax3, h->run);
-  gram1(h, Z, Z, 0, 1, h->ctl);
-  launch_gram_reduce(td, h->gpart, h->nchunks, 1, d, h->G64p, h->GT, 0, 0.0, h->s);
+  gram1(h, Z, Z, 0, 1, h->ctl, h->G64p, h->GT, 0, 0.0);
   {
     RowArgs a = row_base(h);
     a.X = Z; a.B = AZ; a.LX = h->graph ? h->buf[B_LZ] : nullptr;
@@ -342,9 +342,8 @@ void dir_iteration(snmf_ctx* h, const Params& P) {
   }
   int nd = ax_A(h, D, AD, 0.0, nullptr, Z, D, h->pax2, h->run);
   if (h->graph) ax_L(h, D, h->buf[B_LD], D, nullptr, h->pax4, h->run);
-  gram1(h, Z, D, 0, 2, h->ctl);
-  gram1(h, D, D, 1, 2, h->ctl);
-  launch_gram_reduce(td, h->gpart, h->nchunks, 2, d, h->G64p + rr, nullptr, -1, 0.0, h->s);
+  gram1(h, Z, D, 0, 2, h->ctl, h->G64p + rr, nullptr, -1, 0.0);
+  gram1(h, D, D, 1, 2, h->ctl, h->G64p + rr, nullptr, -1, 0.0);
   launch_ctl_dir_ls(h->ctl, h->pax, nz, h->prow, h->nrow, h->pax2, nd, h->G64p, h->G64p + rr,
                     h->G64p + 2 * rr, h->graph ? h->pax3 : nullptr, h->graph ? h->pax4 : nullptr,
                     h->b, h->r, P, h->s);
@@ -353,8 +352,7 @@ void dir_iteration(snmf_ctx* h, const Params& P) {
   int nre = ax_A(h, Wn, AWn, 0.0, nullptr, Wn, nullptr, h->pax, h->recompute);
   int nlx = 0;
   if (h->graph) nlx = ax_L(h, Wn, h->buf[B_LX], Wn, nullptr, h->pax3, h->run);
-  gram1(h, Wn, Wn, 0, 1, h->ctl);
-  launch_gram_reduce(td, h->gpart, h->nchunks, 1, d, h->G64fix, h->GT, 0, 0.0, h->s);
+  gram1(h, Wn, Wn, 0, 1, h->ctl, h->G64fix, h->GT, 0, 0.0);
   {
     RowArgs a = row_base(h);
     a.X = Wn; a.B = AWn; a.LX = h->graph ? h->buf[B_LX] : nullptr;
@@ -399,6 +397,8 @@ snmf_status alloc_buffers(snmf_ctx* h) {
   CK(cudaMalloc(&h->ctl, 2 * h->b * sizeof(Ctl)));
   CK(cudaMalloc(&h->run, sizeof(int)));
   CK(cudaMalloc(&h->recompute, sizeof(int)));
+  CK(cudaMalloc(&h->counters, 16384 * sizeof(unsigned)));
+  CK(cudaMemsetAsync(h->counters, 0, 16384 * sizeof(unsigned), h->s));
   CK(cudaMalloc(&h->dsc, 4096 * sizeof(double)));
   CK(cudaMallocHost(&h->h_flag, sizeof(int)));
   return SNMF_OK;
@@ -883,6 +883,7 @@ snmf_status snmf_destroy(snmf_handle h) {
   cudaFree(h->ctl);
   cudaFree(h->run);
   cudaFree(h->recompute);
+  cudaFree(h->counters);
   if (h->h_flag) cudaFreeHost(h->h_flag);
   cudaFree(h->A_owned);
   cudaFree(h->rowptr_owned);

@@ -2,7 +2,7 @@
 //
 //   k_gram       r x r Gram X_j^T Y_j of each restart j (Eq. (2.1): H H^T, and the
 //                Z^T D, D^T D products of the line-search polynomial); FP64 partials per
-//                row chunk, reduced in a fixed order by k_gram_reduce.
+//                row chunk, reduced in a fixed order by the last CTA of each tile.
 //   k_rowgemm    X G - B (+ gamma L X): the gradients of Eqs. (2.1)-(2.2) with the
 //                r x r factor G in shared memory, fused with the elementwise steps of
 //                Algorithm 1 (Z step, D direction, relaxed update) and the FP64
@@ -24,14 +24,18 @@ inline int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 inline int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
 
 // ------------------------------------------------------------------------------
-// Gram partials: out[chunk][pair][j][p*r+q] = sum_{i in chunk} X[i, j r + p] Y[i, j r + q]
-// CTA: 64x64 output tile, 16x16 threads with 4x4 micro tiles; rows staged 16 at a time.
+// Gram X_j^T Y_j per restart j.  CTA (chunk, tile): a 64x64 output tile over a chunk of
+// rows (16x16 threads, 4x4 micro tiles), FP64 partial written to gpart.  The last CTA of
+// each tile (arrival counter) sums the partials in chunk order and writes G64 (and the
+// factor-type copy with lam_shift * I on the diagonal when pair == tpair): a fixed-order,
+// deterministic two-stage reduction in one launch.
 // ------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gram(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, int b, int64_t ld,
        int64_t chunk, int ntile, double* __restrict__ gpart, int pair, int npairs,
-       const Ctl* __restrict__ ctl, const int* run) {
+       const Ctl* __restrict__ ctl, const int* run, double* __restrict__ G64, T* __restrict__ GT,
+       int tpair, double lam_shift, unsigned* __restrict__ counters) {
   const int j = blockIdx.y / (ntile * ntile);
   const int t = blockIdx.y % (ntile * ntile);
   const int ti = t / ntile, tj = t % ntile;
@@ -40,6 +44,7 @@ k_gram(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, int b
   const int64_t i_end = min(n, i_begin + chunk);
   __shared__ T Xs[16][64 + 1];
   __shared__ T Ys[16][64 + 1];
+  __shared__ unsigned ticket;
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -51,7 +56,6 @@ k_gram(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, int b
     const int64_t cy = (int64_t)j * r + tj * 64;
     const int wx = min(64, r - ti * 64), wy = min(64, r - tj * 64);
     for (int64_t i0 = i_begin; i0 < i_end; i0 += 16) {
-      // load 16 rows x 64 cols of X and Y (4 elements each per thread)
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const int e = threadIdx.x + 256 * m;
@@ -76,7 +80,10 @@ k_gram(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, int b
       __syncthreads();
     }
   }
-  double* out = gpart + (((int64_t)blockIdx.x * npairs + pair) * b + j) * (int64_t)r * r;
+  const int64_t rr2 = (int64_t)r * r;
+  const int64_t tile_base = ((int64_t)pair * b + j) * rr2;   // offset inside one chunk slab
+  const int64_t slab = (int64_t)npairs * b * rr2;
+  double* out = gpart + (int64_t)blockIdx.x * slab + tile_base;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int p = ti * 64 + ty + 16 * a;
@@ -87,49 +94,49 @@ k_gram(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, int b
       if (q < r) out[(int64_t)p * r + q] = (double)acc[a][c];
     }
   }
-}
-
-// G64[pair][j][e] = sum_chunks gpart (fixed order); optional T copy of pair `tpair`
-// with lam_shift * I added (the block matrix H H^T + lambda I of Eq. (2.1)).
-template <typename T>
-__global__ void k_gram_reduce(const double* __restrict__ gpart, int nchunks, int npairs, int b,
-                              int r, double* __restrict__ G64, T* __restrict__ GT, int tpair,
-                              double lam_shift) {
-  const int64_t rr = (int64_t)r * r;
-  const int64_t total = (int64_t)npairs * b * rr;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < nchunks; ++c) s += gpart[(int64_t)c * total + e];
-    G64[e] = s;
-    const int pair = (int)(e / (b * rr));
-    if (GT && pair == tpair) {
-      const int64_t w = e % (b * rr);
-      const int64_t in = w % rr;
-      const int p = (int)(in / r), q = (int)(in % r);
-      GT[w] = (T)(s + ((p == q) ? lam_shift : 0.0));
-    }
+  __threadfence();
+  __syncthreads();
+  const int tile_id = ((pair * b + j) * ntile + ti) * ntile + tj;
+  if (threadIdx.x == 0) ticket = atomicAdd(&counters[tile_id], 1u);
+  __syncthreads();
+  if (ticket != gridDim.x - 1) return;
+  // last CTA of this tile: fixed-order sum over the chunks
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    const int p = ti * 64 + (e >> 6), q = tj * 64 + (e & 63);
+    if (p >= r || q >= r) continue;
+    const int64_t off = tile_base + (int64_t)p * r + q;
+    double sacc = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) sacc += __ldcg(gpart + (int64_t)c * slab + off);
+    G64[off] = sacc;
+    if (GT && pair == tpair) GT[(int64_t)j * rr2 + (int64_t)p * r + q] = (T)(sacc + (p == q ? lam_shift : 0.0));
   }
+  if (threadIdx.x == 0) counters[tile_id] = 0u;  // ready for the next launch
 }
 
 // ------------------------------------------------------------------------------
 // Row GEMM with fused Algorithm-1 epilogues.
 // ------------------------------------------------------------------------------
-template <typename T, int OP, int EPI>
+template <typename T, int OP, int EPI, int BM>
 __global__ void __launch_bounds__(256) k_rowgemm(RowArgs a) {
+  constexpr int MR = BM / 16;  // rows per thread
+  constexpr int XS_ELEMS = BM * 17;
+  constexpr int DS_ELEMS = (EPI == EPI_DIR) ? BM * 65 : 1;
+  constexpr int U_ELEMS = XS_ELEMS > DS_ELEMS ? XS_ELEMS : DS_ELEMS;
   const int j = blockIdx.z;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t row0 = (int64_t)blockIdx.x * 64;
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
   const int col0 = blockIdx.y * 64;  // within restart
   const int r = a.r;
   const int64_t ld = a.ld;
   const int64_t jc = (int64_t)j * r;
-  __shared__ double sh[32];
-  __shared__ T Xs[64][16 + 1];
+  __shared__ double shq[8][8];
+  __shared__ __align__(16) T ubuf[U_ELEMS];   // operand tile, later the D tile
   __shared__ T Gs[16][64 + 1];
+  T (*Xs)[17] = reinterpret_cast<T (*)[17]>(ubuf);
+  T (*Ds)[65] = reinterpret_cast<T (*)[65]>(ubuf);
   const Ctl& cj = a.ctl[j];
   const bool live = cj.active && !(a.run && *a.run == 0);
-  double dq[6] = {0, 0, 0, 0, 0, 0};
+  double dq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (live) {
     const T* G = (const T*)a.G + (int64_t)j * r * r;
     const T inv_rho = (T)(1.0 / cj.rho);
@@ -146,32 +153,33 @@ __global__ void __launch_bounds__(256) k_rowgemm(RowArgs a) {
       T v = Zin[idx] + pb * Din[idx];
       return v > T(0) ? v : T(0);
     };
-    T acc[4][4];
+    T acc[MR][4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < MR; ++p)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
     for (int k0 = 0; k0 < r; k0 += 16) {
-      // stage operand rows (64 x 16) and G rows (16 x 64)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int e = threadIdx.x + 256 * m;
+      for (int e = threadIdx.x; e < BM * 16; e += 256) {
         const int rr = e >> 4, kk = e & 15;
         const int64_t i = row0 + rr;
         Xs[rr][kk] = (i < a.n && k0 + kk < r) ? operand(i, jc + k0 + kk) : T(0);
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int e = threadIdx.x + 256 * m;
         const int gk = e >> 6, gc = e & 63;
         Gs[gk][gc] = (k0 + gk < r && col0 + gc < r) ? G[(int64_t)(k0 + gk) * r + col0 + gc] : T(0);
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < 16; ++kk) {
-        T xa[4], gb[4];
+        T xa[MR], gb[4];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) xa[p] = Xs[ty + 16 * p][kk];
+        for (int p = 0; p < MR; ++p) xa[p] = Xs[ty + 16 * p][kk];
 #pragma unroll
         for (int q = 0; q < 4; ++q) gb[q] = Gs[kk][tx + 16 * q];
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
+        for (int p = 0; p < MR; ++p)
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[p][q] = fma(xa[p], gb[q], acc[p][q]);
       }
@@ -182,14 +190,15 @@ __global__ void __launch_bounds__(256) k_rowgemm(RowArgs a) {
     const T* B = (const T*)a.B;
     const T* LX = (const T*)a.LX;
     const T gam = (T)a.gamma;
+    T dloc[MR][4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
+    for (int p = 0; p < MR; ++p) {
       const int64_t i = row0 + ty + 16 * p;
-      if (i >= a.n) continue;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
+        dloc[p][q] = T(0);
         const int c = col0 + tx + 16 * q;
-        if (c >= r) continue;
+        if (i >= a.n || c >= r) continue;
         const int64_t idx = i * ld + jc + c;
         const T xv = operand(i, jc + c);
         T g = acc[p][q] - B[idx];
@@ -199,11 +208,11 @@ __global__ void __launch_bounds__(256) k_rowgemm(RowArgs a) {
           tq[0] += pgv * pgv;                              // ||P grad||^2
           tq[1] += T(0.5) * (g - B[idx]) * xv;              // f - const (quadratic block)
           if (a.Xold) {
-            const T s = xv - ((const T*)a.Xold)[idx];
-            const T y = g - ((const T*)a.gold)[idx];
-            tq[2] += s * s;
-            tq[3] += s * y;
-            tq[4] += y * y;
+            const T sv = xv - ((const T*)a.Xold)[idx];
+            const T yv = g - ((const T*)a.gold)[idx];
+            tq[2] += sv * sv;
+            tq[3] += sv * yv;
+            tq[4] += yv * yv;
           }
           if (a.Zold) {                                     // f(X') - f(Z), trapezoid (exact)
             tq[5] += T(0.5) * (xv - ((const T*)a.Zold)[idx]) * (g + ((const T*)a.gZold)[idx]);
@@ -215,6 +224,7 @@ __global__ void __launch_bounds__(256) k_rowgemm(RowArgs a) {
           T d = xv - alpha * g;
           d = (d > T(0) ? d : T(0)) - xv;
           ((T*)a.Dout)[idx] = d;
+          dloc[p][q] = d;
           if (a.gZout) ((T*)a.gZout)[idx] = g;
           tq[0] += g * d;                                   // <grad f(Z), D>
           tq[1] += d * d;                                   // ||D||^2
@@ -227,13 +237,62 @@ __global__ void __launch_bounds__(256) k_rowgemm(RowArgs a) {
     }
 #pragma unroll
     for (int m = 0; m < 6; ++m) dq[m] = (double)tq[m];
-  }
-  const int slot = blockIdx.x * gridDim.y + blockIdx.y;
-  double* out = a.part + ((int64_t)slot * a.b + j) * kNQ;
+    if (EPI == EPI_DIR && a.want_q) {
+      // <D G, D> of the line-search quadratic (the whole restart is one column tile)
 #pragma unroll
-  for (int m = 0; m < 6; ++m) {
-    const double v = block_sum(dq[m], sh);
-    if (threadIdx.x == 0) out[m] = v;
+      for (int p = 0; p < MR; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Ds[ty + 16 * p][tx + 16 * q] = dloc[p][q];
+      __syncthreads();
+      T acc2[MR][4];
+#pragma unroll
+      for (int p = 0; p < MR; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc2[p][q] = T(0);
+      for (int k0 = 0; k0 < r; k0 += 16) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int e = threadIdx.x + 256 * m;
+          const int gk = e >> 6, gc = e & 63;
+          Gs[gk][gc] = (k0 + gk < r && gc < r) ? G[(int64_t)(k0 + gk) * r + gc] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          T gb[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) gb[q] = Gs[kk][tx + 16 * q];
+#pragma unroll
+          for (int p = 0; p < MR; ++p) {
+            const T dv = Ds[ty + 16 * p][k0 + kk];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc2[p][q] = fma(dv, gb[q], acc2[p][q]);
+          }
+        }
+        __syncthreads();
+      }
+      T qq = T(0);
+#pragma unroll
+      for (int p = 0; p < MR; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) qq += acc2[p][q] * dloc[p][q];
+      dq[4] = (double)qq;
+    }
+  }
+  // one combined fixed-order reduction of the partial dots
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const double v = warp_sum(dq[m]);
+    if (lane == 0) shq[m][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v += shq[threadIdx.x][w];
+    const int slot = blockIdx.x * gridDim.y + blockIdx.y;
+    a.part[((int64_t)slot * a.b + j) * kNQ + threadIdx.x] = v;
   }
 }
 
@@ -393,7 +452,7 @@ __global__ void k_rho(const double* __restrict__ G64, int r, int iters, double r
     double part = 0.0;
     for (int p = threadIdx.x; p < r; p += blockDim.x) {
       PT s = 0;
-      for (int q = 0; q < r; ++q) s += (in_smem ? Gs[p * r + q] : (PT)Gj[p * r + q]) * v[q];
+      for (int q = 0; q < r; ++q) s += (in_smem ? Gs[q * r + p] : (PT)Gj[q * r + p]) * v[q];  // G symmetric
       w[p] = s;
       part += (double)s * (double)s;
     }
@@ -406,7 +465,7 @@ __global__ void k_rho(const double* __restrict__ G64, int r, int iters, double r
     double part = 0.0;
     for (int p = threadIdx.x; p < r; p += blockDim.x) {
       PT s = 0;
-      for (int q = 0; q < r; ++q) s += (in_smem ? Gs[p * r + q] : (PT)Gj[p * r + q]) * v[q];
+      for (int q = 0; q < r; ++q) s += (in_smem ? Gs[q * r + p] : (PT)Gj[q * r + p]) * v[q];
       part += (double)v[p] * (double)s;
     }
     rho = block_sum(part, sh);
@@ -461,11 +520,13 @@ __global__ void k_ctl_pen_ls(Ctl* __restrict__ ctl, const double* __restrict__ p
   const double gd = reduce_slots(prow, nrow, b, j, 0, sh);
   const double dd = reduce_slots(prow, nrow, b, j, 1, sh);
   const double dzw = reduce_slots(prow, nrow, b, j, 2, sh);
-  const double qg = dot_rr(DtD + (int64_t)j * r * r, G64fix + (int64_t)j * r * r, r, sh);
+  // curvature <D (H H^T + lambda I), D>: from the D kernel (q4) or from the Gram D^T D
+  const double qg = DtD ? dot_rr(DtD + (int64_t)j * r * r, G64fix + (int64_t)j * r * r, r, sh) + c.lam * dd
+                        : reduce_slots(prow, nrow, b, j, 4, sh);
   double dld = 0.0;
   if (graph) dld = reduce_slots(pax, nax, b, j, 0, sh);
   if (threadIdx.x != 0) return;
-  const double q = qg + c.lam * dd + P.gamma * dld;
+  const double q = qg + P.gamma * dld;
   c.gd = gd;
   c.q = q;
   c.fZ = c.f + dzw;
@@ -814,47 +875,49 @@ __global__ void k_ctl_final_dir(Ctl* __restrict__ ctl, const double* __restrict_
 // host launchers
 // ---------------------------------------------------------------------------
 void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pair, int npairs,
-                 double* gpart, int nchunks, const Ctl* ctl, const int* run, cudaStream_t s) {
+                 double* gpart, int nchunks, const Ctl* ctl, const int* run, double* G64, void* GT,
+                 int tpair, double lam_shift, unsigned* counters, cudaStream_t s) {
   const int ntile = (d.r + 63) / 64;
   const int64_t chunk = (d.n + nchunks - 1) / nchunks;
   dim3 grid(nchunks, d.b * ntile * ntile);
   if (tdtype == 0)
     k_gram<double><<<grid, 256, 0, s>>>((const double*)X, (const double*)Y, d.n, d.r, d.b, d.ld, chunk,
-                                        ntile, gpart, pair, npairs, ctl, run);
+                                        ntile, gpart, pair, npairs, ctl, run, G64, (double*)GT, tpair,
+                                        lam_shift, counters);
   else
     k_gram<float><<<grid, 256, 0, s>>>((const float*)X, (const float*)Y, d.n, d.r, d.b, d.ld, chunk,
-                                       ntile, gpart, pair, npairs, ctl, run);
+                                       ntile, gpart, pair, npairs, ctl, run, G64, (float*)GT, tpair,
+                                       lam_shift, counters);
 }
 
-void launch_gram_reduce(int tdtype, const double* gpart, int nchunks, int npairs, const Dims& d,
-                        double* G64, void* GT, int tpair, double lam_shift, cudaStream_t s) {
-  const int64_t total = (int64_t)npairs * d.b * d.r * d.r;
-  const int blocks = (int)imin64((total + 255) / 256, 4096);
-  if (tdtype == 0)
-    k_gram_reduce<double><<<blocks, 256, 0, s>>>(gpart, nchunks, npairs, d.b, d.r, G64, (double*)GT,
-                                                 tpair, lam_shift);
-  else
-    k_gram_reduce<float><<<blocks, 256, 0, s>>>(gpart, nchunks, npairs, d.b, d.r, G64, (float*)GT,
-                                                tpair, lam_shift);
-}
+static int rowgemm_bm(const Dims& d) { return (d.n + 63) / 64 * ((d.r + 63) / 64) * d.b >= 2 * 152 ? 64 : 32; }
 
-int rowgemm_slots(const Dims& d) { return cdiv(d.n, 64) * cdiv(d.r, 64); }
+int rowgemm_slots(const Dims& d) {
+  const int bm = rowgemm_bm(d);
+  return cdiv(d.n, bm) * cdiv(d.r, 64);
+}
 
 void launch_rowgemm(int tdtype, int op, int epi, const RowArgs& a, cudaStream_t s) {
-  dim3 grid(cdiv(a.n, 64), cdiv(a.r, 64), a.b);
-#define RG(T, O, E) k_rowgemm<T, O, E><<<grid, 256, 0, s>>>(a)
+  Dims d;
+  d.n = a.n; d.r = a.r; d.b = a.b; d.N = a.r * a.b; d.ld = a.ld;
+  const int bm = rowgemm_bm(d);
+  dim3 grid(cdiv(a.n, bm), cdiv(a.r, 64), a.b);
+#define RG(T, O, E, M) k_rowgemm<T, O, E, M><<<grid, 256, 0, s>>>(a)
+#define RG_M(T, O, E) \
+  if (bm == 64) RG(T, O, E, 64); else RG(T, O, E, 32);
 #define RG_T(T)                                                   \
   if (epi == EPI_GRAD) {                                          \
-    if (op == OP_LOAD) RG(T, OP_LOAD, EPI_GRAD);                  \
-    else if (op == OP_ZSTEP) RG(T, OP_ZSTEP, EPI_GRAD);           \
-    else RG(T, OP_UPD, EPI_GRAD);                                 \
+    if (op == OP_LOAD) { RG_M(T, OP_LOAD, EPI_GRAD) }             \
+    else if (op == OP_ZSTEP) { RG_M(T, OP_ZSTEP, EPI_GRAD) }      \
+    else { RG_M(T, OP_UPD, EPI_GRAD) }                            \
   } else {                                                        \
-    if (op == OP_LOAD) RG(T, OP_LOAD, EPI_DIR);                   \
-    else if (op == OP_ZSTEP) RG(T, OP_ZSTEP, EPI_DIR);            \
-    else RG(T, OP_UPD, EPI_DIR);                                  \
+    if (op == OP_LOAD) { RG_M(T, OP_LOAD, EPI_DIR) }              \
+    else if (op == OP_ZSTEP) { RG_M(T, OP_ZSTEP, EPI_DIR) }       \
+    else { RG_M(T, OP_UPD, EPI_DIR) }                             \
   }
   if (tdtype == 0) { RG_T(double) } else { RG_T(float) }
 #undef RG_T
+#undef RG_M
 #undef RG
 }
 
@@ -960,21 +1023,21 @@ void launch_convert(int sdtype, int ddtype, const void* src, int64_t rows, int64
 
 void launch_ctl_pen_start(Ctl* ctl, const double* prow, int nrow, int b, const Params& P, int is_w,
                           int first, cudaStream_t s) {
-  k_ctl_pen_start<<<b, 128, 0, s>>>(ctl, prow, nrow, b, P, is_w, first);
+  k_ctl_pen_start<<<b, 256, 0, s>>>(ctl, prow, nrow, b, P, is_w, first);
 }
 void launch_ctl_pen_ls(Ctl* ctl, const double* prow, int nrow, const double* pax, int nax, int b,
                        int r, const double* G64fix, const double* DtD, const Params& P, int graph,
                        cudaStream_t s) {
-  k_ctl_pen_ls<<<b, 128, 0, s>>>(ctl, prow, nrow, pax, nax, b, r, G64fix, DtD, P, graph);
+  k_ctl_pen_ls<<<b, 256, 0, s>>>(ctl, prow, nrow, pax, nax, b, r, G64fix, DtD, P, graph);
 }
 void launch_ctl_pen_upd(Ctl* ctl, const double* prow, int nrow, int b, const Params& P, int is_h,
                         int last, cudaStream_t s) {
-  k_ctl_pen_upd<<<b, 128, 0, s>>>(ctl, prow, nrow, b, P, is_h, last);
+  k_ctl_pen_upd<<<b, 256, 0, s>>>(ctl, prow, nrow, b, P, is_h, last);
 }
 void launch_ctl_dir_init(Ctl* ctl, const double* pax, int nax, const double* prow, int nrow,
                          const double* plx, int nlx, const double* GW, int b, int r, const Params& P,
                          cudaStream_t s) {
-  k_ctl_dir_init<<<b, 128, 0, s>>>(ctl, pax, nax, prow, nrow, plx, nlx, GW, b, r, P);
+  k_ctl_dir_init<<<b, 256, 0, s>>>(ctl, pax, nax, prow, nrow, plx, nlx, GW, b, r, P);
 }
 void launch_ctl_dir_alpha(Ctl* ctl, int b, const Params& P, cudaStream_t s) {
   k_ctl_dir_alpha<<<b, 32, 0, s>>>(ctl, P);
@@ -983,16 +1046,16 @@ void launch_ctl_dir_ls(Ctl* ctl, const double* pz, int nz, const double* prow, i
                        const double* pd, int nd, const double* GZ, const double* ZD,
                        const double* DDm, const double* pgl, const double* pgd, int b, int r,
                        const Params& P, cudaStream_t s) {
-  k_ctl_dir_ls<<<b, 128, 0, s>>>(ctl, pz, nz, prow, nrow, pd, nd, GZ, ZD, DDm, pgl, pgd, b, r, P);
+  k_ctl_dir_ls<<<b, 256, 0, s>>>(ctl, pz, nz, prow, nrow, pd, nd, GZ, ZD, DDm, pgl, pgd, b, r, P);
 }
 void launch_ctl_dir_clip(Ctl* ctl, const double* pclip, int nslots, int b, int* recompute,
                          cudaStream_t s) {
-  k_ctl_dir_clip<<<b, 128, 0, s>>>(ctl, pclip, nslots, b, recompute);
+  k_ctl_dir_clip<<<b, 256, 0, s>>>(ctl, pclip, nslots, b, recompute);
 }
 void launch_ctl_dir_upd(Ctl* ctl, const double* prow, int nrow, const double* pax, int nax,
                         const double* plx, int nlx, const double* GW, const int* recompute, int b,
                         int r, const Params& P, cudaStream_t s) {
-  k_ctl_dir_upd<<<b, 128, 0, s>>>(ctl, prow, nrow, pax, nax, plx, nlx, GW, recompute, b, r, P);
+  k_ctl_dir_upd<<<b, 256, 0, s>>>(ctl, prow, nrow, pax, nax, plx, nlx, GW, recompute, b, r, P);
 }
 void launch_any_active(const Ctl* ctl, int b, int* flag, int* recompute, cudaStream_t s) {
   k_any_active<<<1, 32, 0, s>>>(ctl, b, flag, recompute);
@@ -1000,10 +1063,10 @@ void launch_any_active(const Ctl* ctl, int b, int* flag, int* recompute, cudaStr
 void launch_ctl_final_pen(Ctl* ctl, const double* pax, int nax, const double* prow, int nrow,
                           const double* GW, const double* GH, const double* WH, int b, int r,
                           const Params& P, cudaStream_t s) {
-  k_ctl_final_pen<<<b, 128, 0, s>>>(ctl, pax, nax, prow, nrow, GW, GH, WH, b, r, P);
+  k_ctl_final_pen<<<b, 256, 0, s>>>(ctl, pax, nax, prow, nrow, GW, GH, WH, b, r, P);
 }
 void launch_ctl_final_dir(Ctl* ctl, const double* GW, int b, int r, const Params& P, cudaStream_t s) {
-  k_ctl_final_dir<<<b, 128, 0, s>>>(ctl, GW, b, r, P);
+  k_ctl_final_dir<<<b, 256, 0, s>>>(ctl, GW, b, r, P);
 }
 
 }  // namespace snmf

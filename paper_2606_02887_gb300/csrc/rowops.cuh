@@ -14,7 +14,7 @@ enum { EPI_GRAD = 0, EPI_DIR = 1 };
 // matrix in the factor type.  Partial layout (part[slot][j][q], slot = CTA):
 //   EPI_GRAD: q0 ||P grad||^2, q1 1/2 <g - B, X>, q2 <S,S>, q3 <S,Y>, q4 <Y,Y>,
 //             q5 1/2 <X - Zold, g + gZold>
-//   EPI_DIR : q0 <g, D>, q1 <D, D>, q2 1/2 <Z - Wcur, g + gWcur>, q3 <D, LX>
+//   EPI_DIR : q0 <g, D>, q1 <D, D>, q2 1/2 <Z - Wcur, g + gWcur>, q3 <D, LX>, q4 <D G, D>
 struct RowArgs {
   int64_t n; int r; int b; int64_t ld;
   const void* G;
@@ -33,13 +33,13 @@ struct RowArgs {
   const void* Xold; const void* gold;    // EPI_GRAD: S = X - Xold, Y = g - gold
   const void* Zold; const void* gZold;   // EPI_GRAD: increment f(X) - f(Zold)
   const void* Wcur; const void* gWcur;   // EPI_DIR: increment f(Z) - f(Wcur)
+  int want_q;          // EPI_DIR, one column tile: also <D G, D> -> q4
   double* part;
 };
 
 void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pair, int npairs,
-                 double* gpart, int nchunks, const Ctl* ctl, const int* run, cudaStream_t s);
-void launch_gram_reduce(int tdtype, const double* gpart, int nchunks, int npairs, const Dims& d,
-                        double* G64, void* GT, int tpair, double lam_shift, cudaStream_t s);
+                 double* gpart, int nchunks, const Ctl* ctl, const int* run, double* G64, void* GT,
+                 int tpair, double lam_shift, unsigned* counters, cudaStream_t s);
 int rowgemm_slots(const Dims& d);
 void launch_rowgemm(int tdtype, int op, int epi, const RowArgs& a, cudaStream_t s);
 void launch_zstep(int tdtype, const Dims& d, const void* X, const void* g, void* Z, const Ctl* ctl,
