@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--n", type=int, default=8192)
     p.add_argument("--r", type=int, default=64)
     p.add_argument("--batch", type=int, default=1)
-    p.add_argument("--precision", default="f32", choices=["f64", "f32"])
+    p.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
     p.add_argument("--formulation", default="penalty", choices=["penalty", "direct"])
     p.add_argument("--max-iter", type=int, default=500)
     p.add_argument("--tol", type=float, default=1e-4)
@@ -193,7 +193,7 @@ def main():
     dev = torch.device("cuda", local)
     S.load_library()
 
-    prec = {"f64": S.SNMF_F64, "f32": S.SNMF_F32}[args.precision]
+    prec = {"f64": S.SNMF_F64, "f32": S.SNMF_F32, "bf16": S.SNMF_BF16}[args.precision]
     tdt = torch.float64 if args.precision == "f64" else torch.float32
     A_np, starts = dense_planted_8192(args.r, args.batch + rank * args.batch, n=args.n)
     starts = starts[rank * args.batch:(rank + 1) * args.batch]  # replicas: own restarts per rank
@@ -207,7 +207,7 @@ def main():
                                   tol=args.tol, nonmonotone_M=10)
     stream = torch.cuda.current_stream(dev)
     h = S.snmf_create(S.dense_matrix(A), args.r, opts, stream=stream)
-    a_bytes = A.numel() * A.element_size()
+    a_bytes = A.numel() * (2 if args.precision == "bf16" else A.element_size())
     flush = None if a_bytes > 2 * L2_BYTES else torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def step():
@@ -250,7 +250,8 @@ def main():
     ms_prod, ms_kern = S.snmf_profile_ax(h, 20)
     n, N = args.n, args.r * args.batch
     esz = 8 if args.precision == "f64" else 4
-    alg_bytes = n * n * esz + 2 * n * N * esz
+    a_esz = 2 if args.precision == "bf16" else esz
+    alg_bytes = n * n * a_esz + 2 * n * N * esz
     flops = 2.0 * n * n * N
     peaks, peak_kind = measured_peaks()
     sm_mhz = clk.get("sm_mhz") or SM_MAX_MHZ_NOMINAL
@@ -264,6 +265,14 @@ def main():
                 "aw_gbs": aw_gbs, "aw_hbm_frac": aw_gbs / peaks["hbm_gbs"] if aw_gbs else None,
                 "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "flops_per_launch": flops,
+                "ms_per_launch": ms_kern, "ms_per_product_with_epilogue": ms_prod}
+    elif args.precision == "bf16":
+        roof = {"bound": "hbm", "kernel": "k_split_x + k_gemm_tc (tcgen05 BF16, X as hi+lo BF16 parts)",
+                "achieved": aw_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": aw_gbs / peaks["hbm_gbs"] if aw_gbs else None, "traffic": None,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+                "tensor_tflops": achieved_tflops * 2 if achieved_tflops else None,
+                "alg_bytes_per_launch": alg_bytes, "flops_per_launch": 2 * flops,
                 "ms_per_launch": ms_kern, "ms_per_product_with_epilogue": ms_prod}
     else:
         roof = {"bound": "alu", "kernel": "k_gemm_dense<double>", "achieved": achieved_tflops, "peak": None,

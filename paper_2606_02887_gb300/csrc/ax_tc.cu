@@ -1,0 +1,433 @@
+// Tensor-core A*X product for BF16 A on sm_103a (tcgen05 + TMA + TMEM).
+//
+//   Y (FP32, n x N) = A_bf16 X_hi + A_bf16 X_lo, with X_hi = bf16(X), X_lo = bf16(X - X_hi):
+//   the product sees X to about 2^-17 relative while A stays in BF16 (half the HBM bytes of
+//   FP32).  Both operands are K-major: A row-major (n x lda), the X parts transposed
+//   (N x ldk) by k_split_x.  Tiles: BM = 128 rows (UMMA M = 128, cta_group::1), BN columns
+//   (16..256), BK = 64 (one 128-byte swizzle atom).
+//
+//   warp 0 lane 0 : TMA producer, ring of `stages` (A tile + two X tiles) with full/empty
+//                   mbarriers
+//   warp 1 lane 0 : MMA issuer: per stage 4 K-steps x (hi, lo) tcgen05.mma into one TMEM
+//                   accumulator, tcgen05.commit frees the stage
+//   warps 0-3     : epilogue: tcgen05.ld 32 rows each, store FP32 rows (split-K slice or Y)
+//
+// Every mbarrier wait is bounded by a clock64 budget; on expiry the kernel records an
+// error code, stops issuing, releases its TMEM and returns (no unbounded spin).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "ax_tc.cuh"
+
+namespace snmf {
+
+namespace {
+
+constexpr int BM = 128, BK = 64;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: true when the phase completed, false when the budget ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);        // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)2 << 61;                          // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Instruction descriptor of kind::f16: D FP32, A/B BF16, both K-major, N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+struct TcParams {
+  int64_t n;          // rows of A (M extent) and K extent
+  int N;              // columns of Y
+  int BN;             // tile columns (multiple of 16, <= 256)
+  int stages;
+  int k_iters;        // BK-steps per split
+  int tmem_cols;      // power of two >= BN, >= 32
+  float* Y;           // output base (split z writes Y + z * n * ldy)
+  int64_t ldy;
+  int* err;           // error code (0 = ok)
+  long long budget;   // clock64 budget per wait
+};
+
+__global__ void __launch_bounds__(128, 1)
+k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapXh,
+          const __grid_constant__ CUtensorMap mapXl, TcParams p) {
+  extern __shared__ unsigned char smem_raw[];
+  // 1024-byte aligned ring: [stage][A 128x64 | Xh BNx64 | Xl BNx64] (bf16)
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int BN = p.BN;
+  const uint32_t a_bytes = BM * BK * 2;
+  const uint32_t b_bytes = (uint32_t)BN * BK * 2;
+  const uint32_t stage_bytes = a_bytes + 2 * b_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)p.stages * stage_bytes);
+  uint64_t* empty = full + p.stages;
+  uint64_t* accum = empty + p.stages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  __shared__ int s_fail, s_issued, s_consumed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN;
+  const int m0 = blockIdx.y * BM;
+  const int kbase = blockIdx.z * p.k_iters * BK;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(p.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    int it = 0;
+    for (; it < p.k_iters; ++it) {
+      const int s = it % p.stages;
+      const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u, p.budget)) { atomicExch(p.err, 1); s_fail = 1; break; }
+      unsigned char* st = base + (size_t)s * stage_bytes;
+      mbar_expect_tx(&full[s], stage_bytes);
+      const int kx = kbase + it * BK;
+      tma_load_2d(st, &mapA, &full[s], kx, m0);
+      tma_load_2d(st + a_bytes, &mapXh, &full[s], kx, n0);
+      tma_load_2d(st + a_bytes + b_bytes, &mapXl, &full[s], kx, n0);
+    }
+    s_issued = it;
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = idesc_bf16(BM, BN);
+    int it = 0;
+    for (; it < p.k_iters; ++it) {
+      const int s = it % p.stages;
+      const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
+      if (!mbar_wait(&full[s], ph, p.budget)) { atomicExch(p.err, 2); s_fail = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(base + (size_t)s * stage_bytes);
+      const uint32_t sh = sa + a_bytes, sl = sa + a_bytes + b_bytes;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t da = sdesc(sa + kk * 32);
+        mma_bf16(tmem, da, sdesc(sh + kk * 32), idesc, (it > 0 || kk > 0) ? 1u : 0u);
+        mma_bf16(tmem, da, sdesc(sl + kk * 32), idesc, 1u);
+      }
+      mma_commit(&empty[s]);
+    }
+    s_consumed = it;
+    mma_commit(accum);  // arrives once every MMA issued above has completed
+  }
+  __syncwarp();
+  __syncthreads();  // role loops finished; s_fail / s_issued / s_consumed visible
+  // epilogue: all four warps, each drains its 32 TMEM lanes
+  bool done = mbar_wait(accum, 0, p.budget);
+  done = __all_sync(0xffffffffu, done);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!done && lane == 0) atomicExch(p.err, 3);
+  if (done && !s_fail) {
+    const int row = m0 + warp * 32 + lane;
+    float* Yz = p.Y + (int64_t)blockIdx.z * p.n * p.ldy;
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (row < p.n) {
+        float* yr = Yz + (int64_t)row * p.ldy + n0 + c0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (n0 + c0 + i < p.N) yr[i] = v[i];
+      }
+    }
+  }
+  if (s_fail && threadIdx.x == 0) {
+    // error path: wait (bounded) for the loads this CTA issued but never consumed
+    for (int it = s_consumed; it < s_issued; ++it)
+      if (!mbar_wait(&full[it % p.stages], (uint32_t)(it / p.stages) & 1u, p.budget)) break;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols));
+  }
+}
+
+// X (n x N FP32, ld) -> Xh, Xl (N x ldk BF16, transposed, zero padded in k)
+__global__ void k_split_x(const float* __restrict__ X, int64_t n, int N, int64_t ld,
+                          __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl, int64_t ldk) {
+  __shared__ float t[32][33];
+  const int64_t k0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t k = k0 + i;
+    const int c = c0 + tx;
+    t[i][tx] = (k < n && c < N) ? X[k * ld + c] : 0.0f;
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int c = c0 + i;
+    const int64_t k = k0 + tx;
+    if (c < N && k < ldk) {
+      const float v = t[tx][i];
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+      Xh[(int64_t)c * ldk + k] = hi;
+      Xl[(int64_t)c * ldk + k] = lo;
+    }
+  }
+}
+
+// A (n x n, source type, lda) -> A16 (n x ldk BF16, zero padded columns)
+template <typename TS>
+__global__ void k_to_bf16(const TS* __restrict__ A, int64_t n, int64_t lda, __nv_bfloat16* __restrict__ A16,
+                          int64_t ldk) {
+  const int64_t total = n * ldk;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ldk, k = e % ldk;
+    A16[e] = __float2bfloat16_rn(k < n ? (float)A[i * lda + k] : 0.0f);
+  }
+}
+
+// sum of squares and sum of a BF16 matrix (FP64 partial per block)
+__global__ void k_sums_bf16(const __nv_bfloat16* __restrict__ A, int64_t m, double* __restrict__ part) {
+  __shared__ double sh2[32], sh1[32];
+  double s2 = 0.0, s1 = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)__bfloat162float(A[e]);
+    s2 += v * v;
+    s1 += v;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { sh2[wid] = s2; sh1[wid] = s1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sh2[w]; b += sh1[w]; }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  });
+  return fn;
+}
+
+// 2-D BF16 tensor map: inner extent `inner` (elements, contiguous), `rows` rows, row pitch
+// `ld` elements; box {64, box_rows}; 128-byte swizzle; out-of-range reads are zero.
+int g_last_cu = 0;  // last CUresult of the tensor-map encoder (diagnostics)
+
+bool make_map(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t ld, int box_rows) {
+  EncodeFn enc = get_encode();
+  if (!enc) { g_last_cu = -1; return false; }
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  g_last_cu = (int)r;
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int tc_last_status() { return g_last_cu; }
+
+int64_t tc_ld(int64_t n) { return (n + 63) / 64 * 64; }
+
+void launch_to_bf16(int src_dtype, const void* A, int64_t n, int64_t lda, void* A16, cudaStream_t s) {
+  const int64_t ldk = tc_ld(n);
+  const int blocks = (int)((n * ldk + 255) / 256 < 152 * 32 ? (n * ldk + 255) / 256 : 152 * 32);
+  if (src_dtype == 0)
+    k_to_bf16<double><<<blocks, 256, 0, s>>>((const double*)A, n, lda, (__nv_bfloat16*)A16, ldk);
+  else
+    k_to_bf16<float><<<blocks, 256, 0, s>>>((const float*)A, n, lda, (__nv_bfloat16*)A16, ldk);
+}
+
+int launch_sums_bf16(const void* A16, int64_t elems, double* part, cudaStream_t s) {
+  const int blocks = (int)((elems + 255) / 256 < 1024 ? (elems + 255) / 256 : 1024);
+  k_sums_bf16<<<blocks, 256, 0, s>>>((const __nv_bfloat16*)A16, elems, part);
+  return blocks;
+}
+
+int tc_plan(int64_t n, int N, TcPlan* plan) {
+  TcPlan pl{};
+  pl.BN = N <= 256 ? ((N + 15) / 16 * 16) : 256;
+  pl.tiles_n = (N + pl.BN - 1) / pl.BN;
+  pl.tiles_m = (int)((n + BM - 1) / BM);
+  const int64_t kiters_total = (n + BK - 1) / BK;
+  const uint32_t stage_bytes = BM * BK * 2 + 2u * pl.BN * BK * 2;
+  // two CTAs per SM with a 3-stage ring when it fits in half the SM, else one CTA with
+  // as many stages as fit (at most 6)
+  int per_sm = 1, stages;
+  if (3 * stage_bytes + 4096 <= 110 * 1024) {
+    per_sm = 2;
+    stages = 3;
+  } else {
+    stages = (int)((200 * 1024) / stage_bytes);
+    if (stages > 6) stages = 6;
+    if (stages < 2) stages = 2;
+  }
+  pl.stages = stages;
+  const int tiles = pl.tiles_n * pl.tiles_m;
+  int splits = (152 * per_sm) / tiles;
+  if (splits < 1) splits = 1;
+  while (splits > 1 && kiters_total / splits < 8) --splits;
+  pl.splits = splits;
+  pl.k_iters = (int)((kiters_total + splits - 1) / splits);
+  pl.tmem_cols = 32;
+  while (pl.tmem_cols < pl.BN) pl.tmem_cols *= 2;
+  pl.smem = stage_bytes * stages + 1024 + 8 * (2 * stages + 2) + 64;
+  *plan = pl;
+  return 0;
+}
+
+int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
+                 float* Y, float* ws, size_t ws_elems, int* err, long long budget, cudaStream_t s) {
+  TcPlan pl;
+  tc_plan(n, N, &pl);
+  const int64_t ldk = tc_ld(n);
+  if ((size_t)pl.splits * n * ldx > ws_elems) {
+    // not enough split workspace: recompute the plan without splitting
+    pl.splits = 1;
+    pl.k_iters = (int)((n + BK - 1) / BK);
+  }
+  dim3 sg((unsigned)((ldk + 31) / 32), (unsigned)((N + 31) / 32));
+  k_split_x<<<sg, 256, 0, s>>>(X, n, N, ldx, (__nv_bfloat16*)xh, (__nv_bfloat16*)xl, ldk);
+  CUtensorMap ma, mh, ml;
+  if (!make_map(&ma, A16, ldk, n, ldk, BM) || !make_map(&mh, xh, ldk, N, ldk, pl.BN) ||
+      !make_map(&ml, xl, ldk, N, ldk, pl.BN))
+    return -1;
+  static bool attr_done = false;
+  if (!attr_done) {
+    // the plan never asks for more than ~206 KB; static shared memory comes on top
+    if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024) != cudaSuccess) {
+      g_last_cu = 10000 + (int)cudaGetLastError();
+      return -3;
+    }
+    attr_done = true;
+  }
+  TcParams p;
+  p.n = n;
+  p.N = N;
+  p.BN = pl.BN;
+  p.stages = pl.stages;
+  p.k_iters = pl.k_iters;
+  p.tmem_cols = pl.tmem_cols;
+  p.Y = pl.splits > 1 ? ws : Y;
+  p.ldy = ldx;
+  p.err = err;
+  p.budget = budget;
+  dim3 grid(pl.tiles_n, pl.tiles_m, pl.splits);
+  k_gemm_tc<<<grid, 128, pl.smem, s>>>(ma, mh, ml, p);
+  const cudaError_t le = cudaPeekAtLastError();
+  if (le != cudaSuccess) { g_last_cu = 10000 + (int)le; return -2; }
+  return pl.splits;
+}
+
+}  // namespace snmf

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/snmf.h"
+#include "ax_tc.cuh"
 #include "common.cuh"
 #include "lai.cuh"
 #include "rowops.cuh"
@@ -73,6 +74,11 @@ struct snmf_ctx {
   int* run = nullptr;
   int* recompute = nullptr;
   unsigned* counters = nullptr;  // arrival counters of the fused Gram reduction
+  int* dev_err = nullptr;        // device error code of bounded waits (tensor-core product)
+  void* xh = nullptr;            // BF16 hi / lo parts of the product operand (transposed)
+  void* xl = nullptr;
+  long long budget = 2000000000LL;
+  int tc_fail = 0;               // status of a failed tensor-core launch (encoder / launch error)
   double* dsc = nullptr;   // device scratch doubles
   int* h_flag = nullptr;   // pinned
   std::vector<Ctl> h_ctl;
@@ -130,6 +136,21 @@ Dims dims(const snmf_ctx* h) {
   return d;
 }
 
+// The product kernel alone: CUDA cores (FP64/FP32 dense, CSR) or tcgen05 (BF16 dense).
+// Returns the number of split-K slices written to h->ws (1 = result in Y).
+int product_kernel(snmf_ctx* h, const AxArgs& op, const void* X, void* Y, const int* run) {
+  if (op.kind == AX_DENSE && op.a_dtype == 2) {
+    const int sp = launch_ax_tc(op.A, h->n, (const float*)X, h->N, h->N, h->xh, h->xl, (float*)Y,
+                                (float*)h->ws, h->ws_elems, h->dev_err, h->budget, h->s);
+    if (sp < 1) {
+      h->tc_fail = tc_last_status();
+      return 1;
+    }
+    return sp;
+  }
+  return launch_ax(op, h->tdtype, h->n, h->N, h->N, X, Y, h->ws, h->ws_elems, run, h->s);
+}
+
 // Y = op X (+ c X2), dots <P1, op X> -> part q0, <P2, op X> -> q0+1; returns slot count.
 int ax_apply(snmf_ctx* h, const AxArgs& op, bool use_lai, const void* X, void* Y, double c,
              const void* X2, const void* P1, const void* P2, double* part, const int* run) {
@@ -138,7 +159,7 @@ int ax_apply(snmf_ctx* h, const AxArgs& op, bool use_lai, const void* X, void* Y
   if (use_lai) {
     return lai_apply(h->lai_op, h->tdtype, d, X, Y, c, X2, P1, P2, part, run, h->s);
   }
-  int splits = launch_ax(op, h->tdtype, h->n, h->N, h->N, X, Y, h->ws, h->ws_elems, run, h->s);
+  const int splits = product_kernel(h, op, X, Y, run);
   return launch_ax_finish_impl(h->tdtype, d, Y, h->ws, splits, c, X2, P1, P2, part, 0, run, h->s);
 }
 
@@ -397,6 +418,14 @@ snmf_status alloc_buffers(snmf_ctx* h) {
   CK(cudaMalloc(&h->ctl, 2 * h->b * sizeof(Ctl)));
   CK(cudaMalloc(&h->run, sizeof(int)));
   CK(cudaMalloc(&h->recompute, sizeof(int)));
+  CK(cudaMalloc(&h->dev_err, sizeof(int)));
+  CK(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->s));
+  if (h->kind == AX_DENSE && h->prec == SNMF_BF16) {
+    const size_t xb = (size_t)h->N * tc_ld(h->n) * 2;
+    CK(cudaMalloc(&h->xh, xb));
+    CK(cudaMalloc(&h->xl, xb));
+  }
+  if (h->opt.timeout_cycles > 0) h->budget = h->opt.timeout_cycles;
   CK(cudaMalloc(&h->counters, 16384 * sizeof(unsigned)));
   CK(cudaMemsetAsync(h->counters, 0, 16384 * sizeof(unsigned), h->s));
   CK(cudaMalloc(&h->dsc, 4096 * sizeof(double)));
@@ -480,8 +509,8 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
     if (o.precision == SNMF_BF16 || o.precision == SNMF_FP8)
       return fail(nullptr, SNMF_ERR_ARG, "CSR supports F64/F32 precision");
   }
-  if (o.precision == SNMF_BF16 || o.precision == SNMF_FP8)
-    return fail(nullptr, SNMF_ERR_ARG, "BF16/FP8 precision not available in this build");
+  if (o.precision == SNMF_FP8)
+    return fail(nullptr, SNMF_ERR_ARG, "FP8 precision not available in this build");
   if (o.formulation == SNMF_PENALTY && o.step_controller)
     return fail(nullptr, SNMF_ERR_ARG, "learned step controller not available in this build");
 
@@ -523,7 +552,28 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   if (sync_user(h) != SNMF_OK) return bail(SNMF_ERR_CUDA);
   const int src_dt = Am->dtype == SNMF_F64 ? 0 : 1;
   const int64_t n = h->n;
-  if (h->kind == AX_DENSE) {
+  if (h->kind == AX_DENSE && o.precision == SNMF_BF16) {
+    // owned BF16 copy, K-major with columns padded to a multiple of 64 (tensor-core layout)
+    const void* src = Am->values;
+    void* staging = nullptr;
+    const size_t sbytes = (size_t)n * Am->ld * (src_dt == 0 ? 8 : 4);
+    if (Am->location == SNMF_ON_HOST) {
+      CKC(cudaMalloc(&staging, sbytes));
+      CKC(cudaMemcpyAsync(staging, src, sbytes, cudaMemcpyHostToDevice, h->s));
+      src = staging;
+    }
+    const int64_t ldk = tc_ld(n);
+    CKC(cudaMalloc(&h->A_owned, (size_t)n * ldk * 2));
+    launch_to_bf16(src_dt, src, n, Am->ld, h->A_owned, h->s);
+    if (staging) {
+      CKC(cudaStreamSynchronize(h->s));
+      cudaFree(staging);
+    }
+    h->A.A = h->A_owned;
+    h->A.lda = ldk;
+    h->A.a_dtype = 2;
+    h->A.kind = AX_DENSE;
+  } else if (h->kind == AX_DENSE) {
     // working copy of A in the factor type unless it can be borrowed
     const bool borrow = Am->location == SNMF_ON_DEVICE && src_dt == h->tdtype;
     if (borrow) {
@@ -555,7 +605,7 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
     }
     h->A.a_dtype = h->tdtype;
     h->A.kind = AX_DENSE;
-  } else {
+  } else if (h->kind == AX_CSR) {
     const int64_t nnz = Am->nnz;
     if (Am->location == SNMF_ON_HOST) {
       const int32_t* rp = Am->rowptr;
@@ -595,7 +645,10 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   snmf_status st = alloc_buffers(h);
   if (st != SNMF_OK) return bail(st);
   // ||A||_F^2 and mean(A) of the stored operator
-  if (h->kind == AX_DENSE)
+  if (h->kind == AX_DENSE && h->A.a_dtype == 2) {
+    const int nb = launch_sums_bf16(h->A.A, n * h->A.lda, h->dsc + 16, h->s);  // ||A~||^2 of the stored values
+    launch_sum_pairs(h->dsc + 16, nb, h->dsc, h->s);
+  } else if (h->kind == AX_DENSE)
     launch_matrix_sums(AX_DENSE, h->tdtype, h->A.A, n, h->A.lda, 0, h->dsc + 16, h->dsc, h->s);
   else
     launch_matrix_sums(AX_CSR, h->A.v_dtype, h->A.vals, n, 0, h->A.lda, h->dsc + 16, h->dsc, h->s);
@@ -741,8 +794,22 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
   CK(cudaMemcpyAsync(h->h_ctl.data(), h->ctl, h->b * sizeof(Ctl), cudaMemcpyDeviceToHost, h->s));
   CK(cudaEventRecord(h->evdone, h->s));
   CK(cudaStreamWaitEvent(h->user, h->evdone, 0));
+  int derr = 0;
+  CK(cudaMemcpyAsync(&derr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
+  if (h->tc_fail) {
+    const int tf = h->tc_fail;
+    h->tc_fail = 0;
+    cudaGetLastError();
+    return fail(h, SNMF_ERR_CUDA, "tensor-core product not launched (status " + std::to_string(tf) + ")");
+  }
   CK(cudaGetLastError());
+  if (derr) {
+    CK(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return fail(h, SNMF_ERR_TIMEOUT, "a bounded device wait of the tensor-core product ran out (code " +
+                                         std::to_string(derr) + ")");
+  }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->have_result = true;
@@ -826,7 +893,21 @@ snmf_status snmf_apply(snmf_handle h, const void* X, void* Y, int cols, double* 
                        cudaMemcpyDeviceToDevice, h->s));
   std::vector<double> part((size_t)nax * h->b * kNQ);
   CK(cudaMemcpyAsync(part.data(), h->pax, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  int derr = 0;
+  CK(cudaMemcpyAsync(&derr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
+  if (h->tc_fail) {
+    const int tf = h->tc_fail;
+    h->tc_fail = 0;
+    cudaGetLastError();
+    return fail(h, SNMF_ERR_CUDA, "tensor-core product not launched (status " + std::to_string(tf) + ")");
+  }
+  CK(cudaGetLastError());
+  if (derr) {
+    CK(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return fail(h, SNMF_ERR_TIMEOUT, "a bounded device wait of the tensor-core product ran out");
+  }
   if (xax) {
     double s = 0.0;
     for (int t = 0; t < nax; ++t)
@@ -852,9 +933,7 @@ snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_product, double
   float m1 = 0.f, m2 = 0.f;
   if (!h->lai) {
     CK(cudaEventRecord(e[2], h->s));
-    for (int t = 0; t < iters; ++t)
-      launch_ax(h->A, h->tdtype, h->n, h->N, h->N, h->buf[B_W], h->buf[B_AZ], h->ws, h->ws_elems,
-                nullptr, h->s);
+    for (int t = 0; t < iters; ++t) product_kernel(h, h->A, h->buf[B_W], h->buf[B_AZ], nullptr);
     CK(cudaEventRecord(e[3], h->s));
   }
   CK(cudaStreamSynchronize(h->s));
@@ -884,6 +963,9 @@ snmf_status snmf_destroy(snmf_handle h) {
   cudaFree(h->run);
   cudaFree(h->recompute);
   cudaFree(h->counters);
+  cudaFree(h->dev_err);
+  cudaFree(h->xh);
+  cudaFree(h->xl);
   if (h->h_flag) cudaFreeHost(h->h_flag);
   cudaFree(h->A_owned);
   cudaFree(h->rowptr_owned);

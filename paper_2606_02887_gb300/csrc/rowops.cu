@@ -1008,6 +1008,10 @@ void launch_matrix_sums(int kind, int vdtype, const void* vals, int64_t n, int64
   k_sum_pairs<<<1, 256, 0, s>>>(part, blocks, out);
 }
 
+void launch_sum_pairs(const double* part, int m, double* out, cudaStream_t s) {
+  k_sum_pairs<<<1, 256, 0, s>>>(part, m, out);
+}
+
 void launch_convert(int sdtype, int ddtype, const void* src, int64_t rows, int64_t cols, int64_t lds,
                     void* dst, int64_t ldd, cudaStream_t s) {
   const int blocks = grid1d(rows * cols);

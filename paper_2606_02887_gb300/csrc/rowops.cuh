@@ -80,6 +80,7 @@ void launch_ctl_dir_upd(Ctl* ctl, const double* prow, int nrow, const double* pa
                         const double* plx, int nlx, const double* GW, const int* recompute, int b,
                         int r, const Params& P, cudaStream_t s);
 void init_kernel_attributes();
+void launch_sum_pairs(const double* part, int m, double* out, cudaStream_t s);
 void launch_any_active(const Ctl* ctl, int b, int* flag, int* recompute, cudaStream_t s);
 void launch_ctl_final_pen(Ctl* ctl, const double* pax, int nax, const double* prow, int nrow,
                           const double* GW, const double* GH, const double* WH, int b, int r,
