@@ -140,10 +140,10 @@ k_ax_finish(int64_t n, int r, int64_t ld, T* __restrict__ Y, const T* __restrict
             int splits, double c, const T* __restrict__ X2, const T* __restrict__ P1,
             const T* __restrict__ P2, double* __restrict__ part, int q0, int b,
             const int* run) {
-  __shared__ double sh[32];
+  __shared__ T sh[32];
   const int j = blockIdx.y;
   const int64_t i0 = (int64_t)blockIdx.x * kRowTile;
-  double d1 = 0.0, d2 = 0.0;
+  T d1 = T(0), d2 = T(0);  // per-CTA partials in the working type (FP64 across CTAs)
   if (!(run && *run == 0)) {
     const int tile = kRowTile * r;
     for (int e = threadIdx.x; e < tile; e += blockDim.x) {
@@ -157,18 +157,18 @@ k_ax_finish(int64_t n, int r, int64_t ld, T* __restrict__ Y, const T* __restrict
       } else {
         y = Y[idx];
       }
-      if (P1) d1 += (double)P1[idx] * (double)y;
-      if (P2) d2 += (double)P2[idx] * (double)y;
+      if (P1) d1 += P1[idx] * y;
+      if (P2) d2 += P2[idx] * y;
       if (X2) y = y + (T)c * X2[idx];
       Y[idx] = y;
     }
   }
-  d1 = block_sum(d1, sh);
-  d2 = block_sum(d2, sh);
+  d1 = block_sum_t(d1, sh);
+  d2 = block_sum_t(d2, sh);
   if (threadIdx.x == 0) {
     double* p = part + ((int64_t)blockIdx.x * b + j) * kNQ;
-    p[q0] = d1;
-    p[q0 + 1] = d2;
+    p[q0] = (double)d1;
+    p[q0 + 1] = (double)d2;
   }
 }
 

@@ -174,10 +174,11 @@ int ax_L(snmf_ctx* h, const void* X, void* Y, const void* P1, const void* P2, do
 }
 
 int choose_chunks(int64_t n, int b, int r) {
+  // about one CTA per SM, at least 512 rows per chunk (fewer partials to reduce)
   const int ntile = (r + 63) / 64;
   const int64_t per = (int64_t)b * ntile * ntile;
-  int64_t c = (304 + per - 1) / per;
-  c = std::max<int64_t>(1, std::min<int64_t>(c, n / 256));
+  int64_t c = (152 + per - 1) / per;
+  c = std::max<int64_t>(1, std::min<int64_t>(c, n / 512));
   return (int)c;
 }
 
@@ -190,7 +191,7 @@ void gram1(snmf_ctx* h, const void* X, const void* Y, int pair, int npairs, cons
               ctl ? h->run : nullptr, G64, GT, tpair, lam, h->counters, h->s);
 }
 
-RowArgs row_base(snmf_ctx* h) {
+RowArgs row_base(snmf_ctx* h, const Params* P = nullptr) {
   RowArgs a{};
   a.n = h->n; a.r = h->r; a.b = h->b; a.ld = h->N;
   a.G = h->GT;
@@ -198,6 +199,9 @@ RowArgs row_base(snmf_ctx* h) {
   a.run = h->run;
   a.gamma = h->graph ? h->gamma : 0.0;
   a.part = h->prow;
+  a.counters = h->counters + 16384;
+  a.G64fix = h->G64fix;
+  if (P) a.P = *P;
   return a;
 }
 
@@ -212,24 +216,28 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
   const bool gr = h->graph && !is_w;
   // B = A Xfix + lambda Xfix (Eq. (2.1)/(2.2))
   ax_A(h, Xf, h->buf[B_B], h->lam, Xf, nullptr, nullptr, h->pax, h->run);
-  // G = Xfix^T Xfix (+ lambda I in the factor-type copy); rho_0 = ||Xfix^T Xfix||_2
-  gram1(h, Xf, Xf, 0, 1, h->ctl, h->G64fix, h->GT, 0, h->lam);
-  launch_rho(td, h->G64fix, d, h->opt.power_iters, 1.0, h->ctl, 0, h->s);
+  // G = Xfix^T Xfix (+ lambda I in the factor-type copy); rho_0 = ||Xfix^T Xfix||_2, computed
+  // by the Gram's last CTA when the restart is one tile (FP32 path), else by k_rho
+  const bool rho_fused = td == 1 && h->r <= 64;
+  launch_gram(td, Xf, Xf, d, 0, 1, h->gpart, h->nchunks, h->ctl, h->run, h->G64fix, h->GT, 0, h->lam,
+              h->counters, h->s, rho_fused ? h->ctl : nullptr, h->opt.power_iters, 1.0);
+  if (!rho_fused) launch_rho(td, h->G64fix, d, h->opt.power_iters, 1.0, h->ctl, 0, h->s);
   if (gr) ax_L(h, X, h->buf[B_LX], nullptr, nullptr, h->pax2, h->run);
   {
-    RowArgs a = row_base(h);
+    // gradient at the block start; its last CTA per restart runs the block-start control
+    RowArgs a = row_base(h, &P);
     a.X = X; a.B = h->buf[B_B]; a.LX = gr ? h->buf[B_LX] : nullptr;
     a.gout = h->buf[B_G];
+    a.ctl_mode = is_w ? CTL_START_W : CTL_START_H;
     launch_rowgemm(td, OP_LOAD, EPI_GRAD, a, h->s);
   }
-  launch_ctl_pen_start(h->ctl, h->prow, h->nrow, h->b, P, is_w ? 1 : 0, 0, h->s);
   launch_any_active(h->ctl, h->b, h->run, nullptr, h->s);
   const int K = h->opt.inner_iters;
   const bool fused_q = h->r <= 64 && !gr;
   for (int k = 0; k < K; ++k) {
     // Z = Proj[X - g / rho_0], D = Proj[Z - alpha g(Z)] - Z   (Alg. 1 lines 2-3)
     {
-      RowArgs a = row_base(h);
+      RowArgs a = row_base(h, &P);
       a.B = h->buf[B_B];
       a.Dout = h->buf[B_D]; a.gZout = h->buf[B_GZ];
       a.Wcur = X; a.gWcur = h->buf[B_G];
@@ -241,24 +249,27 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
       } else {
         a.X = X; a.g_in = h->buf[B_G]; a.Xout = h->buf[B_Z];
         a.want_q = fused_q ? 1 : 0;
+        a.ctl_mode = fused_q ? CTL_LS : CTL_NONE;  // line search in the last CTA of each restart
         launch_rowgemm(td, OP_ZSTEP, EPI_DIR, a, h->s);
       }
     }
-    // curvature of the line-search quadratic: <D G, D> from the D kernel (one column
-    // tile) or from the Gram D^T D; graph term <D, L D>
-    if (!fused_q) gram1(h, h->buf[B_D], h->buf[B_D], 0, 1, h->ctl, h->G64p, nullptr, -1, 0.0);
-    int nl = 0;
-    if (gr) nl = ax_L(h, h->buf[B_D], h->buf[B_LD], h->buf[B_D], nullptr, h->pax3, h->run);
-    launch_ctl_pen_ls(h->ctl, h->prow, h->nrow, h->pax3, gr ? nl : 0, h->b, h->r, h->G64fix,
-                      fused_q ? nullptr : h->G64p, P, gr ? 1 : 0, h->s);
+    if (!fused_q) {
+      // curvature of the line-search quadratic from the Gram D^T D; graph term <D, L D>
+      gram1(h, h->buf[B_D], h->buf[B_D], 0, 1, h->ctl, h->G64p, nullptr, -1, 0.0);
+      int nl = 0;
+      if (gr) nl = ax_L(h, h->buf[B_D], h->buf[B_LD], h->buf[B_D], nullptr, h->pax3, h->run);
+      launch_ctl_pen_ls(h->ctl, h->prow, h->nrow, h->pax3, gr ? nl : 0, h->b, h->r, h->G64fix, h->G64p, P,
+                        gr ? 1 : 0, h->s);
+    }
     // X' = Proj[Z + phi beta D], gradient, BB inner products   (Alg. 1 line 4)
     {
-      RowArgs a = row_base(h);
+      RowArgs a = row_base(h, &P);
       a.B = h->buf[B_B];
       a.gout = h->buf[B_G];
       a.Xold = X; a.gold = h->buf[B_G];
       a.Zold = h->buf[B_Z]; a.gZold = h->buf[B_GZ];
       a.Xout = X;
+      a.ctl_mode = is_w ? CTL_UPD_W : (k == K - 1 ? CTL_UPD_H_LAST : CTL_UPD_H);
       if (gr) {
         launch_xupd(td, d, h->buf[B_Z], h->buf[B_D], h->buf[B_XN], nullptr, nullptr, nullptr,
                     h->ctl, h->pclip, h->s);
@@ -270,7 +281,6 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
         launch_rowgemm(td, OP_UPD, EPI_GRAD, a, h->s);
       }
     }
-    launch_ctl_pen_upd(h->ctl, h->prow, h->nrow, h->b, P, is_w ? 0 : 1, k == K - 1 ? 1 : 0, h->s);
   }
 }
 
@@ -282,11 +292,11 @@ void pen_init(snmf_ctx* h, const Params& P) {
   ax_A(h, h->buf[B_W], h->buf[B_B], h->lam, h->buf[B_W], nullptr, nullptr, h->pax, h->run);
   gram1(h, h->buf[B_W], h->buf[B_W], 0, 1, h->ctl, h->G64fix, h->GT, 0, h->lam);
   if (h->graph) ax_L(h, h->buf[B_HT], h->buf[B_LX], nullptr, nullptr, h->pax2, h->run);
-  RowArgs a = row_base(h);
+  RowArgs a = row_base(h, &P);
   a.X = h->buf[B_HT]; a.B = h->buf[B_B]; a.LX = h->graph ? h->buf[B_LX] : nullptr;
   a.gout = h->buf[B_G];
+  a.ctl_mode = CTL_START_INIT;  // records the H gradient of the start
   launch_rowgemm(td, OP_LOAD, EPI_GRAD, a, h->s);
-  launch_ctl_pen_start(h->ctl, h->prow, h->nrow, h->b, P, 0, 1, h->s);
 }
 
 void pen_iteration(snmf_ctx* h, const Params& P) {
@@ -401,7 +411,7 @@ snmf_status alloc_buffers(snmf_ctx* h) {
   h->ws_elems = (h->kind == AX_DENSE) ? 8 * fe : 0;
   if (h->ws_elems) CK(cudaMalloc(&h->ws, h->ws_elems * h->esz));
   const Dims d = dims(h);
-  h->nrow = rowgemm_slots(d);
+  h->nrow = rowgemm_slots(d, h->tdtype);
   h->nax = (int)((h->n + kRowTile - 1) / kRowTile);
   const size_t prec_n = (size_t)std::max(h->nrow, h->nax) * h->b * kNQ;
   double** parts[] = {&h->prow, &h->pax, &h->pax2, &h->pax3, &h->pax4, &h->pclip};
@@ -426,8 +436,8 @@ snmf_status alloc_buffers(snmf_ctx* h) {
     CK(cudaMalloc(&h->xl, xb));
   }
   if (h->opt.timeout_cycles > 0) h->budget = h->opt.timeout_cycles;
-  CK(cudaMalloc(&h->counters, 16384 * sizeof(unsigned)));
-  CK(cudaMemsetAsync(h->counters, 0, 16384 * sizeof(unsigned), h->s));
+  CK(cudaMalloc(&h->counters, (16384 + 4096) * sizeof(unsigned)));  // Gram tiles, then restarts
+  CK(cudaMemsetAsync(h->counters, 0, (16384 + 4096) * sizeof(unsigned), h->s));
   CK(cudaMalloc(&h->dsc, 4096 * sizeof(double)));
   CK(cudaMallocHost(&h->h_flag, sizeof(int)));
   return SNMF_OK;

@@ -87,6 +87,21 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Fixed-order block sum in the working type T (result in every thread); `sh` holds >= 32 T.
+template <typename T>
+__device__ __forceinline__ T block_sum_t(T v, T* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  T t = T(0);
+  for (int w = 0; w < nw; ++w) t += sh[w];
+  __syncthreads();
+  return t;
+}
+
 // Fixed-order block sum over blockDim.x threads (multiple of 32, <= 1024).
 // Result valid in every thread.  `sh` holds >= 32 doubles.
 __device__ __forceinline__ double block_sum(double v, double* sh) {

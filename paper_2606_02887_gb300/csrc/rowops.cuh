@@ -5,6 +5,9 @@
 
 namespace snmf {
 
+// control step fused into the last CTA of a restart (RowArgs::ctl_mode)
+enum { CTL_NONE = 0, CTL_START_W, CTL_START_H, CTL_START_INIT, CTL_LS, CTL_UPD_W, CTL_UPD_H, CTL_UPD_H_LAST };
+
 // operand of the row GEMM X G: loaded, Z = Proj[X - g/rho], or X' = Proj[Z + phi beta D]
 enum { OP_LOAD = 0, OP_ZSTEP = 1, OP_UPD = 2 };
 // epilogue: gradient (+ S/Y and increment dots) or the D direction (+ dots)
@@ -35,12 +38,17 @@ struct RowArgs {
   const void* Wcur; const void* gWcur;   // EPI_DIR: increment f(Z) - f(Wcur)
   int want_q;          // EPI_DIR, one column tile: also <D G, D> -> q4
   double* part;
+  int ctl_mode;        // CTL_*: control step run by the last CTA of each restart
+  unsigned* counters;  // per-restart arrival counters (zero between launches)
+  const double* G64fix;
+  Params P;
 };
 
 void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pair, int npairs,
                  double* gpart, int nchunks, const Ctl* ctl, const int* run, double* G64, void* GT,
-                 int tpair, double lam_shift, unsigned* counters, cudaStream_t s);
-int rowgemm_slots(const Dims& d);
+                 int tpair, double lam_shift, unsigned* counters, cudaStream_t s,
+                 Ctl* rho_ctl = nullptr, int rho_iters = 0, double rho_scale = 1.0);
+int rowgemm_slots(const Dims& d, int tdtype);
 void launch_rowgemm(int tdtype, int op, int epi, const RowArgs& a, cudaStream_t s);
 void launch_zstep(int tdtype, const Dims& d, const void* X, const void* g, void* Z, const Ctl* ctl,
                   cudaStream_t s);
