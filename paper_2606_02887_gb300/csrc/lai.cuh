@@ -13,6 +13,7 @@ struct LaiOp {
   double* lam = nullptr;    // k eigenvalues (device FP64)
   double* xpart = nullptr;  // split-K partials of U^T X [chunk][k][N] (FP64)
   void* M = nullptr;        // E U^T X, k x N (factor type)
+  unsigned* counters = nullptr;  // arrival counters of the U^T X reduction
   int k = 0;
   int nchunks = 0;
   int maxN = 0;
@@ -32,5 +33,9 @@ int lai_build(LaiOp& op, const AxArgs& A, int tdtype, int64_t n, int k, int ell,
               uint64_t seed, int maxN, cudaStream_t s, std::string& msg);
 
 void lai_free(LaiOp& op);
+
+// Out (n x m, ldo) = In (n x K, ldi) M (K x m row-major), K <= 128 (factor type).
+void launch_rowmul(int tdtype, const void* In, int64_t ldi, int K, const void* M, int m, int64_t n, void* Out,
+                   int64_t ldo, const int* run, cudaStream_t s);
 
 }  // namespace snmf

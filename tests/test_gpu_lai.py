@@ -1,0 +1,91 @@
+"""LAI-SNMPBB (Sec. 2.3) on the GPU against the oracle's own sketch (same Philox
+Gaussian stream): the sketched operator U E U^T, and the solve on it."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2606_02887_gb300.snmf as S
+from workloads import chung_lu_csr, planted_dense, uniform_init
+
+from gpu_helpers import gpu_solve, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _apply_lai(h, X, dev, torch, dtype):
+    Xt = torch.tensor(X, dtype=dtype, device=dev)
+    Yt = torch.empty_like(Xt)
+    xax = S.snmf_apply(h, Xt, Yt, X.shape[1])
+    return Yt.cpu().numpy().astype(np.float64), xax
+
+
+def test_lai_operator_matches_oracle_fp64():
+    import torch
+    dev = torch.device("cuda:0")
+    n, rank = 600, 10
+    A, _ = planted_dense(n, rank, 0.01, seed=4101)  # rank-10 signal + small noise: clear gap after 10
+    k, p, q, seed = 10, 6, 2, 4102
+    Uo, lo = O.lai_sketch(lambda X: A @ X, n, k, p, q, seed)
+    op = O.LaiOperator(Uo, lo)
+    X = uniform_init(n, k, 1.0, 4103)
+    h = S.snmf_create(S.dense_matrix(torch.tensor(A, device=dev)), k, S.snmf_default_options(precision=S.SNMF_F64))
+    try:
+        S.snmf_lai_sketch(h, k, p, q, seed)
+        Y, xax = _apply_lai(h, X, dev, torch, torch.float64)
+    finally:
+        S.snmf_destroy(h)
+    ref = O.apply_A(op, X)
+    assert rel(Y, ref) <= 1e-9, rel(Y, ref)
+    assert abs(xax - float(np.sum(X * ref))) <= 1e-9 * abs(xax)
+    # and the sketch reproduces A on its dominant subspace
+    assert rel(Y, A @ X) <= 0.02
+
+
+def test_lai_penalty_solve_matches_oracle_fp64():
+    n, r = 500, 8
+    A, _ = planted_dense(n, r, 0.01, seed=4201)
+    k, p, q, seed = 8, 6, 2, 4202
+    Uo, lo = O.lai_sketch(lambda X: A @ X, n, k, p, q, seed)
+    W0 = uniform_init(n, r, math.sqrt(A.mean() / r), 4203)
+    opts = O.Options(max_iter=6, tol=0.0, memory=10, objective="closed", lambda_sym=0.01 * np.linalg.norm(A))
+    Wo, Ho, _ = O.snmpbb_penalty(O.LaiOperator(Uo, lo), W0, W0, opts)
+    W, H, _, _, _ = gpu_solve(A, W0, r, W0, lai=(k, p, q, seed), max_iter=6, tol=0.0)
+    assert rel(W, Wo) <= 1e-8 and rel(H, Ho) <= 1e-8, (rel(W, Wo), rel(H, Ho))
+
+
+def test_lai_sketch_csr_fp32_power_law():
+    import scipy.sparse as sp
+    import torch
+    dev = torch.device("cuda:0")
+    G = chung_lu_csr(n=20000, mean_degree=16, seed=4301)
+    Asp = sp.csr_matrix((G.values, G.colidx, G.rowptr), shape=(G.n, G.n))
+    k, p, q, seed = 16, 8, 2, 4302
+    Uo, lo = O.lai_sketch(lambda X: Asp @ X, G.n, k, p, q, seed)
+    X = uniform_init(G.n, 4, 1.0, 4303)
+    rp = torch.tensor(G.rowptr, device=dev)
+    ci = torch.tensor(G.colidx, device=dev)
+    va = torch.tensor(G.values, dtype=torch.float32, device=dev)
+    h = S.snmf_create(S.csr_matrix(G.n, rp, ci, va), 4, S.snmf_default_options(precision=S.SNMF_F32))
+    try:
+        S.snmf_lai_sketch(h, k, p, q, seed)
+        Y, _ = _apply_lai(h, X, dev, torch, torch.float32)
+    finally:
+        S.snmf_destroy(h)
+    ref = O.apply_A(O.LaiOperator(Uo, lo), X)
+    assert rel(Y, ref) <= 2e-3, rel(Y, ref)
+
+
+def test_lai_rejects_bad_sizes():
+    import torch
+    dev = torch.device("cuda:0")
+    A = torch.eye(50, dtype=torch.float64, device=dev)
+    h = S.snmf_create(S.dense_matrix(A), 2, S.snmf_default_options(precision=S.SNMF_F64))
+    try:
+        with pytest.raises(S.SnmfError):
+            S.snmf_lai_sketch(h, 40, 20, 1, 1)   # k + p > n
+        with pytest.raises(S.SnmfError):
+            S.snmf_lai_sketch(h, 0, 4, 1, 1)
+    finally:
+        S.snmf_destroy(h)
