@@ -57,7 +57,7 @@ typedef enum {
 } snmf_status;
 
 /* matrix kinds */
-enum { SNMF_DENSE = 0, SNMF_CSR = 1 };
+enum { SNMF_DENSE = 0, SNMF_CSR = 1, SNMF_DENSE_BATCH = 2 };
 /* element types (matrix dtype) and working precisions */
 enum { SNMF_F64 = 0, SNMF_F32 = 1, SNMF_BF16 = 2, SNMF_FP8 = 3 };
 /* where a matrix passed to snmf_create lives */
@@ -74,6 +74,15 @@ enum { SNMF_BB1 = 0, SNMF_BB2 = 1 };
  *          values[nnz]; both triangles stored.
  * dtype is SNMF_F64 or SNMF_F32.  location says whether the three arrays are
  * device or host memory.
+ *   dense batch (SNMF_DENSE_BATCH): nprob independent problems solved together
+ *          (uneven batch; no counterpart in the paper, which solves one problem at a
+ *          time).  batch_desc (host) holds 3 int64 per problem p: n_p, r_p and the element
+ *          offset of A_p in values; A_p is n_p x n_p row-major with leading dimension n_p.
+ *          Requires 1 <= r_p <= min(n_p, 64), penalty form, batch == 1, precision F64
+ *          (with F64 values), F32 or BF16.  The factors W, Ht of snmf_solve are the
+ *          problems' n_p x r_p row-major blocks packed back to back in problem order
+ *          (offset of problem p = sum over q < p of n_q r_q elements); the r argument of
+ *          snmf_create is ignored; n, ld, nnz, rowptr, colidx are unused.
  */
 typedef struct {
   int32_t kind;
@@ -86,6 +95,9 @@ typedef struct {
   const void* values;
   const int32_t* rowptr;
   const int32_t* colidx;
+  int32_t nprob;               /* SNMF_DENSE_BATCH: number of problems                 */
+  int32_t reserved2;
+  const int64_t* batch_desc;   /* SNMF_DENSE_BATCH: host, 3 * nprob entries (see above) */
 } snmf_matrix;
 
 /*
@@ -104,7 +116,17 @@ typedef struct {
   int32_t inner_iters;     /* Algorithm 1 steps per block (penalty), default 5                */
   int32_t max_iter;        /* outer iterations (penalty) or steps (direct), default 500        */
   int32_t power_iters;     /* power iterations for rho = ||G||_2 (Eq. (2.11)), default 50      */
-  int32_t step_controller; /* 0: plain BB; 1: learned step multiplier (needs mlp_weights)     */
+  int32_t step_controller; /* 0: plain BB step (Alg. 1 line 3).  1: learned step multiplier m =
+                              2^(2 tanh o) on the BB step from the MLP o = W2 relu(W1 phi + b1) + b2
+                              (weights in mlp_weights, used in BF16); the proposal is kept only if
+                              the nonmonotone Armijo test accepts it at beta = 1, otherwise the
+                              step falls back to the plain BB direction with ordinary backtracking.
+                              2: record mode: the plain BB trajectory, and at every step the
+                              features phi and the best of 9 multipliers 2^(-2..2 by 1/2) are
+                              recorded (snmf_controller_data).  1 and 2 need the penalty form
+                              and r <= 64.  Features phi: ln(BB1 rho), ln(BB2 rho), ratio of
+                              successive projected-gradient norms, ratio of successive objective
+                              decreases, fraction of zero entries.                               */
   double lambda_sym;       /* penalty weight lambda (Eq. (3)); < 0 -> 0.01 ||A||_F (Sec. 4.1 (1)) */
   double theta;            /* Armijo parameter, default 1e-3 (Sec. 2.4)                        */
   double phi;              /* relaxation factor, default 1.7 (Sec. 2.4)                        */
@@ -117,7 +139,7 @@ typedef struct {
   double init_scale;       /* W == NULL init: U[0,1] * init_scale * sqrt(mean(A)/r), default 2
                               (Sec. 4.1 (4))                                                   */
   uint64_t seed;           /* Philox seed of the default initialisation                         */
-  const float* mlp_weights;/* host, SNMF_MLP_NPARAMS floats (layout in snmf_mlp_*), or NULL   */
+  const float* mlp_weights;/* host, SNMF_MLP_NPARAMS floats: W1[64][5], b1[64], W2[64], b2 (copied) */
   int64_t timeout_cycles;  /* bound on device-side waits (clock64 cycles), 0 = default        */
 } snmf_options;
 
@@ -135,6 +157,8 @@ typedef struct {
   double seconds;          /* device time of the solve (CUDA events)                          */
   int64_t kernel_launches; /* library kernels executed by the solve                          */
   int32_t graph_replays;   /* replays of the captured iteration                              */
+  int32_t ctl_proposals;   /* learned controller: proposals made                             */
+  int32_t ctl_accepted;    /* learned controller: proposals accepted at beta = 1             */
   int32_t reserved;
 } snmf_stats;
 
@@ -258,6 +282,27 @@ SNMF_API snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_produc
 SNMF_API snmf_status snmf_apply_dense_noalloc(const void* A, int dtype, int64_t n, int64_t lda,
                                               const void* X, void* Y, int cols, double* xax,
                                               void* stream);
+
+/*
+ * Record-mode data (step_controller == 2; not in the paper: training data of the learned
+ * step controller).  Copies up to `capacity` recorded samples (features feat[i][5] and target
+ * log2 multipliers targ[i], host arrays) gathered since the last call, then clears the record.
+ * *count receives the number copied.  SNMF_ERR_STATE when the handle is not in record mode.
+ */
+SNMF_API snmf_status snmf_controller_data(snmf_handle h, float* feat, float* targ, int capacity,
+                                          int32_t* count);
+
+/*
+ * Train the step controller's MLP on the GPU (not in the paper).  Loss: mean over samples
+ * of (2 tanh(o) - t)^2, o = W2 relu(W1 phi + b1) + b2; full-batch Adam (beta1 0.9, beta2
+ * 0.999) for `steps` steps with learning rate lr, FP32.
+ *   feats[count][5], targets[count]: host arrays; weights: host, SNMF_MLP_NPARAMS floats, in
+ *   (initial) / out (trained); loss_out: final loss (may be NULL); grad0: gradient of the loss
+ *   at the initial weights (host, SNMF_MLP_NPARAMS floats, may be NULL).
+ * Uses the current CUDA device and the legacy default stream; allocates device memory.
+ */
+SNMF_API snmf_status snmf_mlp_train(const float* feats, const float* targets, int count, float* weights,
+                                    int steps, double lr, double* loss_out, float* grad0);
 
 /* Release every resource of the handle.  NULL is accepted. */
 SNMF_API snmf_status snmf_destroy(snmf_handle h);

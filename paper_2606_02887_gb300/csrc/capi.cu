@@ -16,6 +16,7 @@
 
 #include "../../include/snmf.h"
 #include "ax_tc.cuh"
+#include "batch.cuh"
 #include "common.cuh"
 #include "lai.cuh"
 #include "rowops.cuh"
@@ -78,6 +79,11 @@ struct snmf_ctx {
   void* xh = nullptr;            // BF16 hi / lo parts of the product operand (transposed)
   void* xl = nullptr;
   long long budget = 2000000000LL;
+  __nv_bfloat16* mlp_w = nullptr;  // learned controller weights (BF16)
+  float* rec_feat = nullptr;       // record mode dataset
+  float* rec_targ = nullptr;
+  int* rec_count = nullptr;
+  int rec_cap = 0;
   int tc_fail = 0;               // status of a failed tensor-core launch (encoder / launch error)
   double* dsc = nullptr;   // device scratch doubles
   int* h_flag = nullptr;   // pinned
@@ -90,6 +96,7 @@ struct snmf_ctx {
   cudaEvent_t evdone = nullptr;
   bool have_result = false;
   int ax_count = 0;
+  BatchCtx* bt = nullptr;          // SNMF_DENSE_BATCH handle: the uneven-batch engine
   std::string err;
 };
 
@@ -127,6 +134,12 @@ Params make_params(const snmf_ctx* h) {
   P.rho_factor = h->opt.direct_rho_factor;
   P.normA2 = h->lai ? h->lai_op.normA2 : h->normA2;
   P.gamma = h->graph ? h->gamma : 0.0;
+  P.mlp_w = h->mlp_w;
+  P.rec_feat = h->opt.step_controller == 2 ? h->rec_feat : nullptr;
+  P.rec_targ = h->rec_targ;
+  P.rec_count = h->rec_count;
+  P.rec_cap = h->rec_cap;
+  P.nr = h->n * (int64_t)h->r;
   return P;
 }
 
@@ -250,7 +263,11 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
         a.X = X; a.g_in = h->buf[B_G]; a.Xout = h->buf[B_Z];
         a.want_q = fused_q ? 1 : 0;
         a.ctl_mode = fused_q ? CTL_LS : CTL_NONE;  // line search in the last CTA of each restart
-        launch_rowgemm(td, OP_ZSTEP, EPI_DIR, a, h->s);
+        // learned controller: proposal + plain BB direction; record mode: 9 candidates
+        const int nc = h->opt.step_controller == 1 ? 2 : (h->opt.step_controller == 2 ? kNCand : 1);
+        a.dstore = nc == kNCand ? 4 : 0;
+        a.D2out = h->buf[B_AD];
+        launch_rowgemm(td, OP_ZSTEP, EPI_DIR, a, h->s, nc);
       }
     }
     if (!fused_q) {
@@ -277,7 +294,7 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
         a.X = h->buf[B_XN]; a.LX = h->buf[B_LX];
         launch_rowgemm(td, OP_LOAD, EPI_GRAD, a, h->s);
       } else {
-        a.Zin = h->buf[B_Z]; a.Din = h->buf[B_D];
+        a.Zin = h->buf[B_Z]; a.Din = h->buf[B_D]; a.Din2 = h->buf[B_AD];
         launch_rowgemm(td, OP_UPD, EPI_GRAD, a, h->s);
       }
     }
@@ -456,7 +473,8 @@ snmf_status validate_options(const snmf_options& o) {
       !(o.alpha_min > 0.0 && o.alpha_min < o.alpha_max) || !(o.beta_shrink > 0.0 && o.beta_shrink < 1.0) ||
       !(o.tol >= 0.0) || !(o.direct_rho_factor > 0.0))
     return SNMF_ERR_ARG;
-  if (o.step_controller && !o.mlp_weights) return SNMF_ERR_ARG;
+  if (!valid_enum(o.step_controller, 0, 2)) return SNMF_ERR_ARG;
+  if (o.step_controller == 1 && !o.mlp_weights) return SNMF_ERR_ARG;
   return SNMF_OK;
 }
 
@@ -507,6 +525,27 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   snmf_options o;
   if (opt) o = *opt; else snmf_default_options(&o);
   if (validate_options(o) != SNMF_OK) return fail(nullptr, SNMF_ERR_ARG, "invalid options");
+  if (Am->kind == SNMF_DENSE_BATCH) {
+    std::string ve;
+    if (batch_validate(Am, o, &ve) != SNMF_OK) return fail(nullptr, SNMF_ERR_ARG, ve);
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
+      return fail(nullptr, SNMF_ERR_CUDA, "no CUDA device");
+    init_kernel_attributes();
+    h = new snmf_ctx();
+    h->opt = o;
+    h->prec = o.precision;
+    h->user = (cudaStream_t)stream;
+    std::string e;
+    const snmf_status st = batch_create(&h->bt, Am, o, (cudaStream_t)stream, &e);
+    if (st != SNMF_OK) {
+      delete h;
+      return fail(nullptr, st, e);
+    }
+    h->b = batch_nprob(h->bt);
+    *out = h;
+    return SNMF_OK;
+  }
   if (Am->kind != SNMF_DENSE && Am->kind != SNMF_CSR) return fail(nullptr, SNMF_ERR_ARG, "unknown matrix kind");
   if (Am->dtype != SNMF_F64 && Am->dtype != SNMF_F32) return fail(nullptr, SNMF_ERR_ARG, "A dtype must be F64 or F32");
   if (Am->location != SNMF_ON_DEVICE && Am->location != SNMF_ON_HOST) return fail(nullptr, SNMF_ERR_ARG, "bad location");
@@ -521,8 +560,8 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   }
   if (o.precision == SNMF_FP8)
     return fail(nullptr, SNMF_ERR_ARG, "FP8 precision not available in this build");
-  if (o.formulation == SNMF_PENALTY && o.step_controller)
-    return fail(nullptr, SNMF_ERR_ARG, "learned step controller not available in this build");
+  if (o.step_controller && (o.formulation != SNMF_PENALTY || r > 64))
+    return fail(nullptr, SNMF_ERR_ARG, "the step controller needs the penalty form and r <= 64");
 
   h = new snmf_ctx();
   h->opt = o;
@@ -654,6 +693,20 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   }
   snmf_status st = alloc_buffers(h);
   if (st != SNMF_OK) return bail(st);
+  if (o.step_controller == 1) {
+    std::vector<__nv_bfloat16> wb(kMlpParams);
+    for (int i = 0; i < kMlpParams; ++i) wb[i] = __float2bfloat16_rn(o.mlp_weights[i]);  // BF16 weights
+    CKC(cudaMalloc(&h->mlp_w, kMlpParams * sizeof(__nv_bfloat16)));
+    CKC(cudaMemcpyAsync(h->mlp_w, wb.data(), kMlpParams * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, h->s));
+    CKC(cudaStreamSynchronize(h->s));
+  }
+  if (o.step_controller == 2) {
+    h->rec_cap = 1 << 18;
+    CKC(cudaMalloc(&h->rec_feat, (size_t)h->rec_cap * kMlpIn * sizeof(float)));
+    CKC(cudaMalloc(&h->rec_targ, (size_t)h->rec_cap * sizeof(float)));
+    CKC(cudaMalloc(&h->rec_count, sizeof(int)));
+    CKC(cudaMemsetAsync(h->rec_count, 0, sizeof(int), h->s));
+  }
   // ||A||_F^2 and mean(A) of the stored operator
   if (h->kind == AX_DENSE && h->A.a_dtype == 2) {
     const int nb = launch_sums_bf16(h->A.A, n * h->A.lda, h->dsc + 16, h->s);  // ||A~||^2 of the stored values
@@ -676,6 +729,7 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
 
 snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma) {
   if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
   if (!(gamma >= 0.0)) return fail(h, SNMF_ERR_ARG, "gamma must be >= 0");
   if (gamma == 0.0) { h->graph = false; h->gamma = 0.0; h->exec_form = -1; return SNMF_OK; }
   if (!L) return fail(h, SNMF_ERR_ARG, "implicit Laplacian (L == NULL) not available in this build");
@@ -716,6 +770,7 @@ snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma
 
 snmf_status snmf_lai_sketch(snmf_handle h, int k, int oversample, int power_iters, uint64_t seed) {
   if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
   if (k < 1 || oversample < 0 || power_iters < 0) return fail(h, SNMF_ERR_ARG, "bad sketch sizes");
   const int ell = k + oversample;
   if (ell > 128 || ell > h->n) return fail(h, SNMF_ERR_ARG, "k + oversample must be <= min(n, 128)");
@@ -824,7 +879,7 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->have_result = true;
   // statistics
-  int best = 0, conv = 1, lsf = 0, clip = 0, iters = 0, nan = 0;
+  int best = 0, conv = 1, lsf = 0, clip = 0, iters = 0, nan = 0, tried = 0, acc = 0;
   for (int j = 0; j < h->b; ++j) {
     const Ctl& c = h->h_ctl[j];
     if (c.fin_f < h->h_ctl[best].fin_f) best = j;
@@ -834,6 +889,8 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
     clip += c.clipped;
     iters = std::max(iters, c.iters);
     nan |= c.nan_seen;
+    tried += c.mlp_tried;
+    acc += c.mlp_accept;
   }
   if (out) {
     out->iters = iters;
@@ -844,6 +901,8 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
     out->ax_products = h->axn[0] + h->axn[1] * launched + h->axn[2] + (pen ? 0 : clip);
     out->kernel_launches = launches;
     out->graph_replays = launched;
+    out->ctl_proposals = tried;
+    out->ctl_accepted = acc;
     out->f = h->h_ctl[best].fin_f;
     out->residual = h->h_ctl[best].fin_res;
     out->pg_rel = h->h_ctl[best].fin_pg;
@@ -855,18 +914,21 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
 
 snmf_status snmf_solve(snmf_handle h, void* W, void* Ht, snmf_stats* out) {
   if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return batch_solve(h->bt, false, W, Ht, out, &h->err);
   return solve_impl(h, false, W, Ht, out);
 }
 
 snmf_status snmf_solve_host(snmf_handle h, void* W, void* Ht, snmf_stats* out) {
   if (!h) return SNMF_ERR_STATE;
   if (!W) return fail(h, SNMF_ERR_ARG, "W must not be NULL");
+  if (h->bt) return batch_solve(h->bt, true, W, Ht, out, &h->err);
   return solve_impl(h, true, W, Ht, out);
 }
 
 snmf_status snmf_restart_stats(snmf_handle h, double* f, double* residual, double* pg_rel,
                                int32_t* iters) {
   if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return batch_problem_stats(h->bt, f, residual, pg_rel, iters, &h->err);
   if (!h->have_result) return fail(h, SNMF_ERR_STATE, "no solve has run");
   for (int j = 0; j < h->b; ++j) {
     const Ctl& c = h->h_ctl[j];
@@ -880,6 +942,7 @@ snmf_status snmf_restart_stats(snmf_handle h, double* f, double* residual, doubl
 
 snmf_status snmf_get_factors(snmf_handle h, void* W, void* Ht) {
   if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return batch_get_factors(h->bt, W, Ht, &h->err);
   if (!h->have_result) return fail(h, SNMF_ERR_STATE, "no solve has run");
   const size_t fbytes = (size_t)h->n * h->N * h->esz;
   if (W) CK(cudaMemcpyAsync(W, h->buf[B_W], fbytes, cudaMemcpyDeviceToDevice, h->s));
@@ -891,6 +954,7 @@ snmf_status snmf_get_factors(snmf_handle h, void* W, void* Ht) {
 
 snmf_status snmf_apply(snmf_handle h, const void* X, void* Y, int cols, double* xax) {
   if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
   if (!X || !Y || cols < 1 || cols > h->N) return fail(h, SNMF_ERR_ARG, "bad apply arguments");
   if (sync_user(h) != SNMF_OK) return SNMF_ERR_CUDA;
   const size_t fe = (size_t)h->n * h->N;
@@ -929,6 +993,7 @@ snmf_status snmf_apply(snmf_handle h, const void* X, void* Y, int cols, double* 
 
 snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_product, double* ms_kernel) {
   if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
   if (iters < 1) return fail(h, SNMF_ERR_ARG, "iters must be >= 1");
   if (sync_user(h) != SNMF_OK) return SNMF_ERR_CUDA;
   const Dims d = dims(h);
@@ -957,8 +1022,33 @@ snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_product, double
   return SNMF_OK;
 }
 
+snmf_status snmf_controller_data(snmf_handle h, float* feat, float* targ, int capacity, int32_t* count) {
+  if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
+  if (h->opt.step_controller != 2) return fail(h, SNMF_ERR_STATE, "the handle is not in record mode");
+  if (capacity < 0 || (capacity > 0 && (!feat || !targ))) return fail(h, SNMF_ERR_ARG, "bad buffers");
+  int cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, h->rec_count, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  cnt = std::min(cnt, h->rec_cap);
+  const int m = std::min(cnt, capacity);
+  if (m > 0) {
+    CK(cudaMemcpyAsync(feat, h->rec_feat, (size_t)m * kMlpIn * sizeof(float), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(targ, h->rec_targ, (size_t)m * sizeof(float), cudaMemcpyDeviceToHost, h->s));
+  }
+  CK(cudaMemsetAsync(h->rec_count, 0, sizeof(int), h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (count) *count = m;
+  return SNMF_OK;
+}
+
 snmf_status snmf_destroy(snmf_handle h) {
   if (!h) return SNMF_OK;
+  if (h->bt) {
+    batch_destroy(h->bt);
+    delete h;
+    return SNMF_OK;
+  }
   if (h->s) cudaStreamSynchronize(h->s);
   for (auto& e : h->exec)
     if (e) cudaGraphExecDestroy(e);
@@ -976,6 +1066,10 @@ snmf_status snmf_destroy(snmf_handle h) {
   cudaFree(h->dev_err);
   cudaFree(h->xh);
   cudaFree(h->xl);
+  cudaFree(h->mlp_w);
+  cudaFree(h->rec_feat);
+  cudaFree(h->rec_targ);
+  cudaFree(h->rec_count);
   if (h->h_flag) cudaFreeHost(h->h_flag);
   cudaFree(h->A_owned);
   cudaFree(h->rowptr_owned);

@@ -8,12 +8,16 @@
 //   Gram partials: gpart[chunk][pair][restart][r*r] (double), reduced in fixed order.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace snmf {
 
-constexpr int kNQ = 8;          // dot slots per partial record
+constexpr int kNQ = 32;         // dot slots per partial record
+constexpr int kNCand = 9;       // candidate steps evaluated in the controller's record mode
+constexpr int kMlpIn = 5, kMlpHidden = 64;
+constexpr int kMlpParams = kMlpIn * kMlpHidden + 2 * kMlpHidden + 1;
 constexpr int kMaxHist = 64;    // max nonmonotone memory M
 constexpr int kRowTile = 64;    // rows per CTA of the row kernels
 constexpr int kMaxR = 256;      // max rank per restart
@@ -50,8 +54,15 @@ struct Ctl {
   double gnorm_prev; // ||g_{k-1}|| for the step controller features
   double f_prev, f_prev2;
   double mlp_mult;   // multiplier proposed by the learned controller (1 = plain BB)
-  int mlp_tried;     // 1 when the current step used the proposal
+  int mlp_tried;     // proposals made by the learned controller
   int commit;       // direct: the update of this step is to be committed
+  double cand_alpha[kNCand];  // candidate BB-type steps of the current step (controller modes)
+  int dsel;          // direction used by the update: 0 = D, 1 = D2 (plain BB fallback)
+  int mlp_accept;    // proposals accepted at beta = 1
+  int feat_ok;       // features of the current state are defined (k >= 1 in a block)
+  float feat[kMlpIn];
+  double pg_prev;    // projected-gradient norm of the previous iterate (features)
+  double last_dec;   // previous objective decrease (features)
 };
 
 struct Dims {
@@ -75,6 +86,12 @@ struct Params {
   double rho_factor; // direct form rho scaling
   double normA2;     // ||A||_F^2 of the stored operator
   double gamma;      // graph weight (0 = none)
+  const __nv_bfloat16* mlp_w;  // learned controller weights: W1[64][5], b1[64], W2[64], b2
+  float* rec_feat;   // record mode: features [cap][5]
+  float* rec_targ;   // record mode: target log2 multipliers [cap]
+  int* rec_count;
+  int rec_cap;
+  int64_t nr;        // entries per restart (n * r), for the active-set feature
 };
 
 // ---------------------------------------------------------------------------

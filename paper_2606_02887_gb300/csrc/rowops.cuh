@@ -17,7 +17,9 @@ enum { EPI_GRAD = 0, EPI_DIR = 1 };
 // matrix in the factor type.  Partial layout (part[slot][j][q], slot = CTA):
 //   EPI_GRAD: q0 ||P grad||^2, q1 1/2 <g - B, X>, q2 <S,S>, q3 <S,Y>, q4 <Y,Y>,
 //             q5 1/2 <X - Zold, g + gZold>
-//   EPI_DIR : q0 <g, D>, q1 <D, D>, q2 1/2 <Z - Wcur, g + gWcur>, q3 <D, LX>, q4 <D G, D>
+//   EPI_DIR : q0 <g, D>, q1 <D, D>, q2 1/2 <Z - Wcur, g + gWcur>, q3 <D, LX>, q4 <D G, D>;
+//             candidates m >= 1 (controller modes): q(5+3(m-1)) <g, D_m>, +1 <D_m, D_m>, +2 <D_m G, D_m>
+//   EPI_GRAD: q6 number of zero entries of X
 struct RowArgs {
   int64_t n; int r; int b; int64_t ld;
   const void* G;
@@ -31,7 +33,10 @@ struct RowArgs {
   const int* run;
   void* Xout;          // operand value written (Z for OP_ZSTEP, X' for OP_UPD/OP_LOAD copy)
   void* gout;          // EPI_GRAD: gradient
-  void* Dout;          // EPI_DIR: direction
+  void* Dout;          // EPI_DIR: direction (candidate `dstore`)
+  void* D2out;         // EPI_DIR with two candidates: the plain BB direction
+  const void* Din2;    // OP_UPD: second direction, used where ctl[j].dsel == 1
+  int dstore;          // EPI_DIR: candidate written to Dout
   void* gZout;         // EPI_DIR: gradient at Z
   const void* Xold; const void* gold;    // EPI_GRAD: S = X - Xold, Y = g - gold
   const void* Zold; const void* gZold;   // EPI_GRAD: increment f(X) - f(Zold)
@@ -49,7 +54,7 @@ void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pa
                  int tpair, double lam_shift, unsigned* counters, cudaStream_t s,
                  Ctl* rho_ctl = nullptr, int rho_iters = 0, double rho_scale = 1.0);
 int rowgemm_slots(const Dims& d, int tdtype);
-void launch_rowgemm(int tdtype, int op, int epi, const RowArgs& a, cudaStream_t s);
+void launch_rowgemm(int tdtype, int op, int epi, const RowArgs& a, cudaStream_t s, int ncand = 1);
 void launch_zstep(int tdtype, const Dims& d, const void* X, const void* g, void* Z, const Ctl* ctl,
                   cudaStream_t s);
 int launch_xupd(int tdtype, const Dims& d, const void* Z, const void* D, void* Xn, const void* AZ,

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libsnmf_gb300.so")
 
 SNMF_OK, SNMF_NOT_CONVERGED = 0, 1
 SNMF_ERR_ARG, SNMF_ERR_CUDA, SNMF_ERR_OOM, SNMF_ERR_NUMERIC, SNMF_ERR_TIMEOUT, SNMF_ERR_STATE = -1, -2, -3, -4, -5, -6
-SNMF_DENSE, SNMF_CSR = 0, 1
+SNMF_DENSE, SNMF_CSR, SNMF_DENSE_BATCH = 0, 1, 2
 SNMF_F64, SNMF_F32, SNMF_BF16, SNMF_FP8 = 0, 1, 2, 3
 SNMF_ON_DEVICE, SNMF_ON_HOST = 0, 1
 SNMF_PENALTY, SNMF_DIRECT = 0, 1
@@ -27,7 +27,8 @@ SNMF_MLP_NPARAMS = SNMF_MLP_IN * SNMF_MLP_HIDDEN + 2 * SNMF_MLP_HIDDEN + 1
 EXPORTED = (
     "snmf_default_options", "snmf_create", "snmf_set_graph_reg", "snmf_lai_sketch",
     "snmf_solve", "snmf_solve_host", "snmf_restart_stats", "snmf_get_factors",
-    "snmf_apply", "snmf_profile_ax", "snmf_apply_dense_noalloc", "snmf_destroy", "snmf_last_error",
+    "snmf_apply", "snmf_profile_ax", "snmf_apply_dense_noalloc", "snmf_controller_data",
+    "snmf_mlp_train", "snmf_destroy", "snmf_last_error",
 )
 NOALLOC_SCRATCH_BYTES = 64 << 20
 NOALLOC_MAX_SLICE_PAIR_BYTES = NOALLOC_SCRATCH_BYTES - (1 << 20)
@@ -37,7 +38,8 @@ NOALLOC_MAX_ROWS = 1048320
 class snmf_matrix(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("location", C.c_int32),
                 ("reserved", C.c_int32), ("n", C.c_int64), ("nnz", C.c_int64), ("ld", C.c_int64),
-                ("values", C.c_void_p), ("rowptr", C.c_void_p), ("colidx", C.c_void_p)]
+                ("values", C.c_void_p), ("rowptr", C.c_void_p), ("colidx", C.c_void_p),
+                ("nprob", C.c_int32), ("reserved2", C.c_int32), ("batch_desc", C.c_void_p)]
 
 
 class snmf_options(C.Structure):
@@ -56,7 +58,7 @@ class snmf_stats(C.Structure):
                 ("clipped_steps", C.c_int32), ("best_restart", C.c_int32), ("ax_products", C.c_int32),
                 ("f", C.c_double), ("residual", C.c_double), ("pg_rel", C.c_double),
                 ("seconds", C.c_double), ("kernel_launches", C.c_int64), ("graph_replays", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("ctl_proposals", C.c_int32), ("ctl_accepted", C.c_int32), ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,6 +89,9 @@ def load_library(path: str = LIB_PATH):
     lib.snmf_profile_ax.argtypes = [H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.snmf_apply_dense_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
                                              C.c_int, C.POINTER(C.c_double), C.c_void_p]
+    lib.snmf_controller_data.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int32)]
+    lib.snmf_mlp_train.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double,
+                                   C.POINTER(C.c_double), C.c_void_p]
     lib.snmf_destroy.argtypes = [H]
     lib.snmf_last_error.argtypes = [H]
     lib.snmf_last_error.restype = C.c_char_p
@@ -151,6 +156,21 @@ def csr_matrix(n, rowptr, colidx, values) -> tuple:
                     n=n, nnz=int(values.shape[0]), ld=0, values=_ptr(values), rowptr=_ptr(rowptr),
                     colidx=_ptr(colidx))
     return m, (rowptr, colidx, values)
+
+
+def dense_batch_matrix(values, ns, rs, offsets=None) -> tuple:
+    """snmf_matrix of an uneven batch: ``values`` a flat array (device tensor or host) holding
+    the n_p x n_p row-major problems back to back (or at ``offsets``), ranks ``rs``."""
+    ns = [int(x) for x in ns]
+    rs = [int(x) for x in rs]
+    if offsets is None:
+        offsets = np.concatenate([[0], np.cumsum([n * n for n in ns])[:-1]]).astype(np.int64)
+    desc = np.ascontiguousarray(np.stack([np.asarray(ns, np.int64), np.asarray(rs, np.int64),
+                                          np.asarray(offsets, np.int64)], 1).reshape(-1))
+    dt = SNMF_F64 if str(values.dtype).endswith("float64") else SNMF_F32
+    m = snmf_matrix(kind=SNMF_DENSE_BATCH, dtype=dt, location=SNMF_ON_DEVICE if _is_cuda(values) else SNMF_ON_HOST,
+                    n=0, nnz=0, ld=0, values=_ptr(values), nprob=len(ns), batch_desc=desc.ctypes.data)
+    return m, (values, desc)
 
 
 def snmf_create(matrix, r: int, options: snmf_options | None = None, stream=None, mlp_weights=None):
@@ -245,6 +265,30 @@ def snmf_apply_dense_noalloc(A, X, Y, stream=None):
                             "float32/float64" % (NOALLOC_MAX_ROWS, NOALLOC_MAX_SLICE_PAIR_BYTES))
     _check(lib, None, st)
     return xax.value
+
+
+def snmf_controller_data(h, capacity: int = 1 << 18):
+    """Recorded (features, target log2 multiplier) samples of a record-mode handle."""
+    lib = load_library()
+    feat = np.zeros((capacity, SNMF_MLP_IN), dtype=np.float32)
+    targ = np.zeros(capacity, dtype=np.float32)
+    cnt = C.c_int32()
+    _check(lib, h, lib.snmf_controller_data(h, feat.ctypes.data, targ.ctypes.data, capacity, C.byref(cnt)))
+    return feat[:cnt.value].copy(), targ[:cnt.value].copy()
+
+
+def snmf_mlp_train(feats, targets, weights, steps: int = 1000, lr: float = 1e-2):
+    """Train the controller MLP on the GPU.  Returns (weights, final loss, gradient at the
+    initial weights)."""
+    lib = load_library()
+    f = np.ascontiguousarray(feats, dtype=np.float32)
+    t = np.ascontiguousarray(targets, dtype=np.float32)
+    w = np.array(weights, dtype=np.float32, copy=True)
+    g0 = np.zeros(SNMF_MLP_NPARAMS, dtype=np.float32)
+    loss = C.c_double()
+    _check(lib, None, lib.snmf_mlp_train(f.ctypes.data, t.ctypes.data, len(t), w.ctypes.data, int(steps),
+                                         float(lr), C.byref(loss), g0.ctypes.data))
+    return w, loss.value, g0
 
 
 def snmf_destroy(h):

@@ -1,0 +1,105 @@
+"""Learned step controller on the GPU: training gradients against the FP64 oracle, exact
+fallback behaviour, record mode, and what the trained network gains over plain BB."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle.mlp as OM
+import paper_2606_02887_gb300.snmf as S
+from workloads import planted_dense, uniform_init
+
+from gpu_helpers import rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(A, W0, r, b, controller, weights=None, max_iter=300, tol=1e-4, prec=None):
+    import torch
+    dev = torch.device("cuda:0")
+    At = torch.tensor(A, dtype=torch.float32, device=dev)
+    Wt = torch.tensor(W0, dtype=torch.float32, device=dev)
+    Ht = Wt.clone()
+    o = S.snmf_default_options(precision=prec or S.SNMF_F32, batch=b, step_controller=controller,
+                               max_iter=max_iter, tol=tol, nonmonotone_M=10)
+    h = S.snmf_create(S.dense_matrix(At), r, o, mlp_weights=weights)
+    try:
+        st, stats = S.snmf_solve(h, Wt, Ht)
+        per = S.snmf_restart_stats(h, b)
+    finally:
+        S.snmf_destroy(h)
+    return Wt.cpu().numpy(), Ht.cpu().numpy(), st, stats, per
+
+
+def test_mlp_training_gradient_matches_oracle():
+    g = np.random.default_rng(7)
+    feats = g.normal(0, 1, (5000, 5)).astype(np.float32)
+    targs = g.choice(np.arange(-2, 2.01, 0.5), 5000).astype(np.float32)
+    w = (g.normal(0, 0.5, OM.N_PARAMS)).astype(np.float32)
+    _, _, g0 = S.snmf_mlp_train(feats, targs, w, steps=0, lr=1e-3)
+    ref = OM.gradient(w.astype(np.float64), feats.astype(np.float64), targs.astype(np.float64))
+    assert rel(g0.astype(np.float64), ref) <= 1e-4, rel(g0, ref)
+    # a few Adam steps lower the loss
+    w2, loss, _ = S.snmf_mlp_train(feats, targs, w, steps=200, lr=1e-2)
+    assert loss < OM.loss(w.astype(np.float64), feats, targs)
+    assert abs(loss - OM.loss(w2.astype(np.float64), feats, targs)) <= 1e-4 * max(1.0, loss)
+
+
+def test_zero_weights_reproduce_plain_bb_exactly():
+    """o = 0 gives multiplier 1: the proposal equals the plain BB direction, so the accepted
+    steps and the iterates are the plain method's, bit for bit."""
+    A, _ = planted_dense(300, 6, 0.01, seed=801)
+    W0 = uniform_init(300, 6, math.sqrt(A.mean() / 6), 802)
+    Wp, Hp, _, sp, _ = _solve(A, W0, 6, 1, 0, max_iter=20, tol=0.0)
+    Wl, Hl, _, sl, _ = _solve(A, W0, 6, 1, 1, weights=np.zeros(S.SNMF_MLP_NPARAMS, np.float32), max_iter=20,
+                              tol=0.0)
+    assert np.array_equal(Wp, Wl) and np.array_equal(Hp, Hl)
+    assert sl["ctl_proposals"] > 0
+
+
+def test_record_mode_produces_labelled_states():
+    A, _ = planted_dense(400, 5, seed=811, rel_noise=0.01)
+    W0 = np.concatenate([uniform_init(400, 5, math.sqrt(A.mean() / 5), 812 + j) for j in range(2)], 1)
+    import torch
+    dev = torch.device("cuda:0")
+    o = S.snmf_default_options(precision=S.SNMF_F32, batch=2, step_controller=2, max_iter=30, tol=0.0)
+    h = S.snmf_create(S.dense_matrix(torch.tensor(A, dtype=torch.float32, device=dev)), 5, o)
+    try:
+        Wt = torch.tensor(W0, dtype=torch.float32, device=dev)
+        S.snmf_solve(h, Wt, Wt.clone())
+        f, t = S.snmf_controller_data(h)
+    finally:
+        S.snmf_destroy(h)
+    # 2 restarts x 30 outer iterations x 2 blocks x 4 steps with k >= 1
+    assert len(t) == 2 * 30 * 2 * 4
+    assert np.all(np.isfinite(f)) and set(np.unique(t)) <= set(np.arange(-2, 2.01, 0.5))
+    assert np.all((f[:, 4] >= 0) & (f[:, 4] <= 1))
+
+
+def test_learned_controller_gain_over_plain_bb():
+    """Held-out planted problems (seeds disjoint from the training set), batched restarts:
+    the trained controller must reach the same tolerance and residual, and the test reports
+    its gain in outer iterations and device time over the plain BB step."""
+    from paper_2606_02887_gb300.train_controller import WEIGHTS_PATH, load_weights
+    if not os.path.exists(WEIGHTS_PATH):
+        pytest.skip("no trained controller weights")
+    w = load_weights()
+    g = np.random.default_rng(123456)
+    it_plain = it_learn = t_plain = t_learn = 0.0
+    for p in range(6):
+        n = int(g.integers(256, 2049))
+        r = int(g.integers(4, 33))
+        A, _ = planted_dense(n, r, seed=700000 + p, rel_noise=0.01)
+        W0 = np.concatenate([uniform_init(n, r, math.sqrt(A.mean() / r), 710000 + 16 * p + j) for j in range(4)], 1)
+        Wp, Hp, stp, sp, pp = _solve(A, W0, r, 4, 0)
+        Wl, Hl, stl, sl, pl = _solve(A, W0, r, 4, 1, weights=w)
+        assert stl == S.SNMF_OK, sl
+        assert np.all(pl["pg_rel"] <= 1e-4)
+        assert np.max(np.abs(pl["residual"] - pp["residual"])) <= 1e-3
+        it_plain += pp["iters"].sum()
+        it_learn += pl["iters"].sum()
+        t_plain += sp["seconds"]
+        t_learn += sl["seconds"]
+    print(f"learned controller: outer iterations {it_learn:.0f} vs plain {it_plain:.0f} "
+          f"({100 * (1 - it_learn / it_plain):+.1f}%), device time {t_learn:.3f} s vs {t_plain:.3f} s")

@@ -339,3 +339,24 @@ def test_lambda_default_rule():
     A, _ = _small_problem(10, 2, seed=131)
     assert O.resolve_lambda(A, O.Options()) == pytest.approx(0.01 * np.linalg.norm(A), rel=1e-15)
     assert O.resolve_lambda(A, O.Options(lambda_sym=2.5)) == 2.5
+
+
+# ---------------------------------------------------------------------------
+# Step-controller MLP oracle: backprop vs central finite differences
+# ---------------------------------------------------------------------------
+
+def test_mlp_oracle_gradient_finite_differences():
+    import oracle.mlp as M
+    g = np.random.default_rng(141)
+    w = g.normal(0, 0.5, M.N_PARAMS)
+    phi = g.normal(0, 1, (40, M.N_IN))
+    t = g.uniform(-2, 2, 40)
+    grad = M.gradient(w, phi, t)
+    h = 1e-6
+    for idx in g.choice(M.N_PARAMS, 40, replace=False):
+        e = np.zeros(M.N_PARAMS)
+        e[idx] = h
+        fd = (M.loss(w + e, phi, t) - M.loss(w - e, phi, t)) / (2 * h)
+        assert abs(fd - grad[idx]) <= 1e-6 * max(1.0, abs(fd)), (idx, fd, grad[idx])
+    # zero weights: o = 0, multiplier 1
+    assert np.allclose(M.multiplier(np.zeros(M.N_PARAMS), phi), 1.0)
