@@ -50,6 +50,13 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--workload", default="dense8192", choices=["dense8192", "uneven"],
+                   help="dense8192: one n=8192 problem (restarts); uneven: 256 planted problems of "
+                        "uneven size in one batched solve")
+    p.add_argument("--nprob", type=int, default=256)
+    p.add_argument("--controller", default="auto", choices=["auto", "off", "on"],
+                   help="learned step controller (auto: on when trained weights are present)")
+    p.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparison runs")
     return p.parse_args()
 
 
@@ -172,10 +179,207 @@ def run_reference(args):
     return 0
 
 
+def controller_weights(args):
+    """Trained controller weights shipped with the package (None when absent or disabled)."""
+    if args.controller == "off":
+        return None
+    from paper_2606_02887_gb300.train_controller import WEIGHTS_PATH, load_weights
+    if os.path.exists(WEIGHTS_PATH):
+        return load_weights()
+    if args.controller == "on":
+        raise SystemExit("controller weights not found: " + WEIGHTS_PATH)
+    return None
+
+
+def uneven_problems(count):
+    """256 planted problems, n ~ U{64..2048}, r ~ U{4..32}, 1% relative noise (problem seeds
+    5001..); starts U[0, sqrt(mean(A_p)/r_p)] with seed 6000 + p."""
+    from workloads import uneven_batch, uniform_init
+    out = []
+    for p, (A, _, r) in enumerate(uneven_batch(count, seed=5000)):
+        out.append((A, uniform_init(A.shape[0], r, math.sqrt(A.mean() / r), seed=6000 + p), r))
+    return out
+
+
+def uneven_name(args):
+    return (f"uneven batch: {args.nprob} dense planted problems, n~U{{64..2048}}, r~U{{4..32}}, "
+            f"1% relative noise, penalty form, tol {args.tol:g} relative proj-grad per problem")
+
+
+def run_uneven(args):
+    """Many uneven problems in one batched solve (grouped launches + CUDA graph), against the
+    plain FP32 path solving the same problems one at a time."""
+    import numpy as np
+    import torch
+
+    import paper_2606_02887_gb300.snmf as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    S.load_library()
+    probs = uneven_problems(args.nprob)
+    ns = [A.shape[0] for A, _, _ in probs]
+    rs = [r for _, _, r in probs]
+    vals = torch.tensor(np.concatenate([A.ravel() for A, _, _ in probs]), dtype=torch.float32, device=dev)
+    W0 = torch.tensor(np.concatenate([W.ravel() for _, W, _ in probs]), dtype=torch.float32, device=dev)
+    W = torch.empty_like(W0)
+    H = torch.empty_like(W0)
+    prec = {"f64": S.SNMF_F64, "f32": S.SNMF_F32, "bf16": S.SNMF_BF16}[args.precision]
+    weights = controller_weights(args)
+    ctl = 1 if weights is not None else 0
+    stream = torch.cuda.current_stream(dev)
+
+    def handle(pr, c):
+        o = S.snmf_default_options(precision=pr, max_iter=args.max_iter, tol=args.tol, nonmonotone_M=10,
+                                   step_controller=c)
+        return S.snmf_create(S.dense_batch_matrix(vals, ns, rs), 0, o, stream=stream,
+                             mlp_weights=weights if c else None)
+
+    def solve(h):
+        W.copy_(W0)
+        H.copy_(W0)
+        return S.snmf_solve(h, W, H)
+
+    h = handle(prec, ctl)
+    for _ in range(args.warmup):
+        solve(h)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches, last = 0, None
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        st, stats = solve(h)
+        ev[k][1].record(stream)
+        launches += stats["kernel_launches"]
+        last = (st, stats)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(times)
+    st, stats = last
+    per = S.snmf_restart_stats(h, len(probs))
+    ms_prod, _ = S.snmf_profile_ax(h, 10)
+    esz_a = {"f64": 8, "f32": 4, "bf16": 2}[args.precision]
+    esz = 8 if args.precision == "f64" else 4
+    alg_bytes = sum(n * n * esz_a + 2 * n * r * esz for n, r in zip(ns, rs))
+    flops = sum(2.0 * n * n * r for n, r in zip(ns, rs))
+    S.snmf_destroy(h)
+    peaks, peak_kind = measured_peaks()
+    gbs = alg_bytes / (ms_prod * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_bgemm (grouped A_p X_p, CUDA cores, %s A)" % args.precision,
+            "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+            "traffic": None, "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
+            "flops_per_launch": flops, "tflops": flops / (ms_prod * 1e-3) / 1e12, "ms_per_launch": ms_prod}
+
+    compare = None
+    if not args.no_compare:
+        compare = {}
+        for name, pr, c in (("batched_bf16_plain", S.SNMF_BF16, 0), ("batched_f32_plain", S.SNMF_F32, 0)):
+            if pr == prec and c == ctl:
+                continue
+            hc = handle(pr, c)
+            solve(hc)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stc, sc = solve(hc)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pc = S.snmf_restart_stats(hc, len(probs))
+            S.snmf_destroy(hc)
+            compare[name] = {"s": e0.elapsed_time(e1) / 1e3, "status": stc, "outer_iters_total": int(pc["iters"].sum()),
+                             "max_pg_rel": float(pc["pg_rel"].max())}
+        # plain FP32: one problem per snmf_solve, FP32 A, no controller (device time of the solves)
+        tot, it_plain, res_plain = 0.0, [], []
+        o = S.snmf_default_options(precision=S.SNMF_F32, max_iter=args.max_iter, tol=args.tol, nonmonotone_M=10)
+        for A, W0p, r in probs:
+            At = torch.tensor(A, dtype=torch.float32, device=dev)
+            hp_ = S.snmf_create(S.dense_matrix(At), r, o, stream=stream)
+            Wp = torch.tensor(W0p, dtype=torch.float32, device=dev)
+            stp, sp = S.snmf_solve(hp_, Wp, Wp.clone())
+            S.snmf_destroy(hp_)
+            tot += sp["seconds"]
+            it_plain.append(sp["iters"])
+            res_plain.append(sp["residual"])
+        res_plain = np.array(res_plain)
+        dres = np.abs(per["residual"] - res_plain)
+        compare["plain_f32_one_problem_per_solve"] = {
+            "s": tot, "outer_iters_total": int(np.sum(it_plain)),
+            "speedup_of_value": tot / (ms / 1e3),
+            "residual_max_abs_diff": float(dres.max()), "problems_within_1e-3": int(np.sum(dres <= 1e-3))}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        import oracle as O
+        sample = [0, 1, 2]
+        t0 = time.perf_counter()
+        for p in sample:
+            A, W0p, r = probs[p]
+            O.snmpbb_penalty(A, W0p, W0p, O.Options(max_iter=2, tol=0.0, memory=10, objective="closed"))
+        spi = (time.perf_counter() - t0) / (2.0 * sum(float(ns[p]) ** 2 * rs[p] for p in sample))
+        est = spi * sum(float(n) * n * r * int(it) for n, r, it in zip(ns, rs, per["iters"]))
+        cpu = {"value": est, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": "2 outer iterations of the FP64 oracle on problems 0-2, scaled by n_p^2 r_p x the "
+                         "iterations each problem took on the GPU"}
+
+    e2e = None
+    if not args.no_e2e:
+        vals_h = vals.cpu()
+        W_h = torch.empty_like(W0, device="cpu").pin_memory()
+        H_h = torch.empty_like(W0, device="cpu").pin_memory()
+        W0_h = W0.cpu()
+        o = S.snmf_default_options(precision=prec, max_iter=args.max_iter, tol=args.tol, nonmonotone_M=10,
+                                   step_controller=ctl)
+        et = []
+        for k in range(2):
+            W_h.copy_(W0_h)
+            H_h.copy_(W0_h)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            he = S.snmf_create(S.dense_batch_matrix(vals_h, ns, rs), 0, o, stream=stream,
+                               mlp_weights=weights if ctl else None)
+            S.snmf_solve_host(he, W_h, H_h)
+            S.snmf_destroy(he)
+            torch.cuda.synchronize()
+            if k:
+                et.append(time.perf_counter() - t0)
+        fb = W0.numel() * 4
+        e2e = {"value": statistics.mean(et), "unit": "s", "h2d_bytes_per_step": vals.numel() * 4 + 2 * fb,
+               "d2h_bytes_per_step": 2 * fb,
+               "path": "snmf_create(host A, batch) + snmf_solve_host + snmf_destroy, wall clock"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": uneven_name(args), "nprob": args.nprob, "precision": args.precision,
+                           "controller": "learned" if ctl else "plain BB", "tol": args.tol,
+                           "max_iter": args.max_iter,
+                           "l2": "inputs larger than L2 (sum of A_p %.0f MB)" % (alg_bytes / 2**20),
+                           "parallelism": "single GPU"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+                "solve": {"status": st, "max_iters": stats["iters"], "outer_iters_total": int(per["iters"].sum()),
+                          "max_pg_rel": float(per["pg_rel"].max()), "max_residual": float(per["residual"].max()),
+                          "ctl_proposals": stats["ctl_proposals"], "ctl_accepted": stats["ctl_accepted"],
+                          "ms_per_step_all": times},
+                "compare": compare}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "uneven":
+        return run_uneven(args)
 
     import numpy as np
     import torch

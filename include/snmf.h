@@ -215,6 +215,10 @@ SNMF_API snmf_status snmf_lai_sketch(snmf_handle h, int k, int oversample, int p
  *   out optional statistics.
  * Returns SNMF_OK when every restart met the tolerance, SNMF_NOT_CONVERGED when
  * max_iter was reached first, or an error.
+ * Dense batch handles: W and Ht are the packed per-problem blocks (total sum n_p r_p
+ * elements); W == NULL initialises problem p with Philox seed opt.seed + p.  In *out,
+ * iters is the maximum over problems, f the sum, residual and pg_rel the maxima, and
+ * converged says whether every problem met the tolerance.
  */
 SNMF_API snmf_status snmf_solve(snmf_handle h, void* W, void* Ht, snmf_stats* out);
 
@@ -227,7 +231,8 @@ SNMF_API snmf_status snmf_solve_host(snmf_handle h, void* W, void* Ht, snmf_stat
 
 /*
  * Per-restart results of the last solve (host arrays of length batch; any may be NULL):
- * objective, relative residual, relative projected gradient, iterations.
+ * objective, relative residual, relative projected gradient, iterations.  Dense batch
+ * handles: one entry per problem (length nprob), in problem order.
  */
 SNMF_API snmf_status snmf_restart_stats(snmf_handle h, double* f, double* residual,
                                double* pg_rel, int32_t* iters);
@@ -248,7 +253,8 @@ SNMF_API snmf_status snmf_apply(snmf_handle h, const void* X, void* Y, int cols,
  * A*X products of the handle's factor shape (n x r*batch) on the handle's stream
  * with CUDA events.  *ms_product: mean time of the whole product (kernel and
  * epilogue); *ms_kernel: mean time of the product kernel alone (0 for LAI).
- * Either pointer may be NULL.  Overwrites internal work buffers only.
+ * Either pointer may be NULL.  Overwrites internal work buffers only.  On a dense batch
+ * handle both report one grouped product A_p X_p over every problem (X = the current W).
  */
 SNMF_API snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_product,
                                      double* ms_kernel);

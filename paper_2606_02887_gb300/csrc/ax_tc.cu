@@ -298,6 +298,174 @@ __global__ void k_sums_bf16(const __nv_bfloat16* __restrict__ A, int64_t m, doub
   }
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Grouped product of the uneven batch: CTA = one 128-row tile of one problem.  The ring
+// stage holds the A tile (128 x 64) and up to 64 rows of each X part (bn / 16 boxes of 16
+// rows); 3 stages, so two CTAs share an SM.  Same roles and bounded waits as k_gemm_tc.
+// ---------------------------------------------------------------------------------------
+constexpr int kBStages = 3;
+constexpr uint32_t kBStageA = BM * BK * 2;       // 16 KB
+constexpr uint32_t kBStageB = 64 * BK * 2;       // room for 64 rows of one X part
+constexpr uint32_t kBStageBytes = kBStageA + 2 * kBStageB;
+
+__device__ __forceinline__ bool item_live(const TcItem& it, const unsigned char* ctl, size_t stride,
+                                          size_t off, const int* run) {
+  if (run && *run == 0) return false;
+  if (ctl && *reinterpret_cast<const int*>(ctl + (size_t)it.prob * stride + off) == 0) return false;
+  return true;
+}
+
+__global__ void __launch_bounds__(128, 2)
+k_bgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapXh,
+           const __grid_constant__ CUtensorMap mapXl, const TcItem* __restrict__ items,
+           const float* __restrict__ X, float* __restrict__ Y, int add_lam, const float* __restrict__ P1,
+           double* __restrict__ part, int nq, const unsigned char* __restrict__ ctl, size_t ctl_stride,
+           size_t active_off, const int* __restrict__ run, int* __restrict__ err, long long budget) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)kBStages * kBStageBytes);
+  uint64_t* empty = full + kBStages;
+  uint64_t* accum = empty + kBStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  __shared__ int s_fail, s_issued, s_consumed;
+  __shared__ float s_red[4];
+  const TcItem it = items[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!item_live(it, ctl, ctl_stride, active_off, run)) {
+    if (part && threadIdx.x == 0) part[(int64_t)it.slot * nq] = 0.0;
+    return;
+  }
+  const int bn = it.bn;
+  const uint32_t stage_tx = kBStageA + 2u * (uint32_t)bn * BK * 2;
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    for (int s = 0; s < kBStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(64));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    int i = 0;
+    for (; i < it.kt; ++i) {
+      const int s = i % kBStages;
+      const uint32_t ph = (uint32_t)(i / kBStages) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u, budget)) { atomicExch(err, 11); s_fail = 1; break; }
+      unsigned char* st = base + (size_t)s * kBStageBytes;
+      mbar_expect_tx(&full[s], stage_tx);
+      const int kx = i * BK;
+      tma_load_2d(st, &mapA, &full[s], kx, (int)it.arow);
+      for (int h = 0; h < bn / 16; ++h) {
+        tma_load_2d(st + kBStageA + h * 16 * BK * 2, &mapXh, &full[s], kx, it.xrow + 16 * h);
+        tma_load_2d(st + kBStageA + kBStageB + h * 16 * BK * 2, &mapXl, &full[s], kx, it.xrow + 16 * h);
+      }
+    }
+    s_issued = i;
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16(BM, bn);
+    int i = 0;
+    for (; i < it.kt; ++i) {
+      const int s = i % kBStages;
+      const uint32_t ph = (uint32_t)(i / kBStages) & 1u;
+      if (!mbar_wait(&full[s], ph, budget)) { atomicExch(err, 12); s_fail = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(base + (size_t)s * kBStageBytes);
+      const uint32_t sh = sa + kBStageA, sl = sa + kBStageA + kBStageB;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t da = sdesc(sa + kk * 32);
+        mma_bf16(tmem, da, sdesc(sh + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        mma_bf16(tmem, da, sdesc(sl + kk * 32), idesc, 1u);
+      }
+      mma_commit(&empty[s]);
+    }
+    s_consumed = i;
+    mma_commit(accum);
+  }
+  __syncwarp();
+  __syncthreads();
+  bool done = mbar_wait(accum, 0, budget);
+  done = __all_sync(0xffffffffu, done);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!done && lane == 0) atomicExch(err, 13);
+  float d1 = 0.f;
+  if (done && !s_fail) {
+    const int row = it.m0 + warp * 32 + lane;
+    const bool rv = row < it.n;
+    for (int c0 = 0; c0 < bn; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (rv) {
+        const int64_t rowoff = it.xoff + (int64_t)row * it.r;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int c = c0 + i;
+          if (c < it.r) {
+            float y = v[i];
+            if (P1) d1 += P1[rowoff + c] * y;
+            if (add_lam) y += it.lam * X[rowoff + c];
+            Y[rowoff + c] = y;
+          }
+        }
+      }
+    }
+  }
+  if (part) {
+    for (int o = 16; o > 0; o >>= 1) d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+    if (lane == 0) s_red[warp] = d1;
+  }
+  if (s_fail && threadIdx.x == 0) {
+    for (int i = s_consumed; i < s_issued; ++i)
+      if (!mbar_wait(&full[i % kBStages], (uint32_t)(i / kBStages) & 1u, budget)) break;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (part && threadIdx.x == 0) part[(int64_t)it.slot * nq] = (double)(s_red[0] + s_red[1] + s_red[2] + s_red[3]);
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+  }
+}
+
+// X_p rows m0 .. m0 + 128 (FP32, ld r_p) -> columns of the transposed BF16 hi / lo parts
+__global__ void __launch_bounds__(256)
+k_bsplit_x(const TcItem* __restrict__ items, const float* __restrict__ X, __nv_bfloat16* __restrict__ Xh,
+           __nv_bfloat16* __restrict__ Xl, int64_t lda, const unsigned char* __restrict__ ctl, size_t ctl_stride,
+           size_t active_off, const int* __restrict__ run) {
+  __shared__ float t[BM][65];
+  const TcItem it = items[blockIdx.x];
+  if (!item_live(it, ctl, ctl_stride, active_off, run)) return;
+  const int rows = min(BM, it.n - it.m0);
+  for (int e = threadIdx.x; e < rows * it.r; e += blockDim.x) {
+    const int i = e / it.r, c = e % it.r;
+    t[i][c] = X[it.xoff + (int64_t)(it.m0 + i) * it.r + c];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rows * it.r; e += blockDim.x) {
+    const int c = e / rows, i = e % rows;
+    const float v = t[i][c];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    const int64_t o = (int64_t)(it.xrow + c) * lda + it.m0 + i;
+    Xh[o] = hi;
+    Xl[o] = lo;
+  }
+}
+
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -428,6 +596,36 @@ int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx,
   const cudaError_t le = cudaPeekAtLastError();
   if (le != cudaSuccess) { g_last_cu = 10000 + (int)le; return -2; }
   return pl.splits;
+}
+
+void launch_bsplit_x(const TcItem* items, int nitems, const float* X, void* xh, void* xl, int64_t lda,
+                     const void* ctl, size_t ctl_stride, size_t active_off, const int* run, cudaStream_t s) {
+  k_bsplit_x<<<nitems, 256, 0, s>>>(items, X, (__nv_bfloat16*)xh, (__nv_bfloat16*)xl, lda,
+                                    (const unsigned char*)ctl, ctl_stride, active_off, run);
+}
+
+int launch_bgemm_tc(const void* A16, int64_t lda, int64_t rows_total, const void* xh, const void* xl,
+                    int64_t xt_rows, const TcItem* items, int nitems, const float* X, float* Y, int add_lam,
+                    const float* P1, double* part, int nq, const void* ctl, size_t ctl_stride,
+                    size_t active_off, const int* run, int* err, long long budget, cudaStream_t s) {
+  CUtensorMap ma, mh, ml;
+  if (!make_map(&ma, A16, lda, rows_total, lda, BM) || !make_map(&mh, xh, lda, xt_rows, lda, 16) ||
+      !make_map(&ml, xl, lda, xt_rows, lda, 16))
+    return -1;
+  const size_t smem = (size_t)kBStages * kBStageBytes + 1024 + 8 * (2 * kBStages + 2) + 64;
+  static bool attr_done = false;
+  if (!attr_done) {
+    if (cudaFuncSetAttribute(k_bgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      g_last_cu = 10000 + (int)cudaGetLastError();
+      return -3;
+    }
+    attr_done = true;
+  }
+  k_bgemm_tc<<<nitems, 128, smem, s>>>(ma, mh, ml, items, X, Y, add_lam, P1, part, nq,
+                                       (const unsigned char*)ctl, ctl_stride, active_off, run, err, budget);
+  const cudaError_t le = cudaPeekAtLastError();
+  if (le != cudaSuccess) { g_last_cu = 10000 + (int)le; return -2; }
+  return 0;
 }
 
 }  // namespace snmf

@@ -29,4 +29,33 @@ void launch_to_bf16(int src_dtype, const void* A, int64_t n, int64_t lda, void* 
 int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
                  float* Y, float* ws, size_t ws_elems, int* err, long long budget, cudaStream_t s);
 
+// ---- grouped product of the uneven batch (one CTA per 128-row tile of a problem) ----
+// A_all: BF16, rows of all problems packed, pitch lda; X parts: BF16 hi / lo, row xrow_p + c
+// holds column c of X_p (K-major, pitch lda, zero beyond n_p and beyond r_p).
+struct TcItem {
+  int64_t arow;   // first A_all row of the tile (problem's first row + m0)
+  int64_t xoff;   // element offset of the problem's n_p x r_p factor blocks (ld r_p)
+  int m0;         // first row of the tile within the problem
+  int n;          // n_p
+  int r;          // r_p
+  int bn;         // MMA N: r_p rounded up to a multiple of 16 (<= 64)
+  int xrow;       // first row of the problem's columns in the X parts
+  int kt;         // K tiles of 64 columns
+  int prob;       // problem index (active flag)
+  int slot;       // partial slot of the item
+  float lam;      // lambda_p (epilogue Y += lambda_p X)
+  int pad;
+};
+
+// Xh/Xl rows xrow_p .. xrow_p + r_p, columns m0 .. m0 + 128 of every live item's problem.
+void launch_bsplit_x(const TcItem* items, int nitems, const float* X, void* xh, void* xl, int64_t lda,
+                     const void* ctl, size_t ctl_stride, size_t active_off, const int* run, cudaStream_t s);
+// Y_p rows of every live item = A_p (Xh + Xl) (+ lambda_p X_p), and, when part != NULL, the
+// item's partial <P1, A_p X_p> in part[slot * nq].  Returns 0, or < 0 when the tensor maps
+// cannot be encoded or the launch fails (tc_last_status has the code).
+int launch_bgemm_tc(const void* A16, int64_t lda, int64_t rows_total, const void* xh, const void* xl,
+                    int64_t xt_rows, const TcItem* items, int nitems, const float* X, float* Y, int add_lam,
+                    const float* P1, double* part, int nq, const void* ctl, size_t ctl_stride,
+                    size_t active_off, const int* run, int* err, long long budget, cudaStream_t s);
+
 }  // namespace snmf

@@ -24,10 +24,12 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <numeric>
 #include <string>
 #include <vector>
 
+#include "ax_tc.cuh"
 #include "batch.cuh"
 #include "common.cuh"
 #include "rowops.cuh"
@@ -49,6 +51,8 @@ struct BProb {
   int gch;      // Gram items (row chunks)
   int slot0;    // first partial slot of the row kernels (= index of its first row item)
   int pslot0;   // first partial slot of the product (= index of its first product item)
+  int ntt;      // tensor-core product items (128-row tiles; BF16 A)
+  int tslot0;   // first partial slot of the tensor-core product
   int64_t arow; // first row in A_all
   int64_t xoff; // element offset of the problem's factor blocks
   int64_t goff; // offset of its r x r factor-type matrix
@@ -279,7 +283,10 @@ k_brow(RowArgs base, const BProb* __restrict__ probs, const int2* __restrict__ i
   a.counters = base.counters + it.x;
   a.G64fix = base.G64fix ? base.G64fix + pb.g3off : nullptr;
   a.P.nr = pb.n * (int64_t)pb.r;
-  rowgemm_body<T, OP, EPI, BM, NC>(a, 0, it.y, 0, 1, (unsigned)pb.nrt);
+  if (pb.r <= 32)
+    rowsmall_body<T, OP, EPI, NC>(a, 0, it.y, (unsigned)pb.nrt);
+  else
+    rowgemm_body<T, OP, EPI, BM, NC>(a, 0, it.y, 0, 1, (unsigned)pb.nrt);
 }
 
 // *flag = OR over problems of ctl[p].active
@@ -290,14 +297,16 @@ __global__ void k_bany(const Ctl* __restrict__ ctl, int nprob, int* __restrict__
   if (threadIdx.x == 0) *flag = any;
 }
 
-// final per-problem statistics (one warp per problem)
+// final per-problem statistics (one warp per problem); tc: the product partials are per
+// tensor-core item
 __global__ void k_bfinal(Ctl* __restrict__ ctl, const double* __restrict__ pax, const double* __restrict__ prow,
-                         const double* __restrict__ G64p, const BProb* __restrict__ probs) {
+                         const double* __restrict__ G64p, const BProb* __restrict__ probs, int tc) {
   __shared__ double sh[32];
   const BProb& pb = probs[blockIdx.x];
   const int64_t rr = (int64_t)pb.r * pb.r;
   const double* G = G64p + pb.g3off;
-  final_pen_body(ctl[blockIdx.x], pax + (int64_t)pb.pslot0 * kNQ, pb.npt, prow + (int64_t)pb.slot0 * kNQ,
+  const int ps = tc ? pb.tslot0 : pb.pslot0, np_ = tc ? pb.ntt : pb.npt;
+  final_pen_body(ctl[blockIdx.x], pax + (int64_t)ps * kNQ, np_, prow + (int64_t)pb.slot0 * kNQ,
                  pb.nrt, G, G + rr, G + 2 * rr, 1, 0, pb.r, pb.normA2, sh);
 }
 
@@ -313,6 +322,13 @@ struct BatchCtx {
   std::vector<BProb> hp;
   BProb* dp = nullptr;
   std::vector<int2> h_row, h_prod, h_gram;
+  std::vector<TcItem> h_tc;        // BF16: tensor-core product items
+  TcItem* it_tc = nullptr;
+  void *xh = nullptr, *xl = nullptr;  // BF16 hi / lo parts of the product operand (transposed)
+  int64_t xt_rows = 0;
+  int* dev_err = nullptr;
+  long long budget = 2000000000LL;
+  int tc_fail = 0;
   int2 *it_row = nullptr, *it_prod = nullptr, *it_gram = nullptr;
   int64_t lda = 0, rows_total = 0, xtot = 0;
   void* A = nullptr;
@@ -379,6 +395,17 @@ int row_bm(const BatchCtx* b) { return b->tdtype == 0 ? 32 : 64; }
 // ---- grouped launches -------------------------------------------------------------------
 void bprod(BatchCtx* b, const void* X, void* Y, const void* P1, double* part, const Ctl* ctl, const int* run) {
   const unsigned g = (unsigned)b->h_prod.size();
+  if (b->a_dtype == 2) {
+    // tcgen05: X_p split into BF16 hi / lo parts (transposed), then one CTA per 128-row tile
+    const int nt = (int)b->h_tc.size();
+    launch_bsplit_x(b->it_tc, nt, (const float*)X, b->xh, b->xl, b->lda, ctl, sizeof(Ctl), offsetof(Ctl, active),
+                    run, b->s);
+    if (launch_bgemm_tc(b->A, b->lda, b->rows_total, b->xh, b->xl, b->xt_rows, b->it_tc, nt, (const float*)X,
+                        (float*)Y, 1, (const float*)P1, part, kNQ, ctl, sizeof(Ctl), offsetof(Ctl, active), run,
+                        b->dev_err, b->budget, b->s) < 0)
+      b->tc_fail = tc_last_status() ? tc_last_status() : -1;
+    return;
+  }
   if (b->tdtype == 0)
     k_bgemm<double, double><<<g, 256, 0, b->s>>>((const double*)b->A, b->lda, b->dp, b->it_prod, (const double*)X,
                                                  (double*)Y, 1, (const double*)P1, part, ctl, run);
@@ -427,8 +454,7 @@ void brow(BatchCtx* b, int op, int epi, const RowArgs& a, int nc = 1) {
     if (op == OP_LOAD) BR(T, OP_LOAD, EPI_GRAD, M, 1);                   \
     else BR(T, OP_UPD, EPI_GRAD, M, 1);                                  \
   } else if (nc == 1) BR(T, OP_ZSTEP, EPI_DIR, M, 1);                    \
-  else if (nc == 2) BR(T, OP_ZSTEP, EPI_DIR, M, 2);                      \
-  else BR(T, OP_ZSTEP, EPI_DIR, M, kNCand);
+  else BR(T, OP_ZSTEP, EPI_DIR, M, 2);  /* record mode is not offered on batch handles */
   if (b->tdtype == 0) { BR_T(double, 32) } else { BR_T(float, 64) }
 #undef BR_T
 #undef BR
@@ -506,7 +532,7 @@ void bpen_final(BatchCtx* b, const Params& P) {
   a.ctl = b->ctl + b->nprob;  // second Ctl array: all live
   a.ctl_mode = CTL_NONE;
   brow(b, OP_LOAD, EPI_GRAD, a);
-  k_bfinal<<<b->nprob, 32, 0, b->s>>>(b->ctl, b->pax, b->prow, b->G64p, b->dp);
+  k_bfinal<<<b->nprob, 32, 0, b->s>>>(b->ctl, b->pax, b->prow, b->G64p, b->dp, b->a_dtype == 2 ? 1 : 0);
 }
 
 snmf_status sync_user_b(BatchCtx* b, std::string* err) {
@@ -589,7 +615,8 @@ snmf_status batch_create(BatchCtx** out, const snmf_matrix* Am, const snmf_optio
     BProb& q = b->hp[p];
     q.n = ns[p];
     q.r = (int)rs[p];
-    q.nrt = (int)((ns[p] + bm - 1) / bm);
+    const int rows = rs[p] <= 32 ? small_rows((int)rs[p]) : bm;  // rows per row-kernel item
+    q.nrt = (int)((ns[p] + rows - 1) / rows);
     q.npt = (int)((ns[p] + kPBM - 1) / kPBM);
     q.gch = (int)((ns[p] + kGChunk - 1) / kGChunk);
     q.arow = arow;
@@ -660,7 +687,10 @@ snmf_status batch_create(BatchCtx** out, const snmf_matrix* Am, const snmf_optio
     CKB(cudaMemsetAsync(b->buf[x], 0, (size_t)b->xtot * b->esz, b->s));
   }
   CKB(cudaMalloc(&b->prow, b->h_row.size() * kNQ * sizeof(double)));
-  CKB(cudaMalloc(&b->pax, b->h_prod.size() * kNQ * sizeof(double)));
+  CKB(cudaMalloc(&b->pax, b->h_prod.size() * kNQ * sizeof(double)));  // >= tensor-core items
+  CKB(cudaMalloc(&b->dev_err, sizeof(int)));
+  CKB(cudaMemsetAsync(b->dev_err, 0, sizeof(int), b->s));
+  if (o.timeout_cycles > 0) b->budget = o.timeout_cycles;
   CKB(cudaMalloc(&b->gpart, std::max<int64_t>(gpoff, 1) * sizeof(double)));
   CKB(cudaMalloc(&b->G64fix, g3off * sizeof(double)));
   CKB(cudaMalloc(&b->G64p, g3off * sizeof(double)));
@@ -704,6 +734,44 @@ snmf_status batch_create(BatchCtx** out, const snmf_matrix* Am, const snmf_optio
       b->hp[p].normA2 = sums[2 * p];
       b->hp[p].lam = o.lambda_sym >= 0.0 ? o.lambda_sym : 0.01 * std::sqrt(sums[2 * p]);
       b->sumA[p] = sums[2 * p + 1];
+    }
+    if (b->a_dtype == 2) {
+      // tensor-core items (largest problems first) and the transposed BF16 operand parts:
+      // problem p owns rows xrow_p .. xrow_p + r_p rounded up to 16 (zero beyond r_p / n_p)
+      std::vector<int64_t> xr(np);
+      int64_t xrow = 0;
+      for (int p = 0; p < np; ++p) {
+        xr[p] = xrow;
+        xrow += (b->hp[p].r + 15) / 16 * 16;
+      }
+      b->xt_rows = xrow;
+      for (int p : order) {
+        BProb& q = b->hp[p];
+        q.ntt = (int)((q.n + 127) / 128);
+        q.tslot0 = (int)b->h_tc.size();
+        for (int t = 0; t < q.ntt; ++t) {
+          TcItem ti{};
+          ti.arow = q.arow + 128 * t;
+          ti.xoff = q.xoff;
+          ti.m0 = 128 * t;
+          ti.n = (int)q.n;
+          ti.r = q.r;
+          ti.bn = (q.r + 15) / 16 * 16;
+          ti.xrow = (int)xr[p];
+          ti.kt = (int)((q.n + 63) / 64);
+          ti.prob = p;
+          ti.slot = (int)b->h_tc.size();
+          ti.lam = (float)q.lam;
+          b->h_tc.push_back(ti);
+        }
+      }
+      CKB(cudaMalloc(&b->it_tc, b->h_tc.size() * sizeof(TcItem)));
+      CKB(cudaMemcpyAsync(b->it_tc, b->h_tc.data(), b->h_tc.size() * sizeof(TcItem), cudaMemcpyHostToDevice, b->s));
+      const size_t xb = (size_t)b->xt_rows * b->lda * 2;
+      CKB(cudaMalloc(&b->xh, xb));
+      CKB(cudaMalloc(&b->xl, xb));
+      CKB(cudaMemsetAsync(b->xh, 0, xb, b->s));
+      CKB(cudaMemsetAsync(b->xl, 0, xb, b->s));
     }
     CKB(cudaMemcpyAsync(b->dp, b->hp.data(), np * sizeof(BProb), cudaMemcpyHostToDevice, b->s));
     CKB(cudaStreamSynchronize(b->s));
@@ -786,7 +854,21 @@ snmf_status batch_solve(BatchCtx* b, bool host, void* W, void* Ht, snmf_stats* o
     BCK(cudaEventRecord(b->evsync, b->s));
     BCK(cudaStreamWaitEvent(b->user, b->evsync, 0));
   }
+  if (b->tc_fail) {
+    const int tf = b->tc_fail;
+    b->tc_fail = 0;
+    cudaGetLastError();
+    *err = "tensor-core product not launched (status " + std::to_string(tf) + ")";
+    return SNMF_ERR_CUDA;
+  }
   BCK(cudaGetLastError());
+  int derr = 0;
+  BCK(cudaMemcpy(&derr, b->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (derr) {
+    BCK(cudaMemset(b->dev_err, 0, sizeof(int)));
+    *err = "a bounded device wait of the tensor-core product ran out (code " + std::to_string(derr) + ")";
+    return SNMF_ERR_TIMEOUT;
+  }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, b->ev0, b->ev1);
   b->have_result = true;
@@ -837,6 +919,31 @@ snmf_status batch_problem_stats(BatchCtx* b, double* f, double* residual, double
   return SNMF_OK;
 }
 
+snmf_status batch_profile_ax(BatchCtx* b, int iters, double* ms, std::string* err) {
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  bprod(b, b->buf[XB_W], b->buf[XB_Z], nullptr, nullptr, nullptr, nullptr);  // warm-up
+  BCK(cudaEventRecord(e0, b->s));
+  for (int t = 0; t < iters; ++t) bprod(b, b->buf[XB_W], b->buf[XB_Z], nullptr, nullptr, nullptr, nullptr);
+  BCK(cudaEventRecord(e1, b->s));
+  BCK(cudaStreamSynchronize(b->s));
+  BCK(cudaGetLastError());
+  float m = 0.f;
+  cudaEventElapsedTime(&m, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = m / iters;
+  return SNMF_OK;
+}
+
+int64_t batch_product_bytes(const BatchCtx* b) {
+  const int64_t asz = b->a_dtype == 0 ? 8 : (b->a_dtype == 2 ? 2 : 4);
+  int64_t t = 0;
+  for (const BProb& q : b->hp) t += q.n * q.n * asz + 2 * q.n * q.r * (int64_t)b->esz;
+  return t;
+}
+
 snmf_status batch_get_factors(BatchCtx* b, void* W, void* Ht, std::string* err) {
   if (!b->have_result) { *err = "no solve has run"; return SNMF_ERR_STATE; }
   const size_t fbytes = (size_t)b->xtot * b->esz;
@@ -856,6 +963,10 @@ void batch_destroy(BatchCtx* b) {
   cudaFree(b->it_row);
   cudaFree(b->it_prod);
   cudaFree(b->it_gram);
+  cudaFree(b->it_tc);
+  cudaFree(b->xh);
+  cudaFree(b->xl);
+  cudaFree(b->dev_err);
   for (void* p : b->buf) cudaFree(p);
   double* d[] = {b->prow, b->pax, b->gpart, b->G64fix, b->G64p, b->dsc};
   for (double* p : d) cudaFree(p);

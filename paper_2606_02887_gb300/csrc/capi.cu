@@ -993,7 +993,14 @@ snmf_status snmf_apply(snmf_handle h, const void* X, void* Y, int cols, double* 
 
 snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_product, double* ms_kernel) {
   if (!h) return SNMF_ERR_STATE;
-  if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
+  if (iters < 1) return fail(h, SNMF_ERR_ARG, "iters must be >= 1");
+  if (h->bt) {
+    double ms = 0.0;
+    const snmf_status st = batch_profile_ax(h->bt, iters, &ms, &h->err);
+    if (ms_product) *ms_product = ms;
+    if (ms_kernel) *ms_kernel = ms;
+    return st;
+  }
   if (iters < 1) return fail(h, SNMF_ERR_ARG, "iters must be >= 1");
   if (sync_user(h) != SNMF_OK) return SNMF_ERR_CUDA;
   const Dims d = dims(h);

@@ -670,44 +670,65 @@ __device__ __forceinline__ void rowgemm_body(const RowArgs& a, int j, int bx, in
     const T* LX = (const T*)a.LX;
     const T gam = (T)a.gamma;
     T gl[MR][4], xl[MR][4];  // gradient and operand of the thread's elements
+    // With r <= KC the operand tile of this CTA's rows is still in shared memory.
+    const bool xs_ok = r <= KC && col0 == 0;
 #pragma unroll
     for (int p = 0; p < MR; ++p) {
       const int64_t i = row0 + ty + 16 * p;
+      // the row's loads first: the stores below may alias inputs (Xout / Xold), so
+      // keeping them apart lets all four elements' loads be in flight together
+      bool vq[4];
+      int64_t iq[4];
+      T xq[4], bq[4], lq[4], o0[4], o1[4], o2[4], o3[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = col0 + tx + 16 * q;
+        vq[q] = i < a.n && c < r;
+        iq[q] = i * ld + jc + c;
+        xq[q] = bq[q] = lq[q] = o0[q] = o1[q] = o2[q] = o3[q] = T(0);
+        if (!vq[q]) continue;
+        const int64_t idx = iq[q];
+        xq[q] = xs_ok ? Xs[ty + 16 * p][c] : operand(i, jc + c);
+        bq[q] = B[idx];
+        if (LX) lq[q] = LX[idx];
+        if (EPI == EPI_GRAD) {
+          if (a.Xold) { o0[q] = ((const T*)a.Xold)[idx]; o1[q] = ((const T*)a.gold)[idx]; }
+          if (a.Zold) { o2[q] = ((const T*)a.Zold)[idx]; o3[q] = ((const T*)a.gZold)[idx]; }
+        } else if (a.Wcur) {
+          o0[q] = ((const T*)a.Wcur)[idx];
+          o1[q] = ((const T*)a.gWcur)[idx];
+        }
+      }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         gl[p][q] = T(0);
         xl[p][q] = T(0);
-        const int c = col0 + tx + 16 * q;
-        if (i >= a.n || c >= r) continue;
-        const int64_t idx = i * ld + jc + c;
-        const T xv = operand(i, jc + c);
-        T g = acc[p][q] - B[idx];
-        if (LX) g += gam * LX[idx];
+        if (!vq[q]) continue;
+        const int64_t idx = iq[q];
+        const T xv = xq[q];
+        T g = acc[p][q] - bq[q];
+        if (LX) g += gam * lq[q];
         gl[p][q] = g;
         xl[p][q] = xv;
         if (EPI == EPI_GRAD) {
           const T pgv = xv > T(0) ? g : (g < T(0) ? g : T(0));
           dq[0] += pgv * pgv;                              // ||P grad||^2
-          dq[1] += T(0.5) * (g - B[idx]) * xv;              // f - const (quadratic block)
+          dq[1] += T(0.5) * (g - bq[q]) * xv;               // f - const (quadratic block)
           if (a.Xold) {
-            const T sv = xv - ((const T*)a.Xold)[idx];
-            const T yv = g - ((const T*)a.gold)[idx];
+            const T sv = xv - o0[q];
+            const T yv = g - o1[q];
             dq[2] += sv * sv;
             dq[3] += sv * yv;
             dq[4] += yv * yv;
           }
-          if (a.Zold) {                                     // f(X') - f(Z), trapezoid (exact)
-            dq[5] += T(0.5) * (xv - ((const T*)a.Zold)[idx]) * (g + ((const T*)a.gZold)[idx]);
-          }
+          if (a.Zold) dq[5] += T(0.5) * (xv - o2[q]) * (g + o3[q]);  // f(X') - f(Z), trapezoid (exact)
           if (xv == T(0)) dq[6] += T(1);                    // active (zero) entries
           if (a.gout) ((T*)a.gout)[idx] = g;
-          if (a.Xout) ((T*)a.Xout)[idx] = xv;  // after Xold was read (may alias)
+          if (a.Xout) ((T*)a.Xout)[idx] = xv;
         } else {  // EPI_DIR
           if (a.Xout) ((T*)a.Xout)[idx] = xv;
           if (a.gZout) ((T*)a.gZout)[idx] = g;
-          if (a.Wcur) {                                     // f(Z) - f(W), trapezoid (exact)
-            dq[2] += T(0.5) * (xv - ((const T*)a.Wcur)[idx]) * (g + ((const T*)a.gWcur)[idx]);
-          }
+          if (a.Wcur) dq[2] += T(0.5) * (xv - o0[q]) * (g + o1[q]);  // f(Z) - f(W), trapezoid (exact)
 #pragma unroll
           for (int m = 0; m < NC; ++m) {
             T d = xv - alph[m] * g;
@@ -717,11 +738,12 @@ __device__ __forceinline__ void rowgemm_body(const RowArgs& a, int j, int bx, in
             const int base = m == 0 ? 0 : 5 + 3 * (m - 1);
             dq[base] += g * d;                              // <grad f(Z), D_m>
             dq[base + 1] += d * d;                          // ||D_m||^2
-            if (m == 0 && LX) dq[3] += d * LX[idx];         // <D, L Z> (direct, graph)
+            if (m == 0 && LX) dq[3] += d * lq[q];           // <D, L Z> (direct, graph)
           }
         }
       }
     }
+    __syncthreads();  // the operand tile (read above) and the D tile below share memory
     if (EPI == EPI_DIR && a.want_q) {
       // <D_m G, D_m> of each candidate's line-search quadratic (restart = one column tile)
 #pragma unroll 1
@@ -807,6 +829,186 @@ __device__ __forceinline__ void rowgemm_body(const RowArgs& a, int j, int bx, in
     if (threadIdx.x == 0) ticket = atomicAdd(&a.counters[j], 1u);
     __syncthreads();
         if (ticket == per - 1) {
+      if (threadIdx.x == 0) a.counters[j] = 0u;
+      if (threadIdx.x < 32)
+        fused_control(a.ctl_mode, const_cast<Ctl&>(a.ctl[j]), a.part, (int)per, a.b, a.r, j, a.P, a.G64fix,
+                      nullptr, NC);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------
+// Row GEMM for small ranks (r <= 32) with the same fused epilogues and partial layout as
+// rowgemm_body.  A warp is cut into segments of rp lanes (rp = r rounded up to a power of
+// two); segment s holds one row, lane c of it column c.  Column c of G lives in the lane's
+// registers and the row product sum_k x_k G[k][c] takes the x_k by shuffles within the
+// segment, so no shared-memory staging is needed and every lane does useful work for
+// r = 4 .. 32.  The CTA covers rows_cta = 8 warps x (32 / rp) rows x kSmallIters rows of
+// restart j starting at tile * rows_cta; `per` CTAs per restart.
+// ------------------------------------------------------------------------------
+constexpr int kSmallIters = 4;
+
+__host__ __device__ inline int small_rp(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : (r <= 16 ? 16 : 32)); }
+__host__ __device__ inline int small_rows(int r) { return 8 * (32 / small_rp(r)) * kSmallIters; }
+
+template <typename T, int OP, int EPI, int NC>
+__device__ __forceinline__ void rowsmall_body(const RowArgs& a, int j, int tile, unsigned per) {
+  constexpr int NV = 8;
+  static_assert(NC <= 2, "small-rank row body: at most two candidates");
+  const int r = a.r;
+  const int rp = small_rp(r);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int seg = lane / rp, c = lane % rp, segbase = seg * rp;
+  const int step = 32 / rp;  // rows per warp instruction
+  const int64_t ld = a.ld;
+  const int64_t jc = (int64_t)j * r;
+  const int rows_cta = 8 * step * kSmallIters;
+  __shared__ T shq[NV][8];
+  const Ctl& cj = a.ctl[j];
+  const bool live = cj.active && !(a.run && *a.run == 0);
+  T dq[NV];
+#pragma unroll
+  for (int m = 0; m < NV; ++m) dq[m] = T(0);
+  if (live) {
+    const bool cv = c < r;
+    const T* G = (const T*)a.G + (int64_t)j * r * r;
+    T gcol[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) gcol[k] = (cv && k < r) ? G[k * r + c] : T(0);
+    const T inv_rho = (T)(1.0 / cj.rho);
+    const T pb = (T)cj.phibeta;
+    const T* X = (const T*)a.X;
+    const T* gin = (const T*)a.g_in;
+    const T* Zin = (const T*)a.Zin;
+    const T* Din = (const T*)((OP == OP_UPD && cj.dsel) ? a.Din2 : a.Din);
+    const T* B = (const T*)a.B;
+    T alph[NC];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) alph[m] = (T)(NC == 1 ? cj.alpha : cj.cand_alpha[m]);
+    // products of the segments' rows with column c of G, kSmallIters rows interleaved
+    // (every lane of the warp takes part in the shuffles)
+    auto rowprod = [&](const T* v, T* y) {
+#pragma unroll
+      for (int u = 0; u < kSmallIters; ++u) y[u] = T(0);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        if (k < rp) {
+#pragma unroll
+          for (int u = 0; u < kSmallIters; ++u) {
+            const T xk = __shfl_sync(0xffffffffu, v[u], segbase + k);
+            y[u] = fma(xk, gcol[k], y[u]);
+          }
+        }
+      }
+    };
+    // Loads of all kSmallIters rows first (the stores below may alias some inputs, e.g.
+    // Xout and Xold, so keeping them apart lets every load be in flight at once), then the
+    // row products, then the epilogue and the stores.
+    const int64_t row0 = (int64_t)tile * rows_cta;
+    constexpr int IT = kSmallIters;
+    int64_t idx[IT];
+    bool ev[IT];
+    T xv[IT], bv[IT], e0[IT], e1[IT], e2[IT], e3[IT];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int64_t i = row0 + ((int64_t)it * 8 + wid) * step + seg;
+      ev[it] = cv && i < a.n;
+      idx[it] = i * ld + jc + c;
+      xv[it] = bv[it] = e0[it] = e1[it] = e2[it] = e3[it] = T(0);
+      if (ev[it]) {
+        const int64_t q = idx[it];
+        if (OP == OP_LOAD) xv[it] = X[q];
+        else if (OP == OP_ZSTEP) { const T v = X[q] - gin[q] * inv_rho; xv[it] = v > T(0) ? v : T(0); }
+        else { const T v = Zin[q] + pb * Din[q]; xv[it] = v > T(0) ? v : T(0); }
+        bv[it] = B[q];
+        if (EPI == EPI_GRAD) {
+          if (a.Xold) { e0[it] = ((const T*)a.Xold)[q]; e1[it] = ((const T*)a.gold)[q]; }
+          if (a.Zold) { e2[it] = ((const T*)a.Zold)[q]; e3[it] = ((const T*)a.gZold)[q]; }
+        } else if (a.Wcur) {
+          e0[it] = ((const T*)a.Wcur)[q];
+          e1[it] = ((const T*)a.gWcur)[q];
+        }
+      }
+    }
+    T g[IT];
+    rowprod(xv, g);
+#pragma unroll
+    for (int it = 0; it < IT; ++it) g[it] = ev[it] ? g[it] - bv[it] : T(0);
+    if (EPI == EPI_DIR) {
+      // directions of every candidate, then <D_m G, D_m> with the rows interleaved
+#pragma unroll
+      for (int m = 0; m < NC; ++m) {
+        T d[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+          d[it] = T(0);
+          if (ev[it]) {
+            const T t = xv[it] - alph[m] * g[it];
+            d[it] = (t > T(0) ? t : T(0)) - xv[it];
+            if (m == a.dstore) ((T*)a.Dout)[idx[it]] = d[it];
+            if (NC == 2 && m == 1) ((T*)a.D2out)[idx[it]] = d[it];
+            const int base = m == 0 ? 0 : 5;
+            dq[base] += g[it] * d[it];
+            dq[base + 1] += d[it] * d[it];
+          }
+        }
+        if (a.want_q) {
+          T dg[IT];
+          rowprod(d, dg);  // (D_m G)_c
+#pragma unroll
+          for (int it = 0; it < IT; ++it) dq[m == 0 ? 4 : 7] += dg[it] * d[it];
+        }
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int64_t q = idx[it];
+      if (EPI == EPI_GRAD) {
+        if (ev[it]) {
+          const T gg = g[it], x = xv[it];
+          const T pgv = x > T(0) ? gg : (gg < T(0) ? gg : T(0));
+          dq[0] += pgv * pgv;
+          dq[1] += T(0.5) * (gg - bv[it]) * x;
+          if (a.Xold) {
+            const T sv = x - e0[it];
+            const T yv = gg - e1[it];
+            dq[2] += sv * sv;
+            dq[3] += sv * yv;
+            dq[4] += yv * yv;
+          }
+          if (a.Zold) dq[5] += T(0.5) * (x - e2[it]) * (gg + e3[it]);
+          if (x == T(0)) dq[6] += T(1);
+          if (a.gout) ((T*)a.gout)[q] = gg;
+          if (a.Xout) ((T*)a.Xout)[q] = x;
+        }
+      } else if (ev[it]) {  // EPI_DIR: Z, its gradient, the f(Z) - f(W) increment
+        const T gg = g[it], x = xv[it];
+        if (a.Xout) ((T*)a.Xout)[q] = x;
+        if (a.gZout) ((T*)a.gZout)[q] = gg;
+        if (a.Wcur) dq[2] += T(0.5) * (x - e0[it]) * (gg + e1[it]);
+      }
+    }
+  }
+  // one combined fixed-order reduction of the partial dots
+#pragma unroll
+  for (int m = 0; m < NV; ++m) {
+    const T v = warp_sum(dq[m]);
+    if (lane == 0) shq[m][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    T v = T(0);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v += shq[threadIdx.x][w];
+    a.part[((int64_t)tile * a.b + j) * kNQ + threadIdx.x] = (double)v;
+  }
+  if (a.ctl_mode) {
+    __shared__ unsigned ticket;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) ticket = atomicAdd(&a.counters[j], 1u);
+    __syncthreads();
+    if (ticket == per - 1) {
       if (threadIdx.x == 0) a.counters[j] = 0u;
       if (threadIdx.x < 32)
         fused_control(a.ctl_mode, const_cast<Ctl&>(a.ctl[j]), a.part, (int)per, a.b, a.r, j, a.P, a.G64fix,

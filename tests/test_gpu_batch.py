@@ -105,3 +105,17 @@ def test_batch_zero_iterations_and_zero_weight_controller():
     for p in range(4):
         assert np.array_equal(Wp[p], Wl[p]) and np.array_equal(Hp[p], Hl[p])
     assert sl["ctl_proposals"] > 0
+
+
+def test_batch_bf16_product_through_final_evaluation():
+    """max_iter = 0: the final evaluation's residual comes from the grouped tensor-core
+    product <W, A~ Ht> (A~ = BF16(A)); it must equal the residual computed in FP64 from the
+    BF16-rounded A for every problem size class (ragged 128-row tiles, r = 1..64)."""
+    import torch
+    As, Ws = make_problems(SPECS + [(1000, 33, 31), (129, 16, 33)])
+    W, H, _, _, per = batch_solve(As, Ws, S.SNMF_BF16, max_iter=0, tol=0.0)
+    for p, (A, W0) in enumerate(zip(As, Ws)):
+        Ab = torch.tensor(A, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+        W32 = W0.astype(np.float32).astype(np.float64)
+        res = np.linalg.norm(Ab - W32 @ W32.T) / np.linalg.norm(Ab)
+        assert abs(per["residual"][p] - res) <= 1e-5 * max(1.0, res), (p, per["residual"][p], res)
