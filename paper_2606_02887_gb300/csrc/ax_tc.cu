@@ -319,9 +319,10 @@ __device__ __forceinline__ bool item_live(const TcItem& it, const unsigned char*
 __global__ void __launch_bounds__(128, 2)
 k_bgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapXh,
            const __grid_constant__ CUtensorMap mapXl, const TcItem* __restrict__ items,
-           const float* __restrict__ X, float* __restrict__ Y, int add_lam, const float* __restrict__ P1,
-           double* __restrict__ part, int nq, const unsigned char* __restrict__ ctl, size_t ctl_stride,
-           size_t active_off, const int* __restrict__ run, int* __restrict__ err, long long budget) {
+           const int* __restrict__ cnt, const float* __restrict__ X, float* __restrict__ Y, int add_lam,
+           const float* __restrict__ P1, double* __restrict__ part, int nq, const unsigned char* __restrict__ ctl,
+           size_t ctl_stride, size_t active_off, const int* __restrict__ run, int* __restrict__ err,
+           long long budget) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -331,6 +332,7 @@ k_bgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
   __shared__ int s_fail, s_issued, s_consumed;
   __shared__ float s_red[4];
+  if ((int)blockIdx.x >= *cnt) return;
   const TcItem it = items[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (!item_live(it, ctl, ctl_stride, active_off, run)) {
@@ -443,10 +445,11 @@ k_bgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 
 // X_p rows m0 .. m0 + 128 (FP32, ld r_p) -> columns of the transposed BF16 hi / lo parts
 __global__ void __launch_bounds__(256)
-k_bsplit_x(const TcItem* __restrict__ items, const float* __restrict__ X, __nv_bfloat16* __restrict__ Xh,
-           __nv_bfloat16* __restrict__ Xl, int64_t lda, const unsigned char* __restrict__ ctl, size_t ctl_stride,
-           size_t active_off, const int* __restrict__ run) {
+k_bsplit_x(const TcItem* __restrict__ items, const int* __restrict__ cnt, const float* __restrict__ X,
+           __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl, int64_t lda,
+           const unsigned char* __restrict__ ctl, size_t ctl_stride, size_t active_off, const int* __restrict__ run) {
   __shared__ float t[BM][65];
+  if ((int)blockIdx.x >= *cnt) return;
   const TcItem it = items[blockIdx.x];
   if (!item_live(it, ctl, ctl_stride, active_off, run)) return;
   const int rows = min(BM, it.n - it.m0);
@@ -598,14 +601,16 @@ int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx,
   return pl.splits;
 }
 
-void launch_bsplit_x(const TcItem* items, int nitems, const float* X, void* xh, void* xl, int64_t lda,
-                     const void* ctl, size_t ctl_stride, size_t active_off, const int* run, cudaStream_t s) {
-  k_bsplit_x<<<nitems, 256, 0, s>>>(items, X, (__nv_bfloat16*)xh, (__nv_bfloat16*)xl, lda,
+void launch_bsplit_x(const TcItem* items, int nitems, const int* cnt, const float* X, void* xh, void* xl,
+                     int64_t lda, const void* ctl, size_t ctl_stride, size_t active_off, const int* run,
+                     cudaStream_t s) {
+  k_bsplit_x<<<nitems, 256, 0, s>>>(items, cnt, X, (__nv_bfloat16*)xh, (__nv_bfloat16*)xl, lda,
                                     (const unsigned char*)ctl, ctl_stride, active_off, run);
 }
 
 int launch_bgemm_tc(const void* A16, int64_t lda, int64_t rows_total, const void* xh, const void* xl,
-                    int64_t xt_rows, const TcItem* items, int nitems, const float* X, float* Y, int add_lam,
+                    int64_t xt_rows, const TcItem* items, int nitems, const int* cnt, const float* X, float* Y,
+                    int add_lam,
                     const float* P1, double* part, int nq, const void* ctl, size_t ctl_stride,
                     size_t active_off, const int* run, int* err, long long budget, cudaStream_t s) {
   CUtensorMap ma, mh, ml;
@@ -621,7 +626,7 @@ int launch_bgemm_tc(const void* A16, int64_t lda, int64_t rows_total, const void
     }
     attr_done = true;
   }
-  k_bgemm_tc<<<nitems, 128, smem, s>>>(ma, mh, ml, items, X, Y, add_lam, P1, part, nq,
+  k_bgemm_tc<<<nitems, 128, smem, s>>>(ma, mh, ml, items, cnt, X, Y, add_lam, P1, part, nq,
                                        (const unsigned char*)ctl, ctl_stride, active_off, run, err, budget);
   const cudaError_t le = cudaPeekAtLastError();
   if (le != cudaSuccess) { g_last_cu = 10000 + (int)le; return -2; }

@@ -48,13 +48,16 @@ struct TcItem {
 };
 
 // Xh/Xl rows xrow_p .. xrow_p + r_p, columns m0 .. m0 + 128 of every live item's problem.
-void launch_bsplit_x(const TcItem* items, int nitems, const float* X, void* xh, void* xl, int64_t lda,
-                     const void* ctl, size_t ctl_stride, size_t active_off, const int* run, cudaStream_t s);
+// nitems: grid size; *cnt (device): the items actually present (CTAs beyond it return).
+void launch_bsplit_x(const TcItem* items, int nitems, const int* cnt, const float* X, void* xh, void* xl,
+                     int64_t lda, const void* ctl, size_t ctl_stride, size_t active_off, const int* run,
+                     cudaStream_t s);
 // Y_p rows of every live item = A_p (Xh + Xl) (+ lambda_p X_p), and, when part != NULL, the
 // item's partial <P1, A_p X_p> in part[slot * nq].  Returns 0, or < 0 when the tensor maps
 // cannot be encoded or the launch fails (tc_last_status has the code).
 int launch_bgemm_tc(const void* A16, int64_t lda, int64_t rows_total, const void* xh, const void* xl,
-                    int64_t xt_rows, const TcItem* items, int nitems, const float* X, float* Y, int add_lam,
+                    int64_t xt_rows, const TcItem* items, int nitems, const int* cnt, const float* X, float* Y,
+                    int add_lam,
                     const float* P1, double* part, int nq, const void* ctl, size_t ctl_stride,
                     size_t active_off, const int* run, int* err, long long budget, cudaStream_t s);
 

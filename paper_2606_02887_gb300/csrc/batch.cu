@@ -126,13 +126,15 @@ __global__ void k_bsums_reduce(const BProb* __restrict__ probs, const double* __
 
 // Grouped product (CUDA cores): item (p, t) computes rows t*64 .. of Y_p = A_p X_p over the
 // full K = n_p (A_p rows streamed once, X_p from L2), epilogue Y += lambda_p X and, when
-// P1 is given, the per-item partial <P1, A_p X_p> in partial slot blockIdx.x.
+// P1 is given, the per-item partial <P1, A_p X_p> in the item's partial slot.  CTAs beyond
+// the *cnt items of the (compacted) list return at once.
 template <typename T, typename TA>
 __global__ void __launch_bounds__(256)
 k_bgemm(const TA* __restrict__ A, int64_t lda, const BProb* __restrict__ probs, const int2* __restrict__ items,
-        const T* __restrict__ X, T* __restrict__ Y, int add_lam, const T* __restrict__ P1,
-        double* __restrict__ part, const Ctl* __restrict__ ctl, const int* __restrict__ run) {
+        const int* __restrict__ cnt, const T* __restrict__ X, T* __restrict__ Y, int add_lam,
+        const T* __restrict__ P1, double* __restrict__ part, const Ctl* __restrict__ ctl, const int* __restrict__ run) {
   constexpr int BK = sizeof(T) == 8 ? 16 : 32;
+  if ((int)blockIdx.x >= *cnt) return;
   constexpr int NA = kPBM * BK / 256;
   constexpr int NX = BK * 64 / 256;
   __shared__ T As[2][BK][kPBM + 4];
@@ -224,7 +226,7 @@ k_bgemm(const TA* __restrict__ A, int64_t lda, const BProb* __restrict__ probs, 
   }
   if (part) {
     d1 = block_sum_t(d1, sh);
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kNQ] = (double)d1;
+    if (threadIdx.x == 0) part[(int64_t)(pb.pslot0 + it.y) * kNQ] = (double)d1;
   }
 }
 
@@ -232,10 +234,11 @@ k_bgemm(const TA* __restrict__ A, int64_t lda, const BProb* __restrict__ probs, 
 // of the factor-type copy when use_lam; rho_p fused in the last CTA (FP32 working type).
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_bgram(const BProb* __restrict__ probs, const int2* __restrict__ items, const T* __restrict__ X,
-        const T* __restrict__ Y, double* __restrict__ gpart, int pair, int npairs, const Ctl* __restrict__ ctl,
-        const int* run, double* __restrict__ G64, T* __restrict__ GT, int tpair, int use_lam,
-        unsigned* __restrict__ counters, Ctl* __restrict__ rho_ctl, int rho_iters) {
+k_bgram(const BProb* __restrict__ probs, const int2* __restrict__ items, const int* __restrict__ cnt,
+        const T* __restrict__ X, const T* __restrict__ Y, double* __restrict__ gpart, int pair, int npairs,
+        const Ctl* __restrict__ ctl, const int* run, double* __restrict__ G64, T* __restrict__ GT, int tpair,
+        int use_lam, unsigned* __restrict__ counters, Ctl* __restrict__ rho_ctl, int rho_iters) {
+  if ((int)blockIdx.x >= *cnt) return;  // beyond the (compacted) list
   const int2 it = items[blockIdx.x];
   const BProb& pb = probs[it.x];
   gram_body<T>(X + pb.xoff, Y + pb.xoff, pb.n, pb.r, 1, pb.r, kGChunk, 1, gpart + pb.gpoff, pair, npairs,
@@ -260,7 +263,8 @@ k_brho(const BProb* __restrict__ probs, const double* __restrict__ G64, int iter
 // Grouped row GEMM with the fused Algorithm-1 epilogues and the per-problem control step.
 template <typename T, int OP, int EPI, int BM, int NC>
 __global__ void __launch_bounds__(256, 2)
-k_brow(RowArgs base, const BProb* __restrict__ probs, const int2* __restrict__ items) {
+k_brow(RowArgs base, const BProb* __restrict__ probs, const int2* __restrict__ items, const int* __restrict__ cnt) {
+  if ((int)blockIdx.x >= *cnt) return;  // beyond the (compacted) list
   const int2 it = items[blockIdx.x];
   const BProb& pb = probs[it.x];
   RowArgs a = base;
@@ -283,19 +287,101 @@ k_brow(RowArgs base, const BProb* __restrict__ probs, const int2* __restrict__ i
   a.counters = base.counters + it.x;
   a.G64fix = base.G64fix ? base.G64fix + pb.g3off : nullptr;
   a.P.nr = pb.n * (int64_t)pb.r;
-  if (pb.r <= 32)
-    rowsmall_body<T, OP, EPI, NC>(a, 0, it.y, (unsigned)pb.nrt);
-  else
-    rowgemm_body<T, OP, EPI, BM, NC>(a, 0, it.y, 0, 1, (unsigned)pb.nrt);
+  rowgemm_body<T, OP, EPI, BM, NC>(a, 0, it.y, 0, 1, (unsigned)pb.nrt);
 }
 
-// *flag = OR over problems of ctl[p].active
-__global__ void k_bany(const Ctl* __restrict__ ctl, int nprob, int* __restrict__ flag) {
-  int any = 0;
-  for (int p = threadIdx.x; p < nprob; p += blockDim.x) any |= ctl[p].active;
-  any = __syncthreads_or(any);
-  if (threadIdx.x == 0) *flag = any;
+// The same for problems with r <= 32 through the shared-memory tile body (TileCfg rows per
+// item); dynamic shared memory of rowtile_smem bytes.
+template <typename T, int OP, int EPI, int NC>
+__global__ void __launch_bounds__(256, 3)
+k_browt(RowArgs base, const BProb* __restrict__ probs, const int2* __restrict__ items, const int* __restrict__ cnt) {
+  extern __shared__ __align__(16) unsigned char tsm[];
+  if ((int)blockIdx.x >= *cnt) return;  // beyond the (compacted) list
+  const int2 it = items[blockIdx.x];
+  const BProb& pb = probs[it.x];
+  RowArgs a = base;
+  const size_t o = (size_t)pb.xoff * sizeof(T);
+  auto cs = [&](const void* q) -> const void* { return q ? (const void*)((const char*)q + o) : nullptr; };
+  auto ms = [&](void* q) -> void* { return q ? (void*)((char*)q + o) : nullptr; };
+  a.n = pb.n;
+  a.r = pb.r;
+  a.b = 1;
+  a.ld = pb.r;
+  a.G = (const T*)base.G + pb.goff;
+  a.X = cs(base.X); a.g_in = cs(base.g_in); a.Zin = cs(base.Zin); a.Din = cs(base.Din);
+  a.B = cs(base.B); a.LX = nullptr;
+  a.Xout = ms(base.Xout); a.gout = ms(base.gout); a.Dout = ms(base.Dout); a.D2out = ms(base.D2out);
+  a.Din2 = cs(base.Din2); a.gZout = ms(base.gZout);
+  a.Xold = cs(base.Xold); a.gold = cs(base.gold); a.Zold = cs(base.Zold); a.gZold = cs(base.gZold);
+  a.Wcur = cs(base.Wcur); a.gWcur = cs(base.gWcur);
+  a.ctl = base.ctl + it.x;
+  a.part = base.part + (int64_t)pb.slot0 * kNQ;
+  a.counters = base.counters + it.x;
+  a.G64fix = base.G64fix ? base.G64fix + pb.g3off : nullptr;
+  a.P.nr = pb.n * (int64_t)pb.r;
+  rowtile_body<T, OP, EPI, NC>(a, 0, it.y, (unsigned)pb.nrt, reinterpret_cast<T*>(tsm));
 }
+
+// Work-list compaction: the items of the problems that are still active, in the original
+// order, for the five lists (row items of the tile body, row items of the generic body,
+// Gram chunks, CUDA-core product tiles, tensor-core product tiles); counts to cnt[0..4];
+// *run = any problem active.  One block; problems in list order `order`.
+struct CompactArgs {
+  const int* order;
+  int nprob;
+  const Ctl* ctl;
+  const int2* full[4];
+  int2* comp[4];
+  const TcItem* tfull;
+  TcItem* tcomp;
+  const int* pst;   // [5][nprob]: first item of problem p in each full list
+  const int* psz;   // [5][nprob]: items of problem p in each list
+  int* cnt;
+  int* run;
+};
+
+__global__ void __launch_bounds__(1024) k_bcompact(CompactArgs ca) {
+  __shared__ int sc[5][1024];
+  const int tid = threadIdx.x;
+  const int per = (ca.nprob + 1023) / 1024;
+  const int i0 = min(ca.nprob, tid * per), i1 = min(ca.nprob, i0 + per);
+  int loc[5] = {0, 0, 0, 0, 0};
+  int any = 0;
+  for (int i = i0; i < i1; ++i) {
+    const int p = ca.order[i];
+    if (!ca.ctl[p].active) continue;
+    any = 1;
+    for (int L = 0; L < 5; ++L) loc[L] += ca.psz[L * ca.nprob + p];
+  }
+  for (int L = 0; L < 5; ++L) sc[L][tid] = loc[L];
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan
+    int v[5];
+    for (int L = 0; L < 5; ++L) v[L] = tid >= off ? sc[L][tid - off] : 0;
+    __syncthreads();
+    for (int L = 0; L < 5; ++L) sc[L][tid] += v[L];
+    __syncthreads();
+  }
+  int pos[5];
+  for (int L = 0; L < 5; ++L) pos[L] = sc[L][tid] - loc[L];
+  for (int i = i0; i < i1; ++i) {
+    const int p = ca.order[i];
+    if (!ca.ctl[p].active) continue;
+    for (int L = 0; L < 5; ++L) {
+      const int st = ca.pst[L * ca.nprob + p], sz = ca.psz[L * ca.nprob + p];
+      for (int t = 0; t < sz; ++t) {
+        if (L < 4) ca.comp[L][pos[L] + t] = ca.full[L][st + t];
+        else ca.tcomp[pos[L] + t] = ca.tfull[st + t];
+      }
+      pos[L] += sz;
+    }
+  }
+  any = __syncthreads_or(any);
+  if (tid == 1023)
+    for (int L = 0; L < 5; ++L) ca.cnt[L] = sc[L][1023];
+  if (tid == 0) *ca.run = any;
+}
+
 
 // final per-problem statistics (one warp per problem); tc: the product partials are per
 // tensor-core item
@@ -321,7 +407,9 @@ struct BatchCtx {
   size_t esz = 4;
   std::vector<BProb> hp;
   BProb* dp = nullptr;
-  std::vector<int2> h_row, h_prod, h_gram;
+  std::vector<int2> h_row, h_rowg, h_prod, h_gram;  // row items: tile body (r <= 32) / generic
+  int2* it_rowg = nullptr;
+  int nslot = 0;
   std::vector<TcItem> h_tc;        // BF16: tensor-core product items
   TcItem* it_tc = nullptr;
   void *xh = nullptr, *xl = nullptr;  // BF16 hi / lo parts of the product operand (transposed)
@@ -330,6 +418,13 @@ struct BatchCtx {
   long long budget = 2000000000LL;
   int tc_fail = 0;
   int2 *it_row = nullptr, *it_prod = nullptr, *it_gram = nullptr;
+  // compacted lists of the active problems (rebuilt by k_bcompact), per-problem ranges in the
+  // full lists, counts (cnt_full: constant full sizes; cnt_act: compacted)
+  int2 *c_row = nullptr, *c_rowg = nullptr, *c_gram = nullptr, *c_prod = nullptr;
+  TcItem* c_tc = nullptr;
+  int *pst = nullptr, *psz = nullptr, *d_order = nullptr, *cnt_full = nullptr, *cnt_act = nullptr;
+  std::vector<int> order;
+  bool use_full = false;  // launches being recorded cover every problem (final evaluation)
   int64_t lda = 0, rows_total = 0, xtot = 0;
   void* A = nullptr;
   void* buf[XB_N] = {};
@@ -393,28 +488,41 @@ Params bparams(const BatchCtx* b) {
 int row_bm(const BatchCtx* b) { return b->tdtype == 0 ? 32 : 64; }
 
 // ---- grouped launches -------------------------------------------------------------------
+// list L (0 row tile body, 1 row generic body, 2 Gram, 3 CUDA-core product, 4 tensor-core
+// product) and its device count for the launches being recorded
+const int* bcnt(const BatchCtx* b, int L) { return (b->use_full ? b->cnt_full : b->cnt_act) + L; }
+const int2* blist(const BatchCtx* b, int L) {
+  if (L == 0) return b->use_full ? b->it_row : b->c_row;
+  if (L == 1) return b->use_full ? b->it_rowg : b->c_rowg;
+  if (L == 2) return b->use_full ? b->it_gram : b->c_gram;
+  return b->use_full ? b->it_prod : b->c_prod;
+}
+
 void bprod(BatchCtx* b, const void* X, void* Y, const void* P1, double* part, const Ctl* ctl, const int* run) {
   const unsigned g = (unsigned)b->h_prod.size();
   if (b->a_dtype == 2) {
     // tcgen05: X_p split into BF16 hi / lo parts (transposed), then one CTA per 128-row tile
     const int nt = (int)b->h_tc.size();
-    launch_bsplit_x(b->it_tc, nt, (const float*)X, b->xh, b->xl, b->lda, ctl, sizeof(Ctl), offsetof(Ctl, active),
-                    run, b->s);
-    if (launch_bgemm_tc(b->A, b->lda, b->rows_total, b->xh, b->xl, b->xt_rows, b->it_tc, nt, (const float*)X,
+    const TcItem* tl = b->use_full ? b->it_tc : b->c_tc;
+    launch_bsplit_x(tl, nt, bcnt(b, 4), (const float*)X, b->xh, b->xl, b->lda, ctl, sizeof(Ctl),
+                    offsetof(Ctl, active), run, b->s);
+    if (launch_bgemm_tc(b->A, b->lda, b->rows_total, b->xh, b->xl, b->xt_rows, tl, nt, bcnt(b, 4), (const float*)X,
                         (float*)Y, 1, (const float*)P1, part, kNQ, ctl, sizeof(Ctl), offsetof(Ctl, active), run,
                         b->dev_err, b->budget, b->s) < 0)
       b->tc_fail = tc_last_status() ? tc_last_status() : -1;
     return;
   }
+  const int2* il = blist(b, 3);
+  const int* c = bcnt(b, 3);
   if (b->tdtype == 0)
-    k_bgemm<double, double><<<g, 256, 0, b->s>>>((const double*)b->A, b->lda, b->dp, b->it_prod, (const double*)X,
+    k_bgemm<double, double><<<g, 256, 0, b->s>>>((const double*)b->A, b->lda, b->dp, il, c, (const double*)X,
                                                  (double*)Y, 1, (const double*)P1, part, ctl, run);
   else if (b->a_dtype == 2)
-    k_bgemm<float, __nv_bfloat16><<<g, 256, 0, b->s>>>((const __nv_bfloat16*)b->A, b->lda, b->dp, b->it_prod,
+    k_bgemm<float, __nv_bfloat16><<<g, 256, 0, b->s>>>((const __nv_bfloat16*)b->A, b->lda, b->dp, il, c,
                                                        (const float*)X, (float*)Y, 1, (const float*)P1, part,
                                                        ctl, run);
   else
-    k_bgemm<float, float><<<g, 256, 0, b->s>>>((const float*)b->A, b->lda, b->dp, b->it_prod, (const float*)X,
+    k_bgemm<float, float><<<g, 256, 0, b->s>>>((const float*)b->A, b->lda, b->dp, il, c, (const float*)X,
                                                (float*)Y, 1, (const float*)P1, part, ctl, run);
 }
 
@@ -423,13 +531,13 @@ void bgram(BatchCtx* b, const void* X, const void* Y, int pair, int npairs, cons
   const unsigned g = (unsigned)b->h_gram.size();
   const int it = b->opt.power_iters;
   if (b->tdtype == 0)
-    k_bgram<double><<<g, 256, 0, b->s>>>(b->dp, b->it_gram, (const double*)X, (const double*)Y, b->gpart, pair,
-                                         npairs, ctl, run, G64, (double*)GT, tpair, use_lam, b->counters,
-                                         nullptr, it);
+    k_bgram<double><<<g, 256, 0, b->s>>>(b->dp, blist(b, 2), bcnt(b, 2), (const double*)X, (const double*)Y,
+                                         b->gpart, pair, npairs, ctl, run, G64, (double*)GT, tpair, use_lam,
+                                         b->counters, nullptr, it);
   else
-    k_bgram<float><<<g, 256, 0, b->s>>>(b->dp, b->it_gram, (const float*)X, (const float*)Y, b->gpart, pair,
-                                        npairs, ctl, run, G64, (float*)GT, tpair, use_lam, b->counters,
-                                        rho_ctl, it);
+    k_bgram<float><<<g, 256, 0, b->s>>>(b->dp, blist(b, 2), bcnt(b, 2), (const float*)X, (const float*)Y,
+                                        b->gpart, pair, npairs, ctl, run, G64, (float*)GT, tpair, use_lam,
+                                        b->counters, rho_ctl, it);
   if (b->tdtype == 0 && rho_ctl)
     k_brho<double><<<b->nprob, 256, 0, b->s>>>(b->dp, G64, it, rho_ctl);
 }
@@ -446,9 +554,31 @@ RowArgs brow_base(BatchCtx* b, const Params& P) {
   return a;
 }
 
+template <typename T, int OP, int EPI, int NC>
+void launch_browt(BatchCtx* b, const RowArgs& a) {
+  static bool attr = false;
+  const size_t smem = rowtile_smem<T>(EPI == EPI_DIR ? 2 + NC : 2);
+  if (!attr) {
+    cudaFuncSetAttribute(k_browt<T, OP, EPI, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_browt<T, OP, EPI, NC><<<(unsigned)b->h_row.size(), 256, smem, b->s>>>(a, b->dp, blist(b, 0), bcnt(b, 0));
+}
+
 void brow(BatchCtx* b, int op, int epi, const RowArgs& a, int nc = 1) {
-  const unsigned g = (unsigned)b->h_row.size();
-#define BR(T, O, E, M, C) k_brow<T, O, E, M, C><<<g, 256, 0, b->s>>>(a, b->dp, b->it_row)
+  if (!b->h_row.empty()) {
+#define BT(T)                                                                    \
+    if (epi == EPI_GRAD) {                                                       \
+      if (op == OP_LOAD) launch_browt<T, OP_LOAD, EPI_GRAD, 1>(b, a);            \
+      else launch_browt<T, OP_UPD, EPI_GRAD, 1>(b, a);                           \
+    } else if (nc == 1) launch_browt<T, OP_ZSTEP, EPI_DIR, 1>(b, a);             \
+    else launch_browt<T, OP_ZSTEP, EPI_DIR, 2>(b, a);
+    if (b->tdtype == 0) { BT(double) } else { BT(float) }
+#undef BT
+  }
+  if (b->h_rowg.empty()) return;
+  const unsigned g = (unsigned)b->h_rowg.size();
+#define BR(T, O, E, M, C) k_brow<T, O, E, M, C><<<g, 256, 0, b->s>>>(a, b->dp, blist(b, 1), bcnt(b, 1))
 #define BR_T(T, M)                                                       \
   if (epi == EPI_GRAD) {                                                 \
     if (op == OP_LOAD) BR(T, OP_LOAD, EPI_GRAD, M, 1);                   \
@@ -460,7 +590,22 @@ void brow(BatchCtx* b, int op, int epi, const RowArgs& a, int nc = 1) {
 #undef BR
 }
 
-void bany(BatchCtx* b) { k_bany<<<1, 256, 0, b->s>>>(b->ctl, b->nprob, b->run); }
+// run flag and the compacted work lists of the problems still active
+void bany(BatchCtx* b) {
+  CompactArgs ca;
+  ca.order = b->d_order;
+  ca.nprob = b->nprob;
+  ca.ctl = b->ctl;
+  ca.full[0] = b->it_row; ca.full[1] = b->it_rowg; ca.full[2] = b->it_gram; ca.full[3] = b->it_prod;
+  ca.comp[0] = b->c_row; ca.comp[1] = b->c_rowg; ca.comp[2] = b->c_gram; ca.comp[3] = b->c_prod;
+  ca.tfull = b->it_tc;
+  ca.tcomp = b->c_tc;
+  ca.pst = b->pst;
+  ca.psz = b->psz;
+  ca.cnt = b->cnt_act;
+  ca.run = b->run;
+  k_bcompact<<<1, 1024, 0, b->s>>>(ca);
+}
 
 // one block of Algorithm 1 for all problems (penalty form; mirrors the single-problem path)
 void bpen_block(BatchCtx* b, int xv, int xf, bool is_w, const Params& P) {
@@ -521,7 +666,8 @@ void bpen_iteration(BatchCtx* b, const Params& P) {
 }
 
 void bpen_final(BatchCtx* b, const Params& P) {
-  // every problem contributes: no run flag, no active test
+  // every problem contributes: full work lists, no run flag, no active test
+  b->use_full = true;
   bprod(b, b->buf[XB_HT], b->buf[XB_B], b->buf[XB_W], b->pax, nullptr, nullptr);
   bgram(b, b->buf[XB_W], b->buf[XB_W], 0, 3, nullptr, nullptr, b->G64p, b->GT, 1, 1, nullptr);
   bgram(b, b->buf[XB_HT], b->buf[XB_HT], 1, 3, nullptr, nullptr, b->G64p, b->GT, 1, 1, nullptr);
@@ -533,6 +679,7 @@ void bpen_final(BatchCtx* b, const Params& P) {
   a.ctl_mode = CTL_NONE;
   brow(b, OP_LOAD, EPI_GRAD, a);
   k_bfinal<<<b->nprob, 32, 0, b->s>>>(b->ctl, b->pax, b->prow, b->G64p, b->dp, b->a_dtype == 2 ? 1 : 0);
+  b->use_full = false;
 }
 
 snmf_status sync_user_b(BatchCtx* b, std::string* err) {
@@ -615,7 +762,7 @@ snmf_status batch_create(BatchCtx** out, const snmf_matrix* Am, const snmf_optio
     BProb& q = b->hp[p];
     q.n = ns[p];
     q.r = (int)rs[p];
-    const int rows = rs[p] <= 32 ? small_rows((int)rs[p]) : bm;  // rows per row-kernel item
+    const int rows = rs[p] <= 32 ? (b->tdtype == 0 ? TileCfg<double>::TR : TileCfg<float>::TR) : bm;
     q.nrt = (int)((ns[p] + rows - 1) / rows);
     q.npt = (int)((ns[p] + kPBM - 1) / kPBM);
     q.gch = (int)((ns[p] + kGChunk - 1) / kGChunk);
@@ -635,10 +782,13 @@ snmf_status batch_create(BatchCtx** out, const snmf_matrix* Am, const snmf_optio
   std::vector<int> order(np);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ns[x] > ns[y]; });
+  int nslot = 0;
   for (int p : order) {
     BProb& q = b->hp[p];
-    q.slot0 = (int)b->h_row.size();
-    for (int t = 0; t < q.nrt; ++t) b->h_row.push_back(make_int2(p, t));
+    q.slot0 = nslot;
+    nslot += q.nrt;
+    std::vector<int2>& lst = q.r <= 32 ? b->h_row : b->h_rowg;
+    for (int t = 0; t < q.nrt; ++t) lst.push_back(make_int2(p, t));
     q.pslot0 = (int)b->h_prod.size();
     for (int t = 0; t < q.npt; ++t) b->h_prod.push_back(make_int2(p, t));
     for (int c = 0; c < q.gch; ++c) b->h_gram.push_back(make_int2(p, c));
@@ -675,10 +825,15 @@ snmf_status batch_create(BatchCtx** out, const snmf_matrix* Am, const snmf_optio
   CKB(cudaGetLastError());
   // ---- device tables and workspaces ----
   CKB(cudaMalloc(&b->dp, np * sizeof(BProb)));
-  CKB(cudaMalloc(&b->it_row, b->h_row.size() * sizeof(int2)));
+  b->nslot = nslot;
+  CKB(cudaMalloc(&b->it_row, std::max<size_t>(b->h_row.size(), 1) * sizeof(int2)));
+  CKB(cudaMalloc(&b->it_rowg, std::max<size_t>(b->h_rowg.size(), 1) * sizeof(int2)));
+  if (!b->h_rowg.empty())
+    CKB(cudaMemcpyAsync(b->it_rowg, b->h_rowg.data(), b->h_rowg.size() * sizeof(int2), cudaMemcpyHostToDevice, b->s));
   CKB(cudaMalloc(&b->it_prod, b->h_prod.size() * sizeof(int2)));
   CKB(cudaMalloc(&b->it_gram, b->h_gram.size() * sizeof(int2)));
-  CKB(cudaMemcpyAsync(b->it_row, b->h_row.data(), b->h_row.size() * sizeof(int2), cudaMemcpyHostToDevice, b->s));
+  if (!b->h_row.empty())
+    CKB(cudaMemcpyAsync(b->it_row, b->h_row.data(), b->h_row.size() * sizeof(int2), cudaMemcpyHostToDevice, b->s));
   CKB(cudaMemcpyAsync(b->it_prod, b->h_prod.data(), b->h_prod.size() * sizeof(int2), cudaMemcpyHostToDevice, b->s));
   CKB(cudaMemcpyAsync(b->it_gram, b->h_gram.data(), b->h_gram.size() * sizeof(int2), cudaMemcpyHostToDevice, b->s));
   CKB(cudaMemcpyAsync(b->dp, b->hp.data(), np * sizeof(BProb), cudaMemcpyHostToDevice, b->s));
@@ -686,7 +841,7 @@ snmf_status batch_create(BatchCtx** out, const snmf_matrix* Am, const snmf_optio
     CKB(cudaMalloc(&b->buf[x], (size_t)b->xtot * b->esz));
     CKB(cudaMemsetAsync(b->buf[x], 0, (size_t)b->xtot * b->esz, b->s));
   }
-  CKB(cudaMalloc(&b->prow, b->h_row.size() * kNQ * sizeof(double)));
+  CKB(cudaMalloc(&b->prow, (size_t)b->nslot * kNQ * sizeof(double)));
   CKB(cudaMalloc(&b->pax, b->h_prod.size() * kNQ * sizeof(double)));  // >= tensor-core items
   CKB(cudaMalloc(&b->dev_err, sizeof(int)));
   CKB(cudaMemsetAsync(b->dev_err, 0, sizeof(int), b->s));
@@ -774,6 +929,42 @@ snmf_status batch_create(BatchCtx** out, const snmf_matrix* Am, const snmf_optio
       CKB(cudaMemsetAsync(b->xl, 0, xb, b->s));
     }
     CKB(cudaMemcpyAsync(b->dp, b->hp.data(), np * sizeof(BProb), cudaMemcpyHostToDevice, b->s));
+    CKB(cudaStreamSynchronize(b->s));
+  }
+  // per-problem item ranges of every list (each list holds the problems in `order`),
+  // full counts, and the compacted copies (start as the full lists)
+  {
+    b->order = order;
+    std::vector<int> pst(5 * np, 0), psz(5 * np, 0);
+    auto fill = [&](int L, int i, int p) {
+      if (psz[L * np + p] == 0) pst[L * np + p] = i;
+      psz[L * np + p]++;
+    };
+    for (size_t i = 0; i < b->h_row.size(); ++i) fill(0, (int)i, b->h_row[i].x);
+    for (size_t i = 0; i < b->h_rowg.size(); ++i) fill(1, (int)i, b->h_rowg[i].x);
+    for (size_t i = 0; i < b->h_gram.size(); ++i) fill(2, (int)i, b->h_gram[i].x);
+    for (size_t i = 0; i < b->h_prod.size(); ++i) fill(3, (int)i, b->h_prod[i].x);
+    for (size_t i = 0; i < b->h_tc.size(); ++i) fill(4, (int)i, b->h_tc[i].prob);
+    const int cf[5] = {(int)b->h_row.size(), (int)b->h_rowg.size(), (int)b->h_gram.size(), (int)b->h_prod.size(),
+                       (int)b->h_tc.size()};
+    CKB(cudaMalloc(&b->pst, 5 * np * sizeof(int)));
+    CKB(cudaMalloc(&b->psz, 5 * np * sizeof(int)));
+    CKB(cudaMalloc(&b->d_order, np * sizeof(int)));
+    CKB(cudaMalloc(&b->cnt_full, 5 * sizeof(int)));
+    CKB(cudaMalloc(&b->cnt_act, 5 * sizeof(int)));
+    CKB(cudaMemcpyAsync(b->pst, pst.data(), 5 * np * sizeof(int), cudaMemcpyHostToDevice, b->s));
+    CKB(cudaMemcpyAsync(b->psz, psz.data(), 5 * np * sizeof(int), cudaMemcpyHostToDevice, b->s));
+    CKB(cudaMemcpyAsync(b->d_order, order.data(), np * sizeof(int), cudaMemcpyHostToDevice, b->s));
+    CKB(cudaMemcpyAsync(b->cnt_full, cf, 5 * sizeof(int), cudaMemcpyHostToDevice, b->s));
+    CKB(cudaMemcpyAsync(b->cnt_act, cf, 5 * sizeof(int), cudaMemcpyHostToDevice, b->s));
+    int2** comp[4] = {&b->c_row, &b->c_rowg, &b->c_gram, &b->c_prod};
+    const int2* full[4] = {b->it_row, b->it_rowg, b->it_gram, b->it_prod};
+    for (int L = 0; L < 4; ++L) {
+      CKB(cudaMalloc(comp[L], std::max(cf[L], 1) * sizeof(int2)));
+      if (cf[L]) CKB(cudaMemcpyAsync(*comp[L], full[L], cf[L] * sizeof(int2), cudaMemcpyDeviceToDevice, b->s));
+    }
+    CKB(cudaMalloc(&b->c_tc, std::max(cf[4], 1) * sizeof(TcItem)));
+    if (cf[4]) CKB(cudaMemcpyAsync(b->c_tc, b->it_tc, cf[4] * sizeof(TcItem), cudaMemcpyDeviceToDevice, b->s));
     CKB(cudaStreamSynchronize(b->s));
   }
 #undef CKB
@@ -923,10 +1114,12 @@ snmf_status batch_profile_ax(BatchCtx* b, int iters, double* ms, std::string* er
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
+  b->use_full = true;  // every problem
   bprod(b, b->buf[XB_W], b->buf[XB_Z], nullptr, nullptr, nullptr, nullptr);  // warm-up
   BCK(cudaEventRecord(e0, b->s));
   for (int t = 0; t < iters; ++t) bprod(b, b->buf[XB_W], b->buf[XB_Z], nullptr, nullptr, nullptr, nullptr);
   BCK(cudaEventRecord(e1, b->s));
+  b->use_full = false;
   BCK(cudaStreamSynchronize(b->s));
   BCK(cudaGetLastError());
   float m = 0.f;
@@ -963,6 +1156,10 @@ void batch_destroy(BatchCtx* b) {
   cudaFree(b->it_row);
   cudaFree(b->it_prod);
   cudaFree(b->it_gram);
+  cudaFree(b->it_rowg);
+  for (void* q : {(void*)b->c_row, (void*)b->c_rowg, (void*)b->c_gram, (void*)b->c_prod, (void*)b->c_tc,
+                  (void*)b->pst, (void*)b->psz, (void*)b->d_order, (void*)b->cnt_full, (void*)b->cnt_act})
+    cudaFree(q);
   cudaFree(b->it_tc);
   cudaFree(b->xh);
   cudaFree(b->xl);

@@ -6,6 +6,8 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "rowops.cuh"
 
@@ -525,47 +527,49 @@ gram_body(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, in
   const int tile_id = ((pair * b + j) * ntile + ti) * ntile + tj;
   if (threadIdx.x == 0) ticket = atomicAdd(&counters[tile_id], 1u);
   __syncthreads();
-  if (ticket != nch - 1) return;
-  // last CTA of this tile: fixed-order sum over the chunks
-  // each thread owns 16 tile entries and sums them over the chunks in chunk order, with
-  // the 16 loads of a chunk (and the next chunk's) in flight together
-  // nch: chunks of this tile
-  int64_t off_[16];
-  bool ok_[16];
-  T sacc[16];
+  if (ticket == nch - 1) {
+    // last CTA of this tile: fixed-order sum over the chunks
+    // each thread owns 16 tile entries and sums them over the chunks in chunk order, with
+    // the 16 loads of a chunk (and the next chunk's) in flight together
+    // nch: chunks of this tile
+    int64_t off_[16];
+    bool ok_[16];
+    T sacc[16];
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int e = threadIdx.x + 256 * u;
-    const int p = ti * 64 + (e >> 6), q = tj * 64 + (e & 63);
-    ok_[u] = (p < r && q < r);
-    off_[u] = tile_base + (int64_t)(ok_[u] ? p : 0) * r + (ok_[u] ? q : 0);
-    sacc[u] = T(0);
-  }
+    for (int u = 0; u < 16; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      const int p = ti * 64 + (e >> 6), q = tj * 64 + (e & 63);
+      ok_[u] = (p < r && q < r);
+      off_[u] = tile_base + (int64_t)(ok_[u] ? p : 0) * r + (ok_[u] ? q : 0);
+      sacc[u] = T(0);
+    }
 #pragma unroll 2
-  for (int c = 0; c < nch; ++c) {
-    T v[16];
+    for (int c = 0; c < nch; ++c) {
+      T v[16];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) v[u] = ok_[u] ? __ldcg(gp + (int64_t)c * slab + off_[u]) : T(0);
+      for (int u = 0; u < 16; ++u) v[u] = ok_[u] ? __ldcg(gp + (int64_t)c * slab + off_[u]) : T(0);
 #pragma unroll
-    for (int u = 0; u < 16; ++u) sacc[u] += v[u];
-  }
+      for (int u = 0; u < 16; ++u) sacc[u] += v[u];
+    }
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    if (!ok_[u]) continue;
-    const int e = threadIdx.x + 256 * u;
-    const int p = ti * 64 + (e >> 6), q = tj * 64 + (e & 63);
-    G64[off_[u]] = (double)sacc[u];
-    if (GT && pair == tpair) GT[(int64_t)j * rr2 + (int64_t)p * r + q] = sacc[u] + (p == q ? (T)lam_shift : T(0));
+    for (int u = 0; u < 16; ++u) {
+      if (!ok_[u]) continue;
+      const int e = threadIdx.x + 256 * u;
+      const int p = ti * 64 + (e >> 6), q = tj * 64 + (e & 63);
+      G64[off_[u]] = (double)sacc[u];
+      if (GT && pair == tpair) GT[(int64_t)j * rr2 + (int64_t)p * r + q] = sacc[u] + (p == q ? (T)lam_shift : T(0));
+    }
+    if (threadIdx.x == 0) counters[tile_id] = 0u;  // ready for the next launch
+    if (sizeof(T) == 4 && rho_ctl && ntile == 1 && pair == 0 && rho_ctl[j].active) {
+      // the restart's Gram is complete: rho = rho_scale ||G||_2 here (saves a launch)
+      __shared__ T vv[64], ww[64];
+      __shared__ T Gsr[64 * 64];
+      __shared__ double shr[8];
+      __syncthreads();
+      rho_body<T>(G64 + tile_base, r, rho_iters, rho_scale, rho_ctl[j], vv, ww, Gsr, shr);
+    }
   }
-  if (threadIdx.x == 0) counters[tile_id] = 0u;  // ready for the next launch
-  if (sizeof(T) == 4 && rho_ctl && ntile == 1 && pair == 0 && rho_ctl[j].active) {
-    // the restart's Gram is complete: rho = rho_scale ||G||_2 here (saves a launch)
-    __shared__ T vv[64], ww[64];
-    __shared__ T Gsr[64 * 64];
-    __shared__ double shr[8];
-    __syncthreads();
-    rho_body<T>(G64 + tile_base, r, rho_iters, rho_scale, rho_ctl[j], vv, ww, Gsr, shr);
-  }
+  __syncthreads();  // no early return: a CTA may run several items
 }
 
 // ------------------------------------------------------------------------------
@@ -838,43 +842,88 @@ __device__ __forceinline__ void rowgemm_body(const RowArgs& a, int j, int bx, in
 }
 
 // ------------------------------------------------------------------------------
-// Row GEMM for small ranks (r <= 32) with the same fused epilogues and partial layout as
-// rowgemm_body.  A warp is cut into segments of rp lanes (rp = r rounded up to a power of
-// two); segment s holds one row, lane c of it column c.  Column c of G lives in the lane's
-// registers and the row product sum_k x_k G[k][c] takes the x_k by shuffles within the
-// segment, so no shared-memory staging is needed and every lane does useful work for
-// r = 4 .. 32.  The CTA covers rows_cta = 8 warps x (32 / rp) rows x kSmallIters rows of
-// restart j starting at tile * rows_cta; `per` CTAs per restart.
+// Row GEMM for ranks r <= 32 through shared-memory tiles, with the same fused epilogues
+// and partial layout as rowgemm_body.  A CTA owns TR consecutive rows of restart j:
+//   1. the operand tile (X, Z = Proj[X - g/rho] or X' = Proj[Z + phi beta D]) is staged
+//      with element-contiguous (coalesced) loads; B and the inputs that the epilogue
+//      reads again are kept in registers,
+//   2. the row product X G: TPR threads per row, each CPT columns, G (stride 32, zero
+//      padded) read as 16-byte shared-memory broadcasts,
+//   3. the elementwise epilogue in the same element order as step 1 (coalesced), with
+//      D of each candidate staged for
+//   4. <D G, D> by a second row product.
+// The body has no early return and ends with a barrier.  sm: dynamic shared memory of
+// rowtile_smem bytes.
 // ------------------------------------------------------------------------------
-constexpr int kSmallIters = 4;
+template <typename T>
+struct TileCfg {
+  static constexpr int TR = sizeof(T) == 4 ? 128 : 64;  // rows per tile
+  static constexpr int TPR = 256 / TR;                   // threads per row in the row products
+  static constexpr int CPT = 32 / TPR;                   // columns per thread
+  static constexpr int RS = 33;                          // tile row stride (odd: conflict free)
+  static constexpr int EPT = TR * 32 / 256;              // elements per thread (r = 32)
+};
 
-__host__ __device__ inline int small_rp(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : (r <= 16 ? 16 : 32)); }
-__host__ __device__ inline int small_rows(int r) { return 8 * (32 / small_rp(r)) * kSmallIters; }
+template <typename T>
+__host__ __device__ inline size_t rowtile_smem(int ntile) {
+  return ((size_t)ntile * TileCfg<T>::TR * TileCfg<T>::RS + 32 * 32) * sizeof(T);
+}
+
+// y[u] = (row `row` of src) G[:, part*CPT + u], G (stride 32) read as 16-byte broadcasts
+template <typename T>
+__device__ __forceinline__ void tile_rowprod(const T* __restrict__ src, const T* __restrict__ Gs, int r, int row,
+                                             int part, T* y) {
+  using C = TileCfg<T>;
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int W = 16 / sizeof(T);  // elements per vector
+  constexpr int NVEC = C::CPT / W;
+#pragma unroll
+  for (int u = 0; u < C::CPT; ++u) y[u] = T(0);
+  const T* xr = src + row * C::RS;
+  const V* gc = reinterpret_cast<const V*>(Gs + part * C::CPT);
+#pragma unroll 2
+  for (int k = 0; k < r; ++k) {
+    const T x0 = xr[k];
+#pragma unroll
+    for (int v = 0; v < NVEC; ++v) {
+      const V g0 = gc[(k * 32) / W + v];
+      const T* a0 = reinterpret_cast<const T*>(&g0);
+#pragma unroll
+      for (int w = 0; w < W; ++w) y[v * W + w] = fma(x0, a0[w], y[v * W + w]);
+    }
+  }
+}
 
 template <typename T, int OP, int EPI, int NC>
-__device__ __forceinline__ void rowsmall_body(const RowArgs& a, int j, int tile, unsigned per) {
+__device__ __forceinline__ void rowtile_body(const RowArgs& a, int j, int tile, unsigned per, T* sm) {
+  using C = TileCfg<T>;
   constexpr int NV = 8;
-  static_assert(NC <= 2, "small-rank row body: at most two candidates");
+  static_assert(NC <= 2, "tile row body: at most two candidates");
   const int r = a.r;
-  const int rp = small_rp(r);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int seg = lane / rp, c = lane % rp, segbase = seg * rp;
-  const int step = 32 / rp;  // rows per warp instruction
   const int64_t ld = a.ld;
   const int64_t jc = (int64_t)j * r;
-  const int rows_cta = 8 * step * kSmallIters;
+  T* xs = sm;
+  T* ys = xs + C::TR * C::RS;
+  T* dsm = ys + C::TR * C::RS;                       // NC direction tiles (EPI_DIR)
+  T* Gs = dsm + (EPI == EPI_DIR ? NC : 0) * C::TR * C::RS;
   __shared__ T shq[NV][8];
+  __shared__ unsigned ticket;
   const Ctl& cj = a.ctl[j];
   const bool live = cj.active && !(a.run && *a.run == 0);
   T dq[NV];
 #pragma unroll
   for (int m = 0; m < NV; ++m) dq[m] = T(0);
   if (live) {
-    const bool cv = c < r;
+    const int tid = threadIdx.x;
+    const int64_t row0 = (int64_t)tile * C::TR;
+    const int rows = (int)(a.n - row0 < C::TR ? a.n - row0 : C::TR);
+    const int E = rows * r;
+    const float inv_r = 1.0f / (float)r;
     const T* G = (const T*)a.G + (int64_t)j * r * r;
-    T gcol[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) gcol[k] = (cv && k < r) ? G[k * r + c] : T(0);
+    for (int e = tid; e < 32 * 32; e += 256) {
+      const int k = e >> 5, c = e & 31;
+      Gs[e] = (k < r && c < r) ? G[k * r + c] : T(0);
+    }
     const T inv_rho = (T)(1.0 / cj.rho);
     const T pb = (T)cj.phibeta;
     const T* X = (const T*)a.X;
@@ -882,114 +931,122 @@ __device__ __forceinline__ void rowsmall_body(const RowArgs& a, int j, int tile,
     const T* Zin = (const T*)a.Zin;
     const T* Din = (const T*)((OP == OP_UPD && cj.dsel) ? a.Din2 : a.Din);
     const T* B = (const T*)a.B;
+    // inputs of step 1 that step 3 reads again (same buffers)
+    const bool w_is_x = OP == OP_ZSTEP && a.Wcur == a.X && a.gWcur == a.g_in;
+    const bool zold_is_z = OP == OP_UPD && a.Zold == a.Zin;
+    T in0[C::EPT], in1[C::EPT], bq[C::EPT];
+    // 1. operand tile (and B, so that the epilogue does not wait for it)
+#pragma unroll
+    for (int m = 0; m < C::EPT; ++m) {
+      const int e = tid + 256 * m;
+      in0[m] = in1[m] = bq[m] = T(0);
+      if (e < E) {
+        const int row = (int)(((float)e + 0.5f) * inv_r);  // exact for e < 2^12, r <= 32
+        const int col = e - row * r;
+        const int64_t q = (row0 + row) * ld + jc + col;
+        bq[m] = B[q];
+        T v;
+        if (OP == OP_LOAD) {
+          v = X[q];
+        } else if (OP == OP_ZSTEP) {
+          const T x = X[q], gi = gin[q];
+          const T t = x - gi * inv_rho;
+          v = t > T(0) ? t : T(0);
+          in0[m] = x;
+          in1[m] = gi;
+        } else {
+          const T z = Zin[q];
+          const T t = z + pb * Din[q];
+          v = t > T(0) ? t : T(0);
+          in0[m] = z;
+        }
+        xs[row * C::RS + col] = v;
+      }
+    }
+    __syncthreads();
+    // 2. Y = X G
+    const int prow = tid % C::TR, part = tid / C::TR;
+    if (part * C::CPT < r && prow < rows) {
+      T y[C::CPT];
+      tile_rowprod<T>(xs, Gs, r, prow, part, y);
+#pragma unroll
+      for (int u = 0; u < C::CPT; ++u)
+        if (part * C::CPT + u < r) ys[prow * C::RS + part * C::CPT + u] = y[u];
+    }
+    __syncthreads();
+    // 3. elementwise epilogue
     T alph[NC];
 #pragma unroll
     for (int m = 0; m < NC; ++m) alph[m] = (T)(NC == 1 ? cj.alpha : cj.cand_alpha[m]);
-    // products of the segments' rows with column c of G, kSmallIters rows interleaved
-    // (every lane of the warp takes part in the shuffles)
-    auto rowprod = [&](const T* v, T* y) {
 #pragma unroll
-      for (int u = 0; u < kSmallIters; ++u) y[u] = T(0);
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        if (k < rp) {
-#pragma unroll
-          for (int u = 0; u < kSmallIters; ++u) {
-            const T xk = __shfl_sync(0xffffffffu, v[u], segbase + k);
-            y[u] = fma(xk, gcol[k], y[u]);
-          }
-        }
-      }
-    };
-    // Loads of all kSmallIters rows first (the stores below may alias some inputs, e.g.
-    // Xout and Xold, so keeping them apart lets every load be in flight at once), then the
-    // row products, then the epilogue and the stores.
-    const int64_t row0 = (int64_t)tile * rows_cta;
-    constexpr int IT = kSmallIters;
-    int64_t idx[IT];
-    bool ev[IT];
-    T xv[IT], bv[IT], e0[IT], e1[IT], e2[IT], e3[IT];
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int64_t i = row0 + ((int64_t)it * 8 + wid) * step + seg;
-      ev[it] = cv && i < a.n;
-      idx[it] = i * ld + jc + c;
-      xv[it] = bv[it] = e0[it] = e1[it] = e2[it] = e3[it] = T(0);
-      if (ev[it]) {
-        const int64_t q = idx[it];
-        if (OP == OP_LOAD) xv[it] = X[q];
-        else if (OP == OP_ZSTEP) { const T v = X[q] - gin[q] * inv_rho; xv[it] = v > T(0) ? v : T(0); }
-        else { const T v = Zin[q] + pb * Din[q]; xv[it] = v > T(0) ? v : T(0); }
-        bv[it] = B[q];
-        if (EPI == EPI_GRAD) {
-          if (a.Xold) { e0[it] = ((const T*)a.Xold)[q]; e1[it] = ((const T*)a.gold)[q]; }
-          if (a.Zold) { e2[it] = ((const T*)a.Zold)[q]; e3[it] = ((const T*)a.gZold)[q]; }
-        } else if (a.Wcur) {
-          e0[it] = ((const T*)a.Wcur)[q];
-          e1[it] = ((const T*)a.gWcur)[q];
-        }
-      }
-    }
-    T g[IT];
-    rowprod(xv, g);
-#pragma unroll
-    for (int it = 0; it < IT; ++it) g[it] = ev[it] ? g[it] - bv[it] : T(0);
-    if (EPI == EPI_DIR) {
-      // directions of every candidate, then <D_m G, D_m> with the rows interleaved
-#pragma unroll
-      for (int m = 0; m < NC; ++m) {
-        T d[IT];
-#pragma unroll
-        for (int it = 0; it < IT; ++it) {
-          d[it] = T(0);
-          if (ev[it]) {
-            const T t = xv[it] - alph[m] * g[it];
-            d[it] = (t > T(0) ? t : T(0)) - xv[it];
-            if (m == a.dstore) ((T*)a.Dout)[idx[it]] = d[it];
-            if (NC == 2 && m == 1) ((T*)a.D2out)[idx[it]] = d[it];
-            const int base = m == 0 ? 0 : 5;
-            dq[base] += g[it] * d[it];
-            dq[base + 1] += d[it] * d[it];
-          }
-        }
-        if (a.want_q) {
-          T dg[IT];
-          rowprod(d, dg);  // (D_m G)_c
-#pragma unroll
-          for (int it = 0; it < IT; ++it) dq[m == 0 ? 4 : 7] += dg[it] * d[it];
-        }
-      }
-    }
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int64_t q = idx[it];
+    for (int m = 0; m < C::EPT; ++m) {
+      const int e = tid + 256 * m;
+      if (e >= E) continue;
+      const int row = (int)(((float)e + 0.5f) * inv_r);
+      const int col = e - row * r;
+      const int64_t q = (row0 + row) * ld + jc + col;
+      const int se = row * C::RS + col;
+      const T xv = xs[se];
+      const T g = ys[se] - bq[m];
       if (EPI == EPI_GRAD) {
-        if (ev[it]) {
-          const T gg = g[it], x = xv[it];
-          const T pgv = x > T(0) ? gg : (gg < T(0) ? gg : T(0));
-          dq[0] += pgv * pgv;
-          dq[1] += T(0.5) * (gg - bv[it]) * x;
-          if (a.Xold) {
-            const T sv = x - e0[it];
-            const T yv = gg - e1[it];
-            dq[2] += sv * sv;
-            dq[3] += sv * yv;
-            dq[4] += yv * yv;
-          }
-          if (a.Zold) dq[5] += T(0.5) * (x - e2[it]) * (gg + e3[it]);
-          if (x == T(0)) dq[6] += T(1);
-          if (a.gout) ((T*)a.gout)[q] = gg;
-          if (a.Xout) ((T*)a.Xout)[q] = x;
+        const T pgv = xv > T(0) ? g : (g < T(0) ? g : T(0));
+        dq[0] += pgv * pgv;
+        dq[1] += T(0.5) * (g - bq[m]) * xv;
+        if (a.Xold) {
+          const T sv = xv - ((const T*)a.Xold)[q];
+          const T yv = g - ((const T*)a.gold)[q];
+          dq[2] += sv * sv;
+          dq[3] += sv * yv;
+          dq[4] += yv * yv;
         }
-      } else if (ev[it]) {  // EPI_DIR: Z, its gradient, the f(Z) - f(W) increment
-        const T gg = g[it], x = xv[it];
-        if (a.Xout) ((T*)a.Xout)[q] = x;
-        if (a.gZout) ((T*)a.gZout)[q] = gg;
-        if (a.Wcur) dq[2] += T(0.5) * (x - e0[it]) * (gg + e1[it]);
+        if (a.Zold) {
+          const T zo = zold_is_z ? in0[m] : ((const T*)a.Zold)[q];
+          dq[5] += T(0.5) * (xv - zo) * (g + ((const T*)a.gZold)[q]);
+        }
+        if (xv == T(0)) dq[6] += T(1);
+        if (a.gout) ((T*)a.gout)[q] = g;
+        if (a.Xout) ((T*)a.Xout)[q] = xv;
+      } else {  // EPI_DIR
+        if (a.Xout) ((T*)a.Xout)[q] = xv;
+        if (a.gZout) ((T*)a.gZout)[q] = g;
+        if (a.Wcur) {
+          const T wv = w_is_x ? in0[m] : ((const T*)a.Wcur)[q];
+          const T gw = w_is_x ? in1[m] : ((const T*)a.gWcur)[q];
+          dq[2] += T(0.5) * (xv - wv) * (g + gw);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          T d = xv - alph[c] * g;
+          d = (d > T(0) ? d : T(0)) - xv;
+          if (c == a.dstore) ((T*)a.Dout)[q] = d;
+          if (NC == 2 && c == 1) ((T*)a.D2out)[q] = d;
+          const int base = c == 0 ? 0 : 5;
+          dq[base] += g * d;
+          dq[base + 1] += d * d;
+          dsm[c * C::TR * C::RS + se] = d;
+        }
+      }
+    }
+    // 4. <D_c G, D_c>
+    if (EPI == EPI_DIR && a.want_q) {
+      __syncthreads();
+      if (part * C::CPT < r && prow < rows) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const T* dt = dsm + c * C::TR * C::RS;
+          T y[C::CPT];
+          tile_rowprod<T>(dt, Gs, r, prow, part, y);
+          T qq = T(0);
+#pragma unroll
+          for (int u = 0; u < C::CPT; ++u)
+            if (part * C::CPT + u < r) qq += y[u] * dt[prow * C::RS + part * C::CPT + u];
+          dq[c == 0 ? 4 : 7] += qq;
+        }
       }
     }
   }
   // one combined fixed-order reduction of the partial dots
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int m = 0; m < NV; ++m) {
     const T v = warp_sum(dq[m]);
@@ -1003,7 +1060,6 @@ __device__ __forceinline__ void rowsmall_body(const RowArgs& a, int j, int tile,
     a.part[((int64_t)tile * a.b + j) * kNQ + threadIdx.x] = (double)v;
   }
   if (a.ctl_mode) {
-    __shared__ unsigned ticket;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) ticket = atomicAdd(&a.counters[j], 1u);
@@ -1015,6 +1071,7 @@ __device__ __forceinline__ void rowsmall_body(const RowArgs& a, int j, int tile,
                       nullptr, NC);
     }
   }
+  __syncthreads();  // shared memory free for a following item
 }
 
 }  // namespace
