@@ -274,7 +274,9 @@ def run_uneven(args):
     S.snmf_destroy(h)
     peaks, peak_kind = measured_peaks()
     gbs = alg_bytes / (ms_prod * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_bgemm (grouped A_p X_p, CUDA cores, %s A)" % args.precision,
+    kname = ("k_bsplit_x + k_bgemm_tc (grouped tcgen05 A_p (X_hi + X_lo), BF16 A)" if args.precision == "bf16"
+             else "k_bgemm (grouped A_p X_p, CUDA cores, %s A)" % args.precision)
+    roof = {"bound": "hbm", "kernel": kname,
             "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
             "traffic": None, "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
             "flops_per_launch": flops, "tflops": flops / (ms_prod * 1e-3) / 1e12, "ms_per_launch": ms_prod}
