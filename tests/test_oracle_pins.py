@@ -360,3 +360,44 @@ def test_mlp_oracle_gradient_finite_differences():
         assert abs(fd - grad[idx]) <= 1e-6 * max(1.0, abs(fd)), (idx, fd, grad[idx])
     # zero weights: o = 0, multiplier 1
     assert np.allclose(M.multiplier(np.zeros(M.N_PARAMS), phi), 1.0)
+
+
+def test_fp8_e4m3_codec_pins():
+    """E4M3 from its definition: known codes, the saturation bound, round trip of every
+    finite code, ties to even, the half-ulp error bound, and the tile-scale rule."""
+    import oracle.fp8 as F
+    assert F.decode_e4m3(0x00) == 0.0
+    assert F.decode_e4m3(0x01) == 2.0 ** -9          # smallest subnormal
+    assert F.decode_e4m3(0x08) == 2.0 ** -6          # smallest normal
+    assert F.decode_e4m3(0x38) == 1.0
+    assert F.decode_e4m3(0x7E) == 448.0              # largest finite
+    assert F.decode_e4m3(0xB8) == -1.0
+    assert math.isnan(F.decode_e4m3(0x7F)) and math.isnan(F.decode_e4m3(0xFF))
+    vals = F.table()
+    fin = np.isfinite(vals)
+    assert np.sum(fin) == 254 and np.all(np.diff(vals[:0x7F]) > 0)
+    codes = np.arange(256)[fin]
+    expect = np.where(vals[fin] == 0, 0, codes).astype(np.uint8)   # -0 encodes as +0
+    assert np.array_equal(F.encode_e4m3(vals[fin]), expect)
+    # ties go to the even code: 1.0625 between 1.0 (0x38) and 1.125 (0x39) -> 1.0;
+    # 1.1875 between 1.125 (0x39) and 1.25 (0x3A) -> 1.25
+    assert F.encode_e4m3(np.array([1.0625, 1.1875]))[0] == 0x38
+    assert F.encode_e4m3(np.array([1.0625, 1.1875]))[1] == 0x3A
+    assert F.encode_e4m3(np.array([1e6]))[0] == 0x7E   # saturates
+    g = np.random.default_rng(3)
+    x = np.exp(g.uniform(np.log(2.0 ** -6), np.log(448.0), 10000))
+    q = vals[F.encode_e4m3(x)]
+    assert np.max(np.abs(q - x) / x) <= 2.0 ** -4 + 1e-15   # half an ulp of a 3-bit mantissa
+    A = np.abs(g.normal(0, 3.0, (300, 260)))
+    A[:128, 128:256] = 0.0                               # an all-zero tile
+    codes_, S, At = F.quantize(A)
+    assert S.shape == (3, 3) and S[0, 1] == 1.0
+    for i in range(3):
+        for j in range(3):
+            m = A[i * 128:(i + 1) * 128, j * 128:(j + 1) * 128].max()
+            if m > 0:
+                assert 224.0 < m / S[i, j] <= 448.0 and math.log2(S[i, j]).is_integer()
+    Sf = np.repeat(np.repeat(S, 128, 0), 128, 1)[:300, :260]
+    normal = A / Sf >= 2.0 ** -6
+    assert np.all(np.abs(At - A)[normal] <= 2.0 ** -4 * A[normal] * (1 + 1e-12))
+    assert np.all(np.abs(At - A)[~normal] <= 2.0 ** -10 * Sf[~normal] * (1 + 1e-12))
