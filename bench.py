@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--n", type=int, default=8192)
     p.add_argument("--r", type=int, default=64)
     p.add_argument("--batch", type=int, default=1)
-    p.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
+    p.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16", "fp8"])
     p.add_argument("--formulation", default="penalty", choices=["penalty", "direct"])
     p.add_argument("--max-iter", type=int, default=500)
     p.add_argument("--tol", type=float, default=1e-4)
@@ -230,7 +230,7 @@ def run_uneven(args):
     W0 = torch.tensor(np.concatenate([W.ravel() for _, W, _ in probs]), dtype=torch.float32, device=dev)
     W = torch.empty_like(W0)
     H = torch.empty_like(W0)
-    prec = {"f64": S.SNMF_F64, "f32": S.SNMF_F32, "bf16": S.SNMF_BF16}[args.precision]
+    prec = {"f64": S.SNMF_F64, "f32": S.SNMF_F32, "bf16": S.SNMF_BF16, "fp8": S.SNMF_FP8}[args.precision]
     weights = controller_weights(args)
     ctl = 1 if weights is not None else 0
     stream = torch.cuda.current_stream(dev)
@@ -399,7 +399,7 @@ def main():
     dev = torch.device("cuda", local)
     S.load_library()
 
-    prec = {"f64": S.SNMF_F64, "f32": S.SNMF_F32, "bf16": S.SNMF_BF16}[args.precision]
+    prec = {"f64": S.SNMF_F64, "f32": S.SNMF_F32, "bf16": S.SNMF_BF16, "fp8": S.SNMF_FP8}[args.precision]
     tdt = torch.float64 if args.precision == "f64" else torch.float32
     A_np, starts = dense_planted_8192(args.r, args.batch + rank * args.batch, n=args.n)
     starts = starts[rank * args.batch:(rank + 1) * args.batch]  # replicas: own restarts per rank
@@ -413,7 +413,7 @@ def main():
                                   tol=args.tol, nonmonotone_M=10)
     stream = torch.cuda.current_stream(dev)
     h = S.snmf_create(S.dense_matrix(A), args.r, opts, stream=stream)
-    a_bytes = A.numel() * (2 if args.precision == "bf16" else A.element_size())
+    a_bytes = A.numel() * {"bf16": 2, "fp8": 1}.get(args.precision, A.element_size())
     flush = None if a_bytes > 2 * L2_BYTES else torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def step():
@@ -456,7 +456,7 @@ def main():
     ms_prod, ms_kern = S.snmf_profile_ax(h, 20)
     n, N = args.n, args.r * args.batch
     esz = 8 if args.precision == "f64" else 4
-    a_esz = 2 if args.precision == "bf16" else esz
+    a_esz = {"bf16": 2, "fp8": 1}.get(args.precision, esz)
     alg_bytes = n * n * a_esz + 2 * n * N * esz
     flops = 2.0 * n * n * N
     peaks, peak_kind = measured_peaks()
@@ -464,8 +464,10 @@ def main():
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12  # TFLOP/s at max clock
     achieved_tflops = flops / (ms_kern * 1e-3) / 1e12 if ms_kern > 0 else None
     aw_gbs = alg_bytes / (ms_kern * 1e-3) / 1e9 if ms_kern > 0 else None
-    if args.precision == "f32":
-        roof = {"bound": "alu", "kernel": "k_gemm_dense<float> (CUDA-core FFMA)", "achieved": achieved_tflops,
+    if args.precision in ("f32", "fp8"):
+        kn = "k_gemm_dense<float> (CUDA-core FFMA)" if args.precision == "f32" else \
+            "k_gemm_fp8 (E4M3 codes decoded in registers, CUDA-core FFMA)"
+        roof = {"bound": "alu", "kernel": kn, "achieved": achieved_tflops,
                 "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak if achieved_tflops else None,
                 "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "aw_gbs": aw_gbs, "aw_hbm_frac": aw_gbs / peaks["hbm_gbs"] if aw_gbs else None,

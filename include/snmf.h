@@ -107,7 +107,10 @@ typedef struct {
   int32_t formulation;     /* SNMF_PENALTY (Sec. 2.1, default) | SNMF_DIRECT (Eq. (2))       */
   int32_t precision;       /* SNMF_F64 | SNMF_F32 (default) | SNMF_BF16 | SNMF_FP8: storage of A
                               for the A*X products; accumulation is FP32 (FP64 in SNMF_F64) and
-                              objective, line search and BB inner products are FP64 throughout */
+                              objective, line search and BB inner products are FP64 throughout.
+                              SNMF_FP8 (dense only): E4M3 codes of A / s_t with a power-of-two
+                              scale s_t per 128 x 128 tile (the smallest 2^k with
+                              max|A_t| / 2^k <= 448), round to nearest even, saturating   */
   int32_t batch;           /* b random restarts sharing A (columns r*b), default 1            */
   int32_t nonmonotone_M;   /* 0: eta averaging of Alg. 1 line 4; M > 0: max of the last M
                               objective values (M <= 64).  Default 10                          */

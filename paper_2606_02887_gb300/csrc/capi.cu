@@ -17,6 +17,7 @@
 #include "../../include/snmf.h"
 #include "ax_tc.cuh"
 #include "batch.cuh"
+#include "fp8.cuh"
 #include "common.cuh"
 #include "lai.cuh"
 #include "rowops.cuh"
@@ -46,6 +47,7 @@ struct snmf_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evsync = nullptr;
   AxArgs A{};
   void* A_owned = nullptr;
+  float* A_scale = nullptr;      // FP8: per-tile scales
   int32_t* rowptr_owned = nullptr;
   int32_t* colidx_owned = nullptr;
   void* vals_owned = nullptr;
@@ -152,6 +154,9 @@ Dims dims(const snmf_ctx* h) {
 // The product kernel alone: CUDA cores (FP64/FP32 dense, CSR) or tcgen05 (BF16 dense).
 // Returns the number of split-K slices written to h->ws (1 = result in Y).
 int product_kernel(snmf_ctx* h, const AxArgs& op, const void* X, void* Y, const int* run) {
+  if (op.kind == AX_DENSE && op.a_dtype == 3)
+    return launch_ax_fp8(op.A, op.a_scale, h->n, (const float*)X, h->N, h->N, (float*)Y, (float*)h->ws,
+                         h->ws_elems, run, h->s);
   if (op.kind == AX_DENSE && op.a_dtype == 2) {
     const int sp = launch_ax_tc(op.A, h->n, (const float*)X, h->N, h->N, h->xh, h->xl, (float*)Y,
                                 (float*)h->ws, h->ws_elems, h->dev_err, h->budget, h->s);
@@ -558,8 +563,6 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
     if (o.precision == SNMF_BF16 || o.precision == SNMF_FP8)
       return fail(nullptr, SNMF_ERR_ARG, "CSR supports F64/F32 precision");
   }
-  if (o.precision == SNMF_FP8)
-    return fail(nullptr, SNMF_ERR_ARG, "FP8 precision not available in this build");
   if (o.step_controller && (o.formulation != SNMF_PENALTY || r > 64))
     return fail(nullptr, SNMF_ERR_ARG, "the step controller needs the penalty form and r <= 64");
 
@@ -601,7 +604,30 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   if (sync_user(h) != SNMF_OK) return bail(SNMF_ERR_CUDA);
   const int src_dt = Am->dtype == SNMF_F64 ? 0 : 1;
   const int64_t n = h->n;
-  if (h->kind == AX_DENSE && o.precision == SNMF_BF16) {
+  if (h->kind == AX_DENSE && o.precision == SNMF_FP8) {
+    // owned E4M3 codes with a power-of-two scale per 128 x 128 tile
+    const void* src = Am->values;
+    void* staging = nullptr;
+    const size_t sbytes = (size_t)n * Am->ld * (src_dt == 0 ? 8 : 4);
+    if (Am->location == SNMF_ON_HOST) {
+      CKC(cudaMalloc(&staging, sbytes));
+      CKC(cudaMemcpyAsync(staging, src, sbytes, cudaMemcpyHostToDevice, h->s));
+      src = staging;
+    }
+    const int nt = fp8_ntiles(n);
+    CKC(cudaMalloc(&h->A_owned, (size_t)n * fp8_ld(n)));
+    CKC(cudaMalloc(&h->A_scale, (size_t)nt * nt * sizeof(float)));
+    launch_fp8_encode(src_dt, src, n, Am->ld, h->A_owned, h->A_scale, h->s);
+    if (staging) {
+      CKC(cudaStreamSynchronize(h->s));
+      cudaFree(staging);
+    }
+    h->A.A = h->A_owned;
+    h->A.lda = fp8_ld(n);
+    h->A.a_dtype = 3;
+    h->A.a_scale = h->A_scale;
+    h->A.kind = AX_DENSE;
+  } else if (h->kind == AX_DENSE && o.precision == SNMF_BF16) {
     // owned BF16 copy, K-major with columns padded to a multiple of 64 (tensor-core layout)
     const void* src = Am->values;
     void* staging = nullptr;
@@ -708,7 +734,10 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
     CKC(cudaMemsetAsync(h->rec_count, 0, sizeof(int), h->s));
   }
   // ||A||_F^2 and mean(A) of the stored operator
-  if (h->kind == AX_DENSE && h->A.a_dtype == 2) {
+  if (h->kind == AX_DENSE && h->A.a_dtype == 3) {
+    const int nb = launch_fp8_sums(h->A.A, n, h->A.a_scale, h->dsc + 16, h->s);  // ||A~||^2 of the stored values
+    launch_sum_pairs(h->dsc + 16, nb, h->dsc, h->s);
+  } else if (h->kind == AX_DENSE && h->A.a_dtype == 2) {
     const int nb = launch_sums_bf16(h->A.A, n * h->A.lda, h->dsc + 16, h->s);  // ||A~||^2 of the stored values
     launch_sum_pairs(h->dsc + 16, nb, h->dsc, h->s);
   } else if (h->kind == AX_DENSE)
@@ -1079,6 +1108,7 @@ snmf_status snmf_destroy(snmf_handle h) {
   cudaFree(h->rec_count);
   if (h->h_flag) cudaFreeHost(h->h_flag);
   cudaFree(h->A_owned);
+  cudaFree(h->A_scale);
   cudaFree(h->rowptr_owned);
   cudaFree(h->colidx_owned);
   cudaFree(h->vals_owned);
