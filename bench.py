@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--controller", default="auto", choices=["auto", "off", "on"],
                    help="learned step controller (auto: on when trained weights are present)")
     p.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparison runs")
+    p.add_argument("--autotune", type=int, default=1, help="dense workload: tune the product at create")
+    p.add_argument("--tune-cache", default=None, help="JSON cache of tuned configurations")
     return p.parse_args()
 
 
@@ -410,9 +412,11 @@ def main():
     H = torch.empty_like(W0)
     form = S.SNMF_PENALTY if args.formulation == "penalty" else S.SNMF_DIRECT
     opts = S.snmf_default_options(precision=prec, formulation=form, batch=args.batch, max_iter=args.max_iter,
-                                  tol=args.tol, nonmonotone_M=10)
+                                  tol=args.tol, nonmonotone_M=10, autotune=args.autotune,
+                                  tune_cache=args.tune_cache)
     stream = torch.cuda.current_stream(dev)
     h = S.snmf_create(S.dense_matrix(A), args.r, opts, stream=stream)
+    tuning = S.snmf_tuned_config(h) if args.autotune else None
     a_bytes = A.numel() * {"bf16": 2, "fp8": 1}.get(args.precision, A.element_size())
     flush = None if a_bytes > 2 * L2_BYTES else torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
@@ -534,7 +538,7 @@ def main():
                            else "L2 flushed between timed steps (256 MB write)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk,
+                "clocks": clk, "tuning": tuning,
                 "solve": {"status": st, "iters": stats["iters"], "residual": stats["residual"],
                           "pg_rel": stats["pg_rel"], "ls_fail": stats["ls_fail"],
                           "ax_products": stats["ax_products"], "graph_replays": stats["graph_replays"],

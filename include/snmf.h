@@ -144,6 +144,13 @@ typedef struct {
   uint64_t seed;           /* Philox seed of the default initialisation                         */
   const float* mlp_weights;/* host, SNMF_MLP_NPARAMS floats: W1[64][5], b1[64], W2[64], b2 (copied) */
   int64_t timeout_cycles;  /* bound on device-side waits (clock64 cycles), 0 = default        */
+  int32_t autotune;        /* 1: at snmf_create, time the candidate launch configurations of
+                              the dense A*X product (split-K count; tcgen05 ring depth and CTAs
+                              per SM) on this device and shape and keep the fastest; 0 (default):
+                              built-in heuristics.  No counterpart in the paper.               */
+  int32_t reserved_opt;
+  const char* tune_cache;  /* JSON file of tuned configurations keyed by device name and SM
+                              count (read before timing, updated after); NULL: this process only */
 } snmf_options;
 
 /* Per-solve statistics (best restart = lowest objective). */
@@ -261,6 +268,15 @@ SNMF_API snmf_status snmf_apply(snmf_handle h, const void* X, void* Y, int cols,
  */
 SNMF_API snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_product,
                                      double* ms_kernel);
+
+/*
+ * The product configuration chosen by the autotuner (no counterpart in the paper):
+ * split-K slices, tcgen05 ring stages and CTAs per SM (0 where the kernel has none), the
+ * measured mean time in ms, and *from_cache = 1 when it came from the cache file or an
+ * earlier handle of this process.  SNMF_ERR_STATE when the handle was not tuned.
+ */
+SNMF_API snmf_status snmf_tuned_config(snmf_handle h, int32_t* splits, int32_t* stages, int32_t* per_sm,
+                                       double* ms, int32_t* from_cache);
 
 /*
  * Allocation-free dense product (the paper has no counterpart; this is a service of

@@ -177,15 +177,14 @@ inline int cdiv64(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 }  // namespace
 
 int launch_ax(const AxArgs& a, int tdtype, int64_t n, int cols, int64_t ld, const void* X,
-              void* Y, void* ws, size_t ws_elems, const int* run, cudaStream_t s) {
+              void* Y, void* ws, size_t ws_elems, const int* run, cudaStream_t s, const ProdTune* tune) {
   if (a.kind == AX_DENSE) {
     const int gx = cdiv64(cols, BN), gy = cdiv64(n, BM);
     // split-K: aim for >= 2 CTAs per SM (152 SMs) with chunks of >= 256
     int splits = 1;
     const int target = 2 * 152;
     while (gx * gy * splits < target && n / (splits * 2) >= 256) splits *= 2;
-    const size_t esz = tdtype == 0 ? 8 : 4;
-    (void)esz;
+    if (tune && tune->splits > 0) splits = tune->splits;  // autotuned
     if ((size_t)splits * (size_t)n * (size_t)ld > ws_elems) splits = 1;
     int64_t kchunk = (n + splits - 1) / splits;
     kchunk = (kchunk + BK - 1) / BK * BK;

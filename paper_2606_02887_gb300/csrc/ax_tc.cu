@@ -526,7 +526,7 @@ int launch_sums_bf16(const void* A16, int64_t elems, double* part, cudaStream_t 
   return blocks;
 }
 
-int tc_plan(int64_t n, int N, TcPlan* plan) {
+int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune) {
   TcPlan pl{};
   pl.BN = N <= 256 ? ((N + 15) / 16 * 16) : 256;
   pl.tiles_n = (N + pl.BN - 1) / pl.BN;
@@ -544,11 +544,18 @@ int tc_plan(int64_t n, int N, TcPlan* plan) {
     if (stages > 6) stages = 6;
     if (stages < 2) stages = 2;
   }
+  if (tune && tune->per_sm > 0 && tune->stages > 0) {  // autotuned ring
+    per_sm = tune->per_sm;
+    stages = tune->stages;
+    const size_t cap = per_sm == 2 ? 110 * 1024 : 206 * 1024;
+    if ((size_t)stage_bytes * stages + 4096 > cap || stages < 2) return -1;
+  }
   pl.stages = stages;
   const int tiles = pl.tiles_n * pl.tiles_m;
   int splits = (152 * per_sm) / tiles;
   if (splits < 1) splits = 1;
   while (splits > 1 && kiters_total / splits < 8) --splits;
+  if (tune && tune->splits > 0) splits = (int)(tune->splits < kiters_total ? tune->splits : kiters_total);
   pl.splits = splits;
   pl.k_iters = (int)((kiters_total + splits - 1) / splits);
   pl.tmem_cols = 32;
@@ -559,9 +566,10 @@ int tc_plan(int64_t n, int N, TcPlan* plan) {
 }
 
 int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
-                 float* Y, float* ws, size_t ws_elems, int* err, long long budget, cudaStream_t s) {
+                 float* Y, float* ws, size_t ws_elems, int* err, long long budget, cudaStream_t s,
+                 const ProdTune* tune) {
   TcPlan pl;
-  tc_plan(n, N, &pl);
+  if (tc_plan(n, N, &pl, tune) < 0) tc_plan(n, N, &pl);
   const int64_t ldk = tc_ld(n);
   if ((size_t)pl.splits * n * ldx > ws_elems) {
     // not enough split workspace: recompute the plan without splitting

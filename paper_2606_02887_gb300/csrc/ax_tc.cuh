@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include "tune.cuh"
+
 namespace snmf {
 
 struct TcPlan {
@@ -17,7 +19,9 @@ struct TcPlan {
 int64_t tc_ld(int64_t n);
 // diagnostics of the last launch_ax_tc failure: CUresult of the encoder, or 10000 + cudaError_t
 int tc_last_status();
-int tc_plan(int64_t n, int N, TcPlan* plan);
+// Built-in plan, or the autotuned (per_sm, stages, splits) when `tune` sets them; returns
+// -1 when a tuned ring does not fit in shared memory.
+int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune = nullptr);
 // FP64 partial sums of squares / sums of a BF16 array into part[2*block]; returns blocks.
 int launch_sums_bf16(const void* A16, int64_t elems, double* part, cudaStream_t s);
 // A (n x n, dtype 0 f64 / 1 f32, lda) -> A16 (n x tc_ld(n) BF16, zero-padded columns)
@@ -27,7 +31,8 @@ void launch_to_bf16(int src_dtype, const void* A, int64_t n, int64_t lda, void* 
 // (nonzero after a timed-out wait), budget: clock64 cycles per wait.  Returns the number
 // of splits (1 = Y written directly), or -1 when the tensor maps cannot be encoded.
 int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
-                 float* Y, float* ws, size_t ws_elems, int* err, long long budget, cudaStream_t s);
+                 float* Y, float* ws, size_t ws_elems, int* err, long long budget, cudaStream_t s,
+                 const ProdTune* tune = nullptr);
 
 // ---- grouped product of the uneven batch (one CTA per 128-row tile of a problem) ----
 // A_all: BF16, rows of all problems packed, pitch lda; X parts: BF16 hi / lo, row xrow_p + c

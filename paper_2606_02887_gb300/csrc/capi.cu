@@ -98,7 +98,10 @@ struct snmf_ctx {
   cudaEvent_t evdone = nullptr;
   bool have_result = false;
   int ax_count = 0;
-  BatchCtx* bt = nullptr;          // SNMF_DENSE_BATCH handle: the uneven-batch engine
+  BatchCtx* bt = nullptr;
+  // autotuned product configuration (tuned: 1 measured here, 2 from the cache)
+  TuneEntry tune{};
+  int tuned = 0;          // SNMF_DENSE_BATCH handle: the uneven-batch engine
   std::string err;
 };
 
@@ -154,19 +157,100 @@ Dims dims(const snmf_ctx* h) {
 // The product kernel alone: CUDA cores (FP64/FP32 dense, CSR) or tcgen05 (BF16 dense).
 // Returns the number of split-K slices written to h->ws (1 = result in Y).
 int product_kernel(snmf_ctx* h, const AxArgs& op, const void* X, void* Y, const int* run) {
+  const ProdTune* tn = (h->tuned && &op == &h->A) ? &h->tune.cfg : nullptr;  // the tuned shape only
   if (op.kind == AX_DENSE && op.a_dtype == 3)
     return launch_ax_fp8(op.A, op.a_scale, h->n, (const float*)X, h->N, h->N, (float*)Y, (float*)h->ws,
-                         h->ws_elems, run, h->s);
+                         h->ws_elems, run, h->s, tn);
   if (op.kind == AX_DENSE && op.a_dtype == 2) {
     const int sp = launch_ax_tc(op.A, h->n, (const float*)X, h->N, h->N, h->xh, h->xl, (float*)Y,
-                                (float*)h->ws, h->ws_elems, h->dev_err, h->budget, h->s);
+                                (float*)h->ws, h->ws_elems, h->dev_err, h->budget, h->s, tn);
     if (sp < 1) {
       h->tc_fail = tc_last_status();
       return 1;
     }
     return sp;
   }
-  return launch_ax(op, h->tdtype, h->n, h->N, h->N, X, Y, h->ws, h->ws_elems, run, h->s);
+  return launch_ax(op, h->tdtype, h->n, h->N, h->N, X, Y, h->ws, h->ws_elems, run, h->s, tn);
+}
+
+// Autotuner of the dense product: times every candidate configuration (CUDA events, one
+// warm-up and five timed products each) and keeps the fastest; the result is cached per
+// device and shape (in this process, and in opt.tune_cache when given).
+snmf_status autotune_product(snmf_ctx* h) {
+  if (h->kind != AX_DENSE) return SNMF_OK;
+  static const char* dtn[4] = {"f64", "f32", "bf16", "fp8"};
+  const std::string key = std::string("dense/") + dtn[h->A.a_dtype] + "/n" + std::to_string(h->n) + "/N" +
+                          std::to_string(h->N);
+  const std::string dev = tune_device_key();
+  TuneEntry e;
+  if (tune_lookup(h->opt.tune_cache, dev, key, &e)) {
+    h->tune = e;
+    h->tuned = 2;
+    return SNMF_OK;
+  }
+  std::vector<ProdTune> cand;
+  if (h->A.a_dtype == 2) {
+    const int rings[5][2] = {{2, 2}, {2, 3}, {1, 3}, {1, 4}, {1, 6}};
+    for (auto& rg : rings)
+      for (int sp : {1, 2, 4, 8, 16}) {
+        ProdTune t;
+        t.per_sm = rg[0];
+        t.stages = rg[1];
+        t.splits = sp;
+        TcPlan pl;
+        if (tc_plan(h->n, h->N, &pl, &t) < 0 || pl.splits != sp) continue;
+        if ((size_t)sp * h->n * h->N > h->ws_elems && sp > 1) continue;
+        cand.push_back(t);
+      }
+  } else {
+    for (int sp : {1, 2, 4, 8, 16, 32}) {
+      if (sp > 1 && ((size_t)sp * h->n * h->N > h->ws_elems || h->n / sp < 64)) continue;
+      ProdTune t;
+      t.splits = sp;
+      cand.push_back(t);
+    }
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  TuneEntry best;
+  best.ms = 1e30;
+  h->tuned = 1;
+  for (const ProdTune& t : cand) {
+    h->tune.cfg = t;
+    product_kernel(h, h->A, h->buf[B_W], h->buf[B_AZ], nullptr);  // warm-up
+    CK(cudaEventRecord(e0, h->s));
+    for (int rep = 0; rep < 5; ++rep) product_kernel(h, h->A, h->buf[B_W], h->buf[B_AZ], nullptr);
+    CK(cudaEventRecord(e1, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    if (h->tc_fail) {  // a configuration that did not launch is skipped
+      h->tc_fail = 0;
+      cudaGetLastError();
+      continue;
+    }
+    CK(cudaGetLastError());
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms / 5 < best.ms) {
+      best.cfg = t;
+      best.ms = ms / 5;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int derr = 0;
+  CK(cudaMemcpy(&derr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (derr) {
+    h->tuned = 0;
+    return fail(h, SNMF_ERR_TIMEOUT, "a bounded device wait ran out while tuning the product");
+  }
+  if (best.ms >= 1e30) {
+    h->tuned = 0;
+    return SNMF_OK;
+  }
+  h->tune = best;
+  tune_store(h->opt.tune_cache, dev, key, best);
+  return SNMF_OK;
 }
 
 // Y = op X (+ c X2), dots <P1, op X> -> part q0, <P2, op X> -> q0+1; returns slot count.
@@ -519,6 +603,9 @@ void snmf_default_options(snmf_options* o) {
   o->seed = 0;
   o->mlp_weights = nullptr;
   o->timeout_cycles = 0;
+  o->autotune = 0;
+  o->reserved_opt = 0;
+  o->tune_cache = nullptr;
 }
 
 snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const snmf_options* opt,
@@ -751,6 +838,10 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   h->sumA = sums[1];
   if (!std::isfinite(h->normA2)) { h->err = "A has NaN/Inf entries"; return bail(SNMF_ERR_NUMERIC); }
   h->lam = o.lambda_sym >= 0.0 ? o.lambda_sym : 0.01 * std::sqrt(h->normA2);
+  if (o.autotune) {
+    const snmf_status ts = autotune_product(h);
+    if (ts != SNMF_OK) return bail(ts);
+  }
   *out = h;
   return SNMF_OK;
 #undef CKC
@@ -1055,6 +1146,18 @@ snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_product, double
   (void)d;
   if (ms_product) *ms_product = m1 / iters;
   if (ms_kernel) *ms_kernel = h->lai ? 0.0 : m2 / iters;
+  return SNMF_OK;
+}
+
+snmf_status snmf_tuned_config(snmf_handle h, int32_t* splits, int32_t* stages, int32_t* per_sm, double* ms,
+                              int32_t* from_cache) {
+  if (!h) return SNMF_ERR_STATE;
+  if (!h->tuned) return fail(h, SNMF_ERR_STATE, "the handle was not autotuned");
+  if (splits) *splits = h->tune.cfg.splits;
+  if (stages) *stages = h->tune.cfg.stages;
+  if (per_sm) *per_sm = h->tune.cfg.per_sm;
+  if (ms) *ms = h->tune.ms;
+  if (from_cache) *from_cache = h->tuned == 2 ? 1 : 0;
   return SNMF_OK;
 }
 

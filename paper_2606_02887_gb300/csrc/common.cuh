@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tune.cuh"
+
 namespace snmf {
 
 constexpr int kNQ = 32;         // dot slots per partial record
@@ -158,7 +160,7 @@ struct AxArgs {
 // sums them.  Returns the number of splits used (1 = result already in Y).
 int launch_ax(const AxArgs& a, int tdtype, int64_t n, int cols, int64_t ld,
               const void* X, void* Y, void* ws, size_t ws_elems, const int* run_flag,
-              cudaStream_t s);
+              cudaStream_t s, const ProdTune* tune = nullptr);
 
 // Epilogue of a product over the restarts of d: Y = sum_s ws[s] (splits > 1),
 // per-restart partials <P1, A X> -> part[slot][j][q0], <P2, A X> -> [q0+1], then

@@ -216,10 +216,11 @@ int launch_fp8_sums(const void* A8, int64_t n, const float* scales, double* part
 }
 
 int launch_ax_fp8(const void* A8, const float* scales, int64_t n, const float* X, int cols, int64_t ld, float* Y,
-                  float* ws, size_t ws_elems, const int* run, cudaStream_t s) {
+                  float* ws, size_t ws_elems, const int* run, cudaStream_t s, const ProdTune* tune) {
   const int gx = cdiv64(cols, BN), gy = cdiv64(n, BM);
   int splits = 1;
   while (gx * gy * splits < 2 * 152 && n / (splits * 2) >= 256) splits *= 2;
+  if (tune && tune->splits > 0) splits = tune->splits;  // autotuned
   if ((size_t)splits * (size_t)n * (size_t)ld > ws_elems) splits = 1;
   int64_t kchunk = (n + splits - 1) / splits;
   kchunk = (kchunk + BK - 1) / BK * BK;

@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "tune.cuh"
+
 namespace snmf {
 
 // Leading dimension (bytes) of the code matrix and the number of 128-wide tiles per side.
@@ -21,6 +23,6 @@ int launch_fp8_sums(const void* A8, int64_t n, const float* scales, double* part
 // Y = A~ X (X, Y: n x cols FP32, leading dimension ld); split-K slices go to ws (n x ld
 // each).  Returns the number of splits (1 = result in Y).
 int launch_ax_fp8(const void* A8, const float* scales, int64_t n, const float* X, int cols, int64_t ld, float* Y,
-                  float* ws, size_t ws_elems, const int* run, cudaStream_t s);
+                  float* ws, size_t ws_elems, const int* run, cudaStream_t s, const ProdTune* tune = nullptr);
 
 }  // namespace snmf

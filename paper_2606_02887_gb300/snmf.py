@@ -28,7 +28,7 @@ EXPORTED = (
     "snmf_default_options", "snmf_create", "snmf_set_graph_reg", "snmf_lai_sketch",
     "snmf_solve", "snmf_solve_host", "snmf_restart_stats", "snmf_get_factors",
     "snmf_apply", "snmf_profile_ax", "snmf_apply_dense_noalloc", "snmf_controller_data",
-    "snmf_mlp_train", "snmf_destroy", "snmf_last_error",
+    "snmf_mlp_train", "snmf_tuned_config", "snmf_destroy", "snmf_last_error",
 )
 NOALLOC_SCRATCH_BYTES = 64 << 20
 NOALLOC_MAX_SLICE_PAIR_BYTES = NOALLOC_SCRATCH_BYTES - (1 << 20)
@@ -50,7 +50,8 @@ class snmf_options(C.Structure):
                 ("phi", C.c_double), ("eta", C.c_double), ("alpha_min", C.c_double),
                 ("alpha_max", C.c_double), ("beta_shrink", C.c_double), ("tol", C.c_double),
                 ("direct_rho_factor", C.c_double), ("init_scale", C.c_double), ("seed", C.c_uint64),
-                ("mlp_weights", C.c_void_p), ("timeout_cycles", C.c_int64)]
+                ("mlp_weights", C.c_void_p), ("timeout_cycles", C.c_int64),
+                ("autotune", C.c_int32), ("reserved_opt", C.c_int32), ("tune_cache", C.c_char_p)]
 
 
 class snmf_stats(C.Structure):
@@ -92,6 +93,8 @@ def load_library(path: str = LIB_PATH):
     lib.snmf_controller_data.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int32)]
     lib.snmf_mlp_train.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double,
                                    C.POINTER(C.c_double), C.c_void_p]
+    lib.snmf_tuned_config.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_int32)]
     lib.snmf_destroy.argtypes = [H]
     lib.snmf_last_error.argtypes = [H]
     lib.snmf_last_error.restype = C.c_char_p
@@ -121,6 +124,8 @@ def snmf_default_options(**overrides) -> snmf_options:
     for k, v in overrides.items():
         if k == "mlp_weights":
             continue
+        if k == "tune_cache" and isinstance(v, str):
+            v = v.encode()
         setattr(o, k, v)
     return o
 
@@ -289,6 +294,15 @@ def snmf_mlp_train(feats, targets, weights, steps: int = 1000, lr: float = 1e-2)
     _check(lib, None, lib.snmf_mlp_train(f.ctypes.data, t.ctypes.data, len(t), w.ctypes.data, int(steps),
                                          float(lr), C.byref(loss), g0.ctypes.data))
     return w, loss.value, g0
+
+
+def snmf_tuned_config(h) -> dict:
+    """Product launch configuration chosen by the autotuner of this handle."""
+    lib = load_library()
+    sp, st, ps, fc = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    ms = C.c_double()
+    _check(lib, h, lib.snmf_tuned_config(h, C.byref(sp), C.byref(st), C.byref(ps), C.byref(ms), C.byref(fc)))
+    return dict(splits=sp.value, stages=st.value, per_sm=ps.value, ms=ms.value, from_cache=bool(fc.value))
 
 
 def snmf_destroy(h):

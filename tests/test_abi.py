@@ -36,7 +36,7 @@ def test_struct_layouts_match_header(lib):
     # sizes fixed by the header's field order (LP64)
     assert C.sizeof(S.snmf_matrix) == 4 * 4 + 3 * 8 + 3 * 8 + 2 * 4 + 8
     assert C.sizeof(S.snmf_stats) == 6 * 4 + 4 * 8 + 8 + 4 * 4
-    assert C.sizeof(S.snmf_options) == 10 * 4 + 10 * 8 + 8 + 8 + 8
+    assert C.sizeof(S.snmf_options) == 10 * 4 + 10 * 8 + 8 + 8 + 8 + 2 * 4 + 8
 
 
 def test_default_options(lib):
