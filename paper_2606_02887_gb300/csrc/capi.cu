@@ -190,9 +190,9 @@ snmf_status autotune_product(snmf_ctx* h) {
   }
   std::vector<ProdTune> cand;
   if (h->A.a_dtype == 2) {
-    const int rings[5][2] = {{2, 2}, {2, 3}, {1, 3}, {1, 4}, {1, 6}};
+    const int rings[6][2] = {{2, 2}, {2, 3}, {2, 4}, {1, 3}, {1, 4}, {1, 6}};
     for (auto& rg : rings)
-      for (int sp : {1, 2, 4, 8, 16}) {
+      for (int sp : {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16, 19, 24, 32}) {
         ProdTune t;
         t.per_sm = rg[0];
         t.stages = rg[1];
@@ -203,7 +203,7 @@ snmf_status autotune_product(snmf_ctx* h) {
         cand.push_back(t);
       }
   } else {
-    for (int sp : {1, 2, 4, 8, 16, 32}) {
+    for (int sp : {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 19, 24, 32}) {
       if (sp > 1 && ((size_t)sp * h->n * h->N > h->ws_elems || h->n / sp < 64)) continue;
       ProdTune t;
       t.splits = sp;
