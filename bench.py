@@ -1,10 +1,12 @@
 #!/usr/bin/env python
 """Benchmark of the SNMPBB solve on one GB300 (or N replicas under torchrun).
 
-Metric: time to reach relative projected gradient 1e-4 (seconds per solve, lower
-is better) on the dense planted n = 8192 workload, with the achieved A*W product
-bandwidth / arithmetic rate of the dominant kernel beside it.  A "step" is one
-full solve from the seeded start to the tolerance (penalty form, Sec. 2.1).
+Metric: time to reach relative projected gradient 1e-4 (seconds, lower is better) on
+the dense planted n = 8192, r = 64 workload: by default BF16 A, the learned step
+controller and 8 random restarts in one solve, against the plain FP32 path solving the
+same 8 restarts one at a time (the "compare" block), with the achieved A*W product
+bandwidth of the dominant kernel beside it.  A "step" is one full solve of all restarts
+from their seeded starts to the tolerance (penalty form, Sec. 2.1).
 
   python bench.py [--gpus N --steps K --warmup W] [--r 64 --batch 1 --precision f32]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
@@ -42,8 +44,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=8192)
     p.add_argument("--r", type=int, default=64)
-    p.add_argument("--batch", type=int, default=1)
-    p.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16", "fp8"])
+    p.add_argument("--batch", type=int, default=8, help="random restarts sharing A in one solve")
+    p.add_argument("--precision", default="bf16", choices=["f64", "f32", "bf16", "fp8"])
     p.add_argument("--formulation", default="penalty", choices=["penalty", "direct"])
     p.add_argument("--max-iter", type=int, default=500)
     p.add_argument("--tol", type=float, default=1e-4)
@@ -411,12 +413,19 @@ def main():
     W = torch.empty_like(W0)
     H = torch.empty_like(W0)
     form = S.SNMF_PENALTY if args.formulation == "penalty" else S.SNMF_DIRECT
+    weights = controller_weights(args) if form == S.SNMF_PENALTY and args.r <= 64 else None
+    ctl = 1 if weights is not None else 0
     opts = S.snmf_default_options(precision=prec, formulation=form, batch=args.batch, max_iter=args.max_iter,
                                   tol=args.tol, nonmonotone_M=10, autotune=args.autotune,
-                                  tune_cache=args.tune_cache)
+                                  tune_cache=args.tune_cache, step_controller=ctl)
     stream = torch.cuda.current_stream(dev)
-    h = S.snmf_create(S.dense_matrix(A), args.r, opts, stream=stream)
-    tuning = S.snmf_tuned_config(h) if args.autotune else None
+    h = S.snmf_create(S.dense_matrix(A), args.r, opts, stream=stream, mlp_weights=weights)
+    tuning = None
+    if args.autotune:
+        try:
+            tuning = S.snmf_tuned_config(h)
+        except S.SnmfError:  # no candidate fitted this shape: built-in configuration
+            tuning = {"tuned": False}
     a_bytes = A.numel() * {"bf16": 2, "fp8": 1}.get(args.precision, A.element_size())
     flush = None if a_bytes > 2 * L2_BYTES else torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
@@ -504,7 +513,7 @@ def main():
             H_host.copy_(W0_host)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            he = S.snmf_create(S.dense_matrix(A_host), args.r, opts, stream=stream)
+            he = S.snmf_create(S.dense_matrix(A_host), args.r, opts, stream=stream, mlp_weights=weights)
             S.snmf_solve_host(he, W_host, H_host if form == S.SNMF_PENALTY else None)
             S.snmf_destroy(he)
             torch.cuda.synchronize()
@@ -515,7 +524,32 @@ def main():
         e2e = {"value": statistics.mean(e_times), "unit": "s", "h2d_bytes_per_step": a_bytes + nf * fb,
                "d2h_bytes_per_step": nf * fb,
                "path": "snmf_create(host A) + snmf_solve_host + snmf_destroy, wall clock"}
+    per = S.snmf_restart_stats(h, args.batch)
     S.snmf_destroy(h)
+
+    # the same restarts solved by the plain FP32 path: one restart per snmf_solve, FP32 A,
+    # no controller (device time of each solve, CUDA events inside the library)
+    compare = None
+    if rank == 0 and not args.no_compare:
+        A32 = A.float() if A.dtype != torch.float32 else A
+        o32 = S.snmf_default_options(precision=S.SNMF_F32, formulation=form, max_iter=args.max_iter, tol=args.tol,
+                                     nonmonotone_M=10)
+        hp = S.snmf_create(S.dense_matrix(A32), args.r, o32, stream=stream)
+        tot, its, res = 0.0, [], []
+        for j in range(args.batch):
+            Wj = W0[:, j * args.r:(j + 1) * args.r].float().contiguous()
+            Hj = Wj.clone()
+            stp, sp = S.snmf_solve(hp, Wj, Hj if form == S.SNMF_PENALTY else None)
+            tot += sp["seconds"]
+            its.append(sp["iters"])
+            res.append(sp["residual"])
+        S.snmf_destroy(hp)
+        dres = np.abs(np.asarray(per["residual"]) - np.asarray(res))
+        compare = {"plain_f32_one_restart_per_solve": {
+            "s": tot, "iters": its, "residual": res, "speedup_of_value": tot / (ms_max / 1e3),
+            "residual_max_abs_diff": float(dres.max()), "restarts_within_1e-3": int(np.sum(dres <= 1e-3))},
+            "this_run": {"iters": [int(x) for x in per["iters"]], "residual": [float(x) for x in per["residual"]],
+                         "pg_rel_max": float(np.max(per["pg_rel"]))}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -533,7 +567,7 @@ def main():
                 "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": workload_name(args), "n": args.n, "r": args.r, "batch": args.batch,
                            "precision": args.precision, "formulation": args.formulation, "tol": args.tol,
-                           "max_iter": args.max_iter,
+                           "max_iter": args.max_iter, "controller": "learned" if ctl else "plain BB",
                            "l2": ("inputs larger than L2 (A = %.0f MB)" % (a_bytes / 2**20)) if flush is None
                            else "L2 flushed between timed steps (256 MB write)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -542,7 +576,9 @@ def main():
                 "solve": {"status": st, "iters": stats["iters"], "residual": stats["residual"],
                           "pg_rel": stats["pg_rel"], "ls_fail": stats["ls_fail"],
                           "ax_products": stats["ax_products"], "graph_replays": stats["graph_replays"],
-                          "ms_per_step_all": times}}
+                          "ctl_proposals": stats["ctl_proposals"], "ctl_accepted": stats["ctl_accepted"],
+                          "ms_per_step_all": times},
+                "compare": compare}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

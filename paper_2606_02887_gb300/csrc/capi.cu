@@ -190,7 +190,7 @@ snmf_status autotune_product(snmf_ctx* h) {
   }
   std::vector<ProdTune> cand;
   if (h->A.a_dtype == 2) {
-    const int rings[6][2] = {{2, 2}, {2, 3}, {2, 4}, {1, 3}, {1, 4}, {1, 6}};
+    const int rings[7][2] = {{2, 2}, {2, 3}, {2, 4}, {1, 2}, {1, 3}, {1, 4}, {1, 6}};
     for (auto& rg : rings)
       for (int sp : {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16, 19, 24, 32}) {
         ProdTune t;
