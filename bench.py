@@ -488,11 +488,21 @@ def main():
                 "alg_bytes_per_launch": alg_bytes, "flops_per_launch": flops,
                 "ms_per_launch": ms_kern, "ms_per_product_with_epilogue": ms_prod}
     elif args.precision == "bf16":
-        roof = {"bound": "hbm", "kernel": "k_split_x + k_gemm_tc (tcgen05 BF16, X as hi+lo BF16 parts)",
-                "achieved": aw_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": aw_gbs / peaks["hbm_gbs"] if aw_gbs else None, "traffic": None,
-                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, burst copy)",
-                "tensor_tflops": achieved_tflops * 2 if achieved_tflops else None,
+        # tensor work: the hi and lo parts of X each take one BF16 MMA pass
+        tflops = 2 * flops / (ms_kern * 1e-3) / 1e12
+        ridge = peaks["bf16_tflops"] * 1e12 / (peaks["hbm_gbs"] * 1e9)
+        intensity = 2 * flops / alg_bytes
+        tensor_bound = intensity > ridge
+        roof = {"bound": "tensor" if tensor_bound else "hbm",
+                "kernel": "k_split_x + k_gemm_tc (tcgen05 BF16, X as hi+lo BF16 parts)",
+                "achieved": tflops if tensor_bound else aw_gbs,
+                "peak": peaks["bf16_tflops"] if tensor_bound else peaks["hbm_gbs"],
+                "unit": "TFLOP/s" if tensor_bound else "GB/s",
+                "frac": (tflops / peaks["bf16_tflops"]) if tensor_bound else (aw_gbs / peaks["hbm_gbs"]),
+                "traffic": None,
+                "peak_source": peak_kind + (" bf16_tflops (burst cuBLAS)" if tensor_bound else " hbm_gbs (burst copy)"),
+                "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
+                "aw_gbs": aw_gbs, "aw_hbm_frac": aw_gbs / peaks["hbm_gbs"],
                 "alg_bytes_per_launch": alg_bytes, "flops_per_launch": 2 * flops,
                 "ms_per_launch": ms_kern, "ms_per_product_with_epilogue": ms_prod}
     else:

@@ -8,6 +8,8 @@
 //   k_spmm_csr   : one warp per row, lanes across the factor columns (coalesced rows of X).
 //   k_ax_finish  : fused epilogue: sum of split slices, Y += c X2, and per-restart FP64
 //                  partials of <P1, A X> and <P2, A X> (e.g. tr(W^T A W)).
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace snmf {
@@ -16,9 +18,16 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
 
-template <typename T>
+__device__ __forceinline__ float ld_a(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float ld_a(const float* p) { return *p; }
+__device__ __forceinline__ double ld_a(const double* p) { return *p; }
+
+// TA: stored type of A (T, or BF16 read into FP32 registers: the FP32-accumulated product
+// of the stored BF16 operator, used where the tensor-core accumulation is not accurate
+// enough, i.e. the closed-form objective of the final evaluation)
+template <typename T, typename TA = T>
 __global__ void __launch_bounds__(256)
-k_gemm_dense(const T* __restrict__ A, int64_t lda, const T* __restrict__ X, int64_t ld,
+k_gemm_dense(const TA* __restrict__ A, int64_t lda, const T* __restrict__ X, int64_t ld,
              T* __restrict__ Y, int64_t n, int cols, int64_t kchunk, const int* run) {
   if (run && *run == 0) return;
   __shared__ T As[2][BK][BM + 4];
@@ -50,7 +59,7 @@ k_gemm_dense(const T* __restrict__ A, int64_t lda, const T* __restrict__ X, int6
     for (int m = 0; m < 4; ++m) {
       int64_t r = row0 + la_r + 16 * m;
       int64_t k = k0 + la_c;
-      ra[m] = (r < n && k < k_end) ? A[r * lda + k] : T(0);
+      ra[m] = (r < n && k < k_end) ? (T)ld_a(A + r * lda + k) : T(0);
       int c = col0 + lx_c + 16 * m;
       int64_t kr = k0 + lx_r;
       rx[m] = (kr < k_end && c < cols) ? X[kr * ld + c] : T(0);
@@ -190,7 +199,10 @@ int launch_ax(const AxArgs& a, int tdtype, int64_t n, int cols, int64_t ld, cons
     kchunk = (kchunk + BK - 1) / BK * BK;
     dim3 grid(gx, gy, splits);
     void* out = splits > 1 ? ws : Y;
-    if (tdtype == 0)
+    if (a.a_dtype == 2)
+      k_gemm_dense<float, __nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16*)a.A, a.lda, (const float*)X,
+                                                              ld, (float*)out, n, cols, kchunk, run);
+    else if (tdtype == 0)
       k_gemm_dense<double><<<grid, 256, 0, s>>>((const double*)a.A, a.lda, (const double*)X, ld,
                                                 (double*)out, n, cols, kchunk, run);
     else

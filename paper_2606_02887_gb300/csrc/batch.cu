@@ -425,6 +425,7 @@ struct BatchCtx {
   int *pst = nullptr, *psz = nullptr, *d_order = nullptr, *cnt_full = nullptr, *cnt_act = nullptr;
   std::vector<int> order;
   bool use_full = false;  // launches being recorded cover every problem (final evaluation)
+  bool accurate = false;  // BF16: FP32 CUDA-core product instead of tcgen05 (final evaluation)
   int64_t lda = 0, rows_total = 0, xtot = 0;
   void* A = nullptr;
   void* buf[XB_N] = {};
@@ -500,7 +501,7 @@ const int2* blist(const BatchCtx* b, int L) {
 
 void bprod(BatchCtx* b, const void* X, void* Y, const void* P1, double* part, const Ctl* ctl, const int* run) {
   const unsigned g = (unsigned)b->h_prod.size();
-  if (b->a_dtype == 2) {
+  if (b->a_dtype == 2 && !b->accurate) {
     // tcgen05: X_p split into BF16 hi / lo parts (transposed), then one CTA per 128-row tile
     const int nt = (int)b->h_tc.size();
     const TcItem* tl = b->use_full ? b->it_tc : b->c_tc;
@@ -666,8 +667,11 @@ void bpen_iteration(BatchCtx* b, const Params& P) {
 }
 
 void bpen_final(BatchCtx* b, const Params& P) {
-  // every problem contributes: full work lists, no run flag, no active test
+  // every problem contributes: full work lists, no run flag, no active test.  <W, A Ht> of
+  // the closed-form residual comes from an FP32 CUDA-core product (the tensor-core
+  // accumulation bias would be amplified by the cancellation in the residual).
   b->use_full = true;
+  b->accurate = true;
   bprod(b, b->buf[XB_HT], b->buf[XB_B], b->buf[XB_W], b->pax, nullptr, nullptr);
   bgram(b, b->buf[XB_W], b->buf[XB_W], 0, 3, nullptr, nullptr, b->G64p, b->GT, 1, 1, nullptr);
   bgram(b, b->buf[XB_HT], b->buf[XB_HT], 1, 3, nullptr, nullptr, b->G64p, b->GT, 1, 1, nullptr);
@@ -678,8 +682,9 @@ void bpen_final(BatchCtx* b, const Params& P) {
   a.ctl = b->ctl + b->nprob;  // second Ctl array: all live
   a.ctl_mode = CTL_NONE;
   brow(b, OP_LOAD, EPI_GRAD, a);
-  k_bfinal<<<b->nprob, 32, 0, b->s>>>(b->ctl, b->pax, b->prow, b->G64p, b->dp, b->a_dtype == 2 ? 1 : 0);
+  k_bfinal<<<b->nprob, 32, 0, b->s>>>(b->ctl, b->pax, b->prow, b->G64p, b->dp, 0);
   b->use_full = false;
+  b->accurate = false;
 }
 
 snmf_status sync_user_b(BatchCtx* b, std::string* err) {

@@ -161,7 +161,7 @@ int product_kernel(snmf_ctx* h, const AxArgs& op, const void* X, void* Y, const 
   if (op.kind == AX_DENSE && op.a_dtype == 3)
     return launch_ax_fp8(op.A, op.a_scale, h->n, (const float*)X, h->N, h->N, (float*)Y, (float*)h->ws,
                          h->ws_elems, run, h->s, tn);
-  if (op.kind == AX_DENSE && op.a_dtype == 2) {
+  if (op.kind == AX_DENSE && op.a_dtype == 2 && !op.accurate) {
     const int sp = launch_ax_tc(op.A, h->n, (const float*)X, h->N, h->N, h->xh, h->xl, (float*)Y,
                                 (float*)h->ws, h->ws_elems, h->dev_err, h->budget, h->s, tn);
     if (sp < 1) {
@@ -414,8 +414,13 @@ void pen_iteration(snmf_ctx* h, const Params& P) {
 void pen_final(snmf_ctx* h, const Params& P) {
   const Dims d = dims(h);
   const int td = h->tdtype;
-  // every restart contributes to the final evaluation
-  int nax = ax_apply(h, h->A, h->lai, h->buf[B_HT], h->buf[B_B], h->lam, h->buf[B_HT],
+  // every restart contributes to the final evaluation.  The closed-form objective
+  // ||A||^2 - 2 <W, A Ht> + ... cancels to a small residual, so <W, A Ht> is taken from an
+  // FP32 CUDA-core product of the stored BF16 A: the tensor-core FP32 accumulation carries
+  // a relative bias of about 1e-5 over K = 8192, which that cancellation would amplify.
+  AxArgs fin = h->A;
+  fin.accurate = 1;
+  int nax = ax_apply(h, fin, h->lai, h->buf[B_HT], h->buf[B_B], h->lam, h->buf[B_HT],
                      h->buf[B_W], nullptr, h->pax, nullptr);
   gram1(h, h->buf[B_W], h->buf[B_W], 0, 3, nullptr, h->G64p, h->GT, 1, h->lam);
   gram1(h, h->buf[B_HT], h->buf[B_HT], 1, 3, nullptr, h->G64p, h->GT, 1, h->lam);

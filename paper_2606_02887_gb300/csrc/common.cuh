@@ -153,6 +153,7 @@ struct AxArgs {
   // csr
   const int32_t* rowptr; const int32_t* colidx; const void* vals; int v_dtype;
   int kind;
+  int accurate;  // BF16 dense: FP32 CUDA-core accumulation instead of the tensor-core product
 };
 
 // Y = A X (raw product, T = double/float), n x cols, ld = leading dimension of X and Y.
