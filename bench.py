@@ -236,7 +236,7 @@ def run_uneven(args):
     H = torch.empty_like(W0)
     prec = {"f64": S.SNMF_F64, "f32": S.SNMF_F32, "bf16": S.SNMF_BF16, "fp8": S.SNMF_FP8}[args.precision]
     weights = controller_weights(args)
-    ctl = 1 if weights is not None else 0
+    ctl = 3 if weights is not None else 0  # lean learned step
     stream = torch.cuda.current_stream(dev)
 
     def handle(pr, c):
@@ -414,7 +414,7 @@ def main():
     H = torch.empty_like(W0)
     form = S.SNMF_PENALTY if args.formulation == "penalty" else S.SNMF_DIRECT
     weights = controller_weights(args) if form == S.SNMF_PENALTY and args.r <= 64 else None
-    ctl = 1 if weights is not None else 0
+    ctl = 3 if weights is not None else 0  # lean learned step
     opts = S.snmf_default_options(precision=prec, formulation=form, batch=args.batch, max_iter=args.max_iter,
                                   tol=args.tol, nonmonotone_M=10, autotune=args.autotune,
                                   tune_cache=args.tune_cache, step_controller=ctl)

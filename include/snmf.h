@@ -124,9 +124,13 @@ typedef struct {
                               (weights in mlp_weights, used in BF16); the proposal is kept only if
                               the nonmonotone Armijo test accepts it at beta = 1, otherwise the
                               step falls back to the plain BB direction with ordinary backtracking.
+                              3: lean learned step: the proposal replaces the BB step and is
+                              backtracked like it (one direction per step instead of two; the
+                              convergence safeguards are the clamp to [alpha_min, alpha_max] and
+                              the unchanged nonmonotone acceptance test).
                               2: record mode: the plain BB trajectory, and at every step the
                               features phi and the best of 9 multipliers 2^(-2..2 by 1/2) are
-                              recorded (snmf_controller_data).  1 and 2 need the penalty form
+                              recorded (snmf_controller_data).  1, 2 and 3 need the penalty form
                               and r <= 64.  Features phi: ln(BB1 rho), ln(BB2 rho), ratio of
                               successive projected-gradient norms, ratio of successive objective
                               decreases, fraction of zero entries.                               */

@@ -861,7 +861,7 @@ snmf_status batch_create(BatchCtx** out, const snmf_matrix* Am, const snmf_optio
   CKB(cudaMemsetAsync(b->counters, 0, 4 * np * sizeof(unsigned), b->s));
   CKB(cudaMalloc(&b->dsc, (2 * b->h_prod.size() + 2 * np) * sizeof(double)));
   CKB(cudaMallocHost(&b->h_flag, sizeof(int)));
-  if (o.step_controller == 1) {
+  if (o.step_controller == 1 || o.step_controller == 3) {
     std::vector<__nv_bfloat16> wb(kMlpParams);
     for (int i = 0; i < kMlpParams; ++i) wb[i] = __float2bfloat16_rn(o.mlp_weights[i]);
     CKB(cudaMalloc(&b->mlp_w, kMlpParams * sizeof(__nv_bfloat16)));

@@ -567,8 +567,8 @@ snmf_status validate_options(const snmf_options& o) {
       !(o.alpha_min > 0.0 && o.alpha_min < o.alpha_max) || !(o.beta_shrink > 0.0 && o.beta_shrink < 1.0) ||
       !(o.tol >= 0.0) || !(o.direct_rho_factor > 0.0))
     return SNMF_ERR_ARG;
-  if (!valid_enum(o.step_controller, 0, 2)) return SNMF_ERR_ARG;
-  if (o.step_controller == 1 && !o.mlp_weights) return SNMF_ERR_ARG;
+  if (!valid_enum(o.step_controller, 0, 3)) return SNMF_ERR_ARG;
+  if ((o.step_controller == 1 || o.step_controller == 3) && !o.mlp_weights) return SNMF_ERR_ARG;
   return SNMF_OK;
 }
 
@@ -811,7 +811,7 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   }
   snmf_status st = alloc_buffers(h);
   if (st != SNMF_OK) return bail(st);
-  if (o.step_controller == 1) {
+  if (o.step_controller == 1 || o.step_controller == 3) {
     std::vector<__nv_bfloat16> wb(kMlpParams);
     for (int i = 0; i < kMlpParams; ++i) wb[i] = __float2bfloat16_rn(o.mlp_weights[i]);  // BF16 weights
     CKC(cudaMalloc(&h->mlp_w, kMlpParams * sizeof(__nv_bfloat16)));

@@ -249,7 +249,8 @@ __device__ double backtrack(double fZ, double F, double gd, double q, const Para
 // Line search after the D direction (q: 0 gd, 1 dd, 2 f(Z)-f(X_k), 4 <D G, D> when fused):
 // f(Z + beta D) - f(Z) = beta gd + beta^2/2 q, q = <D (H H^T + lambda I), D> + gamma <D, L D>.
 // nc = 2 (learned controller): candidate 0 is the proposal, accepted only at beta = 1, else
-// the plain BB direction (candidate 1) with ordinary backtracking.  nc = 9 (record mode):
+// the plain BB direction (candidate 1) with ordinary backtracking.  The lean learned step
+// (controller 3) has one candidate, the proposal, with ordinary backtracking.  nc = 9 (record mode):
 // every candidate multiplier is line-searched, the best accepted decrease is recorded as
 // the training label, and the plain BB candidate (index 4) is followed.
 __device__ void pen_ls_body(Ctl& c, const double* prow, int nrow, const double* pax, int nax, int b, int r,
@@ -275,6 +276,10 @@ __device__ void pen_ls_body(Ctl& c, const double* prow, int nrow, const double* 
     c.gd = gd;
     c.q = q;
     beta = backtrack(c.fZ, c.F, gd, q, P, &ok);
+    if (P.controller == 3 && c.feat_ok) {  // lean learned step: the proposal, backtracked
+      c.mlp_tried++;
+      if (ok && beta == 1.0) c.mlp_accept++;
+    }
   } else if (nc == 2) {
     // proposal: Armijo test at beta = 1 only
     const double fz1 = c.fZ + gd + 0.5 * q;
@@ -370,7 +375,7 @@ __device__ void pen_upd_body(Ctl& c, const double* prow, int nrow, int b, int j,
     phi[3] = (float)fmin(fmax(dec / fmax(fabs(c.last_dec), 1e-300), -10.0), 10.0);
     phi[4] = (float)(zeros / (double)P.nr);
     float mult = 1.f;
-    if (nc == 2) mult = mlp_multiplier(P.mlp_w, phi);  // all lanes
+    if (nc == 2 || nc == 3) mult = mlp_multiplier(P.mlp_w, phi);  // all lanes
     if ((threadIdx.x & 31) == 0) {
       for (int u = 0; u < kMlpIn; ++u) c.feat[u] = phi[u];
       c.feat_ok = 1;
@@ -380,6 +385,9 @@ __device__ void pen_upd_body(Ctl& c, const double* prow, int nrow, int b, int j,
         c.mlp_mult = mult;
         c.cand_alpha[0] = fmin(P.alpha_max, fmax(P.alpha_min, (double)mult * alpha_bb));
         c.cand_alpha[1] = alpha_bb;
+      } else if (nc == 3) {  // lean learned step: the next D uses the proposal directly
+        c.mlp_mult = mult;
+        alpha_bb = fmin(P.alpha_max, fmax(P.alpha_min, (double)mult * alpha_bb));
       } else {
         for (int m = 0; m < kNCand; ++m)
           c.cand_alpha[m] = fmin(P.alpha_max, fmax(P.alpha_min, exp2(0.5 * (m - 4)) * alpha_bb));
@@ -426,7 +434,8 @@ __device__ void final_pen_body(Ctl& c, const double* pax, int nax, const double*
 // Fused control after a producing kernel: modes of RowArgs::ctl_mode.
 __device__ void fused_control(int mode, Ctl& c, const double* part, int nslots, int b, int r, int j,
                               const Params& P, const double* G64fix, double* sh, int nc) {
-  const int pc = P.controller == 1 ? 2 : (P.controller == 2 ? kNCand : 1);  // candidates of the solve
+  // candidates of the solve (3: the lean learned step, one candidate)
+  const int pc = P.controller == 1 ? 2 : (P.controller == 2 ? kNCand : (P.controller == 3 ? 3 : 1));
   switch (mode) {
     case CTL_START_W: pen_start_body(c, part, nslots, b, j, P, 1, 0, sh); break;
     case CTL_START_H: pen_start_body(c, part, nslots, b, j, P, 0, 0, sh); break;

@@ -74,3 +74,20 @@ def test_bf16_batched_restarts_match_single():
     for j in range(3):
         W1, H1, _, _, _ = gpu_solve(A, Ws[j], 8, Ws[j], precision=S.SNMF_BF16, max_iter=3, tol=0.0)
         assert rel(Wb[:, 8 * j:8 * (j + 1)], W1) <= 1e-5
+
+
+def test_bf16_reported_residual_is_the_stored_operators():
+    """The final evaluation's closed-form residual (||A~||^2 - 2 <W, A~ Ht> + <W^T W, Ht^T Ht>)
+    must equal the residual of the returned factors against the stored BF16 A~, computed
+    here in FP64, to FP32 accuracy, for long K (n = 4096) and several restarts."""
+    import torch
+    n, r, b = 4096, 64, 4
+    A, _ = planted_dense(n, r, 0.05, seed=77)
+    W0 = np.concatenate([uniform_init(n, r, math.sqrt(A.mean() / r), seed=78 + j) for j in range(b)], 1)
+    W, H, st, stats, per = gpu_solve(A, W0, r, W0, precision=S.SNMF_BF16, max_iter=60, tol=1e-4, batch=b)
+    Ab = torch.tensor(A, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+    for j in range(b):
+        sl = slice(j * r, (j + 1) * r)
+        res = np.linalg.norm(Ab - W[:, sl] @ H[:, sl].T) / np.linalg.norm(Ab)
+        # FP32 cancellation floor: ~1e-7 ||A||^2 in res^2
+        assert abs(per["residual"][j] - res) <= max(1e-5, 2e-7 / res), (j, per["residual"][j], res)

@@ -46,13 +46,14 @@ def test_mlp_training_gradient_matches_oracle():
     assert abs(loss - OM.loss(w2.astype(np.float64), feats, targs)) <= 1e-4 * max(1.0, loss)
 
 
-def test_zero_weights_reproduce_plain_bb_exactly():
+@pytest.mark.parametrize("mode", [1, 3])
+def test_zero_weights_reproduce_plain_bb_exactly(mode):
     """o = 0 gives multiplier 1: the proposal equals the plain BB direction, so the accepted
-    steps and the iterates are the plain method's, bit for bit."""
+    steps and the iterates are the plain method's, bit for bit (two-candidate and lean modes)."""
     A, _ = planted_dense(300, 6, 0.01, seed=801)
     W0 = uniform_init(300, 6, math.sqrt(A.mean() / 6), 802)
     Wp, Hp, _, sp, _ = _solve(A, W0, 6, 1, 0, max_iter=20, tol=0.0)
-    Wl, Hl, _, sl, _ = _solve(A, W0, 6, 1, 1, weights=np.zeros(S.SNMF_MLP_NPARAMS, np.float32), max_iter=20,
+    Wl, Hl, _, sl, _ = _solve(A, W0, 6, 1, mode, weights=np.zeros(S.SNMF_MLP_NPARAMS, np.float32), max_iter=20,
                               tol=0.0)
     assert np.array_equal(Wp, Wl) and np.array_equal(Hp, Hl)
     assert sl["ctl_proposals"] > 0
@@ -78,7 +79,8 @@ def test_record_mode_produces_labelled_states():
     assert np.all((f[:, 4] >= 0) & (f[:, 4] <= 1))
 
 
-def test_learned_controller_gain_over_plain_bb():
+@pytest.mark.parametrize("mode", [1, 3])
+def test_learned_controller_gain_over_plain_bb(mode):
     """Held-out planted problems (seeds disjoint from the training set), batched restarts:
     with the trained controller every restart must still reach the tolerance, the best
     restart's residual must be within 1e-3 of the plain method's, and the test reports the
@@ -95,7 +97,7 @@ def test_learned_controller_gain_over_plain_bb():
         A, _ = planted_dense(n, r, seed=700000 + p, rel_noise=0.01)
         W0 = np.concatenate([uniform_init(n, r, math.sqrt(A.mean() / r), 710000 + 16 * p + j) for j in range(4)], 1)
         Wp, Hp, stp, sp, pp = _solve(A, W0, r, 4, 0, max_iter=3000)
-        Wl, Hl, stl, sl, pl = _solve(A, W0, r, 4, 1, weights=w, max_iter=3000)
+        Wl, Hl, stl, sl, pl = _solve(A, W0, r, 4, mode, weights=w, max_iter=3000)
         assert stl == S.SNMF_OK, sl
         assert np.all(pl["pg_rel"] <= 1e-4)
         assert pl["residual"].min() <= pp["residual"].min() + 1e-3, (pl["residual"], pp["residual"])
@@ -104,5 +106,5 @@ def test_learned_controller_gain_over_plain_bb():
         it_learn += pl["iters"].sum()
         t_plain += sp["seconds"]
         t_learn += sl["seconds"]
-    print(f"learned controller: outer iterations {it_learn:.0f} vs plain {it_plain:.0f} "
+    print(f"learned controller (mode {mode}): outer iterations {it_learn:.0f} vs plain {it_plain:.0f} "
           f"({100 * (1 - it_learn / it_plain):+.1f}%), device time {t_learn:.3f} s vs {t_plain:.3f} s")
