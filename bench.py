@@ -183,6 +183,12 @@ def run_reference(args):
     return 0
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the product kernel, from the
+# ncu captures summarised in profiles/ (k_gemm_tc_dense8192_N512.md, k_bgemm_tc_uneven256.md);
+# keys: (workload, precision, r, batch).  Other configurations report null.
+PROFILED_TRAFFIC = {("dense8192", "bf16", 64, 8): 189.0e6, ("uneven", "bf16", None, None): 875.5e6}
+
+
 def controller_weights(args):
     """Trained controller weights shipped with the package (None when absent or disabled)."""
     if args.controller == "off":
@@ -280,9 +286,10 @@ def run_uneven(args):
     gbs = alg_bytes / (ms_prod * 1e-3) / 1e9
     kname = ("k_bsplit_x + k_bgemm_tc (grouped tcgen05 A_p (X_hi + X_lo), BF16 A)" if args.precision == "bf16"
              else "k_bgemm (grouped A_p X_p, CUDA cores, %s A)" % args.precision)
-    roof = {"bound": "hbm", "kernel": kname,
+    traffic = PROFILED_TRAFFIC.get(("uneven", args.precision, None, None)) if args.nprob == 256 else None
+    roof = {"bound": "hbm", "kernel": kname, "traffic_bytes": traffic,
             "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
-            "traffic": None, "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
+            "traffic": traffic, "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
             "flops_per_launch": flops, "tflops": flops / (ms_prod * 1e-3) / 1e12, "ms_per_launch": ms_prod}
 
     compare = None
@@ -488,6 +495,7 @@ def main():
                 "alg_bytes_per_launch": alg_bytes, "flops_per_launch": flops,
                 "ms_per_launch": ms_kern, "ms_per_product_with_epilogue": ms_prod}
     elif args.precision == "bf16":
+        workload_key = "dense8192" if args.n == 8192 else None
         # tensor work: the hi and lo parts of X each take one BF16 MMA pass
         tflops = 2 * flops / (ms_kern * 1e-3) / 1e12
         ridge = peaks["bf16_tflops"] * 1e12 / (peaks["hbm_gbs"] * 1e9)
@@ -499,7 +507,7 @@ def main():
                 "peak": peaks["bf16_tflops"] if tensor_bound else peaks["hbm_gbs"],
                 "unit": "TFLOP/s" if tensor_bound else "GB/s",
                 "frac": (tflops / peaks["bf16_tflops"]) if tensor_bound else (aw_gbs / peaks["hbm_gbs"]),
-                "traffic": None,
+                "traffic": PROFILED_TRAFFIC.get((workload_key, args.precision, args.r, args.batch)),
                 "peak_source": peak_kind + (" bf16_tflops (burst cuBLAS)" if tensor_bound else " hbm_gbs (burst copy)"),
                 "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
                 "aw_gbs": aw_gbs, "aw_hbm_frac": aw_gbs / peaks["hbm_gbs"],
