@@ -189,6 +189,28 @@ def run_reference(args):
 PROFILED_TRAFFIC = {("dense8192", "bf16", 64, 8): 189.0e6, ("uneven", "bf16", None, None): 875.5e6}
 
 
+def rank_restarts(batch, rank):
+    """Restart indices of this rank: each rank solves its own `batch` restarts (weak scaling,
+    no data exchange between ranks)."""
+    return list(range(rank * batch, (rank + 1) * batch))
+
+
+def uneven_seed(rank):
+    """Problem-set seed of a rank: rank 0 uses the bench's set, others disjoint sets."""
+    return 5000 + 100000 * rank
+
+
+def max_over_ranks(value, world, device=None):
+    """Whole-job time: the maximum over ranks (all_reduce MAX; any backend)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def controller_weights(args):
     """Trained controller weights shipped with the package (None when absent or disabled)."""
     if args.controller == "off":
@@ -201,12 +223,12 @@ def controller_weights(args):
     return None
 
 
-def uneven_problems(count):
+def uneven_problems(count, seed=5000):
     """256 planted problems, n ~ U{64..2048}, r ~ U{4..32}, 1% relative noise (problem seeds
-    5001..); starts U[0, sqrt(mean(A_p)/r_p)] with seed 6000 + p."""
+    seed + 1 ..); starts U[0, sqrt(mean(A_p)/r_p)] with seed 6000 + p."""
     from workloads import uneven_batch, uniform_init
     out = []
-    for p, (A, _, r) in enumerate(uneven_batch(count, seed=5000)):
+    for p, (A, _, r) in enumerate(uneven_batch(count, seed=seed)):
         out.append((A, uniform_init(A.shape[0], r, math.sqrt(A.mean() / r), seed=6000 + p), r))
     return out
 
@@ -233,7 +255,7 @@ def run_uneven(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     S.load_library()
-    probs = uneven_problems(args.nprob)
+    probs = uneven_problems(args.nprob, uneven_seed(rank))  # weak scaling: own problems per rank
     ns = [A.shape[0] for A, _, _ in probs]
     rs = [r for _, _, r in probs]
     vals = torch.tensor(np.concatenate([A.ravel() for A, _, _ in probs]), dtype=torch.float32, device=dev)
@@ -260,6 +282,8 @@ def run_uneven(args):
     for _ in range(args.warmup):
         solve(h)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     clocks = ClockSampler(local)
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -271,9 +295,11 @@ def run_uneven(args):
         launches += stats["kernel_launches"]
         last = (st, stats)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     clk = clocks.stop()
     times = [a.elapsed_time(b) for a, b in ev]
-    ms = statistics.mean(times)
+    ms = max_over_ranks(statistics.mean(times), world, dev)
     st, stats = last
     per = S.snmf_restart_stats(h, len(probs))
     ms_prod, _ = S.snmf_profile_ax(h, 10)
@@ -293,7 +319,7 @@ def run_uneven(args):
             "flops_per_launch": flops, "tflops": flops / (ms_prod * 1e-3) / 1e12, "ms_per_launch": ms_prod}
 
     compare = None
-    if not args.no_compare:
+    if not args.no_compare and rank == 0:
         compare = {}
         for name, pr, c in (("batched_bf16_plain", S.SNMF_BF16, 0), ("batched_f32_plain", S.SNMF_F32, 0)):
             if pr == prec and c == ctl:
@@ -384,6 +410,8 @@ def run_uneven(args):
                           "ms_per_step_all": times},
                 "compare": compare}
         print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
@@ -412,8 +440,9 @@ def main():
 
     prec = {"f64": S.SNMF_F64, "f32": S.SNMF_F32, "bf16": S.SNMF_BF16, "fp8": S.SNMF_FP8}[args.precision]
     tdt = torch.float64 if args.precision == "f64" else torch.float32
-    A_np, starts = dense_planted_8192(args.r, args.batch + rank * args.batch, n=args.n)
-    starts = starts[rank * args.batch:(rank + 1) * args.batch]  # replicas: own restarts per rank
+    mine = rank_restarts(args.batch, rank)  # replicas: own restarts per rank
+    A_np, starts = dense_planted_8192(args.r, mine[-1] + 1, n=args.n)
+    starts = [starts[j] for j in mine]
     W0_np = np.concatenate(starts, axis=1)
     A = torch.tensor(A_np, dtype=tdt, device=dev)
     W0 = torch.tensor(W0_np, dtype=tdt, device=dev)
@@ -466,10 +495,7 @@ def main():
     clk = clocks.stop()
     times = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(times)
-    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
+    ms_max = max_over_ranks(ms, world, dev)
     st, stats = stats_list[-1]
 
     # dominant kernel: the A*X product, timed alone on the library's stream (CUDA events)
