@@ -544,6 +544,29 @@ def main():
                 "unit": "TFLOP/s", "frac": None, "traffic": None, "aw_gbs": aw_gbs,
                 "ms_per_launch": ms_kern}
 
+    # the row kernels of an inner step, timed alone (CUDA events on the library's stream);
+    # per outer iteration: 2 products, 2 K D-step launches, 2 K update launches (K = 5)
+    kernels = {"product": roof}
+    if form == S.SNMF_PENALTY and args.r <= 64:
+        ms_d, ms_u = S.snmf_profile_steps(h, 20)
+        K = opts.inner_iters
+        fb4 = n * N * esz
+        nd = 6 + (1 if ctl == 1 else 0)  # D step: reads X, g, B; writes Z, g(Z), D (+ D2)
+        for name, ms_k, nbuf in (("dstep", ms_d, nd), ("update", ms_u, 8)):  # update: 6 reads, 2 writes
+            gb = nbuf * fb4 / (ms_k * 1e-3) / 1e9
+            kernels[name] = {"bound": "hbm", "kernel": "k_rowgemm<%s>" % ("OP_ZSTEP, EPI_DIR" if name == "dstep"
+                                                                          else "OP_UPD, EPI_GRAD"),
+                             "achieved": gb, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": gb / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_kind,
+                             "alg_bytes_per_launch": nbuf * fb4, "ms_per_launch": ms_k,
+                             "launches_per_outer_iteration": 2 * K,
+                             "note": "working set of one launch fits in L2, as inside the iteration"}
+        per_iter = {"product": 2 * ms_kern, "dstep": 2 * K * ms_d, "update": 2 * K * ms_u}
+        dominant = max(per_iter, key=per_iter.get)
+        roof = dict(kernels[dominant])
+        roof["dominant_by"] = {k: round(v, 4) for k, v in per_iter.items()}
+        roof["dominant_unit"] = "ms of kernel time per outer iteration"
+
     # end to end through the C ABI with host buffers (inputs and result cross PCIe/C2C)
     e2e = None
     if not args.no_e2e:
@@ -615,8 +638,8 @@ def main():
                            "l2": ("inputs larger than L2 (A = %.0f MB)" % (a_bytes / 2**20)) if flush is None
                            else "L2 flushed between timed steps (256 MB write)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "tuning": tuning,
+                "roofline": roof, "roofline_kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk, "tuning": tuning,
                 "solve": {"status": st, "iters": stats["iters"], "residual": stats["residual"],
                           "pg_rel": stats["pg_rel"], "ls_fail": stats["ls_fail"],
                           "ax_products": stats["ax_products"], "graph_replays": stats["graph_replays"],

@@ -274,6 +274,17 @@ SNMF_API snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_produc
                                      double* ms_kernel);
 
 /*
+ * Measurement utility (no counterpart in the paper): mean time (ms, CUDA events on the
+ * handle's stream) of one launch of the D-step kernel (Z step, gradient at Z, D direction,
+ * fused line search; Alg. 1 lines 2-4) and of the update kernel (relaxed update, gradient,
+ * BB inner products) of a W block, each launched `iters` times on the buffers of the last
+ * solve with every restart marked live.  Penalty form without graph term, r <= 64.  It
+ * overwrites the handle's work buffers and the factors held in it (snmf_restart_stats keeps
+ * the solve's results); SNMF_ERR_STATE before a solve.
+ */
+SNMF_API snmf_status snmf_profile_steps(snmf_handle h, int iters, double* ms_dstep, double* ms_update);
+
+/*
  * The product configuration chosen by the autotuner (no counterpart in the paper):
  * split-K slices, tcgen05 ring stages and CTAs per SM (0 where the kernel has none), the
  * measured mean time in ms, and *from_cache = 1 when it came from the cache file or an

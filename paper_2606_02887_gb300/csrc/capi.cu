@@ -1154,6 +1154,64 @@ snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_product, double
   return SNMF_OK;
 }
 
+snmf_status snmf_profile_steps(snmf_handle h, int iters, double* ms_dstep, double* ms_update) {
+  if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
+  if (iters < 1) return fail(h, SNMF_ERR_ARG, "iters must be >= 1");
+  if (h->opt.formulation != SNMF_PENALTY || h->graph || h->r > 64)
+    return fail(h, SNMF_ERR_ARG, "step profiling needs the penalty form without graph term and r <= 64");
+  if (!h->have_result) return fail(h, SNMF_ERR_STATE, "run a solve first (the step kernels read its buffers)");
+  if (sync_user(h) != SNMF_OK) return SNMF_ERR_CUDA;
+  std::vector<Ctl> live(h->h_ctl.begin(), h->h_ctl.begin() + h->b);
+  for (Ctl& c : live) {
+    c.active = 1;
+    c.nan_seen = 0;
+  }
+  CK(cudaMemcpyAsync(h->ctl, live.data(), h->b * sizeof(Ctl), cudaMemcpyHostToDevice, h->s));
+  static const int one = 1;
+  CK(cudaMemcpyAsync(h->run, &one, sizeof(int), cudaMemcpyHostToDevice, h->s));
+  const Params P = make_params(h);
+  const int td = h->tdtype;
+  const int nc = h->opt.step_controller == 1 ? 2 : (h->opt.step_controller == 2 ? kNCand : 1);
+  void* X = h->buf[B_W];
+  RowArgs ad = row_base(h, &P);  // the D step of a W block, as in pen_block
+  ad.B = h->buf[B_B];
+  ad.Dout = h->buf[B_D]; ad.gZout = h->buf[B_GZ];
+  ad.Wcur = X; ad.gWcur = h->buf[B_G];
+  ad.X = X; ad.g_in = h->buf[B_G]; ad.Xout = h->buf[B_Z];
+  ad.want_q = 1;
+  ad.ctl_mode = CTL_LS;
+  ad.dstore = nc == kNCand ? 4 : 0;
+  ad.D2out = h->buf[B_AD];
+  RowArgs au = row_base(h, &P);  // the update of a W block
+  au.B = h->buf[B_B];
+  au.gout = h->buf[B_G];
+  au.Xold = X; au.gold = h->buf[B_G];
+  au.Zold = h->buf[B_Z]; au.gZold = h->buf[B_GZ];
+  au.Xout = X;
+  au.ctl_mode = CTL_UPD_W;
+  au.Zin = h->buf[B_Z]; au.Din = h->buf[B_D]; au.Din2 = h->buf[B_AD];
+  cudaEvent_t e[4];
+  for (auto& x : e) CK(cudaEventCreate(&x));
+  launch_rowgemm(td, OP_ZSTEP, EPI_DIR, ad, h->s, nc);  // warm-up
+  launch_rowgemm(td, OP_UPD, EPI_GRAD, au, h->s);
+  CK(cudaEventRecord(e[0], h->s));
+  for (int t = 0; t < iters; ++t) launch_rowgemm(td, OP_ZSTEP, EPI_DIR, ad, h->s, nc);
+  CK(cudaEventRecord(e[1], h->s));
+  CK(cudaEventRecord(e[2], h->s));
+  for (int t = 0; t < iters; ++t) launch_rowgemm(td, OP_UPD, EPI_GRAD, au, h->s);
+  CK(cudaEventRecord(e[3], h->s));
+  CK(cudaStreamSynchronize(h->s));
+  CK(cudaGetLastError());
+  float m1 = 0.f, m2 = 0.f;
+  cudaEventElapsedTime(&m1, e[0], e[1]);
+  cudaEventElapsedTime(&m2, e[2], e[3]);
+  for (auto& x : e) cudaEventDestroy(x);
+  if (ms_dstep) *ms_dstep = m1 / iters;
+  if (ms_update) *ms_update = m2 / iters;
+  return SNMF_OK;
+}
+
 snmf_status snmf_tuned_config(snmf_handle h, int32_t* splits, int32_t* stages, int32_t* per_sm, double* ms,
                               int32_t* from_cache) {
   if (!h) return SNMF_ERR_STATE;

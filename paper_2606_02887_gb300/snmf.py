@@ -28,7 +28,7 @@ EXPORTED = (
     "snmf_default_options", "snmf_create", "snmf_set_graph_reg", "snmf_lai_sketch",
     "snmf_solve", "snmf_solve_host", "snmf_restart_stats", "snmf_get_factors",
     "snmf_apply", "snmf_profile_ax", "snmf_apply_dense_noalloc", "snmf_controller_data",
-    "snmf_mlp_train", "snmf_tuned_config", "snmf_destroy", "snmf_last_error",
+    "snmf_mlp_train", "snmf_tuned_config", "snmf_profile_steps", "snmf_destroy", "snmf_last_error",
 )
 NOALLOC_SCRATCH_BYTES = 64 << 20
 NOALLOC_MAX_SLICE_PAIR_BYTES = NOALLOC_SCRATCH_BYTES - (1 << 20)
@@ -95,6 +95,7 @@ def load_library(path: str = LIB_PATH):
                                    C.POINTER(C.c_double), C.c_void_p]
     lib.snmf_tuned_config.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                       C.POINTER(C.c_double), C.POINTER(C.c_int32)]
+    lib.snmf_profile_steps.argtypes = [H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.snmf_destroy.argtypes = [H]
     lib.snmf_last_error.argtypes = [H]
     lib.snmf_last_error.restype = C.c_char_p
@@ -294,6 +295,14 @@ def snmf_mlp_train(feats, targets, weights, steps: int = 1000, lr: float = 1e-2)
     _check(lib, None, lib.snmf_mlp_train(f.ctypes.data, t.ctypes.data, len(t), w.ctypes.data, int(steps),
                                          float(lr), C.byref(loss), g0.ctypes.data))
     return w, loss.value, g0
+
+
+def snmf_profile_steps(h, iters: int = 20):
+    """Mean ms of one D-step launch and of one update launch of a W block (after a solve)."""
+    lib = load_library()
+    a, b = C.c_double(), C.c_double()
+    _check(lib, h, lib.snmf_profile_steps(h, int(iters), C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def snmf_tuned_config(h) -> dict:
