@@ -32,7 +32,7 @@ k_gram(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, int b
 }
 
 template <typename T, int OP, int EPI, int BM, int NC>
-__global__ void __launch_bounds__(256, 2) k_rowgemm(RowArgs a) {
+__global__ void __launch_bounds__(256, 3) k_rowgemm(RowArgs a) {
   rowgemm_body<T, OP, EPI, BM, NC>(a, blockIdx.z, blockIdx.x, blockIdx.y, gridDim.y, gridDim.x * gridDim.y);
 }
 

@@ -778,7 +778,7 @@ __device__ __forceinline__ void rowgemm_body(const RowArgs& a, int j, int bx, in
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc2[p][q] = T(0);
         for (int k0 = 0; k0 < r; k0 += KC) {
-          {
+          if (!xs_ok) {  // else G (r <= KC) is still in shared memory from the first product
             constexpr int NG = KC * 64 / 256;
             T gv_[NG];
 #pragma unroll
