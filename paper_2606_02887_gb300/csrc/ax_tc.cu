@@ -530,6 +530,10 @@ int launch_sums_bf16(const void* A16, int64_t elems, double* part, cudaStream_t 
 int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune) {
   TcPlan pl{};
   pl.BN = N <= 256 ? ((N + 15) / 16 * 16) : 256;
+  if (tune && tune->bn > 0) {
+    if (tune->bn % 16 || tune->bn > 256) return -1;
+    pl.BN = tune->bn < pl.BN ? tune->bn : pl.BN;
+  }
   pl.tiles_n = (N + pl.BN - 1) / pl.BN;
   pl.tiles_m = (int)((n + BM - 1) / BM);
   const int64_t kiters_total = (n + BK - 1) / BK;

@@ -191,12 +191,18 @@ snmf_status autotune_product(snmf_ctx* h) {
   std::vector<ProdTune> cand;
   if (h->A.a_dtype == 2) {
     const int rings[7][2] = {{2, 2}, {2, 3}, {2, 4}, {1, 2}, {1, 3}, {1, 4}, {1, 6}};
+    const int bn0 = h->N <= 256 ? (h->N + 15) / 16 * 16 : 256;
+    std::vector<int> bns{bn0};
+    for (int w : {128, 64})
+      if (w < bn0) bns.push_back(w);
+    for (int bn : bns)
     for (auto& rg : rings)
       for (int sp : {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16, 19, 24, 32}) {
         ProdTune t;
         t.per_sm = rg[0];
         t.stages = rg[1];
         t.splits = sp;
+        t.bn = bn;
         TcPlan pl;
         if (tc_plan(h->n, h->N, &pl, &t) < 0 || pl.splits != sp) continue;
         if ((size_t)sp * h->n * h->N > h->ws_elems && sp > 1) continue;

@@ -1,7 +1,7 @@
 // JSON cache of the product autotuner (the search itself runs in capi.cu, where the
 // handle's buffers are).  File layout:
 //   {"format": "...", "devices": {"<name>/<SMs>": {"dense/bf16/n8192/N64":
-//       {"splits": 2, "stages": 3, "per_sm": 2, "ms": 0.0441}, ...}, ...}}
+//       {"splits": 2, "stages": 3, "per_sm": 2, "bn": 64, "ms": 0.0441}, ...}, ...}}
 // The reader accepts any JSON of that shape (objects, strings, numbers, true/false/null);
 // unknown keys are ignored.  Entries of other devices are kept when the file is rewritten.
 #include <cuda_runtime.h>
@@ -96,6 +96,7 @@ struct Parser {
       if (k == "splits") e.cfg.splits = (int)num();
       else if (k == "stages") e.cfg.stages = (int)num();
       else if (k == "per_sm") e.cfg.per_sm = (int)num();
+      else if (k == "bn") e.cfg.bn = (int)num();
       else if (k == "ms") e.ms = num();
       else skip();
     } while (ok && eat(','));
@@ -163,8 +164,9 @@ bool write_file(const char* path, const Table& t) {
     first_dev = false;
     bool first = true;
     for (const auto& e : d.second) {
-      std::fprintf(f, "%s\n      %s: {\"splits\": %d, \"stages\": %d, \"per_sm\": %d, \"ms\": %.6g}", first ? "" : ",",
-                   quoted(e.first).c_str(), e.second.cfg.splits, e.second.cfg.stages, e.second.cfg.per_sm, e.second.ms);
+      std::fprintf(f, "%s\n      %s: {\"splits\": %d, \"stages\": %d, \"per_sm\": %d, \"bn\": %d, \"ms\": %.6g}",
+                   first ? "" : ",", quoted(e.first).c_str(), e.second.cfg.splits, e.second.cfg.stages,
+                   e.second.cfg.per_sm, e.second.cfg.bn, e.second.ms);
       first = false;
     }
     std::fprintf(f, "\n    }");

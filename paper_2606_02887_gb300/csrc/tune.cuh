@@ -11,6 +11,7 @@ struct ProdTune {
   int splits = 0;   // split-K slices
   int stages = 0;   // tcgen05 product: shared-memory ring stages
   int per_sm = 0;   // tcgen05 product: CTAs planned per SM (sets the default split count)
+  int bn = 0;       // tcgen05 product: output columns per CTA tile (multiple of 16, <= 256)
 };
 
 struct TuneEntry {
