@@ -52,9 +52,10 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="dense8192", choices=["dense8192", "uneven"],
+    p.add_argument("--workload", default="dense8192", choices=["dense8192", "uneven", "graph", "lai"],
                    help="dense8192: one n=8192 problem (restarts); uneven: 256 planted problems of "
-                        "uneven size in one batched solve")
+                        "uneven size in one batched solve; graph: Graph-SNMPBB on a 20000-point GMM kNN "
+                        "graph with 32 restarts; lai: LAI-SNMPBB on a 2e6-node Chung-Lu graph")
     p.add_argument("--nprob", type=int, default=256)
     p.add_argument("--controller", default="auto", choices=["auto", "off", "on"],
                    help="learned step controller (auto: on when trained weights are present)")
@@ -415,12 +416,147 @@ def run_uneven(args):
     return 0
 
 
+def _sparse_common(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    return world, rank, torch.device("cuda", local)
+
+
+def _cluster_accuracy(labels, pred, k):
+    """Fraction of points in the best one-to-one matching of clusters to planted labels."""
+    import numpy as np
+    from scipy.optimize import linear_sum_assignment
+    C = np.zeros((k, k))
+    np.add.at(C, (pred, labels), 1)
+    row, col = linear_sum_assignment(-C)
+    return float(C[row, col].sum() / len(labels))
+
+
+def run_sparse(args):
+    """Graph-SNMPBB on the GMM kNN graph (CSR A_hat, CSR L, gamma 0.1, r 20, 32 restarts in one
+    solve) or LAI-SNMPBB on the Chung-Lu graph (k 64 + 10, 2 power iterations, r 32)."""
+    import numpy as np
+    import torch
+
+    import paper_2606_02887_gb300.snmf as S
+    from workloads import chung_lu_csr, gmm_knn_graph, uniform_init
+
+    world, rank, dev = _sparse_common(args)
+    S.load_library()
+    t_gen = time.perf_counter()
+    if args.workload == "graph":
+        A_hat, L, labels, _ = gmm_knn_graph(n=20000, d=64, comps=20, k=10, seed=3000 + 7 * rank)
+        r, b, gamma = 20, 32, 0.1
+    else:
+        A_hat = chung_lu_csr(n=2_000_000, exponent=2.1, mean_degree=16.0, seed=4000 + 7 * rank)
+        L, labels = None, None
+        r, b, gamma = 32, 1, 0.0
+    t_gen = time.perf_counter() - t_gen
+    n = A_hat.n
+    nnz = int(len(A_hat.values))
+    tens = lambda x, dt: torch.tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
+    Am = (tens(A_hat.rowptr, torch.int32), tens(A_hat.colidx, torch.int32), tens(A_hat.values, torch.float32))
+    mean = float(A_hat.values.sum()) / (float(n) * n)
+    W0 = np.concatenate([uniform_init(n, r, math.sqrt(mean / r), seed=3100 + j) for j in range(b)], 1)
+    W0t = torch.tensor(W0, dtype=torch.float32, device=dev)
+    W, H = torch.empty_like(W0t), torch.empty_like(W0t)
+    opts = S.snmf_default_options(precision=S.SNMF_F32, batch=b, max_iter=args.max_iter, tol=args.tol,
+                                  nonmonotone_M=10)
+    stream = torch.cuda.current_stream(dev)
+    h = S.snmf_create(S.csr_matrix(n, *Am), r, opts, stream=stream)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sketch_ms = None
+    if args.workload == "graph":
+        Lm = (tens(L.rowptr, torch.int32), tens(L.colidx, torch.int32), tens(L.values, torch.float32))
+        S.snmf_set_graph_reg(h, S.csr_matrix(n, *Lm), gamma)
+    else:
+        ev0.record(stream)
+        S.snmf_lai_sketch(h, 64, 10, 2, 4242)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sketch_ms = ev0.elapsed_time(ev1)
+
+    def solve():
+        W.copy_(W0t)
+        H.copy_(W0t)
+        return S.snmf_solve(h, W, H)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    times, launches, last = [], 0, None
+    for _ in range(args.steps):
+        ev0.record(stream)
+        st, stats = solve()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        launches += stats["kernel_launches"]
+        last = (st, stats)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(statistics.mean(times), world, dev)
+    st, stats = last
+    per = S.snmf_restart_stats(h, b)
+    ms_prod, ms_kern = S.snmf_profile_ax(h, 10)
+    peaks, peak_kind = measured_peaks()
+    N = r * b
+    if args.workload == "graph":
+        alg = nnz * 8 + (n + 1) * 4 + 2 * n * N * 4  # CSR (col index + value), row pointers, X, Y
+        kname = "k_spmm_csr (+ k_ax_finish)"
+    else:
+        ell = 64
+        alg = 2 * n * ell * 4 + 2 * n * N * 4  # U read by U^T X and by U (Lambda X^), X, Y
+        kname = "k_utx + k_rowmul (LAI product U (Lambda (U^T X)))"
+    gbs = alg / (ms_prod * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": kname, "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_kind,
+            "alg_bytes_per_launch": alg, "ms_per_launch": ms_prod}
+    extra = {}
+    if labels is not None:
+        Wn = W.cpu().numpy()
+        best = int(np.argmin(per["f"]))
+        pred = np.argmax(Wn[:, best * r:(best + 1) * r], axis=1)
+        extra["accuracy_best_restart"] = _cluster_accuracy(np.asarray(labels), pred, r)
+    S.snmf_destroy(h)
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": ("Graph-SNMPBB, GMM kNN graph n=20000 (20 components, d=64, k=10), "
+                                        "gamma 0.1, r=20, 32 restarts" if args.workload == "graph" else
+                                        "LAI-SNMPBB, Chung-Lu n=2e6 (exponent 2.1, mean degree 16), "
+                                        "sketch k=64+10, q=2, r=32"),
+                           "n": n, "nnz": nnz, "r": r, "batch": b, "tol": args.tol, "max_iter": args.max_iter,
+                           "generation_s": t_gen, "sketch_ms": sketch_ms,
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "roofline": roof, "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk,
+                "solve": {"status": st, "iters": stats["iters"], "residual_best": stats["residual"],
+                          "pg_rel": stats["pg_rel"], "ms_per_step_all": times, **extra}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "uneven":
         return run_uneven(args)
+    if args.workload in ("graph", "lai"):
+        return run_sparse(args)
 
     import numpy as np
     import torch
