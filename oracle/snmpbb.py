@@ -189,6 +189,27 @@ def penalty_grad_Ht(A, W, Ht, lam, gamma=0.0, L=None) -> np.ndarray:
 # Algorithm 1 (NMPBB) for one block
 # ----------------------------------------------------------------------------
 
+def laplacian_norm(L, iters: int = 50) -> float:
+    """||L||_2 of the (positive semidefinite) graph Laplacian: the part gamma ||L||_2 that the
+    graph term adds to the Lipschitz constant of the regularised block's gradient.
+
+    Reading (the paper gives rho_0 = ||H H^T||_2 only for the unregularised blocks,
+    Sec. 2.4): the graph-regularised blocks use rho = ||X^T X||_2 + gamma ||L||_2; without
+    the gamma ||L||_2 part the first Z step of the 20000-point kNN workload (||L||_2 = 27,
+    gamma = 0.1) overshoots and the iteration diverges.  Fixed count of power iterations
+    from s_i = 1 + (i mod 2) (not constant: L 1 = 0) and the Rayleigh quotient."""
+    n = L.shape[0]
+    v = 1.0 + (np.arange(n) % 2).astype(np.float64)
+    v /= np.linalg.norm(v)
+    for _ in range(iters):
+        w = np.asarray(L @ v).ravel()
+        nw = float(np.linalg.norm(w))
+        if nw == 0.0:
+            return 0.0
+        v = w / nw
+    return float(v @ np.asarray(L @ v).ravel())
+
+
 def _bb_step(S, Y, rho: float, opts: Options) -> float:
     """Alg. 1 line 3 / Eq. (2.10): alpha = min(a_max, max(a_min, <S,S>/<S,Y>)).
 
@@ -302,8 +323,10 @@ def snmpbb_direct(A, W0, opts: Options, L=None, keep_iterates=False):
     def fgrad(X):
         return direct_gradient(A, X, gamma, L)
 
+    lshift = gamma * laplacian_norm(L, opts.power_iters) if (gamma and L is not None) else 0.0
+
     def rho_fn(X):
-        return opts.direct_rho_factor * spectral_norm(X.T @ X, opts.power_iters)
+        return opts.direct_rho_factor * spectral_norm(X.T @ X, opts.power_iters) + lshift
 
     W0 = np.asarray(W0, dtype=np.float64)
     pg0 = float(np.linalg.norm(projected_gradient(W0, fgrad(W0))))
@@ -343,6 +366,8 @@ def snmpbb_penalty(A, W0, Ht0, opts: Options, L=None, keep_iterates=False):
         return math.sqrt(float(np.sum(a * a)) + float(np.sum(b * b)))
 
     pg0 = joint_pg(W, Ht)
+    # graph term: gamma ||L||_2 joins rho of the H block (reading, see laplacian_norm)
+    lshift = gamma * laplacian_norm(L, opts.power_iters) if (gamma and L is not None) else 0.0
     outer = []
     ls_fail = 0
     pg = pg0
@@ -354,7 +379,7 @@ def snmpbb_penalty(A, W0, Ht0, opts: Options, L=None, keep_iterates=False):
                          lambda X: penalty_grad_W(A, X, Hfix, lam),
                          W, lambda X: rho_w, opts.inner_iters, opts, None, keep_iterates)
         Wfix = W
-        rho_h = spectral_norm(Wfix.T @ Wfix, opts.power_iters)
+        rho_h = spectral_norm(Wfix.T @ Wfix, opts.power_iters) + lshift
         Ht, _, ih = nmpbb(lambda X: penalty_objective(A, Wfix, X, lam, gamma, L, mode),
                           lambda X: penalty_grad_Ht(A, Wfix, X, lam, gamma, L),
                           Ht, lambda X: rho_h, opts.inner_iters, opts, None, keep_iterates)

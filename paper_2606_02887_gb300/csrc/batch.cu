@@ -244,7 +244,7 @@ k_bgram(const BProb* __restrict__ probs, const int2* __restrict__ items, const i
   gram_body<T>(X + pb.xoff, Y + pb.xoff, pb.n, pb.r, 1, pb.r, kGChunk, 1, gpart + pb.gpoff, pair, npairs,
                ctl ? ctl + it.x : nullptr, run, G64 + pb.g3off, GT ? GT + pb.goff : nullptr, tpair,
                use_lam ? pb.lam : 0.0, counters + 3 * it.x, rho_ctl ? rho_ctl + it.x : nullptr, rho_iters,
-               1.0, it.y, pb.gch, 0);
+               1.0, 0.0, it.y, pb.gch, 0);
 }
 
 // rho_p = ||G_p||_2 (FP64 working type), one block per problem
@@ -257,7 +257,7 @@ k_brho(const BProb* __restrict__ probs, const double* __restrict__ G64, int iter
   const BProb& pb = probs[blockIdx.x];
   Ctl& c = ctl[blockIdx.x];
   if (!c.active) return;
-  rho_body<PT>(G64 + pb.g3off, pb.r, iters, 1.0, c, v, w, Gs, sh);
+  rho_body<PT>(G64 + pb.g3off, pb.r, iters, 1.0, 0.0, c, v, w, Gs, sh);
 }
 
 // Grouped row GEMM with the fused Algorithm-1 epilogues and the per-problem control step.

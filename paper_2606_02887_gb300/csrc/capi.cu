@@ -55,6 +55,7 @@ struct snmf_ctx {
   // graph regulariser
   bool graph = false;
   double gamma = 0.0;
+  double normL = 0.0;  // ||L||_2 (power method), enters rho of graph-regularised blocks
   AxArgs L{};
   int32_t* L_rowptr = nullptr;
   int32_t* L_colidx = nullptr;
@@ -327,9 +328,11 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
   // G = Xfix^T Xfix (+ lambda I in the factor-type copy); rho_0 = ||Xfix^T Xfix||_2, computed
   // by the Gram's last CTA when the restart is one tile (FP32 path), else by k_rho
   const bool rho_fused = td == 1 && h->r <= 64;
+  // graph-regularised H block: rho_0 = ||W^T W||_2 + gamma ||L||_2 (Lipschitz constant of its gradient)
+  const double shift = gr ? h->gamma * h->normL : 0.0;
   launch_gram(td, Xf, Xf, d, 0, 1, h->gpart, h->nchunks, h->ctl, h->run, h->G64fix, h->GT, 0, h->lam,
-              h->counters, h->s, rho_fused ? h->ctl : nullptr, h->opt.power_iters, 1.0);
-  if (!rho_fused) launch_rho(td, h->G64fix, d, h->opt.power_iters, 1.0, h->ctl, 0, h->s);
+              h->counters, h->s, rho_fused ? h->ctl : nullptr, h->opt.power_iters, 1.0, shift);
+  if (!rho_fused) launch_rho(td, h->G64fix, d, h->opt.power_iters, 1.0, h->ctl, 0, h->s, shift);
   if (gr) ax_L(h, X, h->buf[B_LX], nullptr, nullptr, h->pax2, h->run);
   {
     // gradient at the block start; its last CTA per restart runs the block-start control
@@ -476,7 +479,8 @@ void dir_iteration(snmf_ctx* h, const Params& P) {
   void *Z = h->buf[B_Z], *AZ = h->buf[B_AZ], *D = h->buf[B_D], *AD = h->buf[B_AD];
   void *Wn = h->buf[B_XN], *AWn = h->buf[B_AWN], *gn = h->buf[B_GN];
   // rho_k = factor ||W^T W||_2 and alpha_k
-  launch_rho(td, h->G64fix, d, h->opt.power_iters, h->opt.direct_rho_factor, h->ctl, 0, h->s);
+  launch_rho(td, h->G64fix, d, h->opt.power_iters, h->opt.direct_rho_factor, h->ctl, 0, h->s,
+             h->graph ? h->gamma * h->normL : 0.0);
   launch_ctl_dir_alpha(h->ctl, h->b, P, h->s);
   launch_zstep(td, d, W, g, Z, h->ctl, h->s);
   int nz = ax_A(h, Z, AZ, 0.0, nullptr, Z, nullptr, h->pax, h->run);
@@ -896,6 +900,50 @@ snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma
   h->graph = true;
   h->gamma = gamma;
   h->exec_form = -1;
+  // ||L||_2 by power_iters power iterations from s_i = 1 + (i mod 2) (L 1 = 0 for a
+  // Laplacian, so the start must not be constant) and the Rayleigh quotient; the device
+  // applies L (CSR product), the host normalises in FP64.
+  {
+    const size_t es = h->esz;
+    std::vector<double> v(n), w(n);
+    std::vector<unsigned char> buf((size_t)n * es);
+    auto put = [&](const std::vector<double>& x, void* dst) -> cudaError_t {
+      for (int64_t i = 0; i < n; ++i) {
+        if (h->tdtype == 0) reinterpret_cast<double*>(buf.data())[i] = x[i];
+        else reinterpret_cast<float*>(buf.data())[i] = (float)x[i];
+      }
+      return cudaMemcpyAsync(dst, buf.data(), (size_t)n * es, cudaMemcpyHostToDevice, h->s);
+    };
+    auto get = [&](const void* src, std::vector<double>* x) -> cudaError_t {
+      const cudaError_t e = cudaMemcpyAsync(buf.data(), src, (size_t)n * es, cudaMemcpyDeviceToHost, h->s);
+      if (e != cudaSuccess) return e;
+      const cudaError_t e2 = cudaStreamSynchronize(h->s);
+      for (int64_t i = 0; i < n; ++i)
+        (*x)[i] = h->tdtype == 0 ? reinterpret_cast<double*>(buf.data())[i] : reinterpret_cast<float*>(buf.data())[i];
+      return e2;
+    };
+    double nv = 0.0;
+    for (int64_t i = 0; i < n; ++i) { v[i] = 1.0 + (double)(i & 1); nv += v[i] * v[i]; }
+    for (auto& x : v) x /= std::sqrt(nv);
+    double lnorm = 0.0;
+    for (int it = 0; it <= h->opt.power_iters; ++it) {
+      CK(put(v, h->buf[B_LZ]));
+      launch_ax(h->L, h->tdtype, n, 1, 1, h->buf[B_LZ], h->buf[B_LD], nullptr, 0, nullptr, h->s);
+      CK(get(h->buf[B_LD], &w));
+      if (it == h->opt.power_iters) {  // Rayleigh quotient v^T L v
+        lnorm = 0.0;
+        for (int64_t i = 0; i < n; ++i) lnorm += v[i] * w[i];
+        break;
+      }
+      double nw = 0.0;
+      for (int64_t i = 0; i < n; ++i) nw += w[i] * w[i];
+      nw = std::sqrt(nw);
+      if (nw == 0.0) break;
+      for (int64_t i = 0; i < n; ++i) v[i] = w[i] / nw;
+    }
+    CK(cudaGetLastError());
+    h->normL = lnorm;
+  }
   return SNMF_OK;
 }
 

@@ -26,9 +26,9 @@ k_gram(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, int b
        int64_t chunk, int ntile, double* __restrict__ gpart, int pair, int npairs,
        const Ctl* __restrict__ ctl, const int* run, double* __restrict__ G64, T* __restrict__ GT,
        int tpair, double lam_shift, unsigned* __restrict__ counters, Ctl* __restrict__ rho_ctl,
-       int rho_iters, double rho_scale) {
+       int rho_iters, double rho_scale, double rho_shift) {
   gram_body<T>(X, Y, n, r, b, ld, chunk, ntile, gpart, pair, npairs, ctl, run, G64, GT, tpair, lam_shift,
-               counters, rho_ctl, rho_iters, rho_scale, blockIdx.x, gridDim.x, blockIdx.y);
+               counters, rho_ctl, rho_iters, rho_scale, rho_shift, blockIdx.x, gridDim.x, blockIdx.y);
 }
 
 template <typename T, int OP, int EPI, int BM, int NC>
@@ -102,7 +102,7 @@ __global__ void k_copy_live(int64_t n, int r, int b, int64_t ld, const T* __rest
 // arithmetic type (double in FP64 precision, float otherwise).
 // ---------------------------------------------------------------------------
 template <typename PT>
-__global__ void k_rho(const double* __restrict__ G64, int r, int iters, double rho_scale,
+__global__ void k_rho(const double* __restrict__ G64, int r, int iters, double rho_scale, double rho_shift,
                       Ctl* __restrict__ ctl, int set_alpha) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ double sh[32];
@@ -111,7 +111,7 @@ __global__ void k_rho(const double* __restrict__ G64, int r, int iters, double r
   Ctl& c = ctl[j];
   if (!c.active) return;
   PT* Gs = ((size_t)r * r * sizeof(PT) <= 96 * 1024) ? reinterpret_cast<PT*>(smem_raw) : nullptr;
-  rho_body<PT>(G64 + (int64_t)j * r * r, r, iters, rho_scale, c, v, w, Gs, sh);
+  rho_body<PT>(G64 + (int64_t)j * r * r, r, iters, rho_scale, rho_shift, c, v, w, Gs, sh);
   (void)set_alpha;
 }
 
@@ -434,18 +434,18 @@ __global__ void k_ctl_final_dir(Ctl* __restrict__ ctl, const double* __restrict_
 void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pair, int npairs,
                  double* gpart, int nchunks, const Ctl* ctl, const int* run, double* G64, void* GT,
                  int tpair, double lam_shift, unsigned* counters, cudaStream_t s, Ctl* rho_ctl,
-                 int rho_iters, double rho_scale) {
+                 int rho_iters, double rho_scale, double rho_shift) {
   const int ntile = (d.r + 63) / 64;
   const int64_t chunk = (d.n + nchunks - 1) / nchunks;
   dim3 grid(nchunks, d.b * ntile * ntile);
   if (tdtype == 0)
     k_gram<double><<<grid, 256, 0, s>>>((const double*)X, (const double*)Y, d.n, d.r, d.b, d.ld, chunk,
                                         ntile, gpart, pair, npairs, ctl, run, G64, (double*)GT, tpair,
-                                        lam_shift, counters, nullptr, 0, 1.0);
+                                        lam_shift, counters, nullptr, 0, 1.0, 0.0);
   else
     k_gram<float><<<grid, 256, 0, s>>>((const float*)X, (const float*)Y, d.n, d.r, d.b, d.ld, chunk,
                                        ntile, gpart, pair, npairs, ctl, run, G64, (float*)GT, tpair,
-                                       lam_shift, counters, rho_ctl, rho_iters, rho_scale);
+                                       lam_shift, counters, rho_ctl, rho_iters, rho_scale, rho_shift);
 }
 
 static int rowgemm_bm(const Dims& d, int tdtype) {
@@ -530,15 +530,15 @@ void init_kernel_attributes() {
 }
 
 void launch_rho(int tdtype, const double* G64, const Dims& d, int iters, double scale, Ctl* ctl,
-                int set_alpha, cudaStream_t s) {
+                int set_alpha, cudaStream_t s, double shift) {
   if (tdtype == 0) {
     size_t sm = (size_t)d.r * d.r * sizeof(double);
     if (sm > 96 * 1024) sm = 0;
-    k_rho<double><<<d.b, 256, sm, s>>>(G64, d.r, iters, scale, ctl, set_alpha);
+    k_rho<double><<<d.b, 256, sm, s>>>(G64, d.r, iters, scale, shift, ctl, set_alpha);
   } else {
     size_t sm = (size_t)d.r * d.r * sizeof(float);
     if (sm > 96 * 1024) sm = 0;
-    k_rho<float><<<d.b, 256, sm, s>>>(G64, d.r, iters, scale, ctl, set_alpha);
+    k_rho<float><<<d.b, 256, sm, s>>>(G64, d.r, iters, scale, shift, ctl, set_alpha);
   }
 }
 

@@ -52,7 +52,7 @@ struct RowArgs {
 void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pair, int npairs,
                  double* gpart, int nchunks, const Ctl* ctl, const int* run, double* G64, void* GT,
                  int tpair, double lam_shift, unsigned* counters, cudaStream_t s,
-                 Ctl* rho_ctl = nullptr, int rho_iters = 0, double rho_scale = 1.0);
+                 Ctl* rho_ctl = nullptr, int rho_iters = 0, double rho_scale = 1.0, double rho_shift = 0.0);
 int rowgemm_slots(const Dims& d, int tdtype);
 void launch_rowgemm(int tdtype, int op, int epi, const RowArgs& a, cudaStream_t s, int ncand = 1);
 void launch_zstep(int tdtype, const Dims& d, const void* X, const void* g, void* Z, const Ctl* ctl,
@@ -61,8 +61,9 @@ int launch_xupd(int tdtype, const Dims& d, const void* Z, const void* D, void* X
                 const void* AD, void* AXn, const Ctl* ctl, double* part, cudaStream_t s);
 void launch_copy_live(int tdtype, const Dims& d, const void* src, void* dst, const Ctl* ctl,
                       cudaStream_t s);
+// rho = scale ||G||_2 + shift per restart (shift: gamma ||L||_2 of a graph-regularised block)
 void launch_rho(int tdtype, const double* G64, const Dims& d, int iters, double scale, Ctl* ctl,
-                int set_alpha, cudaStream_t s);
+                int set_alpha, cudaStream_t s, double shift = 0.0);
 void launch_philox_uniform(int tdtype, void* out, int64_t rows, int cols, int64_t ld, uint64_t seed,
                            double scale, cudaStream_t s);
 void launch_philox_gaussian(int tdtype, void* out, int64_t rows, int cols, uint64_t seed,

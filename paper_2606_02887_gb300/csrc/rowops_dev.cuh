@@ -142,7 +142,7 @@ __device__ double reference(const Ctl& c, const Params& P) {
 // block reduction.  Gs: G in shared memory (PT) or NULL; v, w: shared scratch (r entries);
 // sh: shared scratch of 8 doubles.
 template <typename PT>
-__device__ void rho_body(const double* __restrict__ Gj, int r, int iters, double rho_scale, Ctl& c,
+__device__ void rho_body(const double* __restrict__ Gj, int r, int iters, double rho_scale, double rho_shift, Ctl& c,
                          PT* __restrict__ v, PT* __restrict__ w, PT* __restrict__ Gs, double* sh) {
   const int tid = threadIdx.x, nt = blockDim.x;
   if (Gs)
@@ -198,7 +198,7 @@ __device__ void rho_body(const double* __restrict__ Gj, int r, int iters, double
     for (int u = 0; u < (nt >> 5); ++u) rho += shp[u];
   }
   if (tid == 0) {
-    double rr = rho_scale * (double)rho;
+    double rr = rho_scale * (double)rho + rho_shift;  // shift: gamma ||L||_2 of a graph block
     if (!(rr > 0.0)) rr = 1.0;  // zero Gram: unit scaling
     c.rho = rr;
   }
@@ -463,7 +463,7 @@ gram_body(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, in
           int64_t chunk, int ntile, double* __restrict__ gpart, int pair, int npairs,
           const Ctl* __restrict__ ctl, const int* run, double* __restrict__ G64, T* __restrict__ GT,
           int tpair, double lam_shift, unsigned* __restrict__ counters, Ctl* __restrict__ rho_ctl,
-          int rho_iters, double rho_scale, int cidx, int nch, int jt) {
+          int rho_iters, double rho_scale, double rho_shift, int cidx, int nch, int jt) {
   const int j = jt / (ntile * ntile);
   const int t = jt % (ntile * ntile);
   const int ti = t / ntile, tj = t % ntile;
@@ -575,7 +575,7 @@ gram_body(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, in
       __shared__ T Gsr[64 * 64];
       __shared__ double shr[8];
       __syncthreads();
-      rho_body<T>(G64 + tile_base, r, rho_iters, rho_scale, rho_ctl[j], vv, ww, Gsr, shr);
+      rho_body<T>(G64 + tile_base, r, rho_iters, rho_scale, rho_shift, rho_ctl[j], vv, ww, Gsr, shr);
     }
   }
   __syncthreads();  // no early return: a CTA may run several items

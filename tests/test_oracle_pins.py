@@ -401,3 +401,28 @@ def test_fp8_e4m3_codec_pins():
     normal = A / Sf >= 2.0 ** -6
     assert np.all(np.abs(At - A)[normal] <= 2.0 ** -4 * A[normal] * (1 + 1e-12))
     assert np.all(np.abs(At - A)[~normal] <= 2.0 ** -10 * Sf[~normal] * (1 + 1e-12))
+
+
+def test_laplacian_norm_and_graph_block_descent():
+    """gamma ||L||_2 in rho of the graph block: the power estimate sits just below the top
+    eigenvalue, and the Z step of the regularised H block with that rho decreases f (a
+    projected gradient step with step 1/Lipschitz), while the step without it does not have
+    to (it overshoots on this graph)."""
+    import oracle.snmpbb as SM
+    from workloads import gmm_knn_graph
+    A_hat, L, _, _ = gmm_knn_graph(n=300, d=8, comps=4, k=10, seed=91)
+    Ad, Ld = A_hat.to_dense(), L.to_dense()
+    lmax = np.linalg.eigvalsh(Ld)[-1]
+    est = SM.laplacian_norm(Ld, 50)
+    # a Rayleigh quotient never exceeds the top eigenvalue; 50 iterations get within 2%
+    assert est <= lmax * (1 + 1e-12) and est >= lmax * (1 - 2e-2)
+    g = np.random.default_rng(92)
+    W = g.random((300, 4)) * 0.05
+    Ht = g.random((300, 4)) * 0.05
+    gamma, lam = 0.5, 0.01 * np.linalg.norm(Ad)
+    f = lambda X: SM.penalty_objective(Ad, W, X, lam, gamma, Ld, "explicit")
+    grad = SM.penalty_grad_Ht(Ad, W, Ht, lam, gamma, Ld)
+    rho = np.linalg.eigvalsh(W.T @ W)[-1] + lam + gamma * lmax  # the block's Lipschitz constant
+    Z = SM.proj(Ht - grad / rho)
+    # sufficient decrease of a projected gradient step with step 1/Lipschitz
+    assert f(Z) <= f(Ht) - 0.5 * rho * np.sum((Z - Ht) ** 2) + 1e-12 * abs(f(Ht))
