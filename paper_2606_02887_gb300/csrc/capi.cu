@@ -56,6 +56,7 @@ struct snmf_ctx {
   bool graph = false;
   double gamma = 0.0;
   double normL = 0.0;  // ||L||_2 (power method), enters rho of graph-regularised blocks
+  int use_tile = 0;    // row kernels through the shared-memory tile body (r <= 32)
   AxArgs L{};
   int32_t* L_rowptr = nullptr;
   int32_t* L_colidx = nullptr;
@@ -310,6 +311,7 @@ RowArgs row_base(snmf_ctx* h, const Params* P = nullptr) {
   a.part = h->prow;
   a.counters = h->counters + 16384;
   a.G64fix = h->G64fix;
+  a.tile = h->use_tile;
   if (P) a.P = *P;
   return a;
 }
@@ -534,7 +536,10 @@ snmf_status alloc_buffers(snmf_ctx* h) {
   const Dims d = dims(h);
   h->nrow = rowgemm_slots(d, h->tdtype);
   h->nax = (int)((h->n + kRowTile - 1) / kRowTile);
-  const size_t prec_n = (size_t)std::max(h->nrow, h->nax) * h->b * kNQ;
+  const size_t prec_n = (size_t)std::max(h->nrow, h->nax) * h->b * kNQ;  // >= the tile body's slots
+  // r <= 32, penalty form, at most two step candidates: the tile body (no graph term yet)
+  h->use_tile = (h->r <= 32 && h->opt.formulation == SNMF_PENALTY && h->opt.step_controller != 2) ? 1 : 0;
+  if (h->use_tile) h->nrow = rowgemm_slots(d, h->tdtype, 1);
   double** parts[] = {&h->prow, &h->pax, &h->pax2, &h->pax3, &h->pax4, &h->pclip};
   for (double** p : parts) {
     CK(cudaMalloc(p, prec_n * sizeof(double)));
@@ -866,7 +871,14 @@ snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma
   if (!h) return SNMF_ERR_STATE;
   if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
   if (!(gamma >= 0.0)) return fail(h, SNMF_ERR_ARG, "gamma must be >= 0");
-  if (gamma == 0.0) { h->graph = false; h->gamma = 0.0; h->exec_form = -1; return SNMF_OK; }
+  if (gamma == 0.0) {
+    h->graph = false;
+    h->gamma = 0.0;
+    h->exec_form = -1;
+    h->use_tile = (h->r <= 32 && h->opt.formulation == SNMF_PENALTY && h->opt.step_controller != 2) ? 1 : 0;
+    h->nrow = rowgemm_slots(dims(h), h->tdtype, h->use_tile);
+    return SNMF_OK;
+  }
   if (!L) return fail(h, SNMF_ERR_ARG, "implicit Laplacian (L == NULL) not available in this build");
   if (L->kind != SNMF_CSR) return fail(h, SNMF_ERR_ARG, "L must be CSR");
   if (L->n != h->n) return fail(h, SNMF_ERR_ARG, "L size mismatch");
@@ -900,6 +912,8 @@ snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma
   h->graph = true;
   h->gamma = gamma;
   h->exec_form = -1;
+  h->use_tile = 0;  // the graph term runs through the general row kernel
+  h->nrow = rowgemm_slots(dims(h), h->tdtype, 0);
   // ||L||_2 by power_iters power iterations from s_i = 1 + (i mod 2) (L 1 = 0 for a
   // Laplacian, so the start must not be constant) and the Rayleigh quotient; the device
   // applies L (CSR product), the host normalises in FP64.

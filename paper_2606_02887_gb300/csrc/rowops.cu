@@ -36,6 +36,25 @@ __global__ void __launch_bounds__(256, 3) k_rowgemm(RowArgs a) {
   rowgemm_body<T, OP, EPI, BM, NC>(a, blockIdx.z, blockIdx.x, blockIdx.y, gridDim.y, gridDim.x * gridDim.y);
 }
 
+// r <= 32: the shared-memory tile body, CTA = TileCfg<T>::TR rows of restart blockIdx.z
+template <typename T, int OP, int EPI, int NC>
+__global__ void __launch_bounds__(256, 3) k_rowtile(RowArgs a) {
+  extern __shared__ __align__(16) unsigned char tsm[];
+  rowtile_body<T, OP, EPI, NC>(a, blockIdx.z, blockIdx.x, gridDim.x, reinterpret_cast<T*>(tsm));
+}
+
+template <typename T, int OP, int EPI, int NC>
+void launch_rowtile(const RowArgs& a, cudaStream_t s) {
+  static bool attr = false;
+  const size_t smem = rowtile_smem<T>(EPI == EPI_DIR ? 2 + NC : 2);
+  if (!attr) {
+    cudaFuncSetAttribute(k_rowtile<T, OP, EPI, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  dim3 grid((unsigned)((a.n + TileCfg<T>::TR - 1) / TileCfg<T>::TR), 1, a.b);
+  k_rowtile<T, OP, EPI, NC><<<grid, 256, smem, s>>>(a);
+}
+
 // Elementwise: Z = Proj[X - g / rho] (Alg. 1 line 2) for restarts that are live.
 template <typename T>
 __global__ void k_zstep(int64_t n, int r, int b, int64_t ld, const T* __restrict__ X,
@@ -453,12 +472,26 @@ static int rowgemm_bm(const Dims& d, int tdtype) {
   return (d.n + 63) / 64 * ((d.r + 63) / 64) * d.b >= 2 * 152 ? 64 : 32;
 }
 
-int rowgemm_slots(const Dims& d, int tdtype) {
+int rowgemm_slots(const Dims& d, int tdtype, int tile) {
+  if (tile) return cdiv(d.n, tdtype == 0 ? TileCfg<double>::TR : TileCfg<float>::TR);
   const int bm = rowgemm_bm(d, tdtype);
   return cdiv(d.n, bm) * cdiv(d.r, 64);
 }
 
 void launch_rowgemm(int tdtype, int op, int epi, const RowArgs& a, cudaStream_t s, int ncand) {
+  if (a.tile && a.r <= 32 && !a.LX && ncand <= 2) {
+#define TB(T)                                                                   \
+    if (epi == EPI_GRAD) {                                                      \
+      if (op == OP_LOAD) launch_rowtile<T, OP_LOAD, EPI_GRAD, 1>(a, s);         \
+      else if (op == OP_ZSTEP) launch_rowtile<T, OP_ZSTEP, EPI_GRAD, 1>(a, s);  \
+      else launch_rowtile<T, OP_UPD, EPI_GRAD, 1>(a, s);                        \
+    } else if (op == OP_LOAD) launch_rowtile<T, OP_LOAD, EPI_DIR, 1>(a, s);     \
+    else if (ncand == 1) launch_rowtile<T, OP_ZSTEP, EPI_DIR, 1>(a, s);         \
+    else launch_rowtile<T, OP_ZSTEP, EPI_DIR, 2>(a, s);
+    if (tdtype == 0) { TB(double) } else { TB(float) }
+#undef TB
+    return;
+  }
   Dims d;
   d.n = a.n; d.r = a.r; d.b = a.b; d.N = a.r * a.b; d.ld = a.ld;
   const int bm = rowgemm_bm(d, tdtype);

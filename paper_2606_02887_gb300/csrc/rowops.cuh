@@ -47,13 +47,15 @@ struct RowArgs {
   unsigned* counters;  // per-restart arrival counters (zero between launches)
   const double* G64fix;
   Params P;
+  int tile;            // 1: the shared-memory tile body (r <= 32, no graph term, <= 2 candidates)
 };
 
 void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pair, int npairs,
                  double* gpart, int nchunks, const Ctl* ctl, const int* run, double* G64, void* GT,
                  int tpair, double lam_shift, unsigned* counters, cudaStream_t s,
                  Ctl* rho_ctl = nullptr, int rho_iters = 0, double rho_scale = 1.0, double rho_shift = 0.0);
-int rowgemm_slots(const Dims& d, int tdtype);
+// partial slots per restart written by launch_rowgemm (tile: the tile body's row tiles)
+int rowgemm_slots(const Dims& d, int tdtype, int tile = 0);
 void launch_rowgemm(int tdtype, int op, int epi, const RowArgs& a, cudaStream_t s, int ncand = 1);
 void launch_zstep(int tdtype, const Dims& d, const void* X, const void* g, void* Z, const Ctl* ctl,
                   cudaStream_t s);
