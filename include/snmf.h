@@ -199,12 +199,15 @@ SNMF_API snmf_status snmf_create(snmf_handle* h, const snmf_matrix* A, int r,
 
 /*
  * Graph-SNMPBB (Sec. 2.2, Eq. (5)): add gamma/2 tr(H L H^T) to the objective.
- *   L      NULL: L = I - D^-1/2 A D^-1/2 with D = diag(A e) (the paper's Laplacian);
- *          otherwise an explicit symmetric n x n CSR matrix (SNMF_F32 or SNMF_F64 values,
+ *   L      an explicit symmetric n x n CSR matrix (SNMF_F32 or SNMF_F64 values,
  *          device or host), copied into library memory.
  *   gamma  >= 0; 0 removes the term.
  * Penalty form: the term enters the H block only (Sec. 2.2); direct form:
- * gamma/2 tr(W^T L W).  Errors: SNMF_ERR_ARG (size mismatch, gamma < 0, dense L).
+ * gamma/2 tr(W^T L W).  ||L||_2 is estimated here (power_iters power iterations from
+ * s_i = 1 + (i mod 2), Rayleigh quotient) and gamma ||L||_2 is added to rho of the
+ * regularised block, the Lipschitz constant of its gradient (rho_0 of Sec. 2.4 extended by
+ * the graph term).  L == NULL is not available in this build (SNMF_ERR_ARG).
+ * Errors: SNMF_ERR_ARG (size mismatch, gamma < 0, dense L).
  */
 SNMF_API snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma);
 
