@@ -57,6 +57,7 @@ struct snmf_ctx {
   double gamma = 0.0;
   double normL = 0.0;  // ||L||_2 (power method), enters rho of graph-regularised blocks
   int use_tile = 0;    // row kernels through the shared-memory tile body (r <= 32)
+  int row_bm = 0;      // general row kernel, FP32: rows per CTA (0: built-in choice; autotuned)
   AxArgs L{};
   int32_t* L_rowptr = nullptr;
   int32_t* L_colidx = nullptr;
@@ -175,19 +176,80 @@ int product_kernel(snmf_ctx* h, const AxArgs& op, const void* X, void* Y, const 
   return launch_ax(op, h->tdtype, h->n, h->N, h->N, X, Y, h->ws, h->ws_elems, run, h->s, tn);
 }
 
+// Mean time of one D-step launch and one update launch of a W block (the row kernels of
+// Alg. 1 lines 2-4) on the handle's current buffers, with every restart marked live.
+snmf_status time_steps(snmf_ctx* h, int iters, double* ms_dstep, double* ms_update) {
+  std::vector<Ctl> live(h->b);
+  for (int j = 0; j < h->b; ++j) {
+    live[j] = (j < (int)h->h_ctl.size()) ? h->h_ctl[j] : Ctl{};
+    live[j].active = 1;
+    live[j].nan_seen = 0;
+    if (!(live[j].rho > 0.0)) live[j].rho = 1.0;
+    if (!(live[j].alpha > 0.0)) live[j].alpha = 1.0;
+  }
+  CK(cudaMemcpyAsync(h->ctl, live.data(), h->b * sizeof(Ctl), cudaMemcpyHostToDevice, h->s));
+  static const int one = 1;
+  CK(cudaMemcpyAsync(h->run, &one, sizeof(int), cudaMemcpyHostToDevice, h->s));
+  const Params P = make_params(h);
+  const int td = h->tdtype;
+  const int nc = h->opt.step_controller == 1 ? 2 : (h->opt.step_controller == 2 ? kNCand : 1);
+  void* X = h->buf[B_W];
+  RowArgs ad = row_base(h, &P);  // the D step of a W block, as in pen_block
+  ad.B = h->buf[B_B];
+  ad.Dout = h->buf[B_D]; ad.gZout = h->buf[B_GZ];
+  ad.Wcur = X; ad.gWcur = h->buf[B_G];
+  ad.X = X; ad.g_in = h->buf[B_G]; ad.Xout = h->buf[B_Z];
+  ad.want_q = 1;
+  ad.ctl_mode = CTL_LS;
+  ad.dstore = nc == kNCand ? 4 : 0;
+  ad.D2out = h->buf[B_AD];
+  RowArgs au = row_base(h, &P);  // the update of a W block
+  au.B = h->buf[B_B];
+  au.gout = h->buf[B_G];
+  au.Xold = X; au.gold = h->buf[B_G];
+  au.Zold = h->buf[B_Z]; au.gZold = h->buf[B_GZ];
+  au.Xout = X;
+  au.ctl_mode = CTL_UPD_W;
+  au.Zin = h->buf[B_Z]; au.Din = h->buf[B_D]; au.Din2 = h->buf[B_AD];
+  cudaEvent_t e[4];
+  for (auto& x : e) CK(cudaEventCreate(&x));
+  launch_rowgemm(td, OP_ZSTEP, EPI_DIR, ad, h->s, nc);  // warm-up
+  launch_rowgemm(td, OP_UPD, EPI_GRAD, au, h->s);
+  CK(cudaEventRecord(e[0], h->s));
+  for (int t = 0; t < iters; ++t) launch_rowgemm(td, OP_ZSTEP, EPI_DIR, ad, h->s, nc);
+  CK(cudaEventRecord(e[1], h->s));
+  CK(cudaEventRecord(e[2], h->s));
+  for (int t = 0; t < iters; ++t) launch_rowgemm(td, OP_UPD, EPI_GRAD, au, h->s);
+  CK(cudaEventRecord(e[3], h->s));
+  CK(cudaStreamSynchronize(h->s));
+  CK(cudaGetLastError());
+  float m1 = 0.f, m2 = 0.f;
+  cudaEventElapsedTime(&m1, e[0], e[1]);
+  cudaEventElapsedTime(&m2, e[2], e[3]);
+  for (auto& x : e) cudaEventDestroy(x);
+  if (ms_dstep) *ms_dstep = m1 / iters;
+  if (ms_update) *ms_update = m2 / iters;
+  return SNMF_OK;
+}
+
 // Autotuner of the dense product: times every candidate configuration (CUDA events, one
 // warm-up and five timed products each) and keeps the fastest; the result is cached per
 // device and shape (in this process, and in opt.tune_cache when given).
 snmf_status autotune_product(snmf_ctx* h) {
   if (h->kind != AX_DENSE) return SNMF_OK;
   static const char* dtn[4] = {"f64", "f32", "bf16", "fp8"};
-  const std::string key = std::string("dense/") + dtn[h->A.a_dtype] + "/n" + std::to_string(h->n) + "/N" +
-                          std::to_string(h->N);
+  const std::string key = std::string("dense/") + dtn[h->A.a_dtype] + "/n" + std::to_string(h->n) + "/r" +
+                          std::to_string(h->r) + "/N" + std::to_string(h->N);
   const std::string dev = tune_device_key();
   TuneEntry e;
+  const bool tune_rows = !h->use_tile && h->tdtype == 1 && h->opt.formulation == SNMF_PENALTY && h->r <= 64;
   if (tune_lookup(h->opt.tune_cache, dev, key, &e)) {
     h->tune = e;
     h->tuned = 2;
+    if (tune_rows && (e.cfg.row_bm == 32 || e.cfg.row_bm == 64)) {
+      h->row_bm = e.cfg.row_bm;
+      h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, h->row_bm);
+    }
     return SNMF_OK;
   }
   std::vector<ProdTune> cand;
@@ -257,7 +319,23 @@ snmf_status autotune_product(snmf_ctx* h) {
     return SNMF_OK;
   }
   h->tune = best;
-  tune_store(h->opt.tune_cache, dev, key, best);
+  // the general row kernel's tile height (FP32 penalty form): D step + update per inner step
+  if (tune_rows) {
+    double bt = 1e30;
+    int bbm = 0;
+    for (int bm : {64, 32}) {
+      h->row_bm = bm;
+      h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, bm);
+      double md = 0.0, mu = 0.0;
+      const snmf_status st = time_steps(h, 5, &md, &mu);
+      if (st != SNMF_OK) return st;
+      if (md + mu < bt) { bt = md + mu; bbm = bm; }
+    }
+    h->row_bm = bbm;
+    h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, bbm);
+    h->tune.cfg.row_bm = bbm;
+  }
+  tune_store(h->opt.tune_cache, dev, key, h->tune);
   return SNMF_OK;
 }
 
@@ -312,6 +390,7 @@ RowArgs row_base(snmf_ctx* h, const Params* P = nullptr) {
   a.counters = h->counters + 16384;
   a.G64fix = h->G64fix;
   a.tile = h->use_tile;
+  a.bm = h->row_bm;
   if (P) a.P = *P;
   return a;
 }
@@ -536,7 +615,9 @@ snmf_status alloc_buffers(snmf_ctx* h) {
   const Dims d = dims(h);
   h->nrow = rowgemm_slots(d, h->tdtype);
   h->nax = (int)((h->n + kRowTile - 1) / kRowTile);
-  const size_t prec_n = (size_t)std::max(h->nrow, h->nax) * h->b * kNQ;  // >= the tile body's slots
+  // room for every row-kernel layout (BM = 32 has the most slots; the tile body fewer)
+  const int nrow_max = std::max(h->nrow, rowgemm_slots(d, h->tdtype, 0, 32));
+  const size_t prec_n = (size_t)std::max(nrow_max, h->nax) * h->b * kNQ;
   // r <= 32, penalty form, at most two step candidates: the tile body (no graph term yet)
   h->use_tile = (h->r <= 32 && h->opt.formulation == SNMF_PENALTY && h->opt.step_controller != 2) ? 1 : 0;
   if (h->use_tile) h->nrow = rowgemm_slots(d, h->tdtype, 1);
@@ -876,7 +957,7 @@ snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma
     h->gamma = 0.0;
     h->exec_form = -1;
     h->use_tile = (h->r <= 32 && h->opt.formulation == SNMF_PENALTY && h->opt.step_controller != 2) ? 1 : 0;
-    h->nrow = rowgemm_slots(dims(h), h->tdtype, h->use_tile);
+    h->nrow = rowgemm_slots(dims(h), h->tdtype, h->use_tile, h->row_bm);
     return SNMF_OK;
   }
   if (!L) return fail(h, SNMF_ERR_ARG, "implicit Laplacian (L == NULL) not available in this build");
@@ -913,7 +994,7 @@ snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma
   h->gamma = gamma;
   h->exec_form = -1;
   h->use_tile = 0;  // the graph term runs through the general row kernel
-  h->nrow = rowgemm_slots(dims(h), h->tdtype, 0);
+  h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, h->row_bm);
   // ||L||_2 by power_iters power iterations from s_i = 1 + (i mod 2) (L 1 = 0 for a
   // Laplacian, so the start must not be constant) and the Rayleigh quotient; the device
   // applies L (CSR product), the host normalises in FP64.
@@ -1230,54 +1311,7 @@ snmf_status snmf_profile_steps(snmf_handle h, int iters, double* ms_dstep, doubl
     return fail(h, SNMF_ERR_ARG, "step profiling needs the penalty form without graph term and r <= 64");
   if (!h->have_result) return fail(h, SNMF_ERR_STATE, "run a solve first (the step kernels read its buffers)");
   if (sync_user(h) != SNMF_OK) return SNMF_ERR_CUDA;
-  std::vector<Ctl> live(h->h_ctl.begin(), h->h_ctl.begin() + h->b);
-  for (Ctl& c : live) {
-    c.active = 1;
-    c.nan_seen = 0;
-  }
-  CK(cudaMemcpyAsync(h->ctl, live.data(), h->b * sizeof(Ctl), cudaMemcpyHostToDevice, h->s));
-  static const int one = 1;
-  CK(cudaMemcpyAsync(h->run, &one, sizeof(int), cudaMemcpyHostToDevice, h->s));
-  const Params P = make_params(h);
-  const int td = h->tdtype;
-  const int nc = h->opt.step_controller == 1 ? 2 : (h->opt.step_controller == 2 ? kNCand : 1);
-  void* X = h->buf[B_W];
-  RowArgs ad = row_base(h, &P);  // the D step of a W block, as in pen_block
-  ad.B = h->buf[B_B];
-  ad.Dout = h->buf[B_D]; ad.gZout = h->buf[B_GZ];
-  ad.Wcur = X; ad.gWcur = h->buf[B_G];
-  ad.X = X; ad.g_in = h->buf[B_G]; ad.Xout = h->buf[B_Z];
-  ad.want_q = 1;
-  ad.ctl_mode = CTL_LS;
-  ad.dstore = nc == kNCand ? 4 : 0;
-  ad.D2out = h->buf[B_AD];
-  RowArgs au = row_base(h, &P);  // the update of a W block
-  au.B = h->buf[B_B];
-  au.gout = h->buf[B_G];
-  au.Xold = X; au.gold = h->buf[B_G];
-  au.Zold = h->buf[B_Z]; au.gZold = h->buf[B_GZ];
-  au.Xout = X;
-  au.ctl_mode = CTL_UPD_W;
-  au.Zin = h->buf[B_Z]; au.Din = h->buf[B_D]; au.Din2 = h->buf[B_AD];
-  cudaEvent_t e[4];
-  for (auto& x : e) CK(cudaEventCreate(&x));
-  launch_rowgemm(td, OP_ZSTEP, EPI_DIR, ad, h->s, nc);  // warm-up
-  launch_rowgemm(td, OP_UPD, EPI_GRAD, au, h->s);
-  CK(cudaEventRecord(e[0], h->s));
-  for (int t = 0; t < iters; ++t) launch_rowgemm(td, OP_ZSTEP, EPI_DIR, ad, h->s, nc);
-  CK(cudaEventRecord(e[1], h->s));
-  CK(cudaEventRecord(e[2], h->s));
-  for (int t = 0; t < iters; ++t) launch_rowgemm(td, OP_UPD, EPI_GRAD, au, h->s);
-  CK(cudaEventRecord(e[3], h->s));
-  CK(cudaStreamSynchronize(h->s));
-  CK(cudaGetLastError());
-  float m1 = 0.f, m2 = 0.f;
-  cudaEventElapsedTime(&m1, e[0], e[1]);
-  cudaEventElapsedTime(&m2, e[2], e[3]);
-  for (auto& x : e) cudaEventDestroy(x);
-  if (ms_dstep) *ms_dstep = m1 / iters;
-  if (ms_update) *ms_update = m2 / iters;
-  return SNMF_OK;
+  return time_steps(h, iters, ms_dstep, ms_update);
 }
 
 snmf_status snmf_tuned_config(snmf_handle h, int32_t* splits, int32_t* stages, int32_t* per_sm, double* ms,

@@ -32,7 +32,7 @@ k_gram(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, int b
 }
 
 template <typename T, int OP, int EPI, int BM, int NC>
-__global__ void __launch_bounds__(256, 3) k_rowgemm(RowArgs a) {
+__global__ void __launch_bounds__(256, BM == 32 ? 4 : 3) k_rowgemm(RowArgs a) {
   rowgemm_body<T, OP, EPI, BM, NC>(a, blockIdx.z, blockIdx.x, blockIdx.y, gridDim.y, gridDim.x * gridDim.y);
 }
 
@@ -472,9 +472,9 @@ static int rowgemm_bm(const Dims& d, int tdtype) {
   return (d.n + 63) / 64 * ((d.r + 63) / 64) * d.b >= 2 * 152 ? 64 : 32;
 }
 
-int rowgemm_slots(const Dims& d, int tdtype, int tile) {
+int rowgemm_slots(const Dims& d, int tdtype, int tile, int bm_req) {
   if (tile) return cdiv(d.n, tdtype == 0 ? TileCfg<double>::TR : TileCfg<float>::TR);
-  const int bm = rowgemm_bm(d, tdtype);
+  const int bm = (tdtype == 1 && (bm_req == 32 || bm_req == 64)) ? bm_req : rowgemm_bm(d, tdtype);
   return cdiv(d.n, bm) * cdiv(d.r, 64);
 }
 
@@ -494,7 +494,7 @@ void launch_rowgemm(int tdtype, int op, int epi, const RowArgs& a, cudaStream_t 
   }
   Dims d;
   d.n = a.n; d.r = a.r; d.b = a.b; d.N = a.r * a.b; d.ld = a.ld;
-  const int bm = rowgemm_bm(d, tdtype);
+  const int bm = (tdtype == 1 && (a.bm == 32 || a.bm == 64)) ? a.bm : rowgemm_bm(d, tdtype);
   dim3 grid(cdiv(a.n, bm), cdiv(a.r, 64), a.b);
 #define RG(T, O, E, M, C) k_rowgemm<T, O, E, M, C><<<grid, 256, 0, s>>>(a)
 #define RG_M(T, O, E, C) \

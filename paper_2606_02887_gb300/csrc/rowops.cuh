@@ -48,6 +48,7 @@ struct RowArgs {
   const double* G64fix;
   Params P;
   int tile;            // 1: the shared-memory tile body (r <= 32, no graph term, <= 2 candidates)
+  int bm;              // general body, FP32: rows per CTA (32 or 64; 0 = built-in choice)
 };
 
 void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pair, int npairs,
@@ -55,7 +56,7 @@ void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pa
                  int tpair, double lam_shift, unsigned* counters, cudaStream_t s,
                  Ctl* rho_ctl = nullptr, int rho_iters = 0, double rho_scale = 1.0, double rho_shift = 0.0);
 // partial slots per restart written by launch_rowgemm (tile: the tile body's row tiles)
-int rowgemm_slots(const Dims& d, int tdtype, int tile = 0);
+int rowgemm_slots(const Dims& d, int tdtype, int tile = 0, int bm = 0);
 void launch_rowgemm(int tdtype, int op, int epi, const RowArgs& a, cudaStream_t s, int ncand = 1);
 void launch_zstep(int tdtype, const Dims& d, const void* X, const void* g, void* Z, const Ctl* ctl,
                   cudaStream_t s);

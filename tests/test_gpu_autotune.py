@@ -42,9 +42,10 @@ def test_autotune_search_cache_and_agreement(tmp_path, prec):
         data = json.load(open(cache))
         devs = data["devices"]
         assert len(devs) == 1
-        key = f"dense/{'bf16' if prec == S.SNMF_BF16 else 'f32'}/n{n}/N{r}"
+        key = f"dense/{'bf16' if prec == S.SNMF_BF16 else 'f32'}/n{n}/r{r}/N{r}"
         entry = next(iter(devs.values()))[key]
         assert entry["splits"] == c1["splits"]
+        assert entry["row_bm"] in (0, 32, 64)
         h2 = S.snmf_create(S.dense_matrix(At), r, o)
         try:
             c2 = S.snmf_tuned_config(h2)
