@@ -176,6 +176,63 @@ int product_kernel(snmf_ctx* h, const AxArgs& op, const void* X, void* Y, const 
   return launch_ax(op, h->tdtype, h->n, h->N, h->N, X, Y, h->ws, h->ws_elems, run, h->s, tn);
 }
 
+
+// Y = op X (+ c X2), dots <P1, op X> -> part q0, <P2, op X> -> q0+1; returns slot count.
+int ax_apply(snmf_ctx* h, const AxArgs& op, bool use_lai, const void* X, void* Y, double c,
+             const void* X2, const void* P1, const void* P2, double* part, const int* run) {
+  Dims d = dims(h);
+  h->ax_count++;
+  if (use_lai) {
+    return lai_apply(h->lai_op, h->tdtype, d, X, Y, c, X2, P1, P2, part, run, h->s);
+  }
+  const int splits = product_kernel(h, op, X, Y, run);
+  return launch_ax_finish_impl(h->tdtype, d, Y, h->ws, splits, c, X2, P1, P2, part, 0, run, h->s);
+}
+
+int ax_A(snmf_ctx* h, const void* X, void* Y, double c, const void* X2, const void* P1,
+         const void* P2, double* part, const int* run) {
+  return ax_apply(h, h->A, h->lai, X, Y, c, X2, P1, P2, part, run);
+}
+
+int ax_L(snmf_ctx* h, const void* X, void* Y, const void* P1, const void* P2, double* part,
+         const int* run) {
+  return ax_apply(h, h->L, false, X, Y, 0.0, nullptr, P1, P2, part, run);
+}
+
+int choose_chunks(int64_t n, int b, int r) {
+  // about one CTA per SM, at least 512 rows per chunk (fewer partials to reduce)
+  const int ntile = (r + 63) / 64;
+  const int64_t per = (int64_t)b * ntile * ntile;
+  int64_t c = (152 + per - 1) / per;
+  c = std::max<int64_t>(1, std::min<int64_t>(c, n / 512));
+  return (int)c;
+}
+
+// Gram X^T Y per restart into G64 (+ factor-type copy GT with lam I when pair == tpair);
+// inside the iteration it follows ctl[j].active and the run flag, in the initial and
+// final evaluations (ctl == NULL) every restart is computed.
+void gram1(snmf_ctx* h, const void* X, const void* Y, int pair, int npairs, const Ctl* ctl,
+           double* G64, void* GT, int tpair, double lam) {
+  launch_gram(h->tdtype, X, Y, dims(h), pair, npairs, h->gpart, h->nchunks, ctl,
+              ctl ? h->run : nullptr, G64, GT, tpair, lam, h->counters, h->s);
+}
+
+RowArgs row_base(snmf_ctx* h, const Params* P = nullptr) {
+  RowArgs a{};
+  a.n = h->n; a.r = h->r; a.b = h->b; a.ld = h->N;
+  a.G = h->GT;
+  a.ctl = h->ctl;
+  a.run = h->run;
+  a.gamma = h->graph ? h->gamma : 0.0;
+  a.part = h->prow;
+  a.counters = h->counters + 16384;
+  a.G64fix = h->G64fix;
+  a.tile = h->use_tile;
+  a.bm = h->row_bm;
+  if (P) a.P = *P;
+  return a;
+}
+
 // Mean time of one D-step launch and one update launch of a W block (the row kernels of
 // Alg. 1 lines 2-4) on the handle's current buffers, with every restart marked live.
 snmf_status time_steps(snmf_ctx* h, int iters, double* ms_dstep, double* ms_update) {
@@ -337,62 +394,6 @@ snmf_status autotune_product(snmf_ctx* h) {
   }
   tune_store(h->opt.tune_cache, dev, key, h->tune);
   return SNMF_OK;
-}
-
-// Y = op X (+ c X2), dots <P1, op X> -> part q0, <P2, op X> -> q0+1; returns slot count.
-int ax_apply(snmf_ctx* h, const AxArgs& op, bool use_lai, const void* X, void* Y, double c,
-             const void* X2, const void* P1, const void* P2, double* part, const int* run) {
-  Dims d = dims(h);
-  h->ax_count++;
-  if (use_lai) {
-    return lai_apply(h->lai_op, h->tdtype, d, X, Y, c, X2, P1, P2, part, run, h->s);
-  }
-  const int splits = product_kernel(h, op, X, Y, run);
-  return launch_ax_finish_impl(h->tdtype, d, Y, h->ws, splits, c, X2, P1, P2, part, 0, run, h->s);
-}
-
-int ax_A(snmf_ctx* h, const void* X, void* Y, double c, const void* X2, const void* P1,
-         const void* P2, double* part, const int* run) {
-  return ax_apply(h, h->A, h->lai, X, Y, c, X2, P1, P2, part, run);
-}
-
-int ax_L(snmf_ctx* h, const void* X, void* Y, const void* P1, const void* P2, double* part,
-         const int* run) {
-  return ax_apply(h, h->L, false, X, Y, 0.0, nullptr, P1, P2, part, run);
-}
-
-int choose_chunks(int64_t n, int b, int r) {
-  // about one CTA per SM, at least 512 rows per chunk (fewer partials to reduce)
-  const int ntile = (r + 63) / 64;
-  const int64_t per = (int64_t)b * ntile * ntile;
-  int64_t c = (152 + per - 1) / per;
-  c = std::max<int64_t>(1, std::min<int64_t>(c, n / 512));
-  return (int)c;
-}
-
-// Gram X^T Y per restart into G64 (+ factor-type copy GT with lam I when pair == tpair);
-// inside the iteration it follows ctl[j].active and the run flag, in the initial and
-// final evaluations (ctl == NULL) every restart is computed.
-void gram1(snmf_ctx* h, const void* X, const void* Y, int pair, int npairs, const Ctl* ctl,
-           double* G64, void* GT, int tpair, double lam) {
-  launch_gram(h->tdtype, X, Y, dims(h), pair, npairs, h->gpart, h->nchunks, ctl,
-              ctl ? h->run : nullptr, G64, GT, tpair, lam, h->counters, h->s);
-}
-
-RowArgs row_base(snmf_ctx* h, const Params* P = nullptr) {
-  RowArgs a{};
-  a.n = h->n; a.r = h->r; a.b = h->b; a.ld = h->N;
-  a.G = h->GT;
-  a.ctl = h->ctl;
-  a.run = h->run;
-  a.gamma = h->graph ? h->gamma : 0.0;
-  a.part = h->prow;
-  a.counters = h->counters + 16384;
-  a.G64fix = h->G64fix;
-  a.tile = h->use_tile;
-  a.bm = h->row_bm;
-  if (P) a.P = *P;
-  return a;
 }
 
 // ----------------------------------------------------------------------------
