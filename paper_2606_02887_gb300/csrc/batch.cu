@@ -293,7 +293,7 @@ k_brow(RowArgs base, const BProb* __restrict__ probs, const int2* __restrict__ i
 // The same for problems with r <= 32 through the shared-memory tile body (TileCfg rows per
 // item); dynamic shared memory of rowtile_smem bytes.
 template <typename T, int OP, int EPI, int NC>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, EPI == EPI_GRAD ? 2 : 3)
 k_browt(RowArgs base, const BProb* __restrict__ probs, const int2* __restrict__ items, const int* __restrict__ cnt) {
   extern __shared__ __align__(16) unsigned char tsm[];
   if ((int)blockIdx.x >= *cnt) return;  // beyond the (compacted) list

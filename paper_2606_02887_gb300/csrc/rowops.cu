@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256, BM == 32 ? 4 : 3) k_rowgemm(RowArgs a) {
 
 // r <= 32: the shared-memory tile body, CTA = TileCfg<T>::TR rows of restart blockIdx.z
 template <typename T, int OP, int EPI, int NC>
-__global__ void __launch_bounds__(256, 3) k_rowtile(RowArgs a) {
+__global__ void __launch_bounds__(256, EPI == EPI_GRAD ? 2 : 3) k_rowtile(RowArgs a) {
   extern __shared__ __align__(16) unsigned char tsm[];
   rowtile_body<T, OP, EPI, NC>(a, blockIdx.z, blockIdx.x, gridDim.x, reinterpret_cast<T*>(tsm));
 }

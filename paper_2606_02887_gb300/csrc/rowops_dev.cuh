@@ -944,16 +944,27 @@ __device__ __forceinline__ void rowtile_body(const RowArgs& a, int j, int tile, 
     const bool w_is_x = OP == OP_ZSTEP && a.Wcur == a.X && a.gWcur == a.g_in;
     const bool zold_is_z = OP == OP_UPD && a.Zold == a.Zin;
     T in0[C::EPT], in1[C::EPT], bq[C::EPT];
+    // EPI_GRAD: the epilogue's other inputs (S, Y and increment terms) are loaded here too,
+    // so that every load of the item is in flight in one round trip
+    constexpr int EP = EPI == EPI_GRAD ? C::EPT : 1;
+    T p0[EP], p1[EP], p2[EP];
+    const bool pre_old = EPI == EPI_GRAD && a.Xold != nullptr;
+    const bool pre_z = EPI == EPI_GRAD && a.Zold != nullptr;
     // 1. operand tile (and B, so that the epilogue does not wait for it)
 #pragma unroll
     for (int m = 0; m < C::EPT; ++m) {
       const int e = tid + 256 * m;
       in0[m] = in1[m] = bq[m] = T(0);
+      if (EPI == EPI_GRAD) p0[m % EP] = p1[m % EP] = p2[m % EP] = T(0);
       if (e < E) {
         const int row = (int)(((float)e + 0.5f) * inv_r);  // exact for e < 2^12, r <= 32
         const int col = e - row * r;
         const int64_t q = (row0 + row) * ld + jc + col;
         bq[m] = B[q];
+        if (EPI == EPI_GRAD) {
+          if (pre_old) { p0[m % EP] = ((const T*)a.Xold)[q]; p1[m % EP] = ((const T*)a.gold)[q]; }
+          if (pre_z) p2[m % EP] = ((const T*)a.gZold)[q];
+        }
         T v;
         if (OP == OP_LOAD) {
           v = X[q];
@@ -1001,16 +1012,16 @@ __device__ __forceinline__ void rowtile_body(const RowArgs& a, int j, int tile, 
         const T pgv = xv > T(0) ? g : (g < T(0) ? g : T(0));
         dq[0] += pgv * pgv;
         dq[1] += T(0.5) * (g - bq[m]) * xv;
-        if (a.Xold) {
-          const T sv = xv - ((const T*)a.Xold)[q];
-          const T yv = g - ((const T*)a.gold)[q];
+        if (pre_old) {
+          const T sv = xv - p0[m % EP];
+          const T yv = g - p1[m % EP];
           dq[2] += sv * sv;
           dq[3] += sv * yv;
           dq[4] += yv * yv;
         }
-        if (a.Zold) {
+        if (pre_z) {
           const T zo = zold_is_z ? in0[m] : ((const T*)a.Zold)[q];
-          dq[5] += T(0.5) * (xv - zo) * (g + ((const T*)a.gZold)[q]);
+          dq[5] += T(0.5) * (xv - zo) * (g + p2[m % EP]);
         }
         if (xv == T(0)) dq[6] += T(1);
         if (a.gout) ((T*)a.gout)[q] = g;
