@@ -184,10 +184,27 @@ def run_reference(args):
     return 0
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the product kernel, from the
-# ncu captures summarised in profiles/ (k_gemm_tc_dense8192_N512.md, k_bgemm_tc_uneven256.md);
-# keys: (workload, precision, r, batch).  Other configurations report null.
-PROFILED_TRAFFIC = {("dense8192", "bf16", 64, 8): 189.0e6, ("uneven", "bf16", None, None): 875.5e6}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, from the ncu captures summarised
+# in profiles/ (k_gemm_tc_dense8192_N512.md, k_rowgemm_dstep_dense8192_N512.md,
+# k_bgemm_tc_uneven256.md); keys: (workload, precision, r, batch, kernel), values: (bytes,
+# the tuned tile shapes of the capture, which the run must share).  Other configurations,
+# and runs tuned to other tiles, report null.
+PROFILED_TRAFFIC = {
+    ("dense8192", "bf16", 64, 8, "product"): (191.7e6, {"splits": 4, "bn": 128}),
+    ("dense8192", "bf16", 64, 8, "dstep"): (60.3e6, {"row_bm": 64}),
+    ("uneven", "bf16", None, None, "product"): (875.5e6, {}),
+}
+
+
+def profiled_traffic(key, tuning):
+    """Captured DRAM traffic of one launch, or None when the run's tiles differ from the capture's."""
+    got = PROFILED_TRAFFIC.get(key)
+    if got is None:
+        return None
+    traffic, tiles = got
+    if tiles and not all((tuning or {}).get(k) == v for k, v in tiles.items()):
+        return None
+    return traffic
 
 
 def rank_restarts(batch, rank):
@@ -313,7 +330,7 @@ def run_uneven(args):
     gbs = alg_bytes / (ms_prod * 1e-3) / 1e9
     kname = ("k_bsplit_x + k_bgemm_tc (grouped tcgen05 A_p (X_hi + X_lo), BF16 A)" if args.precision == "bf16"
              else "k_bgemm (grouped A_p X_p, CUDA cores, %s A)" % args.precision)
-    traffic = PROFILED_TRAFFIC.get(("uneven", args.precision, None, None)) if args.nprob == 256 else None
+    traffic = profiled_traffic(("uneven", args.precision, None, None, "product"), None) if args.nprob == 256 else None
     roof = {"bound": "hbm", "kernel": kname, "traffic_bytes": traffic,
             "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
             "traffic": traffic, "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
@@ -669,7 +686,7 @@ def main():
                 "peak": peaks["bf16_tflops"] if tensor_bound else peaks["hbm_gbs"],
                 "unit": "TFLOP/s" if tensor_bound else "GB/s",
                 "frac": (tflops / peaks["bf16_tflops"]) if tensor_bound else (aw_gbs / peaks["hbm_gbs"]),
-                "traffic": PROFILED_TRAFFIC.get((workload_key, args.precision, args.r, args.batch)),
+                "traffic": profiled_traffic((workload_key, args.precision, args.r, args.batch, "product"), tuning),
                 "peak_source": peak_kind + (" bf16_tflops (burst cuBLAS)" if tensor_bound else " hbm_gbs (burst copy)"),
                 "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
                 "aw_gbs": aw_gbs, "aw_hbm_frac": aw_gbs / peaks["hbm_gbs"],
@@ -693,7 +710,9 @@ def main():
             kernels[name] = {"bound": "hbm", "kernel": "k_rowgemm<%s>" % ("OP_ZSTEP, EPI_DIR" if name == "dstep"
                                                                           else "OP_UPD, EPI_GRAD"),
                              "achieved": gb, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                             "frac": gb / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_kind,
+                             "frac": gb / peaks["hbm_gbs"], "peak_source": peak_kind,
+                             "traffic": profiled_traffic(("dense8192" if args.n == 8192 else None, args.precision,
+                                                          args.r, args.batch, name), tuning),
                              "alg_bytes_per_launch": nbuf * fb4, "ms_per_launch": ms_k,
                              "launches_per_outer_iteration": 2 * K,
                              "note": "working set of one launch fits in L2, as inside the iteration"}

@@ -297,6 +297,14 @@ SNMF_API snmf_status snmf_tuned_config(snmf_handle h, int32_t* splits, int32_t* 
                                        double* ms, int32_t* from_cache);
 
 /*
+ * The tile shapes chosen by the same autotuner: *bn = columns of X per tensor-core product
+ * tile (0 where the product kernel has no such choice) and *row_bm = rows per CTA of the
+ * general row kernel (0 where the handle uses the shared-memory tile body, whose height is
+ * fixed).  SNMF_ERR_STATE when the handle was not tuned.
+ */
+SNMF_API snmf_status snmf_tuned_tiles(snmf_handle h, int32_t* bn, int32_t* row_bm);
+
+/*
  * Allocation-free dense product (the paper has no counterpart; this is a service of
  * the library).  Y = A X and <X, A X> for a dense FP32 or FP64 A, computed with the
  * same kernels as snmf_apply, for callers that must not allocate device memory after

@@ -605,6 +605,16 @@ void dir_final(snmf_ctx* h, const Params& P) {
   launch_ctl_final_dir(h->ctl, h->G64fix, h->b, h->r, P, h->s);
 }
 
+// Row kernels through the shared-memory tile body: r <= 32, penalty form, at most two step
+// candidates, no graph term, and enough row tiles to fill the GPU (a tile holds 128 FP32 /
+// 64 FP64 rows; small problems keep the general kernel's finer grid).
+int tile_rule(const snmf_ctx* h) {
+  const int64_t tr = h->tdtype == 0 ? 64 : 128;
+  const int64_t tiles = (h->n + tr - 1) / tr * h->b;
+  return (h->r <= 32 && h->opt.formulation == SNMF_PENALTY && h->opt.step_controller != 2 && !h->graph &&
+          tiles >= 2 * 152) ? 1 : 0;
+}
+
 snmf_status alloc_buffers(snmf_ctx* h) {
   const size_t fe = (size_t)h->n * h->N;
   for (int i = 0; i < NBUF; ++i) {
@@ -619,8 +629,8 @@ snmf_status alloc_buffers(snmf_ctx* h) {
   // room for every row-kernel layout (BM = 32 has the most slots; the tile body fewer)
   const int nrow_max = std::max(h->nrow, rowgemm_slots(d, h->tdtype, 0, 32));
   const size_t prec_n = (size_t)std::max(nrow_max, h->nax) * h->b * kNQ;
-  // r <= 32, penalty form, at most two step candidates: the tile body (no graph term yet)
-  h->use_tile = (h->r <= 32 && h->opt.formulation == SNMF_PENALTY && h->opt.step_controller != 2) ? 1 : 0;
+  // the shared-memory tile body where tile_rule allows it
+  h->use_tile = tile_rule(h);
   if (h->use_tile) h->nrow = rowgemm_slots(d, h->tdtype, 1);
   double** parts[] = {&h->prow, &h->pax, &h->pax2, &h->pax3, &h->pax4, &h->pclip};
   for (double** p : parts) {
@@ -957,7 +967,7 @@ snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma
     h->graph = false;
     h->gamma = 0.0;
     h->exec_form = -1;
-    h->use_tile = (h->r <= 32 && h->opt.formulation == SNMF_PENALTY && h->opt.step_controller != 2) ? 1 : 0;
+    h->use_tile = tile_rule(h);
     h->nrow = rowgemm_slots(dims(h), h->tdtype, h->use_tile, h->row_bm);
     return SNMF_OK;
   }
@@ -1324,6 +1334,14 @@ snmf_status snmf_tuned_config(snmf_handle h, int32_t* splits, int32_t* stages, i
   if (per_sm) *per_sm = h->tune.cfg.per_sm;
   if (ms) *ms = h->tune.ms;
   if (from_cache) *from_cache = h->tuned == 2 ? 1 : 0;
+  return SNMF_OK;
+}
+
+snmf_status snmf_tuned_tiles(snmf_handle h, int32_t* bn, int32_t* row_bm) {
+  if (!h) return SNMF_ERR_STATE;
+  if (!h->tuned) return fail(h, SNMF_ERR_STATE, "the handle was not autotuned");
+  if (bn) *bn = h->tune.cfg.bn;
+  if (row_bm) *row_bm = h->tune.cfg.row_bm;
   return SNMF_OK;
 }
 

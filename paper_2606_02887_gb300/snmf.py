@@ -28,7 +28,7 @@ EXPORTED = (
     "snmf_default_options", "snmf_create", "snmf_set_graph_reg", "snmf_lai_sketch",
     "snmf_solve", "snmf_solve_host", "snmf_restart_stats", "snmf_get_factors",
     "snmf_apply", "snmf_profile_ax", "snmf_apply_dense_noalloc", "snmf_controller_data",
-    "snmf_mlp_train", "snmf_tuned_config", "snmf_profile_steps", "snmf_destroy", "snmf_last_error",
+    "snmf_mlp_train", "snmf_tuned_config", "snmf_tuned_tiles", "snmf_profile_steps", "snmf_destroy", "snmf_last_error",
 )
 NOALLOC_SCRATCH_BYTES = 64 << 20
 NOALLOC_MAX_SLICE_PAIR_BYTES = NOALLOC_SCRATCH_BYTES - (1 << 20)
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH):
     lib.snmf_tuned_config.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                       C.POINTER(C.c_double), C.POINTER(C.c_int32)]
     lib.snmf_profile_steps.argtypes = [H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.snmf_tuned_tiles.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.snmf_destroy.argtypes = [H]
     lib.snmf_last_error.argtypes = [H]
     lib.snmf_last_error.restype = C.c_char_p
@@ -311,7 +312,10 @@ def snmf_tuned_config(h) -> dict:
     sp, st, ps, fc = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
     ms = C.c_double()
     _check(lib, h, lib.snmf_tuned_config(h, C.byref(sp), C.byref(st), C.byref(ps), C.byref(ms), C.byref(fc)))
-    return dict(splits=sp.value, stages=st.value, per_sm=ps.value, ms=ms.value, from_cache=bool(fc.value))
+    bn, bm = C.c_int32(), C.c_int32()
+    _check(lib, h, lib.snmf_tuned_tiles(h, C.byref(bn), C.byref(bm)))
+    return dict(splits=sp.value, stages=st.value, per_sm=ps.value, bn=bn.value, row_bm=bm.value, ms=ms.value,
+                from_cache=bool(fc.value))
 
 
 def snmf_destroy(h):

@@ -46,11 +46,12 @@ def test_autotune_search_cache_and_agreement(tmp_path, prec):
         entry = next(iter(devs.values()))[key]
         assert entry["splits"] == c1["splits"]
         assert entry["row_bm"] in (0, 32, 64)
+        assert (entry["bn"], entry["row_bm"]) == (c1["bn"], c1["row_bm"])
         h2 = S.snmf_create(S.dense_matrix(At), r, o)
         try:
             c2 = S.snmf_tuned_config(h2)
-            assert c2["from_cache"] and {k: c2[k] for k in ("splits", "stages", "per_sm")} == \
-                {k: c1[k] for k in ("splits", "stages", "per_sm")}
+            assert c2["from_cache"] and {k: c2[k] for k in ("splits", "stages", "per_sm", "bn", "row_bm")} == \
+                {k: c1[k] for k in ("splits", "stages", "per_sm", "bn", "row_bm")}
         finally:
             S.snmf_destroy(h2)
         Xn = np.random.default_rng(3).random((n, r)).astype(np.float32)
