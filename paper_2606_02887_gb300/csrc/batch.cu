@@ -440,7 +440,8 @@ struct BatchCtx {
   int rec_cap = 0;
   int* h_flag = nullptr;
   cudaStream_t user = nullptr, s = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evsync = nullptr;
+  cudaStream_t s2 = nullptr;  // side branch: grouped Gram beside the grouped product
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evsync = nullptr, evfork = nullptr, evjoin = nullptr;
   cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
   int nodes[3] = {0, 0, 0};
   std::vector<Ctl> h_ctl;
@@ -528,19 +529,20 @@ void bprod(BatchCtx* b, const void* X, void* Y, const void* P1, double* part, co
 }
 
 void bgram(BatchCtx* b, const void* X, const void* Y, int pair, int npairs, const Ctl* ctl, const int* run,
-           double* G64, void* GT, int tpair, int use_lam, Ctl* rho_ctl) {
+           double* G64, void* GT, int tpair, int use_lam, Ctl* rho_ctl, cudaStream_t st = nullptr) {
   const unsigned g = (unsigned)b->h_gram.size();
   const int it = b->opt.power_iters;
+  if (!st) st = b->s;
   if (b->tdtype == 0)
-    k_bgram<double><<<g, 256, 0, b->s>>>(b->dp, blist(b, 2), bcnt(b, 2), (const double*)X, (const double*)Y,
-                                         b->gpart, pair, npairs, ctl, run, G64, (double*)GT, tpair, use_lam,
-                                         b->counters, nullptr, it);
+    k_bgram<double><<<g, 256, 0, st>>>(b->dp, blist(b, 2), bcnt(b, 2), (const double*)X, (const double*)Y,
+                                       b->gpart, pair, npairs, ctl, run, G64, (double*)GT, tpair, use_lam,
+                                       b->counters, nullptr, it);
   else
-    k_bgram<float><<<g, 256, 0, b->s>>>(b->dp, blist(b, 2), bcnt(b, 2), (const float*)X, (const float*)Y,
-                                        b->gpart, pair, npairs, ctl, run, G64, (float*)GT, tpair, use_lam,
-                                        b->counters, rho_ctl, it);
+    k_bgram<float><<<g, 256, 0, st>>>(b->dp, blist(b, 2), bcnt(b, 2), (const float*)X, (const float*)Y,
+                                      b->gpart, pair, npairs, ctl, run, G64, (float*)GT, tpair, use_lam,
+                                      b->counters, rho_ctl, it);
   if (b->tdtype == 0 && rho_ctl)
-    k_brho<double><<<b->nprob, 256, 0, b->s>>>(b->dp, G64, it, rho_ctl);
+    k_brho<double><<<b->nprob, 256, 0, st>>>(b->dp, G64, it, rho_ctl);
 }
 
 RowArgs brow_base(BatchCtx* b, const Params& P) {
@@ -612,8 +614,14 @@ void bany(BatchCtx* b) {
 void bpen_block(BatchCtx* b, int xv, int xf, bool is_w, const Params& P) {
   void* X = b->buf[xv];
   void* Xf = b->buf[xf];
+  // G = Xf^T Xf (+lam I) and rho depend on Xf alone: they run on the side stream beside the
+  // product (a fork and a join of the captured graph) and share no buffer with it
+  cudaEventRecord(b->evfork, b->s);
+  cudaStreamWaitEvent(b->s2, b->evfork, 0);
+  bgram(b, Xf, Xf, 0, 1, b->ctl, b->run, b->G64fix, b->GT, 0, 1, b->ctl, b->s2);
+  cudaEventRecord(b->evjoin, b->s2);
   bprod(b, Xf, b->buf[XB_B], nullptr, nullptr, b->ctl, b->run);             // B = A Xf + lam Xf
-  bgram(b, Xf, Xf, 0, 1, b->ctl, b->run, b->G64fix, b->GT, 0, 1, b->ctl);   // G = Xf^T Xf (+lam I), rho
+  cudaStreamWaitEvent(b->s, b->evjoin, 0);
   {
     RowArgs a = brow_base(b, P);
     a.X = X; a.B = b->buf[XB_B]; a.gout = b->buf[XB_G];
@@ -754,6 +762,9 @@ snmf_status batch_create(BatchCtx** out, const snmf_matrix* Am, const snmf_optio
   b->a_dtype = o.precision == SNMF_F64 ? 0 : (o.precision == SNMF_BF16 ? 2 : 1);
   b->user = stream;
   CKB(cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking));
+  CKB(cudaStreamCreateWithFlags(&b->s2, cudaStreamNonBlocking));
+  CKB(cudaEventCreateWithFlags(&b->evfork, cudaEventDisableTiming));
+  CKB(cudaEventCreateWithFlags(&b->evjoin, cudaEventDisableTiming));
   CKB(cudaEventCreate(&b->ev0));
   CKB(cudaEventCreate(&b->ev1));
   CKB(cudaEventCreateWithFlags(&b->evsync, cudaEventDisableTiming));
@@ -1154,6 +1165,7 @@ snmf_status batch_get_factors(BatchCtx* b, void* W, void* Ht, std::string* err) 
 void batch_destroy(BatchCtx* b) {
   if (!b) return;
   if (b->s) cudaStreamSynchronize(b->s);
+  if (b->s2) cudaStreamSynchronize(b->s2);
   for (auto& e : b->exec)
     if (e) cudaGraphExecDestroy(e);
   cudaFree(b->A);
@@ -1184,6 +1196,9 @@ void batch_destroy(BatchCtx* b) {
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
   if (b->evsync) cudaEventDestroy(b->evsync);
+  if (b->evfork) cudaEventDestroy(b->evfork);
+  if (b->evjoin) cudaEventDestroy(b->evjoin);
+  if (b->s2) cudaStreamDestroy(b->s2);
   if (b->s) cudaStreamDestroy(b->s);
   delete b;
 }

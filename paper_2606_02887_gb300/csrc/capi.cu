@@ -44,6 +44,8 @@ struct snmf_ctx {
   size_t esz = 4;
   snmf_options opt{};
   cudaStream_t user = nullptr, s = nullptr;
+  cudaStream_t s2 = nullptr;                            // side branch: Gram beside the product
+  cudaEvent_t evfork = nullptr, evjoin = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evsync = nullptr;
   AxArgs A{};
   void* A_owned = nullptr;
@@ -405,16 +407,22 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
   void* X = h->buf[xv];
   void* Xf = h->buf[xf];
   const bool gr = h->graph && !is_w;
-  // B = A Xfix + lambda Xfix (Eq. (2.1)/(2.2))
-  ax_A(h, Xf, h->buf[B_B], h->lam, Xf, nullptr, nullptr, h->pax, h->run);
+  // The Gram and rho_0 depend on Xfix alone, so they run on the side stream beside the
+  // product (a fork and a join of the captured graph); they share no buffer with it.
   // G = Xfix^T Xfix (+ lambda I in the factor-type copy); rho_0 = ||Xfix^T Xfix||_2, computed
   // by the Gram's last CTA when the restart is one tile (FP32 path), else by k_rho
+  cudaEventRecord(h->evfork, h->s);
+  cudaStreamWaitEvent(h->s2, h->evfork, 0);
   const bool rho_fused = td == 1 && h->r <= 64;
   // graph-regularised H block: rho_0 = ||W^T W||_2 + gamma ||L||_2 (Lipschitz constant of its gradient)
   const double shift = gr ? h->gamma * h->normL : 0.0;
   launch_gram(td, Xf, Xf, d, 0, 1, h->gpart, h->nchunks, h->ctl, h->run, h->G64fix, h->GT, 0, h->lam,
-              h->counters, h->s, rho_fused ? h->ctl : nullptr, h->opt.power_iters, 1.0, shift);
-  if (!rho_fused) launch_rho(td, h->G64fix, d, h->opt.power_iters, 1.0, h->ctl, 0, h->s, shift);
+              h->counters, h->s2, rho_fused ? h->ctl : nullptr, h->opt.power_iters, 1.0, shift);
+  if (!rho_fused) launch_rho(td, h->G64fix, d, h->opt.power_iters, 1.0, h->ctl, 0, h->s2, shift);
+  cudaEventRecord(h->evjoin, h->s2);
+  // B = A Xfix + lambda Xfix (Eq. (2.1)/(2.2))
+  ax_A(h, Xf, h->buf[B_B], h->lam, Xf, nullptr, nullptr, h->pax, h->run);
+  cudaStreamWaitEvent(h->s, h->evjoin, 0);
   if (gr) ax_L(h, X, h->buf[B_LX], nullptr, nullptr, h->pax2, h->run);
   {
     // gradient at the block start; its last CTA per restart runs the block-start control
@@ -796,6 +804,9 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   } while (0)
   init_kernel_attributes();
   CKC(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
+  CKC(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
+  CKC(cudaEventCreateWithFlags(&h->evfork, cudaEventDisableTiming));
+  CKC(cudaEventCreateWithFlags(&h->evjoin, cudaEventDisableTiming));
   CKC(cudaEventCreate(&h->ev0));
   CKC(cudaEventCreate(&h->ev1));
   CKC(cudaEventCreateWithFlags(&h->evsync, cudaEventDisableTiming));
@@ -1373,6 +1384,7 @@ snmf_status snmf_destroy(snmf_handle h) {
     return SNMF_OK;
   }
   if (h->s) cudaStreamSynchronize(h->s);
+  if (h->s2) cudaStreamSynchronize(h->s2);
   for (auto& e : h->exec)
     if (e) cudaGraphExecDestroy(e);
   if (h->evdone) cudaEventDestroy(h->evdone);
@@ -1406,6 +1418,9 @@ snmf_status snmf_destroy(snmf_handle h) {
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->evsync) cudaEventDestroy(h->evsync);
+  if (h->evfork) cudaEventDestroy(h->evfork);
+  if (h->evjoin) cudaEventDestroy(h->evjoin);
+  if (h->s2) cudaStreamDestroy(h->s2);
   if (h->s) cudaStreamDestroy(h->s);
   delete h;
   return SNMF_OK;
