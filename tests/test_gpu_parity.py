@@ -22,20 +22,19 @@ ITER_TOL = 1e-10
 ENVELOPE_FACTOR = 10.0
 
 
-def rounding_envelope(run, key, n_iter, seeds=3):
-    """Per-iteration divergence of the oracle from itself under a model of FP64
-    rounding: every projection output is perturbed by unit roundoff u = 2^-53
-    (relative), and every gradient X G - B by the typical rounding of its two
-    large terms, u (sqrt(r) |X G| + sqrt(n) |B|): a length-m sum accumulated in
-    another order differs by about sqrt(m) u relative to the sum of |terms|
-    (here all terms are nonnegative).  This is the spread that two correct FP64
-    implementations with different summation orders show.  Returns e[k-1], the
-    max over seeds.  Only the oracle runs here."""
+def rounding_envelope(run, key, n_iter, seeds=3, u=2.0 ** -53):
+    """Per-iteration divergence of the oracle from itself under a model of
+    rounding: every projection output is perturbed by unit roundoff u (2^-53 for
+    FP64, 2^-24 for FP32; relative), and every gradient X G - B by the typical
+    rounding of its two large terms, u (sqrt(r) |X G| + sqrt(n) |B|): a length-m
+    sum accumulated in another order differs by about sqrt(m) u relative to the
+    sum of |terms| (here all terms are nonnegative).  This is the spread that two
+    correct implementations in that precision with different summation orders
+    show.  Returns e[k-1], the max over seeds.  Only the oracle runs here."""
     import oracle.snmpbb as SM
 
     base = run()
     saved = {k: getattr(SM, k) for k in ("proj", "penalty_grad_W", "penalty_grad_Ht", "direct_gradient")}
-    u = 2.0 ** -53
     out = np.zeros(n_iter)
 
     def noisy_grad(fn, g, scale_fn):
@@ -146,6 +145,31 @@ def test_penalty_fp64_ragged_shapes_and_batch():
                                                                     objective="closed"))
             sl = slice(j * r, (j + 1) * r)
             assert rel(W[:, sl], Wo) <= ITER_TOL and rel(H[:, sl], Ho) <= ITER_TOL, (n, r, b, j)
+
+
+def test_fp32_wide_row_tiles_follow_oracle():
+    """FP32 through the general row kernel's 64-row tiles (chosen when the grid has at least
+    2 x 152 row tiles: here 40 tiles x 8 restarts), with a ragged last tile (n = 2500) and a
+    rank that fills part of a 64-column tile (r = 48): after 3 outer iterations every restart
+    stays within the oracle's own FP32 rounding envelope (the model of rounding_envelope at
+    u = 2^-24, first restart; 8e-4 to 1e-3 for these restarts).  An indexing error would
+    show as O(1)."""
+    n, r, b = 2500, 48, 8
+    A, _ = planted_dense(n, r, 0.01, seed=2500)
+    Ws = [uniform_init(n, r, math.sqrt(A.mean() / r), seed=2600 + j) for j in range(b)]
+    W0 = np.concatenate(Ws, axis=1)
+    W, H, _, _, _ = gpu_solve(A, W0, r, W0, precision=S.SNMF_F32, max_iter=3, tol=0.0, batch=b)
+    opts = O.Options(max_iter=3, tol=0.0, memory=10, objective="closed")
+    env = rounding_envelope(lambda: O.snmpbb_penalty(A, Ws[0], Ws[0], opts, keep_iterates=True)[2]["trace"],
+                            "W", 3, u=2.0 ** -24)
+    worst = 0.0
+    for j in (0, 3, b - 1):  # first, middle and last grid slice of restarts
+        Wo, Ho, _ = O.snmpbb_penalty(A, Ws[j], Ws[j], opts)
+        sl = slice(j * r, (j + 1) * r)
+        worst = max(worst, rel(W[:, sl], Wo), rel(H[:, sl], Ho))
+    print(f"FP32, 64-row tiles, vs the FP64 oracle after 3 outer iterations: max rel {worst:.2e}, "
+          f"FP32 envelope {env[2]:.2e}")
+    assert worst <= env[2]
 
 
 def test_direct_fp64_batch_restarts():
