@@ -362,6 +362,53 @@ def test_mlp_oracle_gradient_finite_differences():
     assert np.allclose(M.multiplier(np.zeros(M.N_PARAMS), phi), 1.0)
 
 
+def test_mlp_parameter_layout_and_multiplier_range():
+    """The parameter vector follows the C ABI's documented layout W1[64][5] (row-major,
+    hidden x input), b1[64], W2[64], b2: hand-built weights with a known output.  W1 routes
+    input i to hidden unit i (i < 5) and hidden unit 5 + i to -input i, W2 sums them, so
+    o = sum_i (relu(phi_i) + relu(-phi_i)) + b2 = sum_i |phi_i| + b2.  The multiplier
+    2^(2 tanh o) lies in (1/4, 4) and is monotone in o."""
+    import oracle.mlp as M
+    assert (M.N_IN, M.N_HID, M.N_PARAMS) == (5, 64, 5 * 64 + 64 + 64 + 1)
+    W1 = np.zeros((M.N_HID, M.N_IN))
+    for i in range(M.N_IN):
+        W1[i, i] = 1.0
+        W1[M.N_IN + i, i] = -1.0
+    b1 = np.zeros(M.N_HID)
+    W2 = np.zeros(M.N_HID)
+    W2[:2 * M.N_IN] = 1.0
+    b2 = -0.25
+    w = np.concatenate([W1.ravel(), b1, W2, [b2]])
+    g = np.random.default_rng(143)
+    phi = g.normal(0, 1, (30, M.N_IN))
+    o, _, _ = M.forward(w, phi)
+    assert np.allclose(o, np.abs(phi).sum(axis=1) + b2, rtol=0, atol=1e-14)
+    m = M.multiplier(w, phi)
+    assert np.all((m > 0.25) & (m < 4.0))
+    order = np.argsort(o)
+    assert np.all(np.diff(m[order]) >= 0)
+    assert M.multiplier(w, np.zeros((1, M.N_IN)))[0] == pytest.approx(2.0 ** (2.0 * math.tanh(b2)), rel=1e-15)
+
+
+def test_projected_gradient_is_the_one_sided_limit():
+    """The projected gradient of min f over X >= 0 is the one-sided derivative
+    lim_{t -> 0+} (X - Proj[X - t g]) / t: g where X > 0, min(g, 0) where X = 0.  Checked
+    with a small step on a matrix with zero entries and gradients of both signs, and its
+    norm vanishes exactly at a KKT point (X >= 0, g >= 0 on the zeros, g = 0 elsewhere)."""
+    g = np.random.default_rng(144)
+    X = g.random((40, 6))
+    X[g.random(X.shape) < 0.4] = 0.0
+    G = g.normal(0, 1, X.shape)
+    t = 1e-9
+    lim = (X - O.proj(X - t * G)) / t
+    pos = X > 1e-6  # away from the kink at the step size used
+    P = O.projected_gradient(X, G)
+    assert np.allclose(P[pos], lim[pos], rtol=0, atol=1e-6)
+    assert np.allclose(P[X == 0], lim[X == 0], rtol=0, atol=1e-6)
+    Gk = np.where(X > 0, 0.0, np.abs(G))
+    assert np.linalg.norm(O.projected_gradient(X, Gk)) == 0.0
+
+
 def test_fp8_e4m3_codec_pins():
     """E4M3 from its definition: known codes, the saturation bound, round trip of every
     finite code, ties to even, the half-ulp error bound, and the tile-scale rule."""
