@@ -58,6 +58,9 @@ def test_invalid_arguments_rejected_before_launch(lib):
     m, _ = S.dense_matrix(A)
     o = S.snmf_default_options()
     assert _create(lib, m, 0, o)[0] == S.SNMF_ERR_ARG            # r < 1
+    m0, _ = S.dense_matrix(A)
+    m0.n = 0                                                     # empty matrix
+    assert _create(lib, m0, 1, o)[0] == S.SNMF_ERR_ARG
     assert _create(lib, m, 9, o)[0] == S.SNMF_ERR_ARG            # r > n
     assert _create(lib, m, 300, o)[0] == S.SNMF_ERR_ARG          # r > 256
     bad = S.snmf_default_options(batch=0)

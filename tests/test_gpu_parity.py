@@ -147,6 +147,24 @@ def test_penalty_fp64_ragged_shapes_and_batch():
             assert rel(W[:, sl], Wo) <= ITER_TOL and rel(H[:, sl], Ho) <= ITER_TOL, (n, r, b, j)
 
 
+def test_zero_start_is_a_fixed_point(cfg1):
+    """W0 = H0 = 0 is a KKT point of the penalty problem (Eq. (3)): both block gradients
+    (W Ht^T - A) Ht + lambda (W - Ht) and its H counterpart vanish there.  The zero Gram
+    gives rho_0 = 0 in the oracle's power method and unit scaling in the library; either
+    way the projection keeps every iterate at 0.  Both sides return zero factors, the
+    relative residual is 1, and no statistic is NaN."""
+    A, _ = cfg1
+    Z0 = np.zeros((A.shape[0], 10))
+    W, H, st, stats, per = gpu_solve(A, Z0, 10, Z0, max_iter=5, tol=1e-4, nonmonotone_M=10)
+    assert st == S.SNMF_OK, stats
+    assert not np.any(W) and not np.any(H)
+    assert stats["residual"] == pytest.approx(1.0, rel=1e-12)
+    assert all(np.isfinite(stats[k]) for k in ("f", "residual", "pg_rel"))
+    assert stats["iters"] <= 2
+    Wo, Ho, info = O.snmpbb_penalty(A, Z0, Z0, O.Options(max_iter=5, tol=1e-4, memory=10, objective="closed"))
+    assert not np.any(Wo) and not np.any(Ho)
+
+
 def test_fp32_wide_row_tiles_follow_oracle():
     """FP32 through the general row kernel's 64-row tiles (chosen when the grid has at least
     2 x 152 row tiles: here 40 tiles x 8 restarts), with a ragged last tile (n = 2500) and a
