@@ -147,6 +147,23 @@ def test_penalty_fp64_ragged_shapes_and_batch():
             assert rel(W[:, sl], Wo) <= ITER_TOL and rel(H[:, sl], Ho) <= ITER_TOL, (n, r, b, j)
 
 
+def test_penalty_fp64_maximum_rank():
+    """The largest rank the library accepts (r = 256: four 64-column tiles per restart, the
+    Gram's rho_0 in the separate power-method kernel) follows the oracle iterate by iterate
+    for 3 outer iterations, at 1e-10 or 10x the oracle's own rounding envelope."""
+    n, r = 300, 256
+    A, _ = planted_dense(n, r, 0.01, seed=256)
+    W0 = uniform_init(n, r, math.sqrt(A.mean() / r), seed=257)
+    opts = O.Options(max_iter=3, tol=0.0, memory=10, objective="closed")
+    _, _, info = O.snmpbb_penalty(A, W0, W0, opts, keep_iterates=True)
+    env = rounding_envelope(lambda: O.snmpbb_penalty(A, W0, W0, opts, keep_iterates=True)[2]["trace"], "W", 3)
+    W, H, st, stats, _ = gpu_solve(A, W0, r, W0, max_iter=3, tol=0.0, nonmonotone_M=10)
+    rec = info["trace"][2]
+    e = max(rel(W, rec["W"]), rel(H, rec["Ht"]))
+    assert st == S.SNMF_NOT_CONVERGED and stats["iters"] == 3   # tol = 0: max_iter ends the solve
+    assert e <= iter_tol(env, 3), (e, env)
+
+
 def test_zero_start_is_a_fixed_point(cfg1):
     """W0 = H0 = 0 is a KKT point of the penalty problem (Eq. (3)): both block gradients
     (W Ht^T - A) Ht + lambda (W - Ht) and its H counterpart vanish there.  The zero Gram
