@@ -31,6 +31,7 @@ from .snmpbb import (  # noqa: F401
     snmpbb_direct,
     snmpbb_penalty,
     resolve_lambda,
+    svd_init,
 )
 from .philox import philox4x32, philox_uniform, philox_gaussian  # noqa: F401
 from .lai import lai_sketch  # noqa: F401

@@ -114,6 +114,20 @@ def resolve_lambda(A, opts: Options) -> float:
     return 0.01 * float(np.linalg.norm(dense_of(A)))
 
 
+def svd_init(A, r: int):
+    """SVD start of Sec. 4.1 guideline (4), recommended there for graph problems: with
+    V ~ U E P^T (the r largest singular values), W_0 = |U E^(1/2)| and H_0 = |E^(1/2) P^T|.
+    Returns (W0, Ht0), Ht0 = H_0^T = |P E^(1/2)|.  The absolute values make the start
+    nonnegative and independent of the sign of each singular-vector pair.  For a symmetric
+    V, P = U up to the signs of V's eigenvalues, so W0 = Ht0."""
+    V = dense_of(A)
+    U, s, Pt = np.linalg.svd(V)
+    e = np.sqrt(s[:r])
+    W0 = np.abs(U[:, :r] * e[None, :])
+    Ht0 = np.abs(Pt[:r, :].T * e[None, :])
+    return W0, Ht0
+
+
 def paper_laplacian(A) -> np.ndarray:
     """L = I - D^-1/2 V D^-1/2 with d_ii = e_i^T V e (Sec. 2.2).
 

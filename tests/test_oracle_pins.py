@@ -409,6 +409,34 @@ def test_projected_gradient_is_the_one_sided_limit():
     assert np.linalg.norm(O.projected_gradient(X, Gk)) == 0.0
 
 
+def test_svd_init_special_cases():
+    """The SVD start of Sec. 4.1 (4) on inputs whose factorization is known in closed form.
+    (a) Rank one with a nonnegative vector, V = v v^T: W0 = Ht0 = v, a zero residual.
+    (b) A nonnegative diagonal with distinct entries: W0 holds sqrt(d_i) e_i for the r
+        largest d_i, so W0 W0^T is the best rank-r approximation (Eckart-Young) and the
+        residual is sqrt(sum of the other d_i^2) / ||d||.
+    (c) A symmetric matrix with a negative eigenvalue among the r largest in magnitude:
+        singular values are |eigenvalues|, the absolute values remove every sign, and
+        W0 = Ht0 = |Q| |lambda|^(1/2) for the eigenvectors Q."""
+    g = np.random.default_rng(146)
+    v = g.random(30)
+    W0, Ht0 = O.svd_init(np.outer(v, v), 1)
+    assert np.allclose(W0[:, 0], v, rtol=1e-12, atol=1e-14) and np.allclose(Ht0, W0, rtol=1e-12, atol=1e-14)
+    d = np.array([9.0, 7.0, 5.0, 3.0, 2.0, 1.0, 0.5])
+    W0, Ht0 = O.svd_init(np.diag(d), 3)
+    E = np.zeros((7, 3))
+    E[[0, 1, 2], [0, 1, 2]] = np.sqrt(d[:3])
+    assert np.allclose(W0, E, atol=1e-14) and np.allclose(Ht0, E, atol=1e-14)
+    res = np.linalg.norm(np.diag(d) - W0 @ Ht0.T) / np.linalg.norm(d)
+    assert res == pytest.approx(math.sqrt(np.sum(d[3:] ** 2)) / np.linalg.norm(d), rel=1e-13)
+    Q, _ = np.linalg.qr(g.normal(size=(12, 12)))
+    lam = np.array([-6.0, 5.0, 4.0] + list(np.linspace(1.0, 0.1, 9)))
+    V = (Q * lam) @ Q.T
+    W0, Ht0 = O.svd_init(V, 3)
+    ref = np.abs(Q[:, :3]) * np.sqrt(np.abs(lam[:3]))[None, :]
+    assert np.allclose(W0, ref, atol=1e-12) and np.allclose(Ht0, ref, atol=1e-12)
+
+
 def test_fp8_e4m3_codec_pins():
     """E4M3 from its definition: known codes, the saturation bound, round trip of every
     finite code, ties to even, the half-ulp error bound, and the tile-scale rule."""
