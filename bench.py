@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparison runs")
     p.add_argument("--autotune", type=int, default=1, help="dense workload: tune the product at create")
     p.add_argument("--tune-cache", default=None, help="JSON cache of tuned configurations")
+    p.add_argument("--cpu-iters", type=int, default=10, help="oracle outer iterations timed for cpu_baseline")
     return p.parse_args()
 
 
@@ -145,6 +146,30 @@ def oracle_seconds_per_iter(A, W0, r, iters, formulation):
     else:
         O.snmpbb_direct(A, W0, opts)
     return (time.perf_counter() - t) / iters
+
+
+def oracle_golden(args):
+    """The FP64 oracle's solve of restart 0 of the dense workload (iterations, residual), as
+    written by tests/golden/make_oracle_iters.py; None for other shapes."""
+    gold = os.path.join(ROOT, "tests", "golden", "oracle_iters_dense8192.json")
+    if args.n != 8192 or args.formulation != "penalty" or not os.path.exists(gold):
+        return None
+    return json.load(open(gold)).get(str(args.r))
+
+
+def residuals_true_A(A_np, W, H, r, b, dev):
+    """||A - W_j H_j^T||_F / ||A||_F per restart against the true (FP64) A, evaluated with
+    torch on the device after the timed region."""
+    import torch
+    Ad = torch.tensor(A_np, dtype=torch.float64, device=dev)
+    nA = float(torch.linalg.norm(Ad))
+    out = []
+    for j in range(b):
+        Wj = W[:, j * r:(j + 1) * r].double()
+        Hj = H[:, j * r:(j + 1) * r].double()
+        out.append(float(torch.linalg.norm(Ad - Wj @ Hj.T)) / nA)
+    del Ad
+    return out
 
 
 def workload_name(args):
@@ -743,11 +768,24 @@ def main():
                 e_times.append(time.perf_counter() - t0)
         fb = W0.numel() * W0.element_size()
         nf = 2 if form == S.SNMF_PENALTY else 1
-        e2e = {"value": statistics.mean(e_times), "unit": "s", "h2d_bytes_per_step": a_bytes + nf * fb,
+        a_host_bytes = A_host.numel() * A_host.element_size()  # A crosses in its host dtype
+        e2e = {"value": statistics.mean(e_times), "unit": "s", "h2d_bytes_per_step": a_host_bytes + nf * fb,
                "d2h_bytes_per_step": nf * fb,
-               "path": "snmf_create(host A) + snmf_solve_host + snmf_destroy, wall clock"}
+               "path": "snmf_create(host A, %s) + snmf_solve_host + snmf_destroy, wall clock; the library "
+                       "converts A to its storage precision on the device" % str(A_host.dtype).replace("torch.", "")}
     per = S.snmf_restart_stats(h, args.batch)
     S.snmf_destroy(h)
+    res_true = residuals_true_A(A_np, W, H if form == S.SNMF_PENALTY else W, args.r, len(mine), dev)
+    error_vs_oracle = None
+    gold = oracle_golden(args)
+    if gold is not None and mine[0] == 0:
+        error_vs_oracle = {
+            "restart": 0, "residual_true_A": res_true[0], "oracle_residual": gold["residual"],
+            "abs_diff": abs(res_true[0] - gold["residual"]), "bar": 1e-3,
+            "within_bar": bool(abs(res_true[0] - gold["residual"]) <= 1e-3),
+            "iters": int(per["iters"][0]), "oracle_iters": gold["iters"],
+            "pg_rel": float(per["pg_rel"][0]), "oracle_pg_rel": gold["pg_rel"],
+            "source": "tests/golden/oracle_iters_dense8192.json (FP64 oracle, same start, penalty form, M=10)"}
 
     # the same restarts solved by the plain FP32 path: one restart per snmf_solve, FP32 A,
     # no controller (device time of each solve, CUDA events inside the library)
@@ -771,16 +809,38 @@ def main():
             "s": tot, "iters": its, "residual": res, "speedup_of_value": tot / (ms_max / 1e3),
             "residual_max_abs_diff": float(dres.max()), "restarts_within_1e-3": int(np.sum(dres <= 1e-3))},
             "this_run": {"iters": [int(x) for x in per["iters"]], "residual": [float(x) for x in per["residual"]],
-                         "pg_rel_max": float(np.max(per["pg_rel"]))}}
+                         "residual_true_A": res_true, "pg_rel_max": float(np.max(per["pg_rel"]))}}
+        if ctl:
+            # the same batched BF16 solve with the plain BB step: separates the controller's
+            # share of the gain from batching and storage precision
+            ob = S.snmf_default_options(precision=prec, formulation=form, batch=args.batch, max_iter=args.max_iter,
+                                        tol=args.tol, nonmonotone_M=10, autotune=args.autotune,
+                                        tune_cache=args.tune_cache, step_controller=0)
+            hb = S.snmf_create(S.dense_matrix(A), args.r, ob, stream=stream)
+            bt = []
+            for k in range(2):
+                W.copy_(W0)
+                H.copy_(W0)
+                stb, sb = S.snmf_solve(hb, W, H if form == S.SNMF_PENALTY else None)
+                bt.append(sb["seconds"])
+            pb = S.snmf_restart_stats(hb, args.batch)
+            S.snmf_destroy(hb)
+            compare["batched_plain_bb_same_precision"] = {
+                "s": bt[-1], "iters": [int(x) for x in pb["iters"]],
+                "residual": [float(x) for x in pb["residual"]], "pg_rel_max": float(np.max(pb["pg_rel"])),
+                "controller_gain": bt[-1] / (ms_max / 1e3),
+                "note": "device time of one solve (CUDA events in the library), second of two runs"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        iters_s = 2
+        iters_s = args.cpu_iters
         spi = oracle_seconds_per_iter(A_np, starts[0], args.r, iters_s, args.formulation)
-        est = spi * stats["iters"] * args.batch
+        iters_to_tol = gold["iters"] if gold is not None else stats["iters"]
+        est = spi * iters_to_tol * args.batch
         cpu = {"value": est, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
                "sample": f"{iters_s} outer iterations of the FP64 oracle (closed-form objective) on restart 0 of "
-                         f"this workload ({spi:.3f} s/iteration), x {stats['iters']} iterations to tolerance "
+                         f"this workload ({spi:.3f} s/iteration), x {iters_to_tol} iterations to tolerance "
+                         f"({'the oracle own count, tests/golden' if gold is not None else 'this run count'}) "
                          f"x {args.batch} restart(s)"}
 
     if rank == 0:
@@ -794,6 +854,7 @@ def main():
                            else "L2 flushed between timed steps (256 MB write)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roof, "roofline_kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "error_vs_oracle": error_vs_oracle,
                 "gpu_launches": launches, "clocks": clk, "tuning": tuning,
                 "solve": {"status": st, "iters": stats["iters"], "residual": stats["residual"],
                           "pg_rel": stats["pg_rel"], "ls_fail": stats["ls_fail"],

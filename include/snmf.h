@@ -147,7 +147,8 @@ typedef struct {
                               (Sec. 4.1 (4))                                                   */
   uint64_t seed;           /* Philox seed of the default initialisation                         */
   const float* mlp_weights;/* host, SNMF_MLP_NPARAMS floats: W1[64][5], b1[64], W2[64], b2 (copied) */
-  int64_t timeout_cycles;  /* bound on device-side waits (clock64 cycles), 0 = default        */
+  int64_t timeout_cycles;  /* bound on device-side waits (clock64 cycles), 0 = default (2e9);
+                              see snmf_set_timeout                                             */
   int32_t autotune;        /* 1: at snmf_create, time the candidate launch configurations of
                               the dense A*X product (split-K count; tcgen05 ring depth and CTAs
                               per SM) on this device and shape and keep the fastest; 0 (default):
@@ -320,16 +321,25 @@ SNMF_API snmf_status snmf_tuned_tiles(snmf_handle h, int32_t* bn, int32_t* row_b
  *   stream cudaStream_t as void*; the call returns after the stream has finished it
  * Scratch: the split-K slices and FP64 partial sums live in one file-scope device
  * array of SNMF_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until
- * the process exits.  It is shared by all calls and keeps the last call's contents
- * (every word a call reads was written by that call, so nothing needs clearing);
- * calls that overlap on the GPU race on it, so issue them one at a time.
- * Set-up: the first call on a device resolves the array's device address on the
- * current device.  Limits: n <= 1048320 and 2 * n * cols * sizeof(element) <=
+ * the process exits: the first SNMF_NOALLOC_PARTIAL_BYTES hold the partial sums (one
+ * 256-byte record per 64-row slice of A, plus the reduced scalar), the rest the split-K
+ * slices.  It is shared by all calls and keeps the last call's contents (every word a
+ * call reads was written by that call, so nothing needs clearing); calls that overlap
+ * on the GPU race on it, so issue them one at a time.
+ * Set-up: the array's device address is resolved with cudaGetSymbolAddress on the
+ * first call made in a CUDA context (the current device's context at the time of the
+ * call) and cached per context; a new context (after cudaDeviceReset, or a driver-API
+ * caller's own context) is resolved again on its first call.  Make that first call
+ * before any stream capture.
+ * Limits: n <= SNMF_NOALLOC_MAX_ROWS and 2 * n * cols * sizeof(element) <=
  * SNMF_NOALLOC_MAX_SLICE_PAIR_BYTES; larger sizes, NULL pointers, lda < n or another
- * dtype return SNMF_ERR_ARG before any launch.  CUDA failures return SNMF_ERR_CUDA.
+ * dtype return SNMF_ERR_ARG before any CUDA call.  CUDA failures return SNMF_ERR_CUDA.
  */
 #define SNMF_NOALLOC_SCRATCH_BYTES (64ull << 20)
-#define SNMF_NOALLOC_MAX_SLICE_PAIR_BYTES (SNMF_NOALLOC_SCRATCH_BYTES - (1ull << 20))
+#define SNMF_NOALLOC_PARTIAL_BYTES (4ull << 20)
+#define SNMF_NOALLOC_MAX_SLICE_PAIR_BYTES (SNMF_NOALLOC_SCRATCH_BYTES - SNMF_NOALLOC_PARTIAL_BYTES)
+/* 64 rows per partial record of 256 bytes; 256 bytes stay free for the reduced scalar */
+#define SNMF_NOALLOC_MAX_ROWS (64ll * (int64_t)((SNMF_NOALLOC_PARTIAL_BYTES - 256) / 256))
 SNMF_API snmf_status snmf_apply_dense_noalloc(const void* A, int dtype, int64_t n, int64_t lda,
                                               const void* X, void* Y, int cols, double* xax,
                                               void* stream);
@@ -354,6 +364,28 @@ SNMF_API snmf_status snmf_controller_data(snmf_handle h, float* feat, float* tar
  */
 SNMF_API snmf_status snmf_mlp_train(const float* feats, const float* targets, int count, float* weights,
                                     int steps, double lr, double* loss_out, float* grad0);
+
+/*
+ * Evaluate the step controller's network as the solver does (not in the paper): for each
+ * of `count` feature vectors feats[i][5] (host) the multiplier m = 2^(2 tanh o),
+ * o = W2 relu(W1 phi + b1) + b2, with the weights rounded to BF16 exactly as snmf_create
+ * rounds opt.mlp_weights and FP32 accumulation on the device, into mult[i] (host).
+ *   weights: host, SNMF_MLP_NPARAMS floats (W1[64][5], b1[64], W2[64], b2).
+ * Uses the current CUDA device and the legacy default stream; allocates device memory.
+ * Errors: SNMF_ERR_ARG (NULL pointer, count < 1), SNMF_ERR_OOM, SNMF_ERR_CUDA.
+ */
+SNMF_API snmf_status snmf_mlp_eval(const float* weights, const float* feats, int count, float* mult);
+
+/*
+ * Failure detection (not in the paper): set the bound, in clock64 cycles, of every device-side
+ * wait of this handle's kernels (the mbarrier waits of the tensor-core products); 0 restores
+ * the default (2e9 cycles, about one second).  A wait that runs out makes the kernel record
+ * an error code, drain the asynchronous copies and tensor-core operations it issued (with a
+ * separate budget of about two seconds) and return; the call that launched it then returns
+ * SNMF_ERR_TIMEOUT and the handle stays usable.  The same bound is set at create by
+ * opt.timeout_cycles.  Errors: SNMF_ERR_ARG (cycles < 0), SNMF_ERR_STATE (NULL handle).
+ */
+SNMF_API snmf_status snmf_set_timeout(snmf_handle h, int64_t cycles);
 
 /* Release every resource of the handle.  NULL is accepted. */
 SNMF_API snmf_status snmf_destroy(snmf_handle h);

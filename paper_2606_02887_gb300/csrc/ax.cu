@@ -183,7 +183,33 @@ k_ax_finish(int64_t n, int r, int64_t ld, T* __restrict__ Y, const T* __restrict
 
 inline int cdiv64(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Structure check of a device-resident CSR matrix before its first product: rowptr[0] = 0,
+// rowptr[n] = nnz, rowptr non-decreasing (bit 0 of *bad) and every column index in [0, n)
+// (bit 1).  Grid-stride; only reads inside rowptr[0..n] and colidx[0..nnz).
+__global__ void k_csr_check(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, int64_t n,
+                            int64_t nnz, int* __restrict__ bad) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int flag = 0;
+  if (t0 == 0 && (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz)) flag |= 1;
+  for (int64_t i = t0; i < n; i += stride)
+    if (rowptr[i + 1] < rowptr[i]) flag |= 1;
+  for (int64_t e = t0; e < nnz; e += stride) {
+    const int32_t c = colidx[e];
+    if (c < 0 || (int64_t)c >= n) flag |= 2;
+  }
+  if (flag) atomicOr(bad, flag);
+}
+
 }  // namespace
+
+void launch_csr_check(const int32_t* rowptr, const int32_t* colidx, int64_t n, int64_t nnz, int* bad,
+                      cudaStream_t s) {
+  const int64_t work = n > nnz ? n : nnz;
+  int blocks = cdiv64(work > 0 ? work : 1, 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_csr_check<<<blocks, 256, 0, s>>>(rowptr, colidx, n, nnz, bad);
+}
 
 int launch_ax(const AxArgs& a, int tdtype, int64_t n, int cols, int64_t ld, const void* X,
               void* Y, void* ws, size_t ws_elems, const int* run, cudaStream_t s, const ProdTune* tune) {

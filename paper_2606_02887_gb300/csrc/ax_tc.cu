@@ -28,6 +28,11 @@ namespace {
 
 constexpr int BM = 128, BK = 64;
 constexpr int kMaxChain = 32;  // K tiles accumulated in one TMEM accumulator at most
+// Budget (clock64 cycles, about 2 s at 2 GHz) of the drain on the error path: after a wait
+// ran out, the CTA still waits for every MMA and bulk copy it issued before it releases its
+// TMEM and exits, so no asynchronous operation targets a finished CTA.  In-flight work
+// completes in microseconds; the budget only bounds a broken pipeline.
+constexpr long long kDrainBudget = 4000000000LL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -210,7 +215,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   bool done = mbar_wait(accum, 0, p.budget);
   done = __all_sync(0xffffffffu, done);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!done && lane == 0) atomicExch(p.err, 3);
+  if (!done && lane == 0) {
+    atomicExch(p.err, 3);
+    s_fail = 1;
+  }
   if (done && !s_fail) {
     const int row = m0 + warp * 32 + lane;
     float* Yz = p.Y + (int64_t)blockIdx.z * p.n * p.ldy;
@@ -225,10 +233,15 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       }
     }
   }
+  __syncthreads();  // s_fail from the epilogue visible
   if (s_fail && threadIdx.x == 0) {
-    // error path: wait (bounded) for the loads this CTA issued but never consumed
+    // error path: drain with its own generous budget (a short wait budget that ran out
+    // must not let the CTA exit with work in flight): every MMA issued above (the accum
+    // commit follows them all), then the loads issued but never consumed
+    const long long drain = p.budget > kDrainBudget ? p.budget : kDrainBudget;
+    mbar_wait(accum, 0, drain);
     for (int it = s_consumed; it < s_issued; ++it)
-      if (!mbar_wait(&full[it % p.stages], (uint32_t)(it / p.stages) & 1u, p.budget)) break;
+      if (!mbar_wait(&full[it % p.stages], (uint32_t)(it / p.stages) & 1u, drain)) break;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -405,7 +418,10 @@ k_bgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
   bool done = mbar_wait(accum, 0, budget);
   done = __all_sync(0xffffffffu, done);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!done && lane == 0) atomicExch(err, 13);
+  if (!done && lane == 0) {
+    atomicExch(err, 13);
+    s_fail = 1;
+  }
   float d1 = 0.f;
   if (done && !s_fail) {
     const int row = it.m0 + warp * 32 + lane;
@@ -432,9 +448,13 @@ k_bgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     for (int o = 16; o > 0; o >>= 1) d1 += __shfl_xor_sync(0xffffffffu, d1, o);
     if (lane == 0) s_red[warp] = d1;
   }
+  __syncthreads();  // s_fail from the epilogue visible
   if (s_fail && threadIdx.x == 0) {
+    // error path: drain every issued MMA and unconsumed load with the generous budget
+    const long long drain = budget > kDrainBudget ? budget : kDrainBudget;
+    mbar_wait(accum, 0, drain);
     for (int i = s_consumed; i < s_issued; ++i)
-      if (!mbar_wait(&full[i % kBStages], (uint32_t)(i / kBStages) & 1u, budget)) break;
+      if (!mbar_wait(&full[i % kBStages], (uint32_t)(i / kBStages) & 1u, drain)) break;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();

@@ -706,6 +706,16 @@ snmf_status sync_user_b(BatchCtx* b, std::string* err) {
 
 int batch_nprob(const BatchCtx* b) { return b ? b->nprob : 0; }
 
+void batch_set_budget(BatchCtx* b, long long cycles) {
+  if (!b) return;
+  b->budget = cycles;
+  // the captured solve graphs hold the old budget in their kernel parameters
+  for (auto& e : b->exec) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
+}
+
 snmf_status batch_validate(const snmf_matrix* Am, const snmf_options& o, std::string* err) {
   const int np = Am->nprob;
   if (np < 1 || !Am->batch_desc || !Am->values) { *err = "dense batch: nprob >= 1, batch_desc and values required"; return SNMF_ERR_ARG; }

@@ -669,6 +669,24 @@ snmf_status alloc_buffers(snmf_ctx* h) {
   return SNMF_OK;
 }
 
+// Structure check of a device-resident CSR matrix (launch_csr_check) on the handle's
+// stream; *bad receives its flags (0 = valid).
+snmf_status check_device_csr(snmf_ctx* h, const int32_t* rowptr, const int32_t* colidx, int64_t n, int64_t nnz,
+                             int* bad) {
+  int* dflag = nullptr;
+  CK(cudaMalloc(&dflag, sizeof(int)));
+  cudaError_t e = cudaMemsetAsync(dflag, 0, sizeof(int), h->s);
+  if (e == cudaSuccess) {
+    launch_csr_check(rowptr, colidx, n, nnz, dflag, h->s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bad, dflag, sizeof(int), cudaMemcpyDeviceToHost, h->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+  cudaFree(dflag);
+  if (e != cudaSuccess) return fail(h, SNMF_ERR_CUDA, std::string("CSR check: ") + cudaGetErrorString(e));
+  return SNMF_OK;
+}
+
 bool valid_enum(int v, int lo, int hi) { return v >= lo && v <= hi; }
 
 snmf_status validate_options(const snmf_options& o) {
@@ -914,11 +932,12 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
       h->A.colidx = h->colidx_owned;
       h->A.vals = h->vals_owned;
     } else {
-      int32_t ends[2] = {0, 0};
-      CKC(cudaMemcpyAsync(&ends[0], Am->rowptr, sizeof(int32_t), cudaMemcpyDeviceToHost, h->s));
-      CKC(cudaMemcpyAsync(&ends[1], Am->rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, h->s));
-      CKC(cudaStreamSynchronize(h->s));
-      if (ends[0] != 0 || ends[1] != nnz) { h->err = "CSR rowptr inconsistent with nnz"; return bail(SNMF_ERR_ARG); }
+      // device-resident CSR: the same structure checks as for host arrays, by a device kernel
+      int bad = 0;
+      const snmf_status cs = check_device_csr(h, Am->rowptr, Am->colidx, n, nnz, &bad);
+      if (cs != SNMF_OK) return bail(cs);
+      if (bad & 1) { h->err = "CSR rowptr inconsistent with nnz or not monotone"; return bail(SNMF_ERR_ARG); }
+      if (bad & 2) { h->err = "CSR column index out of range"; return bail(SNMF_ERR_ARG); }
       h->A.rowptr = Am->rowptr;
       h->A.colidx = Am->colidx;
       h->A.vals = Am->values;
@@ -989,10 +1008,19 @@ snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma
   const int64_t n = h->n, nnz = L->nnz;
   const size_t vb = L->dtype == SNMF_F64 ? 8 : 4;
   const cudaMemcpyKind kd = L->location == SNMF_ON_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (!L->rowptr || !L->colidx || !L->values || nnz < 0) return fail(h, SNMF_ERR_ARG, "L arrays missing");
   if (L->location == SNMF_ON_HOST) {
     if (L->rowptr[0] != 0 || L->rowptr[n] != nnz) return fail(h, SNMF_ERR_ARG, "L rowptr inconsistent");
+    for (int64_t i = 0; i < n; ++i)
+      if (L->rowptr[i + 1] < L->rowptr[i]) return fail(h, SNMF_ERR_ARG, "L rowptr not monotone");
     for (int64_t e = 0; e < nnz; ++e)
       if (L->colidx[e] < 0 || L->colidx[e] >= n) return fail(h, SNMF_ERR_ARG, "L column out of range");
+  } else {
+    int bad = 0;
+    const snmf_status cs = check_device_csr(h, L->rowptr, L->colidx, n, nnz, &bad);
+    if (cs != SNMF_OK) return cs;
+    if (bad & 1) return fail(h, SNMF_ERR_ARG, "L rowptr inconsistent with nnz or not monotone");
+    if (bad & 2) return fail(h, SNMF_ERR_ARG, "L column out of range");
   }
   cudaFree(h->L_rowptr); cudaFree(h->L_colidx); cudaFree(h->L_vals);
   h->L_rowptr = nullptr; h->L_colidx = nullptr; h->L_vals = nullptr;
@@ -1353,6 +1381,17 @@ snmf_status snmf_tuned_tiles(snmf_handle h, int32_t* bn, int32_t* row_bm) {
   if (!h->tuned) return fail(h, SNMF_ERR_STATE, "the handle was not autotuned");
   if (bn) *bn = h->tune.cfg.bn;
   if (row_bm) *row_bm = h->tune.cfg.row_bm;
+  return SNMF_OK;
+}
+
+snmf_status snmf_set_timeout(snmf_handle h, int64_t cycles) {
+  if (!h) return SNMF_ERR_STATE;
+  if (cycles < 0) return fail(h, SNMF_ERR_ARG, "cycles must be >= 0");
+  const long long c = cycles > 0 ? (long long)cycles : 2000000000LL;
+  h->opt.timeout_cycles = cycles;
+  h->budget = c;
+  h->exec_form = -1;  // the captured solve graphs hold the old budget: capture again
+  if (h->bt) batch_set_budget(h->bt, c);
   return SNMF_OK;
 }
 

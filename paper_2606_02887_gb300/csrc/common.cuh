@@ -163,6 +163,12 @@ int launch_ax(const AxArgs& a, int tdtype, int64_t n, int cols, int64_t ld,
               const void* X, void* Y, void* ws, size_t ws_elems, const int* run_flag,
               cudaStream_t s, const ProdTune* tune = nullptr);
 
+// Structure check of a device CSR matrix: *bad |= 1 for a bad rowptr (rowptr[0] != 0,
+// rowptr[n] != nnz or decreasing), |= 2 for a column index outside [0, n).  *bad must be
+// zeroed by the caller.
+void launch_csr_check(const int32_t* rowptr, const int32_t* colidx, int64_t n, int64_t nnz, int* bad,
+                      cudaStream_t s);
+
 // Epilogue of a product over the restarts of d: Y = sum_s ws[s] (splits > 1),
 // per-restart partials <P1, A X> -> part[slot][j][q0], <P2, A X> -> [q0+1], then
 // Y += c * X2 (when X2 != NULL).  Returns the number of partial slots written.

@@ -12,11 +12,24 @@
 
 #include "../../include/snmf.h"
 #include "common.cuh"
+#include "mlp_dev.cuh"
 
 namespace snmf {
 namespace {
 
 constexpr int NP = kMlpParams;
+
+// One warp per feature vector: the solver's inference routine on BF16 weights.
+__global__ void __launch_bounds__(256)
+k_mlp_eval(const __nv_bfloat16* __restrict__ w, const float* __restrict__ feat, int count, float* __restrict__ mult) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= count) return;
+  float phi[kMlpIn];
+#pragma unroll
+  for (int u = 0; u < kMlpIn; ++u) phi[u] = feat[(int64_t)i * kMlpIn + u];
+  const float m = mlp_multiplier(w, phi);
+  if ((threadIdx.x & 31) == 0) mult[i] = m;
+}
 
 // per-CTA partial gradient (NP floats) and loss at pgrad[blockIdx.x][NP + 1]
 __global__ void __launch_bounds__(256)
@@ -156,4 +169,30 @@ extern "C" snmf_status snmf_mlp_train(const float* feats, const float* targets, 
   cleanup();
   return SNMF_OK;
 #undef MCK
+}
+
+extern "C" snmf_status snmf_mlp_eval(const float* weights, const float* feats, int count, float* mult) {
+  if (!weights || !feats || !mult || count < 1) return SNMF_ERR_ARG;
+  std::vector<__nv_bfloat16> wb(NP);
+  for (int i = 0; i < NP; ++i) wb[i] = __float2bfloat16_rn(weights[i]);  // as snmf_create rounds them
+  __nv_bfloat16* dw = nullptr;
+  float *df = nullptr, *dm = nullptr;
+  auto cleanup = [&] { cudaFree(dw); cudaFree(df); cudaFree(dm); };
+  snmf_status st = SNMF_OK;
+#define ECK(call)                                                                                   \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) { st = e_ == cudaErrorMemoryAllocation ? SNMF_ERR_OOM : SNMF_ERR_CUDA; cleanup(); return st; } \
+  } while (0)
+  ECK(cudaMalloc(&dw, NP * sizeof(__nv_bfloat16)));
+  ECK(cudaMalloc(&df, (size_t)count * kMlpIn * sizeof(float)));
+  ECK(cudaMalloc(&dm, (size_t)count * sizeof(float)));
+  ECK(cudaMemcpy(dw, wb.data(), NP * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+  ECK(cudaMemcpy(df, feats, (size_t)count * kMlpIn * sizeof(float), cudaMemcpyHostToDevice));
+  k_mlp_eval<<<(count + 7) / 8, 256>>>(dw, df, count, dm);
+  ECK(cudaGetLastError());
+  ECK(cudaMemcpy(mult, dm, (size_t)count * sizeof(float), cudaMemcpyDeviceToHost));
+#undef ECK
+  cleanup();
+  return st;
 }

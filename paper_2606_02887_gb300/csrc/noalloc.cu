@@ -4,6 +4,7 @@
 // slices and the FP64 partial sums live in one file-scope __device__ array of fixed
 // size instead of memory obtained from cudaMalloc.  Nothing here allocates: no
 // cudaMalloc / cudaFree, no host heap.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -14,15 +15,41 @@
 namespace {
 
 constexpr size_t kScratchBytes = SNMF_NOALLOC_SCRATCH_BYTES;
-constexpr size_t kPartialBytes = 1u << 20;  // FP64 partial sums + the reduced scalar
+constexpr size_t kPartialBytes = SNMF_NOALLOC_PARTIAL_BYTES;  // FP64 partial sums + the reduced scalar
 constexpr int kMaxDevices = 64;
+constexpr int64_t kRecordBytes = (int64_t)snmf::kNQ * sizeof(double);  // one partial record per row slice
+static_assert(kRecordBytes == 256, "SNMF_NOALLOC_MAX_ROWS assumes 256-byte partial records");
+static_assert(SNMF_NOALLOC_MAX_ROWS == (int64_t)snmf::kRowTile * (int64_t)((kPartialBytes - 256) / kRecordBytes),
+              "SNMF_NOALLOC_MAX_ROWS must follow from the partial-sum region");
 
 // Shared by every call on a device; keeps the last call's contents.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Device address of g_scratch per device (the host-side symbol is only a stand-in).
-void* g_scratch_addr[kMaxDevices] = {};
+// Device address of g_scratch per device, valid for the context it was resolved in (the
+// host-side symbol is only a stand-in).  A new context (after a device reset, or a caller's
+// own driver-API context) resolves it again.
+struct ScratchAddr {
+  void* ptr = nullptr;
+  CUcontext ctx = nullptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
 std::mutex g_scratch_mu;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+
+// cuCtxGetCurrent through the runtime's driver entry point (no link against libcuda).
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  });
+  return fn;
+}
 
 // Sum part[slot][0][q] over slots in a fixed order (one block).
 __global__ void k_sum_slots(const double* __restrict__ part, int nslots, int q, double* __restrict__ out) {
@@ -41,24 +68,28 @@ extern "C" snmf_status snmf_apply_dense_noalloc(const void* A, int dtype, int64_
   if (!A || !X || !Y || n < 1 || cols < 1 || lda < n || (dtype != SNMF_F64 && dtype != SNMF_F32))
     return SNMF_ERR_ARG;
   const size_t esz = dtype == SNMF_F64 ? 8 : 4;
-  const int64_t nslots = (n + snmf::kRowTile - 1) / snmf::kRowTile;
   const size_t slice = (size_t)n * (size_t)cols * esz;
-  // two split-K slices must fit beside the partial sums
-  if (2 * slice > kScratchBytes - kPartialBytes ||
-      (size_t)nslots * snmf::kNQ * sizeof(double) + 256 > kPartialBytes)
-    return SNMF_ERR_ARG;
+  // two split-K slices must fit beside the partial sums, one partial record per 64 rows
+  if (n > SNMF_NOALLOC_MAX_ROWS || 2 * slice > SNMF_NOALLOC_MAX_SLICE_PAIR_BYTES) return SNMF_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SNMF_ERR_CUDA;
+  // the current context (NULL before the first runtime call of the thread initialises one)
+  CUcontext ctx = nullptr;
+  const CtxGetCurrentFn get_ctx = ctx_get_current();
+  if (!get_ctx || get_ctx(&ctx) != CUDA_SUCCESS) ctx = nullptr;
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-      // first call on this device (current): resolve the array's device address
+    ScratchAddr& slot = g_scratch_addr[dev];
+    if (!slot.ptr || !ctx || slot.ctx != ctx) {
+      // first call in this context (or the context cannot be identified): resolve the
+      // array's device address here
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return SNMF_ERR_CUDA;
-      g_scratch_addr[dev] = p;
+      slot.ptr = p;
+      slot.ctx = ctx;
     }
-    base = g_scratch_addr[dev];
+    base = slot.ptr;
   }
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* scratch = static_cast<unsigned char*>(base);

@@ -9,6 +9,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "mlp_dev.cuh"
 #include "rowops.cuh"
 
 namespace snmf {
@@ -326,24 +327,6 @@ __device__ void pen_ls_body(Ctl& c, const double* prow, int nrow, const double* 
   if (!isfinite(c.fZ) || !isfinite(q) || !isfinite(gd)) { c.nan_seen = 1; c.active = 0; }
   c.beta = beta;
   c.phibeta = P.phi * beta;
-}
-
-// MLP step controller: o = W2 relu(W1 phi + b1) + b2 with BF16 weights, FP32 accumulation,
-// by one warp; multiplier 2^(2 tanh o).
-__device__ float mlp_multiplier(const __nv_bfloat16* w, const float* phi) {
-  const int lane = threadIdx.x & 31;
-  float part = 0.f;
-#pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int hdn = lane + 32 * u;
-    float z = __bfloat162float(w[kMlpIn * kMlpHidden + hdn]);
-#pragma unroll
-    for (int i = 0; i < kMlpIn; ++i) z = fmaf(__bfloat162float(w[hdn * kMlpIn + i]), phi[i], z);
-    z = fmaxf(z, 0.f);
-    part = fmaf(__bfloat162float(w[kMlpIn * kMlpHidden + kMlpHidden + hdn]), z, part);
-  }
-  const float o = warp_sum(part) + __bfloat162float(w[kMlpParams - 1]);
-  return exp2f(2.f * tanhf(o));
 }
 
 // After the relaxed update (q: 0 pg2, 2 ss, 3 sy, 4 yy, 5 f(X')-f(Z), 6 zero entries).

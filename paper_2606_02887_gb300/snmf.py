@@ -29,10 +29,12 @@ EXPORTED = (
     "snmf_solve", "snmf_solve_host", "snmf_restart_stats", "snmf_get_factors",
     "snmf_apply", "snmf_profile_ax", "snmf_apply_dense_noalloc", "snmf_controller_data",
     "snmf_mlp_train", "snmf_tuned_config", "snmf_tuned_tiles", "snmf_profile_steps", "snmf_destroy", "snmf_last_error",
+    "snmf_mlp_eval", "snmf_set_timeout",
 )
 NOALLOC_SCRATCH_BYTES = 64 << 20
-NOALLOC_MAX_SLICE_PAIR_BYTES = NOALLOC_SCRATCH_BYTES - (1 << 20)
-NOALLOC_MAX_ROWS = 1048320
+NOALLOC_PARTIAL_BYTES = 4 << 20
+NOALLOC_MAX_SLICE_PAIR_BYTES = NOALLOC_SCRATCH_BYTES - NOALLOC_PARTIAL_BYTES
+NOALLOC_MAX_ROWS = 64 * ((NOALLOC_PARTIAL_BYTES - 256) // 256)
 
 
 class snmf_matrix(C.Structure):
@@ -97,6 +99,8 @@ def load_library(path: str = LIB_PATH):
                                       C.POINTER(C.c_double), C.POINTER(C.c_int32)]
     lib.snmf_profile_steps.argtypes = [H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.snmf_tuned_tiles.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.snmf_mlp_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+    lib.snmf_set_timeout.argtypes = [H, C.c_int64]
     lib.snmf_destroy.argtypes = [H]
     lib.snmf_last_error.argtypes = [H]
     lib.snmf_last_error.restype = C.c_char_p
@@ -258,10 +262,23 @@ def snmf_profile_ax(h, iters: int = 20):
 
 def snmf_apply_dense_noalloc(A, X, Y, stream=None):
     """Y = A X and <X, A X> without any device allocation (see include/snmf.h).
-    A: n x n device tensor (float32/float64), X, Y: n x cols device tensors."""
+    A: n x n device tensor (float32/float64, unit column stride), X, Y: contiguous n x cols
+    device tensors of A's dtype on A's device.  The C side sees raw pointers only, so the
+    shapes, dtypes, strides and devices are checked here before the call."""
     lib = load_library()
-    dt = SNMF_F64 if str(A.dtype).endswith("float64") else SNMF_F32
+    for name, t in (("A", A), ("X", X), ("Y", Y)):
+        if not _is_cuda(t) or t.dim() != 2:
+            raise SnmfError(SNMF_ERR_ARG, f"{name} must be a 2-D CUDA tensor")
     n, cols = X.shape
+    if tuple(A.shape) != (n, n) or A.stride(1) != 1 or A.stride(0) < n:
+        raise SnmfError(SNMF_ERR_ARG, f"A must be {n} x {n} with unit column stride (got {tuple(A.shape)})")
+    if tuple(Y.shape) != (n, cols) or not X.is_contiguous() or not Y.is_contiguous():
+        raise SnmfError(SNMF_ERR_ARG, "X and Y must be contiguous n x cols tensors")
+    if not (A.dtype == X.dtype == Y.dtype) or not str(A.dtype).endswith(("float32", "float64")):
+        raise SnmfError(SNMF_ERR_ARG, "A, X and Y must share one dtype, float32 or float64")
+    if not (A.device == X.device == Y.device):
+        raise SnmfError(SNMF_ERR_ARG, "A, X and Y must be on one device")
+    dt = SNMF_F64 if str(A.dtype).endswith("float64") else SNMF_F32
     xax = C.c_double()
     s = None
     if stream is not None:
@@ -296,6 +313,23 @@ def snmf_mlp_train(feats, targets, weights, steps: int = 1000, lr: float = 1e-2)
     _check(lib, None, lib.snmf_mlp_train(f.ctypes.data, t.ctypes.data, len(t), w.ctypes.data, int(steps),
                                          float(lr), C.byref(loss), g0.ctypes.data))
     return w, loss.value, g0
+
+
+def snmf_mlp_eval(weights, feats):
+    """Multipliers 2^(2 tanh o) of the controller network on the device (BF16 weights, as the
+    solver uses them) for feature vectors feats[i][5]."""
+    lib = load_library()
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, SNMF_MLP_IN)
+    out = np.zeros(len(f), dtype=np.float32)
+    _check(lib, None, lib.snmf_mlp_eval(w.ctypes.data, f.ctypes.data, len(f), out.ctypes.data))
+    return out
+
+
+def snmf_set_timeout(h, cycles: int):
+    """Bound (clock64 cycles) of the handle's device-side waits; 0 restores the default."""
+    lib = load_library()
+    return _check(lib, h, lib.snmf_set_timeout(h, int(cycles)))
 
 
 def snmf_profile_steps(h, iters: int = 20):

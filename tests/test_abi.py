@@ -87,3 +87,35 @@ def test_no_cpu_fallback_without_gpu(lib):
     A = np.eye(8)
     st, h = _create(lib, S.dense_matrix(A)[0], 2, S.snmf_default_options())
     assert st == S.SNMF_ERR_CUDA and not h.value
+
+
+def test_noalloc_limits_follow_the_header(lib, repo_root):
+    """The allocation-free product's published limits: the binding's constants equal the
+    header's macros, n = SNMF_NOALLOC_MAX_ROWS + 64 and an oversized slice pair are rejected
+    with SNMF_ERR_ARG before any CUDA call, and n = SNMF_NOALLOC_MAX_ROWS passes the size
+    checks (without a GPU the call then fails with SNMF_ERR_CUDA; it is not run where a GPU
+    is present, because the pointers here are placeholders)."""
+    txt = open(os.path.join(repo_root, "include", "snmf.h")).read()
+    macros = dict(re.findall(r"#define (SNMF_NOALLOC_\w+) (.+)", txt))
+    env = {}
+    for name, expr in macros.items():
+        e = expr.replace("ull", "").replace("ll", "").replace("(int64_t)", "")
+        for k, v in env.items():
+            e = e.replace(k, str(v))
+        env[name] = int(eval(e, {}, {}))
+    assert env["SNMF_NOALLOC_SCRATCH_BYTES"] == S.NOALLOC_SCRATCH_BYTES
+    assert env["SNMF_NOALLOC_MAX_SLICE_PAIR_BYTES"] == S.NOALLOC_MAX_SLICE_PAIR_BYTES
+    assert env["SNMF_NOALLOC_MAX_ROWS"] == S.NOALLOC_MAX_ROWS == 1048512
+    fake = C.c_void_p(0x1000)
+    out = C.c_double()
+    f = lib.snmf_apply_dense_noalloc
+    n_max = S.NOALLOC_MAX_ROWS
+    assert f(fake, S.SNMF_F32, n_max + 64, n_max + 64, fake, fake, 1, C.byref(out), None) == S.SNMF_ERR_ARG
+    cols = S.NOALLOC_MAX_SLICE_PAIR_BYTES // (2 * 4096 * 4) + 1
+    assert f(fake, S.SNMF_F32, 4096, 4096, fake, fake, cols, C.byref(out), None) == S.SNMF_ERR_ARG
+    assert f(fake, 7, 64, 64, fake, fake, 1, C.byref(out), None) == S.SNMF_ERR_ARG
+    assert f(fake, S.SNMF_F32, 64, 32, fake, fake, 1, C.byref(out), None) == S.SNMF_ERR_ARG
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: placeholder pointers must not reach a launch")
+    assert f(fake, S.SNMF_F32, n_max, n_max, fake, fake, 1, C.byref(out), None) == S.SNMF_ERR_CUDA

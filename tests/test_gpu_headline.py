@@ -1,0 +1,256 @@
+"""Oracle parity of the paths the bench runs and of options no other test reaches:
+the headline configuration (BF16 A, lean learned step with the shipped weights, 8
+restarts in one solve, the bench's tuned tile shapes), the controller network's device
+inference, the shared-memory tile body of the single-problem row kernels, the tuned
+tensor-core product tiles, BB2 and the direct form under the eta rule."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2606_02887_gb300.snmf as S
+from workloads import planted_dense, uniform_init
+
+from gpu_helpers import gpu_solve, rel
+from test_gpu_bf16 import bf16_round
+from test_gpu_parity import iter_tol, rounding_envelope
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _device_key():
+    import torch
+    p = torch.cuda.get_device_properties(0)
+    return f"{p.name}/{p.multi_processor_count}"
+
+
+def _forced_tune_cache(path, key, **cfg):
+    """A tuning cache file holding one configuration for this device and shape key."""
+    entry = dict(splits=0, stages=0, per_sm=0, bn=0, row_bm=0, ms=1.0)
+    entry.update(cfg)
+    json.dump({"format": "snmf-tune-1", "devices": {_device_key(): {key: entry}}}, open(path, "w"))
+    return str(path)
+
+
+# ---------------------------------------------------------------------------
+# controller inference
+# ---------------------------------------------------------------------------
+
+def test_mlp_inference_matches_oracle_on_shipped_weights():
+    """The solver's device routine (BF16 weights, FP32 accumulation) against the FP64 oracle
+    network on the same BF16-rounded weights, on features spanning the ranges the solver
+    produces (clamped log steps, ratios in [-10, 10], fractions in [0, 1]) and on features
+    recorded by a record-mode solve."""
+    import torch
+    from paper_2606_02887_gb300.train_controller import load_weights
+
+    w = np.asarray(load_weights(), dtype=np.float32)
+    wb = bf16_round(w).astype(np.float64)
+    g = np.random.default_rng(17)
+    feats = np.stack([g.uniform(-6, 6, 4000), g.uniform(-6, 6, 4000), g.uniform(0, 10, 4000),
+                      g.uniform(-10, 10, 4000), g.uniform(0, 1, 4000)], 1).astype(np.float32)
+    # recorded features of a small record-mode solve
+    A, _ = planted_dense(300, 8, 0.01, seed=401)
+    W0 = uniform_init(300, 8, math.sqrt(A.mean() / 8), seed=402)
+    dev = torch.device("cuda:0")
+    h = S.snmf_create(S.dense_matrix(torch.tensor(A, dtype=torch.float32, device=dev)), 8,
+                      S.snmf_default_options(step_controller=2, max_iter=20, tol=0.0))
+    try:
+        S.snmf_solve(h, torch.tensor(W0, dtype=torch.float32, device=dev),
+                     torch.tensor(W0, dtype=torch.float32, device=dev))
+        rec, _ = S.snmf_controller_data(h)
+    finally:
+        S.snmf_destroy(h)
+    assert len(rec) > 50
+    allf = np.concatenate([feats, rec]).astype(np.float32)
+    got = S.snmf_mlp_eval(w, allf).astype(np.float64)
+    ref = O.mlp.multiplier(wb, allf.astype(np.float64))
+    err = np.abs(got - ref) / ref
+    print(f"controller inference vs oracle: max rel {err.max():.2e} over {len(allf)} feature vectors")
+    assert err.max() <= 2e-5
+    assert ref.min() >= 0.25 * (1 - 1e-12) and ref.max() <= 4.0 * (1 + 1e-12)
+
+
+# ---------------------------------------------------------------------------
+# the headline configuration at n = 2048
+# ---------------------------------------------------------------------------
+
+def test_headline_configuration_matches_oracle_per_restart(tmp_path):
+    """BF16 A, r = 64, 8 restarts in one solve, lean learned step (step_controller 3) with
+    the shipped weights, and the tile shapes the bench's autotuner chooses at n = 8192
+    (128-column tensor-core tiles, 4 K slices, 2 CTAs per SM with a 2-stage ring, 64-row
+    row tiles), forced through the tuning cache.  Every restart reaches relative projected
+    gradient 1e-4, and its final residual against the true A is within 1e-3 of the FP64
+    oracle's solve of the same restart (tests/golden/oracle_dense2048_r64_b8.json, written
+    by make_headline_oracle.py from the oracle alone)."""
+    import torch
+    from paper_2606_02887_gb300.train_controller import load_weights
+    from workloads.configs import dense_planted_8192
+
+    gold = json.load(open(os.path.join(GOLDEN, "oracle_dense2048_r64_b8.json")))
+    n, r, b = gold["n"], gold["r"], gold["batch"]
+    A, starts = dense_planted_8192(r, b, n=n)
+    W0 = np.concatenate(starts, axis=1)
+    dev = torch.device("cuda:0")
+    key = f"dense/bf16/n{n}/r{r}/N{r * b}"
+    cache = _forced_tune_cache(tmp_path / "tune.json", key, splits=4, stages=2, per_sm=2, bn=128, row_bm=64)
+    o = S.snmf_default_options(precision=S.SNMF_BF16, batch=b, max_iter=500, tol=1e-4, nonmonotone_M=10,
+                               step_controller=3, autotune=1, tune_cache=cache)
+    h = S.snmf_create(S.dense_matrix(torch.tensor(A, dtype=torch.float32, device=dev)), r, o,
+                      mlp_weights=load_weights())
+    try:
+        cfg = S.snmf_tuned_config(h)
+        assert cfg["from_cache"] and (cfg["splits"], cfg["bn"], cfg["per_sm"], cfg["stages"]) == (4, 128, 2, 2)
+        W = torch.tensor(W0, dtype=torch.float32, device=dev)
+        H = W.clone()
+        st, stats = S.snmf_solve(h, W, H)
+        per = S.snmf_restart_stats(h, b)
+    finally:
+        S.snmf_destroy(h)
+    assert st == S.SNMF_OK, stats
+    Wn, Hn = W.cpu().numpy().astype(np.float64), H.cpu().numpy().astype(np.float64)
+    nA = np.linalg.norm(A)
+    rows = []
+    for j in range(b):
+        sl = slice(j * r, (j + 1) * r)
+        res = float(np.linalg.norm(A - Wn[:, sl] @ Hn[:, sl].T) / nA)
+        ref = gold["restarts"][j]
+        rows.append((j, res, ref["residual"], float(per["pg_rel"][j]), int(per["iters"][j]), ref["iters"]))
+    print("restart: residual (true A) / oracle, pg_rel, iters / oracle iters")
+    for row in rows:
+        print("  %d: %.6f / %.6f  %.2e  %d / %d" % row)
+    for j, res, ref_res, pg, _, _ in rows:
+        assert gold["restarts"][j]["converged"]
+        assert pg <= 1e-4, (j, pg)
+        assert abs(res - ref_res) <= 1e-3, (j, res, ref_res)
+
+
+# ---------------------------------------------------------------------------
+# shared-memory tile body of the single-problem row kernels (r <= 32, >= 2 x 152 tiles)
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def tile_problem():
+    """n = 4096, r = 16, 10 restarts: 64 (FP64, 64-row tiles) or 32 (FP32, 128-row tiles) row
+    tiles per restart, 640 / 320 in all, above the 2 x 152 that selects the tile body."""
+    n, r, b = 4096, 16, 10
+    A, _ = planted_dense(n, r, 0.02, seed=4096)
+    Ws = [uniform_init(n, r, math.sqrt(A.mean() / r), seed=4100 + j) for j in range(b)]
+    return A, Ws, n, r, b
+
+
+@pytest.mark.parametrize("prec", [S.SNMF_F64, S.SNMF_F32])
+def test_tile_body_single_problem_follows_oracle(tile_problem, prec):
+    """Iterate by iterate after 1, 2 and 4 outer iterations, restarts 0, 4 and 9, at the bar
+    of the other iterate tests: 1e-10 or 10x the oracle's rounding envelope in FP64, the
+    oracle's FP32 rounding envelope (model at u = 2^-24) in FP32."""
+    A, Ws, n, r, b = tile_problem
+    W0 = np.concatenate(Ws, axis=1)
+    opts = O.Options(max_iter=4, tol=0.0, memory=10, objective="closed")
+    u = 2.0 ** -53 if prec == S.SNMF_F64 else 2.0 ** -24
+    env = rounding_envelope(lambda: O.snmpbb_penalty(A, Ws[0], Ws[0], opts, keep_iterates=True)[2]["trace"],
+                            "W", 4, seeds=2, u=u)
+    traces = {j: O.snmpbb_penalty(A, Ws[j], Ws[j], opts, keep_iterates=True)[2]["trace"] for j in (0, 4, 9)}
+    for k in (1, 2, 4):
+        W, H, _, stats, _ = gpu_solve(A, W0, r, W0, precision=prec, max_iter=k, tol=0.0, batch=b,
+                                      nonmonotone_M=10)
+        assert stats["iters"] == k
+        for j, tr in traces.items():
+            sl = slice(j * r, (j + 1) * r)
+            e = max(rel(W[:, sl], tr[k - 1]["W"]), rel(H[:, sl], tr[k - 1]["Ht"]))
+            bar = iter_tol(env, k) if prec == S.SNMF_F64 else env[k - 1]
+            assert e <= bar, (prec, k, j, e, bar)
+
+
+# ---------------------------------------------------------------------------
+# tuned tensor-core product tiles
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,cols,cfg", [
+    (2048, 512, dict(splits=4, stages=2, per_sm=2, bn=128)),
+    (2048, 512, dict(splits=8, stages=4, per_sm=1, bn=64)),
+    (4096, 256, dict(splits=6, stages=2, per_sm=1, bn=256)),
+    (1000, 192, dict(splits=2, stages=2, per_sm=2, bn=64)),
+])
+def test_tuned_product_tiles_match_emulated_operands(tmp_path, n, cols, cfg):
+    """Products with tile shapes the autotuner can choose (64/128/256-column tiles, 1 or 2
+    CTAs per SM, 2 to 8 K slices), forced through the tuning cache, against the exact
+    emulation of the stored BF16 operands (same bar as the built-in configuration)."""
+    import torch
+    dev = torch.device("cuda:0")
+    g = np.random.default_rng(n + cols + cfg["splits"])
+    B = g.random((n, n), dtype=np.float32)
+    A = (B + B.T).astype(np.float32)
+    X = g.random((n, cols), dtype=np.float32)
+    At = bf16_round(A).astype(np.float64)
+    Xh = bf16_round(X)
+    Xl = bf16_round(X - Xh)
+    ref = At @ (Xh.astype(np.float64) + Xl.astype(np.float64))
+    r, b = cols // 8, 8
+    cache = _forced_tune_cache(tmp_path / "tune.json", f"dense/bf16/n{n}/r{r}/N{cols}", **cfg)
+    h = S.snmf_create(S.dense_matrix(torch.tensor(A, device=dev)), r,
+                      S.snmf_default_options(precision=S.SNMF_BF16, batch=b, autotune=1, tune_cache=cache))
+    try:
+        got = S.snmf_tuned_config(h)
+        assert got["from_cache"] and all(got[k] == v for k, v in cfg.items()), got
+        Xt = torch.tensor(X, device=dev)
+        Yt = torch.empty_like(Xt)
+        xax = S.snmf_apply(h, Xt, Yt, cols)
+    finally:
+        S.snmf_destroy(h)
+    Y = Yt.cpu().numpy().astype(np.float64)
+    assert rel(Y, ref) <= 3e-5, rel(Y, ref)
+    assert np.max(np.abs(Y - ref) / np.maximum(np.abs(ref), 1e-30)) <= 3e-5
+    assert abs(xax - float(np.sum(X * ref))) <= 1e-5 * abs(xax)
+
+
+# ---------------------------------------------------------------------------
+# options: BB2, the direct form under the eta rule
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def cfg1():
+    A, _ = planted_dense(500, 10, 0.01, seed=1000)
+    W0 = uniform_init(500, 10, math.sqrt(A.mean() / 10), seed=1001)
+    return A, W0
+
+
+def test_penalty_fp64_bb2_matches_oracle(cfg1):
+    A, W0 = cfg1
+    opts = O.Options(formulation="penalty", memory=10, bb="bb2", max_iter=30, tol=0.0, objective="closed")
+    _, _, info = O.snmpbb_penalty(A, W0, W0, opts, keep_iterates=True)
+    env = rounding_envelope(lambda: O.snmpbb_penalty(A, W0, W0, opts, keep_iterates=True)[2]["trace"], "W", 30)
+    for k in (1, 2, 5, 10, 20, 30):
+        W, H, _, _, _ = gpu_solve(A, W0, 10, W0, max_iter=k, tol=0.0, nonmonotone_M=10, bb_variant=S.SNMF_BB2)
+        rec = info["trace"][k - 1]
+        e = max(rel(W, rec["W"]), rel(H, rec["Ht"]))
+        assert e <= iter_tol(env, k), (k, e, env[k - 1])
+
+
+def test_direct_fp64_eta_rule_matches_oracle(cfg1):
+    A, W0 = cfg1
+    opts = O.Options(formulation="direct", memory=0, eta=0.85, max_iter=30, tol=0.0, objective="closed")
+    _, info = O.snmpbb_direct(A, W0, opts, keep_iterates=True)
+    env = rounding_envelope(lambda: O.snmpbb_direct(A, W0, opts, keep_iterates=True)[1]["trace"], "X", 30)
+    for k in (1, 2, 3, 5, 8, 10, 20, 30):
+        W, _, _, _, _ = gpu_solve(A, W0, 10, formulation=S.SNMF_DIRECT, max_iter=k, tol=0.0, nonmonotone_M=0,
+                                  eta=0.85)
+        e = rel(W, info["trace"][k - 1]["X"])
+        assert e <= iter_tol(env, k), (k, e, env[k - 1])
+
+
+def test_direct_fp64_bb2_matches_oracle(cfg1):
+    A, W0 = cfg1
+    opts = O.Options(formulation="direct", memory=10, bb="bb2", max_iter=20, tol=0.0, objective="closed")
+    _, info = O.snmpbb_direct(A, W0, opts, keep_iterates=True)
+    env = rounding_envelope(lambda: O.snmpbb_direct(A, W0, opts, keep_iterates=True)[1]["trace"], "X", 20)
+    for k in (1, 3, 10, 20):
+        W, _, _, _, _ = gpu_solve(A, W0, 10, formulation=S.SNMF_DIRECT, max_iter=k, tol=0.0, nonmonotone_M=10,
+                                  bb_variant=S.SNMF_BB2)
+        e = rel(W, info["trace"][k - 1]["X"])
+        assert e <= iter_tol(env, k), (k, e, env[k - 1])

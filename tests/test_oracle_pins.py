@@ -191,6 +191,50 @@ def test_bb_step_within_block_curvature():
         assert 1.0 / ev[-1] * (1 - 1e-10) <= s["alpha"] <= 1.0 / ev[0] * (1 + 1e-10)
 
 
+def test_bb2_step_within_block_curvature_and_below_bb1():
+    """BB2 = <S,Y>/<Y,Y> (the least-squares step of Sec. 2.4).  In a block Y = S M with
+    M = H H^T + lambda I (Sec. 3.3), so <S,Y>/<Y,Y> is a Rayleigh quotient of M^-1 taken
+    at S M: it lies in [1/lambda_max(M), 1/lambda_min(M)], and by Cauchy-Schwarz it is
+    at most BB1 = <S,S>/<S,Y> of the same S, Y.  S and Y are rebuilt here from the
+    recorded iterates, independently of the oracle's step routine."""
+    A, W = _small_problem(40, 4, seed=33)
+    lam = 0.5
+    opts = O.Options(formulation="penalty", lambda_sym=lam, max_iter=4, tol=0.0, bb="bb2")
+    Ht = W.copy()
+    M = Ht.T @ Ht + lam * np.eye(4)
+    ev = np.linalg.eigvalsh(M)
+    grad = lambda X: O.penalty_grad_W(A, X, Ht, lam)
+    _, _, info = O.nmpbb(lambda X: O.penalty_objective(A, X, Ht, lam), grad, W,
+                         lambda X: O.spectral_norm(Ht.T @ Ht), 8, opts, keep_iterates=True)
+    xs = [W] + [s["X"] for s in info["trace"]]
+    strictly_below = 0
+    for k, s in enumerate(info["trace"][1:], start=1):
+        S = xs[k] - xs[k - 1]
+        Y = grad(xs[k]) - grad(xs[k - 1])
+        assert np.allclose(Y, S @ M, rtol=1e-10, atol=1e-12)   # Sec. 3.3: the block is quadratic
+        bb1 = np.sum(S * S) / np.sum(S * Y)
+        assert 1.0 / ev[-1] * (1 - 1e-10) <= s["alpha"] <= 1.0 / ev[0] * (1 + 1e-10)
+        assert s["alpha"] <= bb1 * (1 + 1e-12)
+        strictly_below += s["alpha"] < bb1 * (1 - 1e-6)
+    assert strictly_below >= 1  # generic S is no eigen-direction of M: BB2 < BB1 there
+
+
+def test_bb_steps_equal_inverse_curvature_for_isotropic_block():
+    """With H H^T + lambda I = c I (orthogonal, equal-norm columns of Ht) every BB step of
+    a block is exactly 1/c, for BB1 and BB2 alike: S M = c S."""
+    A, W = _small_problem(30, 3, seed=35)
+    lam, c = 0.25, 2.0
+    Ht = np.zeros((30, 3))
+    Ht[[0, 1, 2], [0, 1, 2]] = math.sqrt(c - lam)
+    for bb in ("bb1", "bb2"):
+        opts = O.Options(formulation="penalty", lambda_sym=lam, max_iter=4, tol=0.0, bb=bb)
+        _, _, info = O.nmpbb(lambda X: O.penalty_objective(A, X, Ht, lam),
+                             lambda X: O.penalty_grad_W(A, X, Ht, lam), W,
+                             lambda X: O.spectral_norm(Ht.T @ Ht), 6, opts)
+        for s in info["trace"][1:]:
+            assert abs(s["alpha"] - 1.0 / c) <= 1e-12, (bb, s["alpha"])
+
+
 def test_max_memory_reference():
     A, W = _small_problem(30, 3, seed=41)
     opts = O.Options(formulation="direct", memory=3, max_iter=12, tol=0.0)
