@@ -289,6 +289,17 @@ SNMF_API snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_produc
 SNMF_API snmf_status snmf_profile_steps(snmf_handle h, int iters, double* ms_dstep, double* ms_update);
 
 /*
+ * Measurement utility (no counterpart in the paper): which row-kernel body runs the D step and
+ * the update of this handle's penalty blocks, and their algorithmic bytes per launch (every
+ * n x (r batch) array a launch reads or writes, once).  *body: 0 the general row kernel
+ * (Z and D stored; D step 6 arrays, 7 with the learned step's second direction, update 8),
+ * 1 the shared-memory tile body (same traffic), 2 the recomputing kernels (Z and D not stored:
+ * D step 4 arrays, update 6).  *rows_per_cta: rows of one CTA.  Any pointer may be NULL.
+ */
+SNMF_API snmf_status snmf_step_config(snmf_handle h, int32_t* body, int32_t* rows_per_cta, int64_t* dstep_bytes,
+                                      int64_t* update_bytes);
+
+/*
  * The product configuration chosen by the autotuner (no counterpart in the paper):
  * split-K slices, tcgen05 ring stages and CTAs per SM (0 where the kernel has none), the
  * measured mean time in ms, and *from_cache = 1 when it came from the cache file or an
@@ -299,9 +310,11 @@ SNMF_API snmf_status snmf_tuned_config(snmf_handle h, int32_t* splits, int32_t* 
 
 /*
  * The tile shapes chosen by the same autotuner: *bn = columns of X per tensor-core product
- * tile (0 where the product kernel has no such choice) and *row_bm = rows per CTA of the
- * general row kernel (0 where the handle uses the shared-memory tile body, whose height is
- * fixed).  SNMF_ERR_STATE when the handle was not tuned.
+ * tile (0 where the product kernel has no such choice) and *row_bm = rows per CTA of the row
+ * kernels of a step (FP32 penalty form: the recomputing kernels' 64 / 128 (r = 16: 128 / 256)
+ * where snmf_step_config reports body 2, else the general kernel's 32 / 64; 0 where the
+ * shared-memory tile body with its fixed height runs).  SNMF_ERR_STATE when the handle was not
+ * tuned.
  */
 SNMF_API snmf_status snmf_tuned_tiles(snmf_handle h, int32_t* bn, int32_t* row_bm);
 

@@ -59,6 +59,7 @@ struct snmf_ctx {
   double gamma = 0.0;
   double normL = 0.0;  // ||L||_2 (power method), enters rho of graph-regularised blocks
   int use_tile = 0;    // row kernels through the shared-memory tile body (r <= 32)
+  int use_fuse = 0;    // D step and update through rowfuse.cu (FP32, r in {16, 32, 64}, no Z / D stored)
   int row_bm = 0;      // general row kernel, FP32: rows per CTA (0: built-in choice; autotuned)
   AxArgs L{};
   int32_t* L_rowptr = nullptr;
@@ -270,15 +271,23 @@ snmf_status time_steps(snmf_ctx* h, int iters, double* ms_dstep, double* ms_upda
   au.Xout = X;
   au.ctl_mode = CTL_UPD_W;
   au.Zin = h->buf[B_Z]; au.Din = h->buf[B_D]; au.Din2 = h->buf[B_AD];
+  auto dstep = [&] {
+    if (h->use_fuse) launch_rowfuse_dstep(ad, h->row_bm, h->s);
+    else launch_rowgemm(td, OP_ZSTEP, EPI_DIR, ad, h->s, nc);
+  };
+  auto update = [&] {
+    if (h->use_fuse) launch_rowfuse_update(au, h->row_bm, h->s);
+    else launch_rowgemm(td, OP_UPD, EPI_GRAD, au, h->s);
+  };
   cudaEvent_t e[4];
   for (auto& x : e) CK(cudaEventCreate(&x));
-  launch_rowgemm(td, OP_ZSTEP, EPI_DIR, ad, h->s, nc);  // warm-up
-  launch_rowgemm(td, OP_UPD, EPI_GRAD, au, h->s);
+  dstep();  // warm-up
+  update();
   CK(cudaEventRecord(e[0], h->s));
-  for (int t = 0; t < iters; ++t) launch_rowgemm(td, OP_ZSTEP, EPI_DIR, ad, h->s, nc);
+  for (int t = 0; t < iters; ++t) dstep();
   CK(cudaEventRecord(e[1], h->s));
   CK(cudaEventRecord(e[2], h->s));
-  for (int t = 0; t < iters; ++t) launch_rowgemm(td, OP_UPD, EPI_GRAD, au, h->s);
+  for (int t = 0; t < iters; ++t) update();
   CK(cudaEventRecord(e[3], h->s));
   CK(cudaStreamSynchronize(h->s));
   CK(cudaGetLastError());
@@ -301,13 +310,18 @@ snmf_status autotune_product(snmf_ctx* h) {
                           std::to_string(h->r) + "/N" + std::to_string(h->N);
   const std::string dev = tune_device_key();
   TuneEntry e;
-  const bool tune_rows = !h->use_tile && h->tdtype == 1 && h->opt.formulation == SNMF_PENALTY && h->r <= 64;
+  const bool tune_rows =
+      (!h->use_tile || h->use_fuse) && h->tdtype == 1 && h->opt.formulation == SNMF_PENALTY && h->r <= 64;
+  // rows per CTA offered to the search: the fused kernels' heights, else the general kernel's
+  std::vector<int> bms;
+  if (h->use_fuse) bms = h->r == 16 ? std::vector<int>{128, 256} : std::vector<int>{128, 64};
+  else bms = {64, 32};
   if (tune_lookup(h->opt.tune_cache, dev, key, &e)) {
     h->tune = e;
     h->tuned = 2;
-    if (tune_rows && (e.cfg.row_bm == 32 || e.cfg.row_bm == 64)) {
+    if (tune_rows && std::find(bms.begin(), bms.end(), e.cfg.row_bm) != bms.end()) {
       h->row_bm = e.cfg.row_bm;
-      h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, h->row_bm);
+      if (!h->use_tile) h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, h->row_bm);
     }
     return SNMF_OK;
   }
@@ -382,16 +396,16 @@ snmf_status autotune_product(snmf_ctx* h) {
   if (tune_rows) {
     double bt = 1e30;
     int bbm = 0;
-    for (int bm : {64, 32}) {
+    for (int bm : bms) {
       h->row_bm = bm;
-      h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, bm);
+      if (!h->use_tile) h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, bm);
       double md = 0.0, mu = 0.0;
       const snmf_status st = time_steps(h, 5, &md, &mu);
       if (st != SNMF_OK) return st;
       if (md + mu < bt) { bt = md + mu; bbm = bm; }
     }
     h->row_bm = bbm;
-    h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, bbm);
+    if (!h->use_tile) h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, bbm);
     h->tune.cfg.row_bm = bbm;
   }
   tune_store(h->opt.tune_cache, dev, key, h->tune);
@@ -435,6 +449,20 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
   launch_any_active(h->ctl, h->b, h->run, nullptr, h->s);
   const int K = h->opt.inner_iters;
   const bool fused_q = h->r <= 64 && !gr;
+  if (h->use_fuse && !gr) {
+    // D step (g(Z) and the line search) and the update recomputing Z and D (rowfuse.cu)
+    for (int k = 0; k < K; ++k) {
+      RowArgs a = row_base(h, &P);
+      a.X = X; a.g_in = h->buf[B_G]; a.B = h->buf[B_B]; a.gZout = h->buf[B_GZ];
+      a.ctl_mode = CTL_LS;
+      launch_rowfuse_dstep(a, h->row_bm, h->s);
+      RowArgs u = row_base(h, &P);
+      u.Xout = X; u.gout = h->buf[B_G]; u.gZold = h->buf[B_GZ]; u.B = h->buf[B_B];
+      u.ctl_mode = is_w ? CTL_UPD_W : (k == K - 1 ? CTL_UPD_H_LAST : CTL_UPD_H);
+      launch_rowfuse_update(u, h->row_bm, h->s);
+    }
+    return;
+  }
   for (int k = 0; k < K; ++k) {
     // Z = Proj[X - g / rho_0], D = Proj[Z - alpha g(Z)] - Z   (Alg. 1 lines 2-3)
     {
@@ -623,6 +651,13 @@ int tile_rule(const snmf_ctx* h) {
           tiles >= 2 * 152) ? 1 : 0;
 }
 
+// D step and update through rowfuse.cu: FP32 factors, r in {16, 32, 64}, penalty form, the
+// plain or the lean learned step (one direction per step), no graph term.
+int fuse_rule(const snmf_ctx* h) {
+  return (rowfuse_supported(h->tdtype, h->r) && h->opt.formulation == SNMF_PENALTY &&
+          (h->opt.step_controller == 0 || h->opt.step_controller == 3) && !h->graph) ? 1 : 0;
+}
+
 snmf_status alloc_buffers(snmf_ctx* h) {
   const size_t fe = (size_t)h->n * h->N;
   for (int i = 0; i < NBUF; ++i) {
@@ -640,6 +675,7 @@ snmf_status alloc_buffers(snmf_ctx* h) {
   // the shared-memory tile body where tile_rule allows it
   h->use_tile = tile_rule(h);
   if (h->use_tile) h->nrow = rowgemm_slots(d, h->tdtype, 1);
+  h->use_fuse = fuse_rule(h);
   double** parts[] = {&h->prow, &h->pax, &h->pax2, &h->pax3, &h->pax4, &h->pclip};
   for (double** p : parts) {
     CK(cudaMalloc(p, prec_n * sizeof(double)));
@@ -998,6 +1034,7 @@ snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma
     h->gamma = 0.0;
     h->exec_form = -1;
     h->use_tile = tile_rule(h);
+    h->use_fuse = fuse_rule(h);
     h->nrow = rowgemm_slots(dims(h), h->tdtype, h->use_tile, h->row_bm);
     return SNMF_OK;
   }
@@ -1044,6 +1081,7 @@ snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma
   h->gamma = gamma;
   h->exec_form = -1;
   h->use_tile = 0;  // the graph term runs through the general row kernel
+  h->use_fuse = 0;
   h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, h->row_bm);
   // ||L||_2 by power_iters power iterations from s_i = 1 + (i mod 2) (L 1 = 0 for a
   // Laplacian, so the start must not be constant) and the Rayleigh quotient; the device
@@ -1381,6 +1419,34 @@ snmf_status snmf_tuned_tiles(snmf_handle h, int32_t* bn, int32_t* row_bm) {
   if (!h->tuned) return fail(h, SNMF_ERR_STATE, "the handle was not autotuned");
   if (bn) *bn = h->tune.cfg.bn;
   if (row_bm) *row_bm = h->tune.cfg.row_bm;
+  return SNMF_OK;
+}
+
+snmf_status snmf_step_config(snmf_handle h, int32_t* body, int32_t* rows_per_cta, int64_t* dstep_bytes,
+                             int64_t* update_bytes) {
+  if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
+  const int64_t fb = h->n * (int64_t)h->N * (int64_t)h->esz;  // one n x (r b) factor array
+  const int nc = h->opt.step_controller == 1 ? 2 : (h->opt.step_controller == 2 ? kNCand : 1);
+  int kind = 0, rows = 0;
+  int64_t bd = 0, bu = 0;
+  if (h->use_fuse) {
+    kind = 2;
+    rows = rowfuse_bm(h->r, h->row_bm);
+    bd = 4 * fb;  // X, g, B in; g(Z) out
+    bu = 6 * fb;  // X, g, g(Z), B in; X', g(X') out
+  } else {
+    kind = h->use_tile ? 1 : 0;
+    const Dims d = dims(h);
+    rows = h->use_tile ? (int)((h->n + rowgemm_slots(d, h->tdtype, 1) - 1) / rowgemm_slots(d, h->tdtype, 1))
+                       : (int)((h->n + h->nrow / ((h->r + 63) / 64) - 1) / (h->nrow / ((h->r + 63) / 64)));
+    bd = (6 + (nc == 2 ? 1 : 0)) * fb;  // X, g, B in; Z, g(Z), D (+ the second direction) out
+    bu = 8 * fb;                        // Z, D, B, X, g, g(Z) in; X', g(X') out
+  }
+  if (body) *body = kind;
+  if (rows_per_cta) *rows_per_cta = rows;
+  if (dstep_bytes) *dstep_bytes = bd;
+  if (update_bytes) *update_bytes = bu;
   return SNMF_OK;
 }
 

@@ -51,6 +51,15 @@ struct RowArgs {
   int bm;              // general body, FP32: rows per CTA (32 or 64; 0 = built-in choice)
 };
 
+// Row kernels of a step for FP32 penalty blocks with r in {16, 32, 64} (rowfuse.cu): the D step
+// writes g(Z) only (RowArgs X, g_in, B -> gZout; fused line search, ctl_mode CTL_LS) and the
+// update recomputes Z and D from X, g, g(Z) (RowArgs Xout = X and gout = g, updated in place,
+// gZold, B; ctl_mode CTL_UPD_*).  bm: rows per CTA (64 or 128; r = 16: 128 or 256).
+bool rowfuse_supported(int tdtype, int r);
+int rowfuse_bm(int r, int bm_req);
+void launch_rowfuse_dstep(const RowArgs& a, int bm, cudaStream_t s);
+void launch_rowfuse_update(const RowArgs& a, int bm, cudaStream_t s);
+
 void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pair, int npairs,
                  double* gpart, int nchunks, const Ctl* ctl, const int* run, double* G64, void* GT,
                  int tpair, double lam_shift, unsigned* counters, cudaStream_t s,

@@ -29,7 +29,7 @@ EXPORTED = (
     "snmf_solve", "snmf_solve_host", "snmf_restart_stats", "snmf_get_factors",
     "snmf_apply", "snmf_profile_ax", "snmf_apply_dense_noalloc", "snmf_controller_data",
     "snmf_mlp_train", "snmf_tuned_config", "snmf_tuned_tiles", "snmf_profile_steps", "snmf_destroy", "snmf_last_error",
-    "snmf_mlp_eval", "snmf_set_timeout",
+    "snmf_mlp_eval", "snmf_set_timeout", "snmf_step_config",
 )
 NOALLOC_SCRATCH_BYTES = 64 << 20
 NOALLOC_PARTIAL_BYTES = 4 << 20
@@ -101,6 +101,8 @@ def load_library(path: str = LIB_PATH):
     lib.snmf_tuned_tiles.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.snmf_mlp_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
     lib.snmf_set_timeout.argtypes = [H, C.c_int64]
+    lib.snmf_step_config.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_int64)]
     lib.snmf_destroy.argtypes = [H]
     lib.snmf_last_error.argtypes = [H]
     lib.snmf_last_error.restype = C.c_char_p
@@ -330,6 +332,16 @@ def snmf_set_timeout(h, cycles: int):
     """Bound (clock64 cycles) of the handle's device-side waits; 0 restores the default."""
     lib = load_library()
     return _check(lib, h, lib.snmf_set_timeout(h, int(cycles)))
+
+
+def snmf_step_config(h) -> dict:
+    """Row-kernel body of the D step and update (0 general, 1 tile, 2 recomputing), rows per CTA
+    and the algorithmic bytes of one launch of each."""
+    lib = load_library()
+    body, rows = C.c_int32(), C.c_int32()
+    bd, bu = C.c_int64(), C.c_int64()
+    _check(lib, h, lib.snmf_step_config(h, C.byref(body), C.byref(rows), C.byref(bd), C.byref(bu)))
+    return dict(body=body.value, rows_per_cta=rows.value, dstep_bytes=bd.value, update_bytes=bu.value)
 
 
 def snmf_profile_steps(h, iters: int = 20):
