@@ -153,7 +153,10 @@ typedef struct {
                               the dense A*X product (split-K count; tcgen05 ring depth and CTAs
                               per SM) on this device and shape and keep the fastest; 0 (default):
                               built-in heuristics.  No counterpart in the paper.               */
-  int32_t reserved_opt;
+  int32_t x_parts;         /* SNMF_BF16 tensor-core product: X enters as 2 BF16 parts hi + lo
+                              (0 or 2, default: the product sees X to about 2^-17) or as 1 part,
+                              X rounded to BF16 (one MMA pass, half the tensor work); the stored A
+                              is BF16 either way.  No counterpart in the paper.                */
   const char* tune_cache;  /* JSON file of tuned configurations keyed by device name and SM
                               count (read before timing, updated after); NULL: this process only */
 } snmf_options;

@@ -21,6 +21,7 @@
 #include <mutex>
 
 #include "ax_tc.cuh"
+#include "common.cuh"
 
 namespace snmf {
 
@@ -123,10 +124,14 @@ struct TcParams {
   int stages;
   int k_iters;        // BK-steps per split
   int tmem_cols;      // power of two >= BN, >= 32
-  float* Y;           // output base (split z writes Y + z * n * ldy)
+  int xparts;         // 2: X as hi + lo BF16 parts (two MMAs per K step), 1: hi only
+  int splits;         // K slices (gridDim.z)
+  float* Y;           // unfused: output base (split z writes Y + z * n * ldy); fused: the slices
   int64_t ldy;
   int* err;           // error code (0 = ok)
   long long budget;   // clock64 budget per wait
+  const int* run;     // device run flag of a solve (NULL: always run); 0 = stopped, skip the launch
+  TcEpilogue e;       // fused epilogue (e.fused = 1)
 };
 
 __global__ void __launch_bounds__(128, 1)
@@ -139,17 +144,20 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   const int BN = p.BN;
   const uint32_t a_bytes = BM * BK * 2;
   const uint32_t b_bytes = (uint32_t)BN * BK * 2;
-  const uint32_t stage_bytes = a_bytes + 2 * b_bytes;
+  const uint32_t stage_bytes = a_bytes + (uint32_t)p.xparts * b_bytes;
   uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)p.stages * stage_bytes);
   uint64_t* empty = full + p.stages;
   uint64_t* accum = empty + p.stages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
   __shared__ int s_fail, s_issued, s_consumed;
+  __shared__ unsigned s_ticket;
+  __shared__ float s_red[4][2];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN;
   const int m0 = blockIdx.y * BM;
   const int kbase = blockIdx.z * p.k_iters * BK;
+  if (p.run && *p.run == 0) return;  // the solve has stopped: every CTA of the launch skips
 
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -184,7 +192,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       const int kx = kbase + it * BK;
       tma_load_2d(st, &mapA, &full[s], kx, m0);
       tma_load_2d(st + a_bytes, &mapXh, &full[s], kx, n0);
-      tma_load_2d(st + a_bytes + b_bytes, &mapXl, &full[s], kx, n0);
+      if (p.xparts == 2) tma_load_2d(st + a_bytes + b_bytes, &mapXl, &full[s], kx, n0);
     }
     s_issued = it;
   } else if (warp == 1 && lane == 0) {
@@ -202,7 +210,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       for (int kk = 0; kk < BK / 16; ++kk) {
         const uint64_t da = sdesc(sa + kk * 32);
         mma_bf16(tmem, da, sdesc(sh + kk * 32), idesc, (it > 0 || kk > 0) ? 1u : 0u);
-        mma_bf16(tmem, da, sdesc(sl + kk * 32), idesc, 1u);
+        if (p.xparts == 2) mma_bf16(tmem, da, sdesc(sl + kk * 32), idesc, 1u);
       }
       mma_commit(&empty[s]);
     }
@@ -219,17 +227,101 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     atomicExch(p.err, 3);
     s_fail = 1;
   }
-  if (done && !s_fail) {
-    const int row = m0 + warp * 32 + lane;
+  __syncthreads();  // the CTA decides as one: s_fail from every warp visible
+  const bool ok = !s_fail;
+  const int row = m0 + warp * 32 + lane;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  if (ok && !p.e.fused) {
     float* Yz = p.Y + (int64_t)blockIdx.z * p.n * p.ldy;
     for (int c0 = 0; c0 < BN; c0 += 16) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_ld16(trow + (uint32_t)c0, v);
       if (row < p.n) {
         float* yr = Yz + (int64_t)row * p.ldy + n0 + c0;
 #pragma unroll
         for (int i = 0; i < 16; ++i)
           if (n0 + c0 + i < p.N) yr[i] = v[i];
+      }
+    }
+  }
+  if (p.e.fused) {
+    // Split K: every slice publishes its partial tile; the last slice of the tile to arrive
+    // (arrival counter) sums the slices in slice order, so the result does not depend on the
+    // arrival order, and runs the epilogue (Y += c X2, partials <P1, A X>, <P2, A X>).
+    bool last = ok;
+    if (p.splits > 1) {
+      if (ok && row < p.n) {
+        float* Wz = p.Y + (int64_t)blockIdx.z * p.n * p.ldy + (int64_t)row * p.ldy + n0;
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          float v[16];
+          tmem_ld16(trow + (uint32_t)c0, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (n0 + c0 + i < p.N) Wz[c0 + i] = v[i];
+        }
+      }
+      __threadfence();
+      __syncthreads();
+      // a CTA whose waits ran out still arrives (its slice is not valid, the call reports the
+      // error), so the counter returns to zero for the next launch in every case
+      const unsigned tile = blockIdx.y * gridDim.x + blockIdx.x;
+      if (threadIdx.x == 0) s_ticket = atomicAdd(&p.e.counters[tile], 1u);
+      __syncthreads();
+      const bool arrived_last = s_ticket == (unsigned)(p.splits - 1);
+      if (arrived_last) {
+        __threadfence();
+        if (threadIdx.x == 0) p.e.counters[tile] = 0u;  // ready for the next launch
+      }
+      last = ok && arrived_last;
+    }
+    if (last) {
+      const int rr = p.e.r;
+      const bool dots = p.e.P1 || p.e.P2;
+      float d1 = 0.f, d2 = 0.f;
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)c0, v);
+        if (row < p.n) {
+          const int64_t base_idx = (int64_t)row * p.ldy + n0 + c0;
+          if (p.splits > 1) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              float y = 0.f;
+              for (int z = 0; z < p.splits; ++z)
+                y += (z == (int)blockIdx.z) ? v[i] : __ldcg(p.Y + (int64_t)z * p.n * p.ldy + base_idx + i);
+              v[i] = y;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            if (n0 + c0 + i >= p.N) continue;
+            const int64_t idx = base_idx + i;
+            float y = v[i];
+            if (p.e.P1) d1 += p.e.P1[idx] * y;
+            if (p.e.P2) d2 += p.e.P2[idx] * y;
+            if (p.e.X2) y += p.e.c * p.e.X2[idx];
+            p.e.Y[idx] = y;
+          }
+        }
+        if (dots && ((n0 + c0 + 16) % rr == 0 || c0 + 16 >= BN)) {
+          // end of restart j = (n0 + c0) / r inside this tile: the partials of its two 64-row
+          // slots (warps 0-1 and 2-3), summed in a fixed order
+          d1 = warp_sum(d1);
+          d2 = warp_sum(d2);
+          if (lane == 0) { s_red[warp][0] = d1; s_red[warp][1] = d2; }
+          __syncthreads();
+          const int j = (n0 + c0) / rr;
+          if (threadIdx.x < 2 && j < p.e.b) {
+            const int64_t slot = 2 * (int64_t)blockIdx.y + threadIdx.x;
+            if (slot * 64 < p.n) {
+              double* q = p.e.part + (slot * p.e.b + j) * kNQ + p.e.q0;
+              q[0] = (double)(s_red[2 * threadIdx.x][0] + s_red[2 * threadIdx.x + 1][0]);
+              q[1] = (double)(s_red[2 * threadIdx.x][1] + s_red[2 * threadIdx.x + 1][1]);
+            }
+          }
+          __syncthreads();
+          d1 = d2 = 0.f;
+        }
       }
     }
   }
@@ -269,9 +361,8 @@ __global__ void k_split_x(const float* __restrict__ X, int64_t n, int N, int64_t
     if (c < N && k < ldk) {
       const float v = t[tx][i];
       const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
       Xh[(int64_t)c * ldk + k] = hi;
-      Xl[(int64_t)c * ldk + k] = lo;
+      if (Xl) Xl[(int64_t)c * ldk + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
     }
   }
 }
@@ -547,7 +638,7 @@ int launch_sums_bf16(const void* A16, int64_t elems, double* part, cudaStream_t 
   return blocks;
 }
 
-int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune) {
+int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune, int xparts) {
   TcPlan pl{};
   pl.BN = N <= 256 ? ((N + 15) / 16 * 16) : 256;
   if (tune && tune->bn > 0) {
@@ -557,7 +648,7 @@ int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune) {
   pl.tiles_n = (N + pl.BN - 1) / pl.BN;
   pl.tiles_m = (int)((n + BM - 1) / BM);
   const int64_t kiters_total = (n + BK - 1) / BK;
-  const uint32_t stage_bytes = BM * BK * 2 + 2u * pl.BN * BK * 2;
+  const uint32_t stage_bytes = BM * BK * 2 + (uint32_t)xparts * pl.BN * BK * 2;
   // two CTAs per SM with a 3-stage ring when it fits in half the SM, else one CTA with
   // as many stages as fit (at most 6)
   int per_sm = 1, stages;
@@ -598,11 +689,14 @@ int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune) {
   return 0;
 }
 
-int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
-                 float* Y, float* ws, size_t ws_elems, int* err, long long budget, cudaStream_t s,
-                 const ProdTune* tune) {
+namespace {
+
+// Shared launcher of k_gemm_tc: fused epilogue when epi != NULL && epi->fused.
+int launch_tc_impl(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl, int xparts,
+                   float* Y, float* ws, size_t ws_elems, int* err, long long budget, const TcEpilogue* epi,
+                   const int* run, cudaStream_t s, const ProdTune* tune) {
   TcPlan pl;
-  if (tc_plan(n, N, &pl, tune) < 0) tc_plan(n, N, &pl);
+  if (tc_plan(n, N, &pl, tune, xparts) < 0) tc_plan(n, N, &pl, nullptr, xparts);
   const int64_t ldk = tc_ld(n);
   if ((size_t)pl.splits * n * ldx > ws_elems) {
     // not enough split workspace: recompute the plan without splitting
@@ -610,10 +704,11 @@ int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx,
     pl.k_iters = (int)((n + BK - 1) / BK);
   }
   dim3 sg((unsigned)((ldk + 31) / 32), (unsigned)((N + 31) / 32));
-  k_split_x<<<sg, 256, 0, s>>>(X, n, N, ldx, (__nv_bfloat16*)xh, (__nv_bfloat16*)xl, ldk);
+  k_split_x<<<sg, 256, 0, s>>>(X, n, N, ldx, (__nv_bfloat16*)xh, xparts == 2 ? (__nv_bfloat16*)xl : nullptr,
+                               ldk);
   CUtensorMap ma, mh, ml;
   if (!make_map(&ma, A16, ldk, n, ldk, BM) || !make_map(&mh, xh, ldk, N, ldk, pl.BN) ||
-      !make_map(&ml, xl, ldk, N, ldk, pl.BN))
+      !make_map(&ml, xparts == 2 ? xl : xh, ldk, N, ldk, pl.BN))
     return -1;
   static bool attr_done = false;
   if (!attr_done) {
@@ -631,15 +726,40 @@ int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx,
   p.stages = pl.stages;
   p.k_iters = pl.k_iters;
   p.tmem_cols = pl.tmem_cols;
+  p.xparts = xparts;
+  p.splits = pl.splits;
   p.Y = pl.splits > 1 ? ws : Y;
   p.ldy = ldx;
   p.err = err;
   p.budget = budget;
+  p.run = run;
+  if (epi && epi->fused) p.e = *epi;
   dim3 grid(pl.tiles_n, pl.tiles_m, pl.splits);
   k_gemm_tc<<<grid, 128, pl.smem, s>>>(ma, mh, ml, p);
   const cudaError_t le = cudaPeekAtLastError();
   if (le != cudaSuccess) { g_last_cu = 10000 + (int)le; return -2; }
-  return pl.splits;
+  return (epi && epi->fused) ? 0 : pl.splits;
+}
+
+}  // namespace
+
+int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
+                 float* Y, float* ws, size_t ws_elems, int* err, long long budget, cudaStream_t s,
+                 const ProdTune* tune, int xparts) {
+  return launch_tc_impl(A16, n, X, N, ldx, xh, xl, xparts, Y, ws, ws_elems, err, budget, nullptr, nullptr, s,
+                        tune);
+}
+
+int launch_ax_tc_fused(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
+                       int xparts, float* ws, size_t ws_elems, int* err, long long budget, const TcEpilogue& epi,
+                       const int* run, cudaStream_t s, const ProdTune* tune) {
+  return launch_tc_impl(A16, n, X, N, ldx, xh, xl, xparts, epi.Y, ws, ws_elems, err, budget, &epi, run, s, tune);
+}
+
+int tc_tiles(int64_t n, int N, const ProdTune* tune, int xparts) {
+  TcPlan pl;
+  if (tc_plan(n, N, &pl, tune, xparts) < 0) tc_plan(n, N, &pl, nullptr, xparts);
+  return pl.tiles_n * pl.tiles_m;
 }
 
 void launch_bsplit_x(const TcItem* items, int nitems, const int* cnt, const float* X, void* xh, void* xl,

@@ -15,13 +15,32 @@ struct TcPlan {
   size_t smem;
 };
 
+// Epilogue fused into the tensor-core product (fused = 1): the last K slice of each output
+// tile to finish sums the slices in slice order and writes Y = A X (+ c X2), with the
+// per-restart partials <P1, A X> -> part[slot][j][q0], <P2, A X> -> [q0 + 1] over 64-row
+// slots (P1 / P2 may be NULL; with either set, r must be a multiple of 16 dividing the tile
+// width).  counters: one zeroed unsigned per output tile, left zeroed.
+struct TcEpilogue {
+  int fused = 0;
+  float* Y = nullptr;
+  unsigned* counters = nullptr;
+  float c = 0.f;
+  const float* X2 = nullptr;
+  const float* P1 = nullptr;
+  const float* P2 = nullptr;
+  double* part = nullptr;
+  int q0 = 0;
+  int r = 1;
+  int b = 1;
+};
+
 // Leading dimension (elements) of the BF16 copy of A and of the transposed X parts.
 int64_t tc_ld(int64_t n);
 // diagnostics of the last launch_ax_tc failure: CUresult of the encoder, or 10000 + cudaError_t
 int tc_last_status();
 // Built-in plan, or the autotuned (per_sm, stages, splits) when `tune` sets them; returns
 // -1 when a tuned ring does not fit in shared memory.
-int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune = nullptr);
+int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune = nullptr, int xparts = 2);
 // FP64 partial sums of squares / sums of a BF16 array into part[2*block]; returns blocks.
 int launch_sums_bf16(const void* A16, int64_t elems, double* part, cudaStream_t s);
 // A (n x n, dtype 0 f64 / 1 f32, lda) -> A16 (n x tc_ld(n) BF16, zero-padded columns)
@@ -32,7 +51,17 @@ void launch_to_bf16(int src_dtype, const void* A, int64_t n, int64_t lda, void* 
 // of splits (1 = Y written directly), or -1 when the tensor maps cannot be encoded.
 int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
                  float* Y, float* ws, size_t ws_elems, int* err, long long budget, cudaStream_t s,
-                 const ProdTune* tune = nullptr);
+                 const ProdTune* tune = nullptr, int xparts = 2);
+// The same product with the epilogue fused (see TcEpilogue) and X seen as xparts BF16 parts
+// (2: hi + lo, 1: X rounded to BF16, one MMA pass).  The slices of a split K go to ws.  Returns
+// 0 when the product and epilogue are complete in Y, or < 0 as launch_ax_tc.  xl may be NULL
+// when xparts == 1.  run: a solve's device run flag (NULL: always); when it reads 0 the launch
+// does nothing.
+int launch_ax_tc_fused(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
+                       int xparts, float* ws, size_t ws_elems, int* err, long long budget, const TcEpilogue& epi,
+                       const int* run, cudaStream_t s, const ProdTune* tune = nullptr);
+// Output tiles of the product's plan (counters a fused launch needs).
+int tc_tiles(int64_t n, int N, const ProdTune* tune = nullptr, int xparts = 2);
 
 // ---- grouped product of the uneven batch (one CTA per 128-row tile of a problem) ----
 // A_all: BF16, rows of all problems packed, pitch lda; X parts: BF16 hi / lo, row xrow_p + c

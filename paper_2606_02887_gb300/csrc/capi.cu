@@ -86,6 +86,8 @@ struct snmf_ctx {
   int* dev_err = nullptr;        // device error code of bounded waits (tensor-core product)
   void* xh = nullptr;            // BF16 hi / lo parts of the product operand (transposed)
   void* xl = nullptr;
+  int xparts = 2;                // BF16 product: X as hi + lo parts (2) or rounded to BF16 (1)
+  unsigned* tcount = nullptr;    // BF16 product: arrival counters of the fused split-K epilogue
   long long budget = 2000000000LL;
   __nv_bfloat16* mlp_w = nullptr;  // learned controller weights (BF16)
   float* rec_feat = nullptr;       // record mode dataset
@@ -160,16 +162,54 @@ Dims dims(const snmf_ctx* h) {
   return d;
 }
 
-// The product kernel alone: CUDA cores (FP64/FP32 dense, CSR) or tcgen05 (BF16 dense).
-// Returns the number of split-K slices written to h->ws (1 = result in Y).
-int product_kernel(snmf_ctx* h, const AxArgs& op, const void* X, void* Y, const int* run) {
+// Epilogue of Y = op X (+ c X2) with partials <P1, op X>, <P2, op X> fused into the BF16
+// tensor-core product where its tiles allow it (dots: r a multiple of 16 dividing the tile
+// width); fused = 0 otherwise (the separate finish pass runs).
+TcEpilogue tc_epilogue(snmf_ctx* h, void* Y, double c, const void* X2, const void* P1, const void* P2,
+                       double* part) {
+  TcEpilogue e;
+  if (!h->tcount) return e;
+  if (P1 || P2) {
+    TcPlan pl;
+    const ProdTune* tn = h->tuned ? &h->tune.cfg : nullptr;
+    if (tc_plan(h->n, h->N, &pl, tn, h->xparts) < 0) tc_plan(h->n, h->N, &pl, nullptr, h->xparts);
+    if (h->r % 16 != 0 || pl.BN % h->r != 0) return e;
+  }
+  e.fused = 1;
+  e.Y = (float*)Y;
+  e.counters = h->tcount;
+  e.c = (float)c;
+  e.X2 = (const float*)X2;
+  e.P1 = (const float*)P1;
+  e.P2 = (const float*)P2;
+  e.part = part;
+  e.q0 = 0;
+  e.r = h->r;
+  e.b = h->b;
+  return e;
+}
+
+// The product kernel: CUDA cores (FP64/FP32 dense, CSR) or tcgen05 (BF16 dense).  Returns the
+// number of split-K slices written to h->ws (1 = result in Y), or 0 when the epilogue `epi`
+// was fused into the product (the result, c X2 and the partials are complete).
+int product_kernel(snmf_ctx* h, const AxArgs& op, const void* X, void* Y, const int* run,
+                   const TcEpilogue* epi = nullptr) {
   const ProdTune* tn = (h->tuned && &op == &h->A) ? &h->tune.cfg : nullptr;  // the tuned shape only
   if (op.kind == AX_DENSE && op.a_dtype == 3)
     return launch_ax_fp8(op.A, op.a_scale, h->n, (const float*)X, h->N, h->N, (float*)Y, (float*)h->ws,
                          h->ws_elems, run, h->s, tn);
   if (op.kind == AX_DENSE && op.a_dtype == 2 && !op.accurate) {
+    if (epi && epi->fused) {
+      const int rc = launch_ax_tc_fused(op.A, h->n, (const float*)X, h->N, h->N, h->xh, h->xl, h->xparts,
+                                        (float*)h->ws, h->ws_elems, h->dev_err, h->budget, *epi, run, h->s, tn);
+      if (rc < 0) {
+        h->tc_fail = tc_last_status();
+        return 1;
+      }
+      return 0;
+    }
     const int sp = launch_ax_tc(op.A, h->n, (const float*)X, h->N, h->N, h->xh, h->xl, (float*)Y,
-                                (float*)h->ws, h->ws_elems, h->dev_err, h->budget, h->s, tn);
+                                (float*)h->ws, h->ws_elems, h->dev_err, h->budget, h->s, tn, h->xparts);
     if (sp < 1) {
       h->tc_fail = tc_last_status();
       return 1;
@@ -188,7 +228,10 @@ int ax_apply(snmf_ctx* h, const AxArgs& op, bool use_lai, const void* X, void* Y
   if (use_lai) {
     return lai_apply(h->lai_op, h->tdtype, d, X, Y, c, X2, P1, P2, part, run, h->s);
   }
-  const int splits = product_kernel(h, op, X, Y, run);
+  TcEpilogue epi;
+  if (op.kind == AX_DENSE && op.a_dtype == 2 && !op.accurate) epi = tc_epilogue(h, Y, c, X2, P1, P2, part);
+  const int splits = product_kernel(h, op, X, Y, run, &epi);
+  if (splits == 0) return (int)((h->n + kRowTile - 1) / kRowTile);  // epilogue done in the product
   return launch_ax_finish_impl(h->tdtype, d, Y, h->ws, splits, c, X2, P1, P2, part, 0, run, h->s);
 }
 
@@ -306,8 +349,8 @@ snmf_status time_steps(snmf_ctx* h, int iters, double* ms_dstep, double* ms_upda
 snmf_status autotune_product(snmf_ctx* h) {
   if (h->kind != AX_DENSE) return SNMF_OK;
   static const char* dtn[4] = {"f64", "f32", "bf16", "fp8"};
-  const std::string key = std::string("dense/") + dtn[h->A.a_dtype] + "/n" + std::to_string(h->n) + "/r" +
-                          std::to_string(h->r) + "/N" + std::to_string(h->N);
+  const std::string key = std::string("dense/") + dtn[h->A.a_dtype] + (h->A.a_dtype == 2 && h->xparts == 1 ? "x1" : "") +
+                          "/n" + std::to_string(h->n) + "/r" + std::to_string(h->r) + "/N" + std::to_string(h->N);
   const std::string dev = tune_device_key();
   TuneEntry e;
   const bool tune_rows =
@@ -341,7 +384,7 @@ snmf_status autotune_product(snmf_ctx* h) {
         t.splits = sp;
         t.bn = bn;
         TcPlan pl;
-        if (tc_plan(h->n, h->N, &pl, &t) < 0 || pl.splits != sp) continue;
+        if (tc_plan(h->n, h->N, &pl, &t, h->xparts) < 0 || pl.splits != sp) continue;
         if ((size_t)sp * h->n * h->N > h->ws_elems && sp > 1) continue;
         cand.push_back(t);
       }
@@ -359,11 +402,13 @@ snmf_status autotune_product(snmf_ctx* h) {
   TuneEntry best;
   best.ms = 1e30;
   h->tuned = 1;
+  // timed as the solve runs it: B = A X + lambda X (epilogue fused into the BF16 product)
+  const TcEpilogue tepi = tc_epilogue(h, h->buf[B_AZ], h->lam, h->buf[B_W], nullptr, nullptr, h->pax);
   for (const ProdTune& t : cand) {
     h->tune.cfg = t;
-    product_kernel(h, h->A, h->buf[B_W], h->buf[B_AZ], nullptr);  // warm-up
+    product_kernel(h, h->A, h->buf[B_W], h->buf[B_AZ], nullptr, &tepi);  // warm-up
     CK(cudaEventRecord(e0, h->s));
-    for (int rep = 0; rep < 5; ++rep) product_kernel(h, h->A, h->buf[B_W], h->buf[B_AZ], nullptr);
+    for (int rep = 0; rep < 5; ++rep) product_kernel(h, h->A, h->buf[B_W], h->buf[B_AZ], nullptr, &tepi);
     CK(cudaEventRecord(e1, h->s));
     CK(cudaStreamSynchronize(h->s));
     if (h->tc_fail) {  // a configuration that did not launch is skipped
@@ -696,6 +741,10 @@ snmf_status alloc_buffers(snmf_ctx* h) {
     const size_t xb = (size_t)h->N * tc_ld(h->n) * 2;
     CK(cudaMalloc(&h->xh, xb));
     CK(cudaMalloc(&h->xl, xb));
+    // one counter per output tile of any plan: 128-row tiles x tiles of >= 16 columns
+    const size_t nt = (size_t)((h->n + 127) / 128) * ((h->N + 15) / 16);
+    CK(cudaMalloc(&h->tcount, nt * sizeof(unsigned)));
+    CK(cudaMemsetAsync(h->tcount, 0, nt * sizeof(unsigned), h->s));
   }
   if (h->opt.timeout_cycles > 0) h->budget = h->opt.timeout_cycles;
   CK(cudaMalloc(&h->counters, (16384 + 4096) * sizeof(unsigned)));  // Gram tiles, then restarts
@@ -736,7 +785,7 @@ snmf_status validate_options(const snmf_options& o) {
       !(o.alpha_min > 0.0 && o.alpha_min < o.alpha_max) || !(o.beta_shrink > 0.0 && o.beta_shrink < 1.0) ||
       !(o.tol >= 0.0) || !(o.direct_rho_factor > 0.0))
     return SNMF_ERR_ARG;
-  if (!valid_enum(o.step_controller, 0, 3)) return SNMF_ERR_ARG;
+  if (!valid_enum(o.step_controller, 0, 3) || !valid_enum(o.x_parts, 0, 2)) return SNMF_ERR_ARG;
   if ((o.step_controller == 1 || o.step_controller == 3) && !o.mlp_weights) return SNMF_ERR_ARG;
   return SNMF_OK;
 }
@@ -778,7 +827,7 @@ void snmf_default_options(snmf_options* o) {
   o->mlp_weights = nullptr;
   o->timeout_cycles = 0;
   o->autotune = 0;
-  o->reserved_opt = 0;
+  o->x_parts = 0;
   o->tune_cache = nullptr;
 }
 
@@ -832,6 +881,7 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   h->kind = Am->kind == SNMF_DENSE ? AX_DENSE : AX_CSR;
   h->prec = o.precision;
   h->tdtype = (o.precision == SNMF_F64) ? 0 : 1;
+  h->xparts = o.x_parts == 1 ? 1 : 2;
   h->esz = h->tdtype == 0 ? 8 : 4;
   h->n = Am->n;
   h->r = r;
@@ -1377,7 +1427,8 @@ snmf_status snmf_profile_ax(snmf_handle h, int iters, double* ms_product, double
   float m1 = 0.f, m2 = 0.f;
   if (!h->lai) {
     CK(cudaEventRecord(e[2], h->s));
-    for (int t = 0; t < iters; ++t) product_kernel(h, h->A, h->buf[B_W], h->buf[B_AZ], nullptr);
+    const TcEpilogue pepi = tc_epilogue(h, h->buf[B_AZ], 0.0, nullptr, h->buf[B_W], nullptr, h->pax);
+    for (int t = 0; t < iters; ++t) product_kernel(h, h->A, h->buf[B_W], h->buf[B_AZ], nullptr, &pepi);
     CK(cudaEventRecord(e[3], h->s));
   }
   CK(cudaStreamSynchronize(h->s));
@@ -1506,6 +1557,7 @@ snmf_status snmf_destroy(snmf_handle h) {
   cudaFree(h->dev_err);
   cudaFree(h->xh);
   cudaFree(h->xl);
+  cudaFree(h->tcount);
   cudaFree(h->mlp_w);
   cudaFree(h->rec_feat);
   cudaFree(h->rec_targ);

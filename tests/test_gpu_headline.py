@@ -80,14 +80,16 @@ def test_mlp_inference_matches_oracle_on_shipped_weights():
 # the headline configuration at n = 2048
 # ---------------------------------------------------------------------------
 
-def test_headline_configuration_matches_oracle_per_restart(tmp_path):
+@pytest.mark.parametrize("x_parts", [2, 1])
+def test_headline_configuration_matches_oracle_per_restart(tmp_path, x_parts):
     """BF16 A, r = 64, 8 restarts in one solve, lean learned step (step_controller 3) with
     the shipped weights, and the tile shapes the bench's autotuner chooses at n = 8192
     (128-column tensor-core tiles, 4 K slices, 2 CTAs per SM with a 2-stage ring, 64-row
     row tiles), forced through the tuning cache.  Every restart reaches relative projected
     gradient 1e-4, and its final residual against the true A is within 1e-3 of the FP64
     oracle's solve of the same restart (tests/golden/oracle_dense2048_r64_b8.json, written
-    by make_headline_oracle.py from the oracle alone)."""
+    by make_headline_oracle.py from the oracle alone).  x_parts = 2: the product sees X as
+    BF16 hi + lo parts; x_parts = 1: X rounded to BF16 (one tensor-core pass)."""
     import torch
     from paper_2606_02887_gb300.train_controller import load_weights
     from workloads.configs import dense_planted_8192
@@ -97,10 +99,10 @@ def test_headline_configuration_matches_oracle_per_restart(tmp_path):
     A, starts = dense_planted_8192(r, b, n=n)
     W0 = np.concatenate(starts, axis=1)
     dev = torch.device("cuda:0")
-    key = f"dense/bf16/n{n}/r{r}/N{r * b}"
+    key = f"dense/bf16{'x1' if x_parts == 1 else ''}/n{n}/r{r}/N{r * b}"
     cache = _forced_tune_cache(tmp_path / "tune.json", key, splits=4, stages=2, per_sm=2, bn=128, row_bm=64)
     o = S.snmf_default_options(precision=S.SNMF_BF16, batch=b, max_iter=500, tol=1e-4, nonmonotone_M=10,
-                               step_controller=3, autotune=1, tune_cache=cache)
+                               step_controller=3, autotune=1, tune_cache=cache, x_parts=x_parts)
     h = S.snmf_create(S.dense_matrix(torch.tensor(A, dtype=torch.float32, device=dev)), r, o,
                       mlp_weights=load_weights())
     try:
@@ -254,3 +256,29 @@ def test_direct_fp64_bb2_matches_oracle(cfg1):
                                   bb_variant=S.SNMF_BB2)
         e = rel(W, info["trace"][k - 1]["X"])
         assert e <= iter_tol(env, k), (k, e, env[k - 1])
+
+
+@pytest.mark.parametrize("n,cols,r", [(8192, 512, 64), (2048, 128, 16), (1000, 96, 32), (333, 20, 10)])
+def test_one_part_product_matches_emulated_operands(n, cols, r):
+    """x_parts = 1: the product A~ bf16(X) with the epilogue fused into the tensor-core kernel
+    (split-K reduction by the last slice, <X, A X> partials where r divides the tile), against
+    the exact emulation of the stored BF16 operands."""
+    import torch
+    dev = torch.device("cuda:0")
+    g = np.random.default_rng(n + cols)
+    B = g.random((n, n), dtype=np.float32)
+    A = (B + B.T).astype(np.float32)
+    X = g.random((n, cols), dtype=np.float32)
+    ref = bf16_round(A).astype(np.float64) @ bf16_round(X).astype(np.float64)
+    h = S.snmf_create(S.dense_matrix(torch.tensor(A, device=dev)), r,
+                      S.snmf_default_options(precision=S.SNMF_BF16, batch=cols // r, x_parts=1))
+    try:
+        Xt = torch.tensor(X, device=dev)
+        Yt = torch.full_like(Xt, float("nan"))
+        xax = S.snmf_apply(h, Xt, Yt, cols)
+    finally:
+        S.snmf_destroy(h)
+    Y = Yt.cpu().numpy().astype(np.float64)
+    assert rel(Y, ref) <= 3e-5, rel(Y, ref)
+    assert np.max(np.abs(Y - ref) / np.maximum(np.abs(ref), 1e-30)) <= 3e-5
+    assert abs(xax - float(np.sum(X * ref))) <= 1e-5 * abs(xax)
