@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--autotune", type=int, default=1, help="dense workload: tune the product at create")
     p.add_argument("--tune-cache", default=None, help="JSON cache of tuned configurations")
     p.add_argument("--cpu-iters", type=int, default=10, help="oracle outer iterations timed for cpu_baseline")
+    p.add_argument("--x-parts", type=int, default=2, choices=[1, 2],
+                   help="BF16 product: X as hi + lo BF16 parts (2) or rounded to BF16 (1)")
     return p.parse_args()
 
 
@@ -215,8 +217,6 @@ def run_reference(args):
 # the tuned tile shapes of the capture, which the run must share).  Other configurations,
 # and runs tuned to other tiles, report null.
 PROFILED_TRAFFIC = {
-    ("dense8192", "bf16", 64, 8, "product"): (191.7e6, {"splits": 4, "bn": 128}),
-    ("dense8192", "bf16", 64, 8, "dstep"): (60.3e6, {"row_bm": 64}),
     ("uneven", "bf16", None, None, "product"): (875.5e6, {}),
 }
 
@@ -631,7 +631,7 @@ def main():
     ctl = 3 if weights is not None else 0  # lean learned step
     opts = S.snmf_default_options(precision=prec, formulation=form, batch=args.batch, max_iter=args.max_iter,
                                   tol=args.tol, nonmonotone_M=10, autotune=args.autotune,
-                                  tune_cache=args.tune_cache, step_controller=ctl)
+                                  tune_cache=args.tune_cache, step_controller=ctl, x_parts=args.x_parts)
     stream = torch.cuda.current_stream(dev)
     h = S.snmf_create(S.dense_matrix(A), args.r, opts, stream=stream, mlp_weights=weights)
     tuning = None
@@ -700,22 +700,27 @@ def main():
                 "ms_per_launch": ms_kern, "ms_per_product_with_epilogue": ms_prod}
     elif args.precision == "bf16":
         workload_key = "dense8192" if args.n == 8192 else None
-        # tensor work: the hi and lo parts of X each take one BF16 MMA pass
-        tflops = 2 * flops / (ms_kern * 1e-3) / 1e12
+        # the method's flops 2 n^2 N; the tensor pipes execute x_parts times that (X as hi + lo
+        # BF16 parts takes two MMA passes)
+        tflops = flops / (ms_kern * 1e-3) / 1e12
         ridge = peaks["bf16_tflops"] * 1e12 / (peaks["hbm_gbs"] * 1e9)
-        intensity = 2 * flops / alg_bytes
+        intensity = args.x_parts * flops / alg_bytes
         tensor_bound = intensity > ridge
         roof = {"bound": "tensor" if tensor_bound else "hbm",
-                "kernel": "k_split_x + k_gemm_tc (tcgen05 BF16, X as hi+lo BF16 parts)",
+                "kernel": "k_split_x + k_gemm_tc (tcgen05 BF16, X as %s, split-K reduced and epilogue fused "
+                          "in the kernel)" % ("hi+lo BF16 parts" if args.x_parts == 2 else "one BF16 part"),
                 "achieved": tflops if tensor_bound else aw_gbs,
                 "peak": peaks["bf16_tflops"] if tensor_bound else peaks["hbm_gbs"],
                 "unit": "TFLOP/s" if tensor_bound else "GB/s",
                 "frac": (tflops / peaks["bf16_tflops"]) if tensor_bound else (aw_gbs / peaks["hbm_gbs"]),
-                "traffic": profiled_traffic((workload_key, args.precision, args.r, args.batch, "product"), tuning),
+                "traffic": profiled_traffic((workload_key, args.precision, args.r, args.batch, "product",
+                                             args.x_parts), tuning),
                 "peak_source": peak_kind + (" bf16_tflops (burst cuBLAS)" if tensor_bound else " hbm_gbs (burst copy)"),
                 "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
+                "tensor_pipe_tflops": args.x_parts * tflops,
                 "aw_gbs": aw_gbs, "aw_hbm_frac": aw_gbs / peaks["hbm_gbs"],
-                "alg_bytes_per_launch": alg_bytes, "flops_per_launch": 2 * flops,
+                "alg_bytes_per_launch": alg_bytes, "flops_per_launch": flops,
+                "flops_note": "method flops 2 n^2 N; the tensor pipes execute x_parts x that",
                 "ms_per_launch": ms_kern, "ms_per_product_with_epilogue": ms_prod}
     else:
         roof = {"bound": "alu", "kernel": "k_gemm_dense<double>", "achieved": achieved_tflops, "peak": None,
@@ -728,18 +733,22 @@ def main():
     if form == S.SNMF_PENALTY and args.r <= 64:
         ms_d, ms_u = S.snmf_profile_steps(h, 20)
         K = opts.inner_iters
-        fb4 = n * N * esz
-        nd = 6 + (1 if ctl == 1 else 0)  # D step: reads X, g, B; writes Z, g(Z), D (+ D2)
-        for name, ms_k, nbuf in (("dstep", ms_d, nd), ("update", ms_u, 8)):  # update: 6 reads, 2 writes
-            gb = nbuf * fb4 / (ms_k * 1e-3) / 1e9
-            kernels[name] = {"bound": "hbm", "kernel": "k_rowgemm<%s>" % ("OP_ZSTEP, EPI_DIR" if name == "dstep"
-                                                                          else "OP_UPD, EPI_GRAD"),
+        # the library reports which row-kernel body runs and the arrays each launch moves
+        sc = S.snmf_step_config(h)
+        body = {0: "k_rowgemm (general)", 1: "k_rowtile (shared-memory tile body)",
+                2: "k_rowfuse (Z and D recomputed, not stored)"}[sc["body"]]
+        names = {"dstep": ("k_rowfuse_dstep" if sc["body"] == 2 else "k_rowgemm<OP_ZSTEP, EPI_DIR>"),
+                 "update": ("k_rowfuse_update" if sc["body"] == 2 else "k_rowgemm<OP_UPD, EPI_GRAD>")}
+        for name, ms_k, nbytes in (("dstep", ms_d, sc["dstep_bytes"]), ("update", ms_u, sc["update_bytes"])):
+            gb = nbytes / (ms_k * 1e-3) / 1e9
+            kernels[name] = {"bound": "hbm", "kernel": names[name], "body": body,
+                             "rows_per_cta": sc["rows_per_cta"],
                              "achieved": gb, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                              "frac": gb / peaks["hbm_gbs"], "peak_source": peak_kind,
                              "traffic": profiled_traffic(("dense8192" if args.n == 8192 else None, args.precision,
-                                                          args.r, args.batch, name), tuning),
-                             "alg_bytes_per_launch": nbuf * fb4, "ms_per_launch": ms_k,
-                             "launches_per_outer_iteration": 2 * K,
+                                                          args.r, args.batch, name, sc["body"]), tuning),
+                             "alg_bytes_per_launch": nbytes, "arrays_per_launch": nbytes // (n * N * esz),
+                             "ms_per_launch": ms_k, "launches_per_outer_iteration": 2 * K,
                              "note": "working set of one launch fits in L2, as inside the iteration"}
         per_iter = {"product": 2 * ms_kern, "dstep": 2 * K * ms_d, "update": 2 * K * ms_u}
         dominant = max(per_iter, key=per_iter.get)
@@ -815,7 +824,7 @@ def main():
             # share of the gain from batching and storage precision
             ob = S.snmf_default_options(precision=prec, formulation=form, batch=args.batch, max_iter=args.max_iter,
                                         tol=args.tol, nonmonotone_M=10, autotune=args.autotune,
-                                        tune_cache=args.tune_cache, step_controller=0)
+                                        tune_cache=args.tune_cache, step_controller=0, x_parts=args.x_parts)
             hb = S.snmf_create(S.dense_matrix(A), args.r, ob, stream=stream)
             bt = []
             for k in range(2):

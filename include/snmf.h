@@ -62,8 +62,12 @@ enum { SNMF_DENSE = 0, SNMF_CSR = 1, SNMF_DENSE_BATCH = 2 };
 enum { SNMF_F64 = 0, SNMF_F32 = 1, SNMF_BF16 = 2, SNMF_FP8 = 3 };
 /* where a matrix passed to snmf_create lives */
 enum { SNMF_ON_DEVICE = 0, SNMF_ON_HOST = 1 };
-/* formulations */
-enum { SNMF_PENALTY = 0, SNMF_DIRECT = 1 };
+/* formulations: the penalty form (Sec. 2.1, Eq. (3)), the single-variable objective (Eq. (2)),
+   and the naive symmetric use of Algorithm 1 that Sec. 2.1 describes before the penalty form
+   (the W block with H = W^T held fixed and lambda = 0, then H <- W^T; the paper reports that it
+   performs poorly, which the rank-one case shows: the block solve w <- A w / ||w||^2 alternates
+   between two norms) */
+enum { SNMF_PENALTY = 0, SNMF_DIRECT = 1, SNMF_NAIVE = 2 };
 /* BB step variants */
 enum { SNMF_BB1 = 0, SNMF_BB2 = 1 };
 
@@ -104,7 +108,9 @@ typedef struct {
  * Solver options.  snmf_default_options fills the documented defaults.
  */
 typedef struct {
-  int32_t formulation;     /* SNMF_PENALTY (Sec. 2.1, default) | SNMF_DIRECT (Eq. (2))       */
+  int32_t formulation;     /* SNMF_PENALTY (Sec. 2.1, default) | SNMF_DIRECT (Eq. (2)) |
+                              SNMF_NAIVE (Sec. 2.1: W block with H = W^T, then H <- W^T; no
+                              lambda, no graph term, plain BB step; Ht in/out is W)         */
   int32_t precision;       /* SNMF_F64 | SNMF_F32 (default) | SNMF_BF16 | SNMF_FP8: storage of A
                               for the A*X products; accumulation is FP32 (FP64 in SNMF_F64) and
                               objective, line search and BB inner products are FP64 throughout.

@@ -30,8 +30,10 @@ from .snmpbb import (  # noqa: F401
     nmpbb,
     snmpbb_direct,
     snmpbb_penalty,
+    snmpbb_naive,
     resolve_lambda,
     svd_init,
 )
 from .philox import philox4x32, philox_uniform, philox_gaussian  # noqa: F401
 from .lai import lai_sketch  # noqa: F401
+from . import mlp  # noqa: F401

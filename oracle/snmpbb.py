@@ -357,6 +357,46 @@ def snmpbb_direct(A, W0, opts: Options, L=None, keep_iterates=False):
     return W, info
 
 
+def snmpbb_naive(A, W0, opts: Options, keep_iterates=False):
+    """The naive symmetric use of NMPBB that the paper describes before the penalty form
+    (Sec. 2.1): each outer iteration runs Algorithm 1 on the W block of 1/2 ||V - W H||^2 with
+    H = W^T held fixed (the NMF objective: no penalty term, rho_0 = ||W^T W||_2), then sets
+    H <- W^T, i.e. Ht = W.
+
+    Stopping reading (the paper gives none for this variant): the projected gradient of the
+    W block at (W, H = W^T) relative to its value at W_0, after every outer iteration.
+    Returns (W, info) with one iterate record per outer iteration."""
+    zero = dataclasses.replace(opts, lambda_sym=0.0, gamma=0.0)
+    mode = opts.objective
+    W = np.array(W0, dtype=np.float64, copy=True)
+
+    def pg_of(W):
+        return float(np.linalg.norm(projected_gradient(W, penalty_grad_W(A, W, W, 0.0))))
+
+    pg0 = pg_of(W)
+    outer = []
+    ls_fail = 0
+    pg = pg0
+    for it in range(1, opts.max_iter + 1):
+        Hfix = W
+        rho = spectral_norm(Hfix.T @ Hfix, opts.power_iters)
+        W, _, iw = nmpbb(lambda X: penalty_objective(A, X, Hfix, 0.0, 0.0, None, mode),
+                         lambda X: penalty_grad_W(A, X, Hfix, 0.0),
+                         W, lambda X: rho, opts.inner_iters, zero, None, keep_iterates)
+        ls_fail += iw["ls_fail"]
+        pg = pg_of(W)
+        rec = dict(i=it, rho=rho, pg=pg, w_trace=iw["trace"], f=penalty_objective(A, W, W, 0.0, 0.0, None, mode))
+        if keep_iterates:
+            rec["W"] = W.copy()
+        outer.append(rec)
+        if pg <= opts.tol * pg0:
+            break
+    Ad = dense_of(A)
+    info = dict(trace=outer, iters=len(outer), pg0=pg0, pg=pg, ls_fail=ls_fail,
+                residual=float(np.linalg.norm(Ad - W @ W.T) / np.linalg.norm(Ad)))
+    return W, info
+
+
 def snmpbb_penalty(A, W0, Ht0, opts: Options, L=None, keep_iterates=False):
     """SNMPBB / Graph-SNMPBB (Sec. 2.1-2.2): alternate Algorithm 1 over the W block
     (rho_0 = ||H H^T||_2 = ||Ht^T Ht||_2, lambda omitted, Eq. (2.11)) and the H block

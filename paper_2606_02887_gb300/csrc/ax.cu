@@ -10,6 +10,8 @@
 //                  partials of <P1, A X> and <P2, A X> (e.g. tr(W^T A W)).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace snmf {
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(256)
 k_ax_finish(int64_t n, int r, int64_t ld, T* __restrict__ Y, const T* __restrict__ ws,
             int splits, double c, const T* __restrict__ X2, const T* __restrict__ P1,
             const T* __restrict__ P2, double* __restrict__ part, int q0, int b,
-            const int* run) {
+            const int* run, int dots_after) {
   __shared__ T sh[32];
   const int j = blockIdx.y;
   const int64_t i0 = (int64_t)blockIdx.x * kRowTile;
@@ -166,9 +168,15 @@ k_ax_finish(int64_t n, int r, int64_t ld, T* __restrict__ Y, const T* __restrict
       } else {
         y = Y[idx];
       }
-      if (P1) d1 += P1[idx] * y;
-      if (P2) d2 += P2[idx] * y;
+      if (!dots_after) {
+        if (P1) d1 += P1[idx] * y;
+        if (P2) d2 += P2[idx] * y;
+      }
       if (X2) y = y + (T)c * X2[idx];
+      if (dots_after) {
+        if (P1) d1 += P1[idx] * y;
+        if (P2) d2 += P2[idx] * y;
+      }
       Y[idx] = y;
     }
   }
@@ -261,17 +269,90 @@ int launch_ax(const AxArgs& a, int tdtype, int64_t n, int cols, int64_t ld, cons
 
 int launch_ax_finish_impl(int tdtype, const Dims& d, void* Y, const void* ws, int splits,
                           double c, const void* X2, const void* P1, const void* P2,
-                          double* part, int q0, const int* run, cudaStream_t s) {
+                          double* part, int q0, const int* run, cudaStream_t s, int dots_after) {
   dim3 grid(cdiv64(d.n, kRowTile), d.b);
   if (tdtype == 0)
     k_ax_finish<double><<<grid, 256, 0, s>>>(d.n, d.r, d.ld, (double*)Y, (const double*)ws, splits,
                                              c, (const double*)X2, (const double*)P1,
-                                             (const double*)P2, part, q0, d.b, run);
+                                             (const double*)P2, part, q0, d.b, run, dots_after);
   else
     k_ax_finish<float><<<grid, 256, 0, s>>>(d.n, d.r, d.ld, (float*)Y, (const float*)ws, splits, c,
                                             (const float*)X2, (const float*)P1, (const float*)P2,
-                                            part, q0, d.b, run);
+                                            part, q0, d.b, run, dots_after);
   return grid.x;
+}
+
+// ---------------------------------------------------------------------------------------
+// The paper's normalized graph Laplacian L = I - D^-1/2 A D^-1/2, d_i = sum_j a_ij (Sec. 2.2):
+// the scaling s_i = d_i^-1/2 (0 for rows of zero degree) and the operator -D^-1/2 A D^-1/2
+// in the factor type, applied as L X = X + (-D^-1/2 A D^-1/2) X.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+template <typename TA>
+__global__ void k_degree_scale(int kind, const TA* __restrict__ A, int64_t lda, const int32_t* __restrict__ rowptr,
+                               int64_t n, double* __restrict__ s) {
+  // one warp per row, FP64 sum in a fixed order (lane stride, then a fixed butterfly)
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= n) return;
+  double acc = 0.0;
+  if (kind == AX_DENSE) {
+    for (int64_t k = lane; k < n; k += 32) acc += (double)ld_a(A + i * lda + k);
+  } else {
+    for (int64_t e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) acc += (double)A[e];
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) s[i] = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
+}
+
+template <typename TA, typename T>
+__global__ void k_scaled_neg_csr(const TA* __restrict__ vals, const int32_t* __restrict__ rowptr,
+                                 const int32_t* __restrict__ colidx, int64_t n, const double* __restrict__ s,
+                                 T* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= n) return;
+  for (int64_t e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32)
+    out[e] = (T)(-(s[i] * (double)vals[e] * s[colidx[e]]));
+}
+
+template <typename TA, typename T>
+__global__ void k_scaled_neg_dense(const TA* __restrict__ A, int64_t lda, int64_t n, const double* __restrict__ s,
+                                   T* __restrict__ out) {
+  const int64_t total = n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, k = e % n;
+    out[e] = (T)(-(s[i] * (double)ld_a(A + i * lda + k) * s[k]));
+  }
+}
+
+}  // namespace
+
+void launch_normalized_adjacency(const AxArgs& a, int tdtype, int64_t n, double* s, void* out, cudaStream_t st) {
+  const int rb = cdiv64(n, 8);
+  if (a.kind == AX_DENSE) {
+    const int blocks = (int)std::min<int64_t>(cdiv64(n * n, 256), 152 * 32);
+    if (a.a_dtype == 0) {
+      k_degree_scale<double><<<rb, 256, 0, st>>>(AX_DENSE, (const double*)a.A, a.lda, nullptr, n, s);
+      if (tdtype == 0) k_scaled_neg_dense<double, double><<<blocks, 256, 0, st>>>((const double*)a.A, a.lda, n, s, (double*)out);
+      else k_scaled_neg_dense<double, float><<<blocks, 256, 0, st>>>((const double*)a.A, a.lda, n, s, (float*)out);
+    } else {
+      k_degree_scale<float><<<rb, 256, 0, st>>>(AX_DENSE, (const float*)a.A, a.lda, nullptr, n, s);
+      if (tdtype == 0) k_scaled_neg_dense<float, double><<<blocks, 256, 0, st>>>((const float*)a.A, a.lda, n, s, (double*)out);
+      else k_scaled_neg_dense<float, float><<<blocks, 256, 0, st>>>((const float*)a.A, a.lda, n, s, (float*)out);
+    }
+    return;
+  }
+  if (a.v_dtype == 0) {
+    k_degree_scale<double><<<rb, 256, 0, st>>>(AX_CSR, (const double*)a.vals, 0, a.rowptr, n, s);
+    if (tdtype == 0) k_scaled_neg_csr<double, double><<<rb, 256, 0, st>>>((const double*)a.vals, a.rowptr, a.colidx, n, s, (double*)out);
+    else k_scaled_neg_csr<double, float><<<rb, 256, 0, st>>>((const double*)a.vals, a.rowptr, a.colidx, n, s, (float*)out);
+  } else {
+    k_degree_scale<float><<<rb, 256, 0, st>>>(AX_CSR, (const float*)a.vals, 0, a.rowptr, n, s);
+    if (tdtype == 0) k_scaled_neg_csr<float, double><<<rb, 256, 0, st>>>((const float*)a.vals, a.rowptr, a.colidx, n, s, (double*)out);
+    else k_scaled_neg_csr<float, float><<<rb, 256, 0, st>>>((const float*)a.vals, a.rowptr, a.colidx, n, s, (float*)out);
+  }
 }
 
 }  // namespace snmf

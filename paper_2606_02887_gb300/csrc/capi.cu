@@ -65,6 +65,8 @@ struct snmf_ctx {
   int32_t* L_rowptr = nullptr;
   int32_t* L_colidx = nullptr;
   void* L_vals = nullptr;
+  bool L_implicit = false;  // L = I - D^-1/2 A D^-1/2: h->L holds -D^-1/2 A D^-1/2, applied as X + (h->L) X
+  double* L_scale = nullptr;  // d_i^-1/2
   // LAI sketch
   bool lai = false;
   LaiOp lai_op{};
@@ -220,9 +222,11 @@ int product_kernel(snmf_ctx* h, const AxArgs& op, const void* X, void* Y, const 
 }
 
 
-// Y = op X (+ c X2), dots <P1, op X> -> part q0, <P2, op X> -> q0+1; returns slot count.
+// Y = op X (+ c X2), dots <P1, op X> -> part q0, <P2, op X> -> q0+1 (dots_after: of the final
+// Y); returns slot count.
 int ax_apply(snmf_ctx* h, const AxArgs& op, bool use_lai, const void* X, void* Y, double c,
-             const void* X2, const void* P1, const void* P2, double* part, const int* run) {
+             const void* X2, const void* P1, const void* P2, double* part, const int* run,
+             int dots_after = 0) {
   Dims d = dims(h);
   h->ax_count++;
   if (use_lai) {
@@ -232,7 +236,7 @@ int ax_apply(snmf_ctx* h, const AxArgs& op, bool use_lai, const void* X, void* Y
   if (op.kind == AX_DENSE && op.a_dtype == 2 && !op.accurate) epi = tc_epilogue(h, Y, c, X2, P1, P2, part);
   const int splits = product_kernel(h, op, X, Y, run, &epi);
   if (splits == 0) return (int)((h->n + kRowTile - 1) / kRowTile);  // epilogue done in the product
-  return launch_ax_finish_impl(h->tdtype, d, Y, h->ws, splits, c, X2, P1, P2, part, 0, run, h->s);
+  return launch_ax_finish_impl(h->tdtype, d, Y, h->ws, splits, c, X2, P1, P2, part, 0, run, h->s, dots_after);
 }
 
 int ax_A(snmf_ctx* h, const void* X, void* Y, double c, const void* X2, const void* P1,
@@ -240,8 +244,11 @@ int ax_A(snmf_ctx* h, const void* X, void* Y, double c, const void* X2, const vo
   return ax_apply(h, h->A, h->lai, X, Y, c, X2, P1, P2, part, run);
 }
 
+// Y = L X with <P1, L X>, <P2, L X> partials; the paper's normalized Laplacian as
+// X + (-D^-1/2 A D^-1/2) X, an explicit CSR L directly.
 int ax_L(snmf_ctx* h, const void* X, void* Y, const void* P1, const void* P2, double* part,
          const int* run) {
+  if (h->L_implicit) return ax_apply(h, h->L, false, X, Y, 1.0, X, P1, P2, part, run, 1);
   return ax_apply(h, h->L, false, X, Y, 0.0, nullptr, P1, P2, part, run);
 }
 
@@ -315,11 +322,11 @@ snmf_status time_steps(snmf_ctx* h, int iters, double* ms_dstep, double* ms_upda
   au.ctl_mode = CTL_UPD_W;
   au.Zin = h->buf[B_Z]; au.Din = h->buf[B_D]; au.Din2 = h->buf[B_AD];
   auto dstep = [&] {
-    if (h->use_fuse) launch_rowfuse_dstep(ad, h->row_bm, h->s);
+    if (h->use_fuse) launch_rowfuse_dstep(ad, h->row_bm, nc, h->s);
     else launch_rowgemm(td, OP_ZSTEP, EPI_DIR, ad, h->s, nc);
   };
   auto update = [&] {
-    if (h->use_fuse) launch_rowfuse_update(au, h->row_bm, h->s);
+    if (h->use_fuse) launch_rowfuse_update(au, h->row_bm, nc, h->s);
     else launch_rowgemm(td, OP_UPD, EPI_GRAD, au, h->s);
   };
   cudaEvent_t e[4];
@@ -354,7 +361,7 @@ snmf_status autotune_product(snmf_ctx* h) {
   const std::string dev = tune_device_key();
   TuneEntry e;
   const bool tune_rows =
-      (!h->use_tile || h->use_fuse) && h->tdtype == 1 && h->opt.formulation == SNMF_PENALTY && h->r <= 64;
+      (!h->use_tile || h->use_fuse) && h->tdtype == 1 && h->opt.formulation != SNMF_DIRECT && h->r <= 64;
   // rows per CTA offered to the search: the fused kernels' heights, else the general kernel's
   std::vector<int> bms;
   if (h->use_fuse) bms = h->r == 16 ? std::vector<int>{128, 256} : std::vector<int>{128, 64};
@@ -460,7 +467,7 @@ snmf_status autotune_product(snmf_ctx* h) {
 // ----------------------------------------------------------------------------
 // penalty form (Sec. 2.1-2.2): one block of Algorithm 1 over Xvar with Xfix fixed
 // ----------------------------------------------------------------------------
-void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
+void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P, bool naive = false) {
   const Dims d = dims(h);
   const int td = h->tdtype;
   void* X = h->buf[xv];
@@ -495,16 +502,19 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
   const int K = h->opt.inner_iters;
   const bool fused_q = h->r <= 64 && !gr;
   if (h->use_fuse && !gr) {
-    // D step (g(Z) and the line search) and the update recomputing Z and D (rowfuse.cu)
+    // D step (g(Z) and the line search) and the update recomputing Z and D (rowfuse.cu);
+    // the learned step with fallback (controller 1) carries the plain BB direction as well
+    const int nc = h->opt.step_controller == 1 ? 2 : 1;
     for (int k = 0; k < K; ++k) {
       RowArgs a = row_base(h, &P);
       a.X = X; a.g_in = h->buf[B_G]; a.B = h->buf[B_B]; a.gZout = h->buf[B_GZ];
       a.ctl_mode = CTL_LS;
-      launch_rowfuse_dstep(a, h->row_bm, h->s);
+      launch_rowfuse_dstep(a, h->row_bm, nc, h->s);
       RowArgs u = row_base(h, &P);
       u.Xout = X; u.gout = h->buf[B_G]; u.gZold = h->buf[B_GZ]; u.B = h->buf[B_B];
-      u.ctl_mode = is_w ? CTL_UPD_W : (k == K - 1 ? CTL_UPD_H_LAST : CTL_UPD_H);
-      launch_rowfuse_update(u, h->row_bm, h->s);
+      u.ctl_mode = is_w ? (naive && k == K - 1 ? CTL_UPD_W_LAST_NAIVE : CTL_UPD_W)
+                        : (k == K - 1 ? CTL_UPD_H_LAST : CTL_UPD_H);
+      launch_rowfuse_update(u, h->row_bm, nc, h->s);
     }
     return;
   }
@@ -547,7 +557,8 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P) {
       a.Xold = X; a.gold = h->buf[B_G];
       a.Zold = h->buf[B_Z]; a.gZold = h->buf[B_GZ];
       a.Xout = X;
-      a.ctl_mode = is_w ? CTL_UPD_W : (k == K - 1 ? CTL_UPD_H_LAST : CTL_UPD_H);
+      a.ctl_mode = is_w ? (naive && k == K - 1 ? CTL_UPD_W_LAST_NAIVE : CTL_UPD_W)
+                        : (k == K - 1 ? CTL_UPD_H_LAST : CTL_UPD_H);
       if (gr) {
         launch_xupd(td, d, h->buf[B_Z], h->buf[B_D], h->buf[B_XN], nullptr, nullptr, nullptr,
                     h->ctl, h->pclip, h->s);
@@ -580,6 +591,17 @@ void pen_init(snmf_ctx* h, const Params& P) {
 void pen_iteration(snmf_ctx* h, const Params& P) {
   pen_block(h, B_W, B_HT, true, P);
   pen_block(h, B_HT, B_W, false, P);
+  launch_any_active(h->ctl, h->b, h->run, nullptr, h->s);
+}
+
+// The naive symmetric variant (Sec. 2.1, before the penalty form): Algorithm 1 on the W block
+// with H = W^T fixed (lambda = 0), then H <- W^T.  The start needs nothing beyond the state
+// the host sets; one outer iteration is the W block and the copy.
+void naive_init(snmf_ctx* h) { launch_any_active(h->ctl, h->b, h->run, nullptr, h->s); }
+
+void naive_iteration(snmf_ctx* h, const Params& P) {
+  pen_block(h, B_W, B_HT, true, P, true);
+  cudaMemcpyAsync(h->buf[B_HT], h->buf[B_W], (size_t)h->n * h->N * h->esz, cudaMemcpyDeviceToDevice, h->s);
   launch_any_active(h->ctl, h->b, h->run, nullptr, h->s);
 }
 
@@ -692,15 +714,16 @@ void dir_final(snmf_ctx* h, const Params& P) {
 int tile_rule(const snmf_ctx* h) {
   const int64_t tr = h->tdtype == 0 ? 64 : 128;
   const int64_t tiles = (h->n + tr - 1) / tr * h->b;
-  return (h->r <= 32 && h->opt.formulation == SNMF_PENALTY && h->opt.step_controller != 2 && !h->graph &&
+  return (h->r <= 32 && h->opt.formulation != SNMF_DIRECT && h->opt.step_controller != 2 && !h->graph &&
           tiles >= 2 * 152) ? 1 : 0;
 }
 
 // D step and update through rowfuse.cu: FP32 factors, r in {16, 32, 64}, penalty form, the
-// plain or the lean learned step (one direction per step), no graph term.
+// plain step or a learned step (with or without the fallback direction; not record mode), no
+// graph term.
 int fuse_rule(const snmf_ctx* h) {
-  return (rowfuse_supported(h->tdtype, h->r) && h->opt.formulation == SNMF_PENALTY &&
-          (h->opt.step_controller == 0 || h->opt.step_controller == 3) && !h->graph) ? 1 : 0;
+  return (rowfuse_supported(h->tdtype, h->r) && h->opt.formulation != SNMF_DIRECT &&
+          h->opt.step_controller != 2 && !h->graph) ? 1 : 0;
 }
 
 snmf_status alloc_buffers(snmf_ctx* h) {
@@ -775,7 +798,7 @@ snmf_status check_device_csr(snmf_ctx* h, const int32_t* rowptr, const int32_t* 
 bool valid_enum(int v, int lo, int hi) { return v >= lo && v <= hi; }
 
 snmf_status validate_options(const snmf_options& o) {
-  if (!valid_enum(o.formulation, 0, 1) || !valid_enum(o.precision, 0, 3) ||
+  if (!valid_enum(o.formulation, 0, 2) || !valid_enum(o.precision, 0, 3) ||
       !valid_enum(o.bb_variant, 0, 1))
     return SNMF_ERR_ARG;
   if (o.batch < 1 || o.nonmonotone_M < 0 || o.nonmonotone_M > kMaxHist || o.max_ls < 1 ||
@@ -875,6 +898,8 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   }
   if (o.step_controller && (o.formulation != SNMF_PENALTY || r > 64))
     return fail(nullptr, SNMF_ERR_ARG, "the step controller needs the penalty form and r <= 64");
+  if (o.formulation == SNMF_NAIVE && o.step_controller)
+    return fail(nullptr, SNMF_ERR_ARG, "the naive variant runs the plain BB step");
 
   h = new snmf_ctx();
   h->opt = o;
@@ -1066,6 +1091,7 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   h->sumA = sums[1];
   if (!std::isfinite(h->normA2)) { h->err = "A has NaN/Inf entries"; return bail(SNMF_ERR_NUMERIC); }
   h->lam = o.lambda_sym >= 0.0 ? o.lambda_sym : 0.01 * std::sqrt(h->normA2);
+  if (o.formulation == SNMF_NAIVE) h->lam = 0.0;  // the naive variant has no penalty term
   if (o.autotune) {
     const snmf_status ts = autotune_product(h);
     if (ts != SNMF_OK) return bail(ts);
@@ -1077,6 +1103,8 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
 
 snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma) {
   if (!h) return SNMF_ERR_STATE;
+  if (h->opt.formulation == SNMF_NAIVE && gamma != 0.0)
+    return fail(h, SNMF_ERR_ARG, "the naive variant has no H block for the graph term");
   if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
   if (!(gamma >= 0.0)) return fail(h, SNMF_ERR_ARG, "gamma must be >= 0");
   if (gamma == 0.0) {
@@ -1088,7 +1116,35 @@ snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma
     h->nrow = rowgemm_slots(dims(h), h->tdtype, h->use_tile, h->row_bm);
     return SNMF_OK;
   }
-  if (!L) return fail(h, SNMF_ERR_ARG, "implicit Laplacian (L == NULL) not available in this build");
+  if (!L) {
+    // the paper's L = I - D^-1/2 A D^-1/2 (Sec. 2.2), from the handle's own A
+    if (h->lai) return fail(h, SNMF_ERR_STATE, "the implicit Laplacian needs A itself, not a LAI sketch");
+    if (h->kind == AX_DENSE && h->A.a_dtype > 1)
+      return fail(h, SNMF_ERR_ARG, "the implicit Laplacian needs A stored in F32 or F64 precision");
+    const int64_t n = h->n;
+    const size_t fe = h->kind == AX_DENSE ? (size_t)n * n : (size_t)std::max<int64_t>(h->A.lda, 1);
+    cudaFree(h->L_rowptr); cudaFree(h->L_colidx); cudaFree(h->L_vals); cudaFree(h->L_scale);
+    h->L_rowptr = nullptr; h->L_colidx = nullptr; h->L_vals = nullptr; h->L_scale = nullptr;
+    CK(cudaMalloc(&h->L_scale, (size_t)n * sizeof(double)));
+    CK(cudaMalloc(&h->L_vals, fe * h->esz));
+    launch_normalized_adjacency(h->A, h->tdtype, n, h->L_scale, h->L_vals, h->s);
+    CK(cudaGetLastError());
+    h->L = AxArgs{};
+    if (h->kind == AX_DENSE) {
+      h->L.kind = AX_DENSE;
+      h->L.A = h->L_vals;
+      h->L.lda = n;
+      h->L.a_dtype = h->tdtype;
+    } else {
+      h->L.kind = AX_CSR;
+      h->L.rowptr = h->A.rowptr;  // A's pattern (owned by the handle or borrowed for its lifetime)
+      h->L.colidx = h->A.colidx;
+      h->L.vals = h->L_vals;
+      h->L.v_dtype = h->tdtype;
+      h->L.lda = h->A.lda;
+    }
+    h->L_implicit = true;
+  } else {
   if (L->kind != SNMF_CSR) return fail(h, SNMF_ERR_ARG, "L must be CSR");
   if (L->n != h->n) return fail(h, SNMF_ERR_ARG, "L size mismatch");
   if (L->dtype != SNMF_F64 && L->dtype != SNMF_F32) return fail(h, SNMF_ERR_ARG, "L dtype");
@@ -1127,6 +1183,9 @@ snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma
   h->L.vals = h->L_vals;
   h->L.v_dtype = L->dtype == SNMF_F64 ? 0 : 1;
   h->L.lda = nnz;
+  h->L_implicit = false;
+  }
+  const int64_t n = h->n;
   h->graph = true;
   h->gamma = gamma;
   h->exec_form = -1;
@@ -1163,6 +1222,8 @@ snmf_status snmf_set_graph_reg(snmf_handle h, const snmf_matrix* L, double gamma
       CK(put(v, h->buf[B_LZ]));
       launch_ax(h->L, h->tdtype, n, 1, 1, h->buf[B_LZ], h->buf[B_LD], nullptr, 0, nullptr, h->s);
       CK(get(h->buf[B_LD], &w));
+      if (h->L_implicit)
+        for (int64_t i = 0; i < n; ++i) w[i] += v[i];  // L v = v + (-D^-1/2 A D^-1/2) v
       if (it == h->opt.power_iters) {  // Rayleigh quotient v^T L v
         lnorm = 0.0;
         for (int64_t i = 0; i < n; ++i) lnorm += v[i] * w[i];
@@ -1208,9 +1269,10 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
     const double upper = h->opt.init_scale * std::sqrt(std::max(mean, 0.0) / h->r);
     launch_philox_uniform(h->tdtype, h->buf[B_W], h->n, h->N, h->N, h->opt.seed, upper, h->s);
   }
-  const bool pen = h->opt.formulation == SNMF_PENALTY;
+  const bool naive = h->opt.formulation == SNMF_NAIVE;
+  const bool pen = h->opt.formulation == SNMF_PENALTY || naive;  // the naive variant runs the W block
   if (pen) {
-    if (Ht) CK(cudaMemcpyAsync(h->buf[B_HT], Ht, fbytes, kin, h->s));
+    if (Ht && !naive) CK(cudaMemcpyAsync(h->buf[B_HT], Ht, fbytes, kin, h->s));
     else CK(cudaMemcpyAsync(h->buf[B_HT], h->buf[B_W], fbytes, cudaMemcpyDeviceToDevice, h->s));
   }
   // control state: restarts active; second array = "all live" view for final passes
@@ -1227,15 +1289,15 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
   CK(cudaMemcpyAsync(h->recompute, &zero, sizeof(int), cudaMemcpyHostToDevice, h->s));
   const Params P = make_params(h);
   // capture init / iteration / final once per configuration (buffers are fixed)
-  const int form = pen ? 0 : 1;
+  const int form = naive ? 2 : (pen ? 0 : 1);
   if (h->exec_form != form) {
     for (int g = 0; g < 3; ++g) {
       if (h->exec[g]) { cudaGraphExecDestroy(h->exec[g]); h->exec[g] = nullptr; }
       cudaGraph_t gr;
       CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
       h->ax_count = 0;
-      if (g == 0) { if (pen) pen_init(h, P); else dir_init(h, P); }
-      else if (g == 1) { if (pen) pen_iteration(h, P); else dir_iteration(h, P); }
+      if (g == 0) { if (naive) naive_init(h); else if (pen) pen_init(h, P); else dir_init(h, P); }
+      else if (g == 1) { if (naive) naive_iteration(h, P); else if (pen) pen_iteration(h, P); else dir_iteration(h, P); }
       else { if (pen) pen_final(h, P); else dir_final(h, P); }
       CK(cudaStreamEndCapture(h->s, &gr));
       size_t nn = 0;
@@ -1446,7 +1508,7 @@ snmf_status snmf_profile_steps(snmf_handle h, int iters, double* ms_dstep, doubl
   if (!h) return SNMF_ERR_STATE;
   if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
   if (iters < 1) return fail(h, SNMF_ERR_ARG, "iters must be >= 1");
-  if (h->opt.formulation != SNMF_PENALTY || h->graph || h->r > 64)
+  if (h->opt.formulation == SNMF_DIRECT || h->graph || h->r > 64)
     return fail(h, SNMF_ERR_ARG, "step profiling needs the penalty form without graph term and r <= 64");
   if (!h->have_result) return fail(h, SNMF_ERR_STATE, "run a solve first (the step kernels read its buffers)");
   if (sync_user(h) != SNMF_OK) return SNMF_ERR_CUDA;
@@ -1571,6 +1633,7 @@ snmf_status snmf_destroy(snmf_handle h) {
   cudaFree(h->L_rowptr);
   cudaFree(h->L_colidx);
   cudaFree(h->L_vals);
+  cudaFree(h->L_scale);
   lai_free(h->lai_op);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);

@@ -171,9 +171,16 @@ void launch_csr_check(const int32_t* rowptr, const int32_t* colidx, int64_t n, i
 
 // Epilogue of a product over the restarts of d: Y = sum_s ws[s] (splits > 1),
 // per-restart partials <P1, A X> -> part[slot][j][q0], <P2, A X> -> [q0+1], then
-// Y += c * X2 (when X2 != NULL).  Returns the number of partial slots written.
+// Y += c * X2 (when X2 != NULL); dots_after = 1 takes the partials of the final Y instead.
+// Returns the number of partial slots written.
 int launch_ax_finish_impl(int tdtype, const Dims& d, void* Y, const void* ws, int splits,
                           double c, const void* X2, const void* P1, const void* P2,
-                          double* part, int q0, const int* run_flag, cudaStream_t s);
+                          double* part, int q0, const int* run_flag, cudaStream_t s, int dots_after = 0);
+
+// The paper's normalized Laplacian L = I - D^-1/2 A D^-1/2 (Sec. 2.2) of a dense (FP64/FP32)
+// or CSR A: s[i] = d_i^-1/2 (0 where d_i <= 0, d_i the FP64 row sum) and out = the entries of
+// -D^-1/2 A D^-1/2 in the factor type (dense: n x n with leading dimension n; CSR: the values
+// on A's pattern), so that L X = X + out X.
+void launch_normalized_adjacency(const AxArgs& a, int tdtype, int64_t n, double* s, void* out, cudaStream_t st);
 
 }  // namespace snmf

@@ -119,7 +119,7 @@ __device__ __forceinline__ void row_product(const float* Ts, const float* Gs, in
 // Fixed-order CTA reduction of the 8 partial values, slot write, and the control step of
 // the last CTA of restart j (arrival counter, as in the general row kernel).
 __device__ __forceinline__ void finish_partials(const RowArgs& a, const float (&dq)[8], int j, int slot,
-                                                unsigned per, float (*shq)[8], unsigned* ticket) {
+                                                unsigned per, float (*shq)[8], unsigned* ticket, int nc) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
@@ -141,7 +141,7 @@ __device__ __forceinline__ void finish_partials(const RowArgs& a, const float (&
     if (threadIdx.x == 0) a.counters[j] = 0u;
     if (threadIdx.x < 32)
       fused_control(a.ctl_mode, const_cast<Ctl&>(a.ctl[j]), a.part, (int)per, a.b, a.r, j, a.P, a.G64fix, nullptr,
-                    1);
+                    nc);
   }
 }
 
@@ -153,9 +153,12 @@ __device__ __forceinline__ void load_gram(const RowArgs& a, int j, float* Gs) {
 
 // ---------------------------------------------------------------------------------------
 // D step: q0 <g(Z), D>, q1 ||D||^2, q2 f(Z) - f(X) (trapezoid, exact for the quadratic
-// block), q4 <D G, D>; q3, q5-q7 zero.
+// block), q4 <D G, D>; q3 zero.  NC = 2 (learned step with fallback): D is the proposal's
+// direction (step cand_alpha[0]) and q5 <g(Z), D_1>, q6 ||D_1||^2, q7 <D_1 G, D_1> belong to
+// the plain BB direction D_1 (step cand_alpha[1]); the line search picks one (Ctl::dsel) and
+// the update recomputes that one.  NC = 1: q5-q7 zero, step Ctl::alpha.
 // ---------------------------------------------------------------------------------------
-template <int R, int MR>
+template <int R, int MR, int NC>
 __global__ void __launch_bounds__(256, MR >= 8 ? 2 : 3) k_rowfuse_dstep(RowArgs a) {
   using C = FuseCfg<R, MR>;
   extern __shared__ __align__(16) float fsm[];
@@ -178,7 +181,8 @@ __global__ void __launch_bounds__(256, MR >= 8 ? 2 : 3) k_rowfuse_dstep(RowArgs 
     const float* B = (const float*)a.B;
     float* gZo = (float*)a.gZout;
     const float inv_rho = (float)(1.0 / cj.rho);
-    const float alpha = (float)cj.alpha;
+    const float alpha = (float)(NC == 1 ? cj.alpha : cj.cand_alpha[0]);
+    const float alpha1 = (float)(NC == 1 ? cj.alpha : cj.cand_alpha[1]);
     load_gram<R>(a, j, Gs);
     float v[MR][4];
     {  // Z tile (transposed) for the row product
@@ -201,7 +205,8 @@ __global__ void __launch_bounds__(256, MR >= 8 ? 2 : 3) k_rowfuse_dstep(RowArgs 
     __syncthreads();
     float acc[MR][4];
     row_product<R, MR>(Ts, Gs, tx, ty, acc);
-    // epilogue: g(Z), D, the partial inner products; D kept in acc for <D G, D>
+    // epilogue: g(Z), D, the partial inner products; D kept in acc for <D G, D> (NC = 2:
+    // g(Z) kept in v for the second direction)
 #pragma unroll
     for (int p = 0; p < MR; ++p) {
       const int64_t i = row0 + p;
@@ -218,12 +223,18 @@ __global__ void __launch_bounds__(256, MR >= 8 ? 2 : 3) k_rowfuse_dstep(RowArgs 
           dq[0] += gz[q] * d;
           dq[1] += d * d;
           dq[2] += 0.5f * (z - x) * (gz[q] + gx);
+          if (NC == 2) {
+            const float d1 = dir1(z, gz[q], alpha1);
+            dq[5] += gz[q] * d1;
+            dq[6] += d1 * d1;
+            v[p][q] = d1;
+          }
           acc[p][q] = d;
         }
         st4(gZo + off, make_float4(gz[0], gz[1], gz[2], gz[3]));
       } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
+        for (int q = 0; q < 4; ++q) acc[p][q] = v[p][q] = 0.f;
       }
     }
     __syncthreads();  // every thread is done reading the Z tile
@@ -237,15 +248,27 @@ __global__ void __launch_bounds__(256, MR >= 8 ? 2 : 3) k_rowfuse_dstep(RowArgs 
 #pragma unroll
       for (int q = 0; q < 4; ++q) qq = fmaf(dg[p][q], acc[p][q], qq);
     dq[4] = qq;
+    if (NC == 2) {  // <D_1 G, D_1> of the plain BB direction
+      __syncthreads();
+      store_transposed<R, MR>(Ts, v, tx, ty);
+      __syncthreads();
+      row_product<R, MR>(Ts, Gs, tx, ty, dg);
+      float q1 = 0.f;
+#pragma unroll
+      for (int p = 0; p < MR; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) q1 = fmaf(dg[p][q], v[p][q], q1);
+      dq[7] = q1;
+    }
   }
-  finish_partials(a, dq, j, blockIdx.x, gridDim.x, shq, &ticket);
+  finish_partials(a, dq, j, blockIdx.x, gridDim.x, shq, &ticket, NC);
 }
 
 // ---------------------------------------------------------------------------------------
 // Update: q0 ||P grad f(X')||^2, q1 1/2 <g' - B, X'>, q2 <S,S>, q3 <S,Y>, q4 <Y,Y>,
 // q5 f(X') - f(Z) (trapezoid), q6 zero entries of X'; q7 zero.
 // ---------------------------------------------------------------------------------------
-template <int R, int MR>
+template <int R, int MR, int NC>
 __global__ void __launch_bounds__(256, MR >= 8 ? 2 : 3) k_rowfuse_update(RowArgs a) {
   using C = FuseCfg<R, MR>;
   extern __shared__ __align__(16) float fsm[];
@@ -268,7 +291,9 @@ __global__ void __launch_bounds__(256, MR >= 8 ? 2 : 3) k_rowfuse_update(RowArgs
     const float* gZ = (const float*)a.gZold;
     const float* B = (const float*)a.B;
     const float inv_rho = (float)(1.0 / cj.rho);
-    const float alpha = (float)cj.alpha;
+    // the step of the direction the line search kept: NC = 2 selects the proposal or the
+    // plain BB direction (dsel); the same float as the D step used
+    const float alpha = (float)(NC == 1 ? cj.alpha : cj.cand_alpha[cj.dsel ? 1 : 0]);
     const float pb = (float)cj.phibeta;
     load_gram<R>(a, j, Gs);
     float v[MR][4];
@@ -325,35 +350,41 @@ __global__ void __launch_bounds__(256, MR >= 8 ? 2 : 3) k_rowfuse_update(RowArgs
       st4(g + off, make_float4(go[0], go[1], go[2], go[3]));
     }
   }
-  finish_partials(a, dq, j, blockIdx.x, gridDim.x, shq, &ticket);
+  finish_partials(a, dq, j, blockIdx.x, gridDim.x, shq, &ticket, NC);
 }
 
-template <int R, int MR>
+template <int R, int MR, int NC>
 void launch_pair(int which, const RowArgs& a, cudaStream_t s) {
   using C = FuseCfg<R, MR>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_rowfuse_dstep<R, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
-    cudaFuncSetAttribute(k_rowfuse_update<R, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    cudaFuncSetAttribute(k_rowfuse_dstep<R, MR, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    cudaFuncSetAttribute(k_rowfuse_update<R, MR, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     attr = true;
   }
   dim3 grid((unsigned)((a.n + C::BM - 1) / C::BM), (unsigned)a.b);
-  if (which == 0) k_rowfuse_dstep<R, MR><<<grid, 256, C::smem, s>>>(a);
-  else k_rowfuse_update<R, MR><<<grid, 256, C::smem, s>>>(a);
+  if (which == 0) k_rowfuse_dstep<R, MR, NC><<<grid, 256, C::smem, s>>>(a);
+  else k_rowfuse_update<R, MR, NC><<<grid, 256, C::smem, s>>>(a);
 }
 
-void dispatch(int which, const RowArgs& a, int bm, cudaStream_t s) {
+template <int NC>
+void dispatch_nc(int which, const RowArgs& a, int bm, cudaStream_t s) {
   switch (a.r) {
     case 64:
-      if (bm == 64) launch_pair<64, 4>(which, a, s); else launch_pair<64, 8>(which, a, s);
+      if (bm == 64) launch_pair<64, 4, NC>(which, a, s); else launch_pair<64, 8, NC>(which, a, s);
       break;
     case 32:
-      if (bm == 64) launch_pair<32, 2>(which, a, s); else launch_pair<32, 4>(which, a, s);
+      if (bm == 64) launch_pair<32, 2, NC>(which, a, s); else launch_pair<32, 4, NC>(which, a, s);
       break;
     default:
-      if (bm == 256) launch_pair<16, 4>(which, a, s); else launch_pair<16, 2>(which, a, s);
+      if (bm == 256) launch_pair<16, 4, NC>(which, a, s); else launch_pair<16, 2, NC>(which, a, s);
       break;
   }
+}
+
+void dispatch(int which, const RowArgs& a, int bm, int nc, cudaStream_t s) {
+  if (nc == 2) dispatch_nc<2>(which, a, bm, s);
+  else dispatch_nc<1>(which, a, bm, s);
 }
 
 }  // namespace
@@ -365,8 +396,12 @@ int rowfuse_bm(int r, int bm_req) {
   return bm_req == 64 ? 64 : 128;
 }
 
-void launch_rowfuse_dstep(const RowArgs& a, int bm, cudaStream_t s) { dispatch(0, a, rowfuse_bm(a.r, bm), s); }
+void launch_rowfuse_dstep(const RowArgs& a, int bm, int nc, cudaStream_t s) {
+  dispatch(0, a, rowfuse_bm(a.r, bm), nc, s);
+}
 
-void launch_rowfuse_update(const RowArgs& a, int bm, cudaStream_t s) { dispatch(1, a, rowfuse_bm(a.r, bm), s); }
+void launch_rowfuse_update(const RowArgs& a, int bm, int nc, cudaStream_t s) {
+  dispatch(1, a, rowfuse_bm(a.r, bm), nc, s);
+}
 
 }  // namespace snmf

@@ -6,7 +6,8 @@
 namespace snmf {
 
 // control step fused into the last CTA of a restart (RowArgs::ctl_mode)
-enum { CTL_NONE = 0, CTL_START_W, CTL_START_H, CTL_START_INIT, CTL_LS, CTL_UPD_W, CTL_UPD_H, CTL_UPD_H_LAST };
+enum { CTL_NONE = 0, CTL_START_W, CTL_START_H, CTL_START_INIT, CTL_LS, CTL_UPD_W, CTL_UPD_H, CTL_UPD_H_LAST,
+       CTL_UPD_W_LAST_NAIVE };
 
 // operand of the row GEMM X G: loaded, Z = Proj[X - g/rho], or X' = Proj[Z + phi beta D]
 enum { OP_LOAD = 0, OP_ZSTEP = 1, OP_UPD = 2 };
@@ -54,11 +55,12 @@ struct RowArgs {
 // Row kernels of a step for FP32 penalty blocks with r in {16, 32, 64} (rowfuse.cu): the D step
 // writes g(Z) only (RowArgs X, g_in, B -> gZout; fused line search, ctl_mode CTL_LS) and the
 // update recomputes Z and D from X, g, g(Z) (RowArgs Xout = X and gout = g, updated in place,
-// gZold, B; ctl_mode CTL_UPD_*).  bm: rows per CTA (64 or 128; r = 16: 128 or 256).
+// gZold, B; ctl_mode CTL_UPD_*).  bm: rows per CTA (64 or 128; r = 16: 128 or 256).  nc = 2:
+// the learned step with fallback (the proposal and the plain BB direction, Ctl::cand_alpha).
 bool rowfuse_supported(int tdtype, int r);
 int rowfuse_bm(int r, int bm_req);
-void launch_rowfuse_dstep(const RowArgs& a, int bm, cudaStream_t s);
-void launch_rowfuse_update(const RowArgs& a, int bm, cudaStream_t s);
+void launch_rowfuse_dstep(const RowArgs& a, int bm, int nc, cudaStream_t s);
+void launch_rowfuse_update(const RowArgs& a, int bm, int nc, cudaStream_t s);
 
 void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pair, int npairs,
                  double* gpart, int nchunks, const Ctl* ctl, const int* run, double* G64, void* GT,

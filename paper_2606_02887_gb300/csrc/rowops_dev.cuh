@@ -386,6 +386,8 @@ __device__ void pen_upd_body(Ctl& c, const double* prow, int nrow, int b, int j,
   if (is_h_block) {
     c.pgH2 = pg2;
     if (last) c.iters++;
+  } else if (last) {
+    c.iters++;  // naive variant: the W block is the whole outer iteration
   }
   if (!isfinite(c.f)) { c.nan_seen = 1; c.active = 0; }
 }
@@ -427,6 +429,7 @@ __device__ void fused_control(int mode, Ctl& c, const double* part, int nslots, 
     case CTL_UPD_W: pen_upd_body(c, part, nslots, b, j, P, 0, 0, sh, pc); break;
     case CTL_UPD_H: pen_upd_body(c, part, nslots, b, j, P, 1, 0, sh, pc); break;
     case CTL_UPD_H_LAST: pen_upd_body(c, part, nslots, b, j, P, 1, 1, sh, pc); break;
+    case CTL_UPD_W_LAST_NAIVE: pen_upd_body(c, part, nslots, b, j, P, 0, 1, sh, pc); break;
     default: break;
   }
 }

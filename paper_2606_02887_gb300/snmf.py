@@ -19,7 +19,7 @@ SNMF_ERR_ARG, SNMF_ERR_CUDA, SNMF_ERR_OOM, SNMF_ERR_NUMERIC, SNMF_ERR_TIMEOUT, S
 SNMF_DENSE, SNMF_CSR, SNMF_DENSE_BATCH = 0, 1, 2
 SNMF_F64, SNMF_F32, SNMF_BF16, SNMF_FP8 = 0, 1, 2, 3
 SNMF_ON_DEVICE, SNMF_ON_HOST = 0, 1
-SNMF_PENALTY, SNMF_DIRECT = 0, 1
+SNMF_PENALTY, SNMF_DIRECT, SNMF_NAIVE = 0, 1, 2
 SNMF_BB1, SNMF_BB2 = 0, 1
 SNMF_MLP_IN, SNMF_MLP_HIDDEN = 5, 64
 SNMF_MLP_NPARAMS = SNMF_MLP_IN * SNMF_MLP_HIDDEN + 2 * SNMF_MLP_HIDDEN + 1

@@ -15,6 +15,7 @@ def torch_dev():
 def gpu_solve(A, W0, r, Ht0=None, precision=S.SNMF_F64, csr=None, L=None, gamma=0.0,
               lai=None, host=False, **opt):
     """Solve with the library.  A: dense numpy (or None with csr=(rowptr, colidx, vals)).
+    L: an explicit CSR triple, or "paper" for the normalized Laplacian of A (L == NULL).
     Returns (W, Ht, status, stats, per-restart stats)."""
     torch, dev = torch_dev()
     tdt = torch.float64 if precision == S.SNMF_F64 else torch.float32
@@ -33,7 +34,9 @@ def gpu_solve(A, W0, r, Ht0=None, precision=S.SNMF_F64, csr=None, L=None, gamma=
     o = S.snmf_default_options(precision=precision, **opt)
     h = S.snmf_create(m, r, o)
     try:
-        if L is not None:
+        if isinstance(L, str) and L == "paper":
+            S.snmf_set_graph_reg(h, None, gamma)  # L = I - D^-1/2 A D^-1/2 of the handle's A
+        elif L is not None:
             lrp, lci, lva = L
             lt = (torch.tensor(lrp, dtype=torch.int32, device=dev),
                   torch.tensor(lci, dtype=torch.int32, device=dev),

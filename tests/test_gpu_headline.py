@@ -282,3 +282,24 @@ def test_one_part_product_matches_emulated_operands(n, cols, r):
     assert rel(Y, ref) <= 3e-5, rel(Y, ref)
     assert np.max(np.abs(Y - ref) / np.maximum(np.abs(ref), 1e-30)) <= 3e-5
     assert abs(xax - float(np.sum(X * ref))) <= 1e-5 * abs(xax)
+
+
+def test_naive_variant_fp64_matches_oracle(cfg1):
+    """The naive symmetric variant (SNMF_NAIVE: the W block with H = W^T fixed and no penalty,
+    then H <- W^T) iterate by iterate against oracle.snmpbb_naive, and FP32 through the
+    recomputing row kernels at the oracle's FP32 rounding envelope."""
+    A, W0 = cfg1
+    opts = O.Options(memory=10, max_iter=20, tol=0.0, objective="closed")
+    _, info = O.snmpbb_naive(A, W0, opts, keep_iterates=True)
+    for k in (1, 2, 5, 10, 20):
+        W, H, st, stats, _ = gpu_solve(A, W0, 10, W0, max_iter=k, tol=0.0, nonmonotone_M=10,
+                                       formulation=S.SNMF_NAIVE)
+        assert stats["iters"] == k
+        assert rel(W, info["trace"][k - 1]["W"]) <= ITER_NAIVE, k
+        assert np.array_equal(W, H)  # H <- W^T after every block
+    W, _, _, _, _ = gpu_solve(A, W0, 10, W0, precision=S.SNMF_F32, max_iter=3, tol=0.0, nonmonotone_M=10,
+                              formulation=S.SNMF_NAIVE)
+    assert rel(W, info["trace"][2]["W"]) <= 1e-4
+
+
+ITER_NAIVE = 1e-10

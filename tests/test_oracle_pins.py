@@ -235,6 +235,49 @@ def test_bb_steps_equal_inverse_curvature_for_isotropic_block():
             assert abs(s["alpha"] - 1.0 / c) <= 1e-12, (bb, s["alpha"])
 
 
+def test_naive_variant_rank_one_is_the_exact_block_recursion():
+    """Naive symmetric NMPBB (Sec. 2.1, before the penalty form), r = 1, entrywise positive V:
+    the W block 1/2 ||V - w h^T||^2 with h = w_k fixed has the isotropic Hessian ||h||^2 I,
+    so the first Z step (rho_0 = ||h||^2) lands on its minimiser V h / ||h||^2 and D = 0
+    after it.  Each outer iteration is therefore w_{k+1} = V w_k / ||w_k||^2 exactly: a
+    power iteration whose direction tends to the Perron vector v_1 while the norm alternates,
+    ||w_k|| ||w_{k+1}|| -> lambda_1 (c -> lambda_1 / c along v_1): the naive coupling does
+    not settle, as the paper reports.  Checked against the recursion and numpy's eigensolver."""
+    g = np.random.default_rng(91)
+    B = g.random((30, 30))
+    V = B + B.T + 1.0
+    lam, U = np.linalg.eigh(V)
+    v1 = np.abs(U[:, -1])
+    w0 = g.random((30, 1))
+    _, info = O.snmpbb_naive(V, w0, O.Options(max_iter=60, tol=0.0, memory=10), keep_iterates=True)
+    ws = [w0[:, 0]] + [rec["W"][:, 0] for rec in info["trace"]]
+    for k in range(1, len(ws)):
+        step = V @ ws[k - 1] / float(ws[k - 1] @ ws[k - 1])
+        assert np.allclose(ws[k], step, rtol=1e-10, atol=0.0), k
+    w_last, w_prev = ws[-1], ws[-2]
+    assert abs(float(np.linalg.norm(w_last) * np.linalg.norm(w_prev)) - lam[-1]) <= 1e-8 * lam[-1]
+    assert np.allclose(w_last / np.linalg.norm(w_last), v1, atol=1e-10)
+
+
+def test_naive_variant_planted_fixed_point_and_block_monotone():
+    """A planted exact factor W* (V = W* W*^T) is a fixed point: its W-block gradient
+    W* (W*^T W*) - V W* vanishes, so the first step leaves it in place.  From a random start,
+    with phi = 1 and the eta rule, each block's reference F_k decreases (Sec. 3.1) and the
+    objective 1/2 ||V - W W^T||^2 at the block ends does not increase by more than rounding."""
+    g = np.random.default_rng(92)
+    Ws = g.random((25, 3))
+    V = Ws @ Ws.T
+    W, info = O.snmpbb_naive(V, Ws, O.Options(max_iter=2, tol=0.0, memory=10))
+    assert np.allclose(W, Ws, rtol=0, atol=1e-13)
+    W0 = uniform_init(25, 3, math.sqrt(V.mean() / 3), seed=93)
+    _, info = O.snmpbb_naive(V, W0, O.Options(max_iter=20, tol=0.0, phi=1.0, memory=0))
+    for rec in info["trace"]:
+        prevF = math.inf
+        for s in rec["w_trace"]:
+            assert s["F"] <= prevF * (1 + 1e-13) + 1e-12
+            prevF = s["F"]
+
+
 def test_max_memory_reference():
     A, W = _small_problem(30, 3, seed=41)
     opts = O.Options(formulation="direct", memory=3, max_iter=12, tol=0.0)
