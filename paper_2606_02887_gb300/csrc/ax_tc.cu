@@ -250,14 +250,16 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     // arrival order, and runs the epilogue (Y += c X2, partials <P1, A X>, <P2, A X>).
     bool last = ok;
     if (p.splits > 1) {
-      if (ok && row < p.n) {
+      if (ok) {  // CTA-uniform: every lane of every warp runs the warp-collective TMEM loads
         float* Wz = p.Y + (int64_t)blockIdx.z * p.n * p.ldy + (int64_t)row * p.ldy + n0;
         for (int c0 = 0; c0 < BN; c0 += 16) {
           float v[16];
           tmem_ld16(trow + (uint32_t)c0, v);
+          if (row < p.n) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (n0 + c0 + i < p.N) Wz[c0 + i] = v[i];
+            for (int i = 0; i < 16; ++i)
+              if (n0 + c0 + i < p.N) Wz[c0 + i] = v[i];
+          }
         }
       }
       __threadfence();
@@ -513,8 +515,9 @@ k_bgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     atomicExch(err, 13);
     s_fail = 1;
   }
+  __syncthreads();  // the CTA decides as one (the TMEM loads below are warp-collective)
   float d1 = 0.f;
-  if (done && !s_fail) {
+  if (!s_fail) {
     const int row = it.m0 + warp * 32 + lane;
     const bool rv = row < it.n;
     for (int c0 = 0; c0 < bn; c0 += 16) {

@@ -42,3 +42,54 @@ def test_two_gloo_ranks_partition_and_max():
     assert set(r0[0]).isdisjoint(r1[0]) and sorted(r0[0] + r1[0]) == list(range(6))
     assert r0[1] == r1[1] == 11.0
     assert len(set(r0[2])) == 2 and r0[2] == r1[2]
+
+
+def _shard_main(rank, world, port, out):
+    """Row-partitioned A X, Gram and inner products of one problem on two gloo ranks, the
+    local compute done with numpy (standing in for the GPU kernels on each rank)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2606_02887_gb300 import rowshard
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        n, N = 203, 12
+        g = np.random.default_rng(7)
+        B = g.random((n, n))
+        A = B + B.T
+        X = g.random((n, N))
+        lo, hi = rowshard.row_ranges(n, world)[rank]
+        A_rows = torch.tensor(A[lo:hi])
+        X_loc = torch.tensor(X[lo:hi])
+        Y_loc = rowshard.sharded_product(A_rows, X_loc, rank, world, n, lambda a, x: a @ x)
+        G = rowshard.sharded_gram(X_loc, lambda x: x.T @ x)
+        d = rowshard.sharded_dots([float((X_loc * Y_loc).sum()), float((X_loc * X_loc).sum())])
+        out[rank] = (lo, hi, Y_loc.numpy(), G.numpy(), d.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_row_partition_matches_single_rank():
+    import numpy as np
+
+    from paper_2606_02887_gb300.rowshard import row_ranges
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    os.environ["PYTHONPATH"] = root + os.pathsep + os.environ.get("PYTHONPATH", "")
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_shard_main, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    n, N = 203, 12
+    g = np.random.default_rng(7)
+    B = g.random((n, n))
+    A = B + B.T
+    X = g.random((n, N))
+    Y = np.concatenate([res[k][2] for k in range(world)], axis=0)
+    assert [(res[k][0], res[k][1]) for k in range(world)] == row_ranges(n, world)
+    assert np.allclose(Y, A @ X, rtol=1e-12)
+    for k in range(world):
+        assert np.allclose(res[k][3], X.T @ X, rtol=1e-12)
+        assert np.allclose(res[k][4], [np.sum(X * (A @ X)), np.sum(X * X)], rtol=1e-12)
+    assert row_ranges(10, 3) == [(0, 4), (4, 7), (7, 10)]
