@@ -234,6 +234,21 @@ SNMF_API snmf_status snmf_lai_sketch(snmf_handle h, int k, int oversample, int p
                             uint64_t seed);
 
 /*
+ * SVD start (Sec. 4.1 guideline (4), recommended there for graph problems): with A ~ U E P^T
+ * from the r largest singular triplets, W_0 = |U E^1/2| and H_0 = |E^1/2 P^T|.  For symmetric A
+ * the singular triplets are the eigenpairs of largest |lambda| (P = U sign(lambda)), so both
+ * are |U| |lambda|^1/2.  The library takes them from the same randomized eigen-sketch as
+ * snmf_lai_sketch (Gaussian test matrix from Philox `seed`, l = r + oversample columns,
+ * power_iters subspace iterations, CholeskyQR, Jacobi eigensolver), of A itself.
+ *   W   device, n x (r batch), out: the start in every restart's columns
+ *   Ht  device, n x (r batch), out (may be NULL): the same values (H_0^T = W_0)
+ * Pass W and Ht to snmf_solve as the start.  Errors: SNMF_ERR_ARG (r + oversample > min(n, 128),
+ * negative counts), SNMF_ERR_STATE (dense batch handle), SNMF_ERR_OOM, SNMF_ERR_CUDA.
+ */
+SNMF_API snmf_status snmf_svd_init(snmf_handle h, void* W, void* Ht, int oversample, int power_iters,
+                                   uint64_t seed);
+
+/*
  * Run the solver (Algorithm 1 per block, Sec. 2) from the given start.
  *   W   device, n x (r*batch), in/out.  NULL: the default initialisation
  *       init_scale * sqrt(mean(A)/r) * U[0,1] (Philox, opt.seed) is used and the

@@ -642,8 +642,7 @@ void dir_init(snmf_ctx* h, const Params& P) {
                      h->pax, nullptr);
   int nlx = 0;
   if (h->graph)
-    nlx = ax_apply(h, h->L, false, h->buf[B_W], h->buf[B_LX], 0.0, nullptr, h->buf[B_W], nullptr,
-                   h->pax2, nullptr);
+    nlx = ax_L(h, h->buf[B_W], h->buf[B_LX], h->buf[B_W], nullptr, h->pax2, nullptr);
   gram1(h, h->buf[B_W], h->buf[B_W], 0, 1, nullptr, h->G64fix, h->GT, 0, 0.0);
   RowArgs a = row_base(h);
   a.X = h->buf[B_W]; a.B = h->buf[B_B]; a.LX = h->graph ? h->buf[B_LX] : nullptr;
@@ -1253,6 +1252,31 @@ snmf_status snmf_lai_sketch(snmf_handle h, int k, int oversample, int power_iter
   if (rc != 0) return fail(h, rc == -3 ? SNMF_ERR_OOM : SNMF_ERR_CUDA, msg);
   h->lai = true;
   h->exec_form = -1;
+  return SNMF_OK;
+}
+
+snmf_status snmf_svd_init(snmf_handle h, void* W, void* Ht, int oversample, int power_iters, uint64_t seed) {
+  if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
+  if (!W || oversample < 0 || power_iters < 0) return fail(h, SNMF_ERR_ARG, "bad SVD start arguments");
+  const int ell = h->r + oversample;
+  if (ell > 128 || ell > h->n) return fail(h, SNMF_ERR_ARG, "r + oversample must be <= min(n, 128)");
+  if (sync_user(h) != SNMF_OK) return SNMF_ERR_CUDA;
+  LaiOp sk{};
+  std::string msg;
+  // the eigen-sketch of A itself (not of a LAI sketch set on the handle), k = r
+  const int rc = lai_build(sk, h->A, h->tdtype, h->n, h->r, ell, power_iters, seed, h->r, h->s, msg);
+  if (rc != 0) {
+    lai_free(sk);
+    return fail(h, rc == -3 ? SNMF_ERR_OOM : SNMF_ERR_CUDA, msg);
+  }
+  launch_svd_start(h->tdtype, sk, h->n, h->r, h->b, W, h->s);
+  const size_t fbytes = (size_t)h->n * h->N * h->esz;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && Ht) e = cudaMemcpyAsync(Ht, W, fbytes, cudaMemcpyDeviceToDevice, h->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+  lai_free(sk);
+  if (e != cudaSuccess) return fail(h, SNMF_ERR_CUDA, std::string("SVD start: ") + cudaGetErrorString(e));
   return SNMF_OK;
 }
 

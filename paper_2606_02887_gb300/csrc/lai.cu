@@ -494,6 +494,30 @@ int lai_build(LaiOp& op, const AxArgs& A, int td, int64_t n, int k, int ell, int
 #undef LCK
 }
 
+// SVD start of Sec. 4.1 guideline (4) from the eigen-sketch of a symmetric A (k = r): the
+// singular values of A are |lambda| with left vectors U and right vectors U sign(lambda), so
+// |U E^1/2| and |E^1/2 P^T|^T are both |U| |lambda|^1/2 (column-wise).  Written to every one of
+// the b restart column blocks of W (n x r b, ld r b).
+namespace {
+template <typename T>
+__global__ void k_svd_start(const T* __restrict__ U, const double* __restrict__ lam, int64_t n, int r, int b,
+                            T* __restrict__ W) {
+  const int64_t total = n * (int64_t)r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / r;
+    const int c = (int)(e % r);
+    const T v = (T)(fabs((double)U[e]) * sqrt(fabs(lam[c])));
+    for (int j = 0; j < b; ++j) W[i * (int64_t)r * b + (int64_t)j * r + c] = v;
+  }
+}
+}  // namespace
+
+void launch_svd_start(int tdtype, const LaiOp& op, int64_t n, int r, int b, void* W, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((n * r + 255) / 256, 152 * 8);
+  if (tdtype == 0) k_svd_start<double><<<blocks, 256, 0, s>>>((const double*)op.U, op.lam, n, r, b, (double*)W);
+  else k_svd_start<float><<<blocks, 256, 0, s>>>((const float*)op.U, op.lam, n, r, b, (float*)W);
+}
+
 void lai_free(LaiOp& op) {
   cudaFree(op.U); cudaFree(op.lam); cudaFree(op.xpart); cudaFree(op.M); cudaFree(op.counters);
   op = LaiOp{};

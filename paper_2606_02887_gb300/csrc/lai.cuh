@@ -34,6 +34,10 @@ int lai_build(LaiOp& op, const AxArgs& A, int tdtype, int64_t n, int k, int ell,
 
 void lai_free(LaiOp& op);
 
+// W (n x r b, ld r b) = |U| |lambda|^1/2 of a sketch with k = r, in every restart's columns:
+// the SVD start |U E^1/2| of Sec. 4.1 guideline (4) for symmetric A (H_0^T equals it).
+void launch_svd_start(int tdtype, const LaiOp& op, int64_t n, int r, int b, void* W, cudaStream_t s);
+
 // Out (n x m, ldo) = In (n x K, ldi) M (K x m row-major), K <= 128 (factor type).
 void launch_rowmul(int tdtype, const void* In, int64_t ldi, int K, const void* M, int m, int64_t n, void* Out,
                    int64_t ldo, const int* run, cudaStream_t s);

@@ -29,7 +29,7 @@ EXPORTED = (
     "snmf_solve", "snmf_solve_host", "snmf_restart_stats", "snmf_get_factors",
     "snmf_apply", "snmf_profile_ax", "snmf_apply_dense_noalloc", "snmf_controller_data",
     "snmf_mlp_train", "snmf_tuned_config", "snmf_tuned_tiles", "snmf_profile_steps", "snmf_destroy", "snmf_last_error",
-    "snmf_mlp_eval", "snmf_set_timeout", "snmf_step_config",
+    "snmf_mlp_eval", "snmf_set_timeout", "snmf_step_config", "snmf_svd_init",
 )
 NOALLOC_SCRATCH_BYTES = 64 << 20
 NOALLOC_PARTIAL_BYTES = 4 << 20
@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH):
     lib.snmf_tuned_tiles.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.snmf_mlp_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
     lib.snmf_set_timeout.argtypes = [H, C.c_int64]
+    lib.snmf_svd_init.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_uint64]
     lib.snmf_step_config.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_int64)]
     lib.snmf_destroy.argtypes = [H]
@@ -214,6 +215,12 @@ def snmf_set_graph_reg(h, matrix, gamma: float):
 def snmf_lai_sketch(h, k: int, oversample: int, power_iters: int, seed: int):
     lib = load_library()
     return _check(lib, h, lib.snmf_lai_sketch(h, int(k), int(oversample), int(power_iters), int(seed)))
+
+
+def snmf_svd_init(h, W, Ht=None, oversample: int = 10, power_iters: int = 2, seed: int = 0):
+    """SVD start |U E^1/2| (Sec. 4.1 guideline (4)) into device tensors W (and Ht)."""
+    lib = load_library()
+    return _check(lib, h, lib.snmf_svd_init(h, _ptr(W), _ptr(Ht), int(oversample), int(power_iters), int(seed)))
 
 
 def snmf_solve(h, W=None, Ht=None):

@@ -55,8 +55,14 @@ def test_autotune_search_cache_and_agreement(tmp_path, prec):
         finally:
             S.snmf_destroy(h2)
         Xn = np.random.default_rng(3).random((n, r)).astype(np.float32)
-        # two correct FP32 accumulation orders of the same product
-        assert rel(_apply(h1, Xn), _apply(h0, Xn)) <= 1e-6
+        # two correct accumulation orders of the same product (split counts chosen by timing).
+        # FP32 CUDA cores: sums of n nonnegative terms in two orders differ by about sqrt(n) u
+        # (u = 2^-24) relative; 8 sqrt(n) u = 2.2e-5 at n = 2048.  BF16 tensor cores: the FP32
+        # accumulation drifts low in proportion to the K-chain length (a -5.7e-6 relative
+        # rescaling over K = 8192, test_gpu_bf16.py), so different split counts differ by up
+        # to that drift; the 3e-5 bar of the emulated-operand test holds for both.
+        bar = 8.0 * math.sqrt(n) * 2.0 ** -24 if prec == S.SNMF_F32 else 3e-5
+        assert rel(_apply(h1, Xn), _apply(h0, Xn)) <= bar
         with pytest.raises(S.SnmfError):
             S.snmf_tuned_config(h0)
     finally:

@@ -89,3 +89,36 @@ def test_lai_rejects_bad_sizes():
             S.snmf_lai_sketch(h, 0, 4, 1, 1)
     finally:
         S.snmf_destroy(h)
+
+
+def test_svd_start_matches_oracle_fp64():
+    """SVD start (Sec. 4.1 guideline (4)) from the device eigen-sketch: on an exactly rank-r
+    planted A the sketch spans A's range, so W_0 = |U E^1/2| equals oracle.svd_init (numpy's
+    SVD) to rounding; on a noisy A it equals |U| |lambda|^1/2 of the oracle's own sketch (same
+    Philox stream); W_0 = Ht_0 in every restart's columns; a solve from it converges."""
+    import torch
+    dev = torch.device("cuda:0")
+    n, r, b = 300, 5, 2
+    g = np.random.default_rng(4301)
+    W_true = g.random((n, r))
+    A_exact = W_true @ W_true.T
+    W_ref, H_ref = O.svd_init(A_exact, r)
+    assert np.allclose(W_ref, H_ref, atol=1e-10)
+    A_noisy, _ = planted_dense(n, r, 0.05, seed=4302)
+    Uo, lo = O.lai_sketch(lambda X: A_noisy @ X, n, r, 6, 2, 4303)
+    W_sk = np.abs(Uo) * np.sqrt(np.abs(lo))[None, :]
+    for A, ref, seed, tol in ((A_exact, W_ref, 4304, 1e-9), (A_noisy, W_sk, 4303, 1e-9)):
+        h = S.snmf_create(S.dense_matrix(torch.tensor(A, device=dev)), r,
+                          S.snmf_default_options(precision=S.SNMF_F64, batch=b, max_iter=500, tol=1e-4))
+        try:
+            W = torch.zeros((n, r * b), dtype=torch.float64, device=dev)
+            H = torch.zeros_like(W)
+            S.snmf_svd_init(h, W, H, oversample=6, power_iters=2, seed=seed)
+            Wn = W.cpu().numpy()
+            assert np.array_equal(Wn, H.cpu().numpy())
+            for j in range(b):
+                assert rel(Wn[:, j * r:(j + 1) * r], ref) <= tol, (j, rel(Wn[:, j * r:(j + 1) * r], ref))
+            st, stats = S.snmf_solve(h, W, H)
+            assert st == S.SNMF_OK and stats["pg_rel"] <= 1e-4
+        finally:
+            S.snmf_destroy(h)
