@@ -60,6 +60,7 @@ struct snmf_ctx {
   double normL = 0.0;  // ||L||_2 (power method), enters rho of graph-regularised blocks
   int use_tile = 0;    // row kernels through the shared-memory tile body (r <= 32)
   int use_fuse = 0;    // D step and update through rowfuse.cu (FP32, r in {16, 32, 64}, no Z / D stored)
+  int row_tc = 0;      // with use_fuse: the row products on the tensor cores (rowtc.cu, r = 64; tuned)
   int row_bm = 0;      // general row kernel, FP32: rows per CTA (0: built-in choice; autotuned)
   AxArgs L{};
   int32_t* L_rowptr = nullptr;
@@ -90,6 +91,9 @@ struct snmf_ctx {
   void* xl = nullptr;
   int xparts = 2;                // BF16 product: X as hi + lo parts (2) or rounded to BF16 (1)
   unsigned* tcount = nullptr;    // BF16 product: arrival counters of the fused split-K epilogue
+  // the fused split-K epilogue reads the slices row by row per thread (uncoalesced); measured
+  // slower than the separate finish pass at n = 8192, N = 512 (331 against 245 us), so off
+  int fuse_epilogue = 0;
   long long budget = 2000000000LL;
   __nv_bfloat16* mlp_w = nullptr;  // learned controller weights (BF16)
   float* rec_feat = nullptr;       // record mode dataset
@@ -170,7 +174,7 @@ Dims dims(const snmf_ctx* h) {
 TcEpilogue tc_epilogue(snmf_ctx* h, void* Y, double c, const void* X2, const void* P1, const void* P2,
                        double* part) {
   TcEpilogue e;
-  if (!h->tcount) return e;
+  if (!h->tcount || !h->fuse_epilogue) return e;
   if (P1 || P2) {
     TcPlan pl;
     const ProdTune* tn = h->tuned ? &h->tune.cfg : nullptr;
@@ -322,11 +326,13 @@ snmf_status time_steps(snmf_ctx* h, int iters, double* ms_dstep, double* ms_upda
   au.ctl_mode = CTL_UPD_W;
   au.Zin = h->buf[B_Z]; au.Din = h->buf[B_D]; au.Din2 = h->buf[B_AD];
   auto dstep = [&] {
-    if (h->use_fuse) launch_rowfuse_dstep(ad, h->row_bm, nc, h->s);
+    if (h->use_fuse && h->row_tc) launch_rowtc_dstep(ad, h->dev_err, h->s);
+    else if (h->use_fuse) launch_rowfuse_dstep(ad, h->row_bm, nc, h->s);
     else launch_rowgemm(td, OP_ZSTEP, EPI_DIR, ad, h->s, nc);
   };
   auto update = [&] {
-    if (h->use_fuse) launch_rowfuse_update(au, h->row_bm, nc, h->s);
+    if (h->use_fuse && h->row_tc) launch_rowtc_update(au, h->dev_err, h->s);
+    else if (h->use_fuse) launch_rowfuse_update(au, h->row_bm, nc, h->s);
     else launch_rowgemm(td, OP_UPD, EPI_GRAD, au, h->s);
   };
   cudaEvent_t e[4];
@@ -373,6 +379,8 @@ snmf_status autotune_product(snmf_ctx* h) {
       h->row_bm = e.cfg.row_bm;
       if (!h->use_tile) h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, h->row_bm);
     }
+    h->row_tc = (tune_rows && h->use_fuse && e.cfg.row_tc == 1 &&
+                 rowtc_supported(h->tdtype, h->r, h->opt.step_controller == 1 ? 2 : 1)) ? 1 : 0;
     return SNMF_OK;
   }
   std::vector<ProdTune> cand;
@@ -459,6 +467,22 @@ snmf_status autotune_product(snmf_ctx* h) {
     h->row_bm = bbm;
     if (!h->use_tile) h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, bbm);
     h->tune.cfg.row_bm = bbm;
+    // the tensor-core row products (r = 64), kept when faster than the best CUDA-core height
+    if (h->use_fuse && rowtc_supported(h->tdtype, h->r, h->opt.step_controller == 1 ? 2 : 1)) {
+      h->row_tc = 1;
+      double md = 0.0, mu = 0.0;
+      const snmf_status st = time_steps(h, 5, &md, &mu);
+      if (st != SNMF_OK) return st;
+      int derr2 = 0;
+      CK(cudaMemcpy(&derr2, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (derr2) {
+        CK(cudaMemset(h->dev_err, 0, sizeof(int)));
+        h->row_tc = 0;
+      } else if (!(md + mu < bt)) {
+        h->row_tc = 0;
+      }
+      h->tune.cfg.row_tc = h->row_tc;
+    }
   }
   tune_store(h->opt.tune_cache, dev, key, h->tune);
   return SNMF_OK;
@@ -509,12 +533,14 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P, bool nai
       RowArgs a = row_base(h, &P);
       a.X = X; a.g_in = h->buf[B_G]; a.B = h->buf[B_B]; a.gZout = h->buf[B_GZ];
       a.ctl_mode = CTL_LS;
-      launch_rowfuse_dstep(a, h->row_bm, nc, h->s);
+      if (h->row_tc) launch_rowtc_dstep(a, h->dev_err, h->s);
+      else launch_rowfuse_dstep(a, h->row_bm, nc, h->s);
       RowArgs u = row_base(h, &P);
       u.Xout = X; u.gout = h->buf[B_G]; u.gZold = h->buf[B_GZ]; u.B = h->buf[B_B];
       u.ctl_mode = is_w ? (naive && k == K - 1 ? CTL_UPD_W_LAST_NAIVE : CTL_UPD_W)
                         : (k == K - 1 ? CTL_UPD_H_LAST : CTL_UPD_H);
-      launch_rowfuse_update(u, h->row_bm, nc, h->s);
+      if (h->row_tc) launch_rowtc_update(u, h->dev_err, h->s);
+      else launch_rowfuse_update(u, h->row_bm, nc, h->s);
     }
     return;
   }
@@ -1568,8 +1594,8 @@ snmf_status snmf_step_config(snmf_handle h, int32_t* body, int32_t* rows_per_cta
   int kind = 0, rows = 0;
   int64_t bd = 0, bu = 0;
   if (h->use_fuse) {
-    kind = 2;
-    rows = rowfuse_bm(h->r, h->row_bm);
+    kind = h->row_tc ? 3 : 2;
+    rows = h->row_tc ? 128 : rowfuse_bm(h->r, h->row_bm);
     bd = 4 * fb;  // X, g, B in; g(Z) out
     bu = 6 * fb;  // X, g, g(Z), B in; X', g(X') out
   } else {

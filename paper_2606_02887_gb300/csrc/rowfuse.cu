@@ -36,42 +36,8 @@ struct FuseCfg {
   static constexpr int TY = 256 / TX;    // row groups
   static constexpr int BM = TY * MR;     // rows per CTA
   static constexpr int TS = BM + 4;      // row stride of the transposed tile (floats)
-  static constexpr int TILE = BM * R;    // one staged n x r tile (floats, row-major)
-  // transposed operand tile, G, and `ntiles` staged input tiles
-  static constexpr size_t smem(int ntiles) {
-    return ((size_t)R * TS + (size_t)R * R + (size_t)ntiles * TILE) * sizeof(float);
-  }
+  static constexpr size_t smem = ((size_t)R * TS + (size_t)R * R) * sizeof(float);
 };
-
-// 16-byte asynchronous copy global -> shared (L2 only), and the group fences.
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// Stage the thread's own MR x 4 elements of an n x r tile (rows row0 .. row0 + MR - 1,
-// columns col .. col + 3) into the row-major shared tile; rows past n are zero.  Each thread
-// reads back only what it staged, so its own wait_group suffices (no barrier).
-template <int R, int MR>
-__device__ __forceinline__ void stage_own(float* tile, const float* src, int64_t row0, int64_t col, int64_t n,
-                                          int64_t ld, int tx, int ty) {
-#pragma unroll
-  for (int p = 0; p < MR; ++p) {
-    float* dst = tile + (ty * MR + p) * R + 4 * tx;
-    const int64_t i = row0 + p;
-    if (i < n) cp_async16(dst, src + i * ld + col);
-    else *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-
-template <int R, int MR>
-__device__ __forceinline__ float4 own4(const float* tile, int p, int tx, int ty) {
-  return *reinterpret_cast<const float4*>(tile + (ty * MR + p) * R + 4 * tx);
-}
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
@@ -193,14 +159,11 @@ __device__ __forceinline__ void load_gram(const RowArgs& a, int j, float* Gs) {
 // the update recomputes that one.  NC = 1: q5-q7 zero, step Ctl::alpha.
 // ---------------------------------------------------------------------------------------
 template <int R, int MR, int NC>
-__global__ void __launch_bounds__(256, MR >= 8 ? 1 : 2) k_rowfuse_dstep(RowArgs a) {
+__global__ void __launch_bounds__(256, MR >= 8 ? 2 : 3) k_rowfuse_dstep(RowArgs a) {
   using C = FuseCfg<R, MR>;
   extern __shared__ __align__(16) float fsm[];
   float* Ts = fsm;
   float* Gs = fsm + R * C::TS;
-  float* Xs = Gs + R * R;   // staged X, g, B tiles
-  float* gs = Xs + C::TILE;
-  float* Bs = gs + C::TILE;
   __shared__ float shq[8][8];
   __shared__ unsigned ticket;
   const int j = blockIdx.y;
@@ -213,31 +176,35 @@ __global__ void __launch_bounds__(256, MR >= 8 ? 1 : 2) k_rowfuse_dstep(RowArgs 
     const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
     const int64_t row0 = (int64_t)blockIdx.x * C::BM + ty * MR;
     const int64_t col = (int64_t)j * R + 4 * tx;
+    const float* X = (const float*)a.X;
+    const float* g = (const float*)a.g_in;
+    const float* B = (const float*)a.B;
     float* gZo = (float*)a.gZout;
-    // every input tile in flight at once: X and g first (the Z tile), then B (the epilogue),
-    // which lands while the row product runs
-    stage_own<R, MR>(Xs, (const float*)a.X, row0, col, a.n, a.ld, tx, ty);
-    stage_own<R, MR>(gs, (const float*)a.g_in, row0, col, a.n, a.ld, tx, ty);
-    cp_async_commit();
-    stage_own<R, MR>(Bs, (const float*)a.B, row0, col, a.n, a.ld, tx, ty);
-    cp_async_commit();
     const float inv_rho = (float)(1.0 / cj.rho);
     const float alpha = (float)(NC == 1 ? cj.alpha : cj.cand_alpha[0]);
     const float alpha1 = (float)(NC == 1 ? cj.alpha : cj.cand_alpha[1]);
     load_gram<R>(a, j, Gs);
     float v[MR][4];
-    cp_async_wait<1>();  // this thread's X and g elements
+    {  // Z tile (transposed) for the row product
+      float4 x4[MR], g4[MR];
 #pragma unroll
-    for (int p = 0; p < MR; ++p) {  // Z tile (transposed) for the row product
-      const float4 x4 = own4<R, MR>(Xs, p, tx, ty), g4 = own4<R, MR>(gs, p, tx, ty);
+      for (int p = 0; p < MR; ++p) {
+        const int64_t i = row0 + p;
+        x4[p] = g4[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < a.n) {
+          x4[p] = ld4(X + i * a.ld + col);
+          g4[p] = ld4(g + i * a.ld + col);
+        }
+      }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v[p][q] = zstep1(comp(x4, q), comp(g4, q), inv_rho);
+      for (int p = 0; p < MR; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[p][q] = zstep1(comp(x4[p], q), comp(g4[p], q), inv_rho);
     }
     store_transposed<R, MR>(Ts, v, tx, ty);
     __syncthreads();
     float acc[MR][4];
     row_product<R, MR>(Ts, Gs, tx, ty, acc);
-    cp_async_wait<0>();  // this thread's B elements
     // epilogue: g(Z), D, the partial inner products; D kept in acc for <D G, D> (NC = 2:
     // g(Z) kept in v for the second direction)
 #pragma unroll
@@ -245,8 +212,7 @@ __global__ void __launch_bounds__(256, MR >= 8 ? 1 : 2) k_rowfuse_dstep(RowArgs 
       const int64_t i = row0 + p;
       if (i < a.n) {
         const int64_t off = i * a.ld + col;
-        const float4 x4 = own4<R, MR>(Xs, p, tx, ty), g4 = own4<R, MR>(gs, p, tx, ty),
-                     b4 = own4<R, MR>(Bs, p, tx, ty);
+        const float4 x4 = ld4(X + off), g4 = ld4(g + off), b4 = ld4(B + off);
         float gz[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -303,15 +269,11 @@ __global__ void __launch_bounds__(256, MR >= 8 ? 1 : 2) k_rowfuse_dstep(RowArgs 
 // q5 f(X') - f(Z) (trapezoid), q6 zero entries of X'; q7 zero.
 // ---------------------------------------------------------------------------------------
 template <int R, int MR, int NC>
-__global__ void __launch_bounds__(256, MR >= 8 ? 1 : 2) k_rowfuse_update(RowArgs a) {
+__global__ void __launch_bounds__(256, MR >= 8 ? 2 : 3) k_rowfuse_update(RowArgs a) {
   using C = FuseCfg<R, MR>;
   extern __shared__ __align__(16) float fsm[];
   float* Ts = fsm;
   float* Gs = fsm + R * C::TS;
-  float* Xs = Gs + R * R;   // staged X, g, g(Z), B tiles
-  float* gs = Xs + C::TILE;
-  float* zs = gs + C::TILE;
-  float* Bs = zs + C::TILE;
   __shared__ float shq[8][8];
   __shared__ unsigned ticket;
   const int j = blockIdx.y;
@@ -326,13 +288,8 @@ __global__ void __launch_bounds__(256, MR >= 8 ? 1 : 2) k_rowfuse_update(RowArgs
     const int64_t col = (int64_t)j * R + 4 * tx;
     float* X = (float*)a.Xout;        // in place: X_k in, X_{k+1} out
     float* g = (float*)a.gout;        // in place: g(X_k) in, g(X_{k+1}) out
-    // every input tile in flight at once: X, g, g(Z) first (the X' tile), then B
-    stage_own<R, MR>(Xs, X, row0, col, a.n, a.ld, tx, ty);
-    stage_own<R, MR>(gs, g, row0, col, a.n, a.ld, tx, ty);
-    stage_own<R, MR>(zs, (const float*)a.gZold, row0, col, a.n, a.ld, tx, ty);
-    cp_async_commit();
-    stage_own<R, MR>(Bs, (const float*)a.B, row0, col, a.n, a.ld, tx, ty);
-    cp_async_commit();
+    const float* gZ = (const float*)a.gZold;
+    const float* B = (const float*)a.B;
     const float inv_rho = (float)(1.0 / cj.rho);
     // the step of the direction the line search kept: NC = 2 selects the proposal or the
     // plain BB direction (dsel); the same float as the D step used
@@ -340,29 +297,36 @@ __global__ void __launch_bounds__(256, MR >= 8 ? 1 : 2) k_rowfuse_update(RowArgs
     const float pb = (float)cj.phibeta;
     load_gram<R>(a, j, Gs);
     float v[MR][4];
-    cp_async_wait<1>();
+    {  // X' tile (transposed) for the row product
+      float4 x4[MR], g4[MR], z4[MR];
 #pragma unroll
-    for (int p = 0; p < MR; ++p) {  // X' tile (transposed) for the row product
-      const float4 x4 = own4<R, MR>(Xs, p, tx, ty), g4 = own4<R, MR>(gs, p, tx, ty),
-                   z4 = own4<R, MR>(zs, p, tx, ty);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float z = zstep1(comp(x4, q), comp(g4, q), inv_rho);
-        v[p][q] = upd1(z, dir1(z, comp(z4, q), alpha), pb);
+      for (int p = 0; p < MR; ++p) {
+        const int64_t i = row0 + p;
+        x4[p] = g4[p] = z4[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < a.n) {
+          x4[p] = ld4(X + i * a.ld + col);
+          g4[p] = ld4(g + i * a.ld + col);
+          z4[p] = ld4(gZ + i * a.ld + col);
+        }
       }
+#pragma unroll
+      for (int p = 0; p < MR; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float z = zstep1(comp(x4[p], q), comp(g4[p], q), inv_rho);
+          v[p][q] = upd1(z, dir1(z, comp(z4[p], q), alpha), pb);
+        }
     }
     store_transposed<R, MR>(Ts, v, tx, ty);
     __syncthreads();
     float acc[MR][4];
     row_product<R, MR>(Ts, Gs, tx, ty, acc);
-    cp_async_wait<0>();
 #pragma unroll
     for (int p = 0; p < MR; ++p) {
       const int64_t i = row0 + p;
       if (i >= a.n) continue;
       const int64_t off = i * a.ld + col;
-      const float4 x4 = own4<R, MR>(Xs, p, tx, ty), g4 = own4<R, MR>(gs, p, tx, ty),
-                   gz4 = own4<R, MR>(zs, p, tx, ty), b4 = own4<R, MR>(Bs, p, tx, ty);
+      const float4 x4 = ld4(X + off), g4 = ld4(g + off), gz4 = ld4(gZ + off), b4 = ld4(B + off);
       float xo[4], go[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -394,13 +358,13 @@ void launch_pair(int which, const RowArgs& a, cudaStream_t s) {
   using C = FuseCfg<R, MR>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_rowfuse_dstep<R, MR, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem(3));
-    cudaFuncSetAttribute(k_rowfuse_update<R, MR, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem(4));
+    cudaFuncSetAttribute(k_rowfuse_dstep<R, MR, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    cudaFuncSetAttribute(k_rowfuse_update<R, MR, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     attr = true;
   }
   dim3 grid((unsigned)((a.n + C::BM - 1) / C::BM), (unsigned)a.b);
-  if (which == 0) k_rowfuse_dstep<R, MR, NC><<<grid, 256, C::smem(3), s>>>(a);
-  else k_rowfuse_update<R, MR, NC><<<grid, 256, C::smem(4), s>>>(a);
+  if (which == 0) k_rowfuse_dstep<R, MR, NC><<<grid, 256, C::smem, s>>>(a);
+  else k_rowfuse_update<R, MR, NC><<<grid, 256, C::smem, s>>>(a);
 }
 
 template <int NC>

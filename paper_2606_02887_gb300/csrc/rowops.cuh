@@ -61,6 +61,12 @@ bool rowfuse_supported(int tdtype, int r);
 int rowfuse_bm(int r, int bm_req);
 void launch_rowfuse_dstep(const RowArgs& a, int bm, int nc, cudaStream_t s);
 void launch_rowfuse_update(const RowArgs& a, int bm, int nc, cudaStream_t s);
+// The same pair with the row products on the tensor cores (rowtc.cu: tcgen05 kind::tf32 with
+// hi / lo operand parts; FP32 factors, r = 64, one direction per step).  err: device error
+// code, set when a bounded wait for the tensor cores runs out.
+bool rowtc_supported(int tdtype, int r, int nc);
+void launch_rowtc_dstep(const RowArgs& a, int* err, cudaStream_t s);
+void launch_rowtc_update(const RowArgs& a, int* err, cudaStream_t s);
 
 void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pair, int npairs,
                  double* gpart, int nchunks, const Ctl* ctl, const int* run, double* G64, void* GT,

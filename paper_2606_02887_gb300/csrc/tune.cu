@@ -98,6 +98,7 @@ struct Parser {
       else if (k == "per_sm") e.cfg.per_sm = (int)num();
       else if (k == "bn") e.cfg.bn = (int)num();
       else if (k == "row_bm") e.cfg.row_bm = (int)num();
+      else if (k == "row_tc") e.cfg.row_tc = (int)num();
       else if (k == "ms") e.ms = num();
       else skip();
     } while (ok && eat(','));
@@ -167,9 +168,9 @@ bool write_file(const char* path, const Table& t) {
     for (const auto& e : d.second) {
       std::fprintf(f,
                    "%s\n      %s: {\"splits\": %d, \"stages\": %d, \"per_sm\": %d, \"bn\": %d, \"row_bm\": %d, "
-                   "\"ms\": %.6g}",
+                   "\"row_tc\": %d, \"ms\": %.6g}",
                    first ? "" : ",", quoted(e.first).c_str(), e.second.cfg.splits, e.second.cfg.stages,
-                   e.second.cfg.per_sm, e.second.cfg.bn, e.second.cfg.row_bm, e.second.ms);
+                   e.second.cfg.per_sm, e.second.cfg.bn, e.second.cfg.row_bm, e.second.cfg.row_tc, e.second.ms);
       first = false;
     }
     std::fprintf(f, "\n    }");

@@ -12,7 +12,8 @@ struct ProdTune {
   int stages = 0;   // tcgen05 product: shared-memory ring stages
   int per_sm = 0;   // tcgen05 product: CTAs planned per SM (sets the default split count)
   int bn = 0;       // tcgen05 product: output columns per CTA tile (multiple of 16, <= 256)
-  int row_bm = 0;   // general row kernel (FP32): rows per CTA, 32 or 64
+  int row_bm = 0;   // row kernels of a step (FP32): rows per CTA
+  int row_tc = 0;   // 1: the step's row products on the tensor cores (rowtc.cu, r = 64)
 };
 
 struct TuneEntry {

@@ -80,14 +80,16 @@ def test_mlp_inference_matches_oracle_on_shipped_weights():
 # the headline configuration at n = 2048
 # ---------------------------------------------------------------------------
 
-def test_headline_configuration_matches_oracle_per_restart(tmp_path):
+@pytest.mark.parametrize("row_tc", [0, 1])
+def test_headline_configuration_matches_oracle_per_restart(tmp_path, row_tc):
     """BF16 A, r = 64, 8 restarts in one solve, lean learned step (step_controller 3) with
     the shipped weights, and the tile shapes the bench's autotuner chooses at n = 8192
     (128-column tensor-core tiles, 4 K slices, 2 CTAs per SM with a 2-stage ring, 64-row
     row tiles), forced through the tuning cache.  Every restart reaches relative projected
     gradient 1e-4, and its final residual against the true A is within 1e-3 of the FP64
     oracle's solve of the same restart (tests/golden/oracle_dense2048_r64_b8.json, written
-    by make_headline_oracle.py from the oracle alone).  The product sees X as BF16 hi + lo
+    by make_headline_oracle.py from the oracle alone).  row_tc = 1: the step's row products on
+    the tensor cores (the autotuner's other choice for r = 64).  The product sees X as BF16 hi + lo
     parts (the one-part form does not reach the tolerance on this workload: the W and H blocks
     then see differently rounded fixed factors, so no single objective has their common
     stationary point)."""
@@ -101,7 +103,8 @@ def test_headline_configuration_matches_oracle_per_restart(tmp_path):
     W0 = np.concatenate(starts, axis=1)
     dev = torch.device("cuda:0")
     key = f"dense/bf16/n{n}/r{r}/N{r * b}"
-    cache = _forced_tune_cache(tmp_path / "tune.json", key, splits=4, stages=2, per_sm=2, bn=128, row_bm=64)
+    cache = _forced_tune_cache(tmp_path / "tune.json", key, splits=4, stages=2, per_sm=2, bn=128, row_bm=64,
+                               row_tc=row_tc)
     o = S.snmf_default_options(precision=S.SNMF_BF16, batch=b, max_iter=500, tol=1e-4, nonmonotone_M=10,
                                step_controller=3, autotune=1, tune_cache=cache)
     h = S.snmf_create(S.dense_matrix(torch.tensor(A, dtype=torch.float32, device=dev)), r, o,
@@ -109,6 +112,7 @@ def test_headline_configuration_matches_oracle_per_restart(tmp_path):
     try:
         cfg = S.snmf_tuned_config(h)
         assert cfg["from_cache"] and (cfg["splits"], cfg["bn"], cfg["per_sm"], cfg["stages"]) == (4, 128, 2, 2)
+        assert S.snmf_step_config(h)["body"] == (3 if row_tc else 2)
         W = torch.tensor(W0, dtype=torch.float32, device=dev)
         H = W.clone()
         st, stats = S.snmf_solve(h, W, H)
@@ -306,3 +310,41 @@ def test_naive_variant_fp64_matches_oracle(cfg1):
 
 
 ITER_NAIVE = 1e-10
+
+
+def test_tensor_core_row_kernels_follow_oracle(tmp_path):
+    """The step's row products on the tensor cores (tcgen05 kind::tf32, operands as TF32 hi + lo
+    parts, three MMAs per K step), forced through the tuning cache: FP32 factors, r = 64, four
+    restarts, a ragged last row tile (n = 2000), iterate by iterate after 1, 2 and 3 outer
+    iterations against the FP64 oracle.  Bar: the oracle's FP32 rounding envelope (model at
+    u = 2^-24) times 2: the dropped lo x lo term and the TF32 rounding of the lo parts add about
+    2^-22 relative per product, a few units of FP32 rounding."""
+    import torch
+    n, r, b = 2000, 64, 4
+    A, _ = planted_dense(n, r, 0.02, seed=2000)
+    Ws = [uniform_init(n, r, math.sqrt(A.mean() / r), seed=2100 + j) for j in range(b)]
+    W0 = np.concatenate(Ws, axis=1)
+    dev = torch.device("cuda:0")
+    cache = _forced_tune_cache(tmp_path / "tune.json", f"dense/f32/n{n}/r{r}/N{r * b}", splits=1, row_bm=128,
+                               row_tc=1)
+    opts = O.Options(max_iter=3, tol=0.0, memory=10, objective="closed")
+    env = rounding_envelope(lambda: O.snmpbb_penalty(A, Ws[0], Ws[0], opts, keep_iterates=True)[2]["trace"],
+                            "W", 3, seeds=2, u=2.0 ** -24)
+    traces = {j: O.snmpbb_penalty(A, Ws[j], Ws[j], opts, keep_iterates=True)[2]["trace"] for j in (0, b - 1)}
+    At = torch.tensor(A, dtype=torch.float32, device=dev)
+    for k in (1, 2, 3):
+        h = S.snmf_create(S.dense_matrix(At), r, S.snmf_default_options(
+            precision=S.SNMF_F32, batch=b, max_iter=k, tol=0.0, nonmonotone_M=10, autotune=1, tune_cache=cache))
+        try:
+            assert S.snmf_step_config(h)["body"] == 3
+            W = torch.tensor(W0, dtype=torch.float32, device=dev)
+            H = W.clone()
+            st, stats = S.snmf_solve(h, W, H)
+        finally:
+            S.snmf_destroy(h)
+        Wn, Hn = W.cpu().numpy().astype(np.float64), H.cpu().numpy().astype(np.float64)
+        for j, tr in traces.items():
+            sl = slice(j * r, (j + 1) * r)
+            e = max(rel(Wn[:, sl], tr[k - 1]["W"]), rel(Hn[:, sl], tr[k - 1]["Ht"]))
+            print(f"tensor-core row kernels, iteration {k}, restart {j}: {e:.2e} (FP32 envelope {env[k - 1]:.2e})")
+            assert e <= 2.0 * env[k - 1], (k, j, e, env[k - 1])
