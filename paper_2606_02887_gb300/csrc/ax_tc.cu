@@ -245,21 +245,44 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     }
   }
   if (p.e.fused) {
-    // Split K: every slice publishes its partial tile; the last slice of the tile to arrive
-    // (arrival counter) sums the slices in slice order, so the result does not depend on the
-    // arrival order, and runs the epilogue (Y += c X2, partials <P1, A X>, <P2, A X>).
+    // The accumulator leaves TMEM in 64-column chunks through a shared-memory tile (the ring is
+    // free once the accumulator is complete), so every global access below is a coalesced
+    // 16-byte access along a row.  Split K: every slice publishes its partial tile; the last
+    // slice of the tile to arrive (arrival counter) sums the slices in slice order (the result
+    // does not depend on the arrival order) and runs the epilogue: Y = sum (+ c X2), and the
+    // per-restart partials <P1, A X>, <P2, A X> of the tile's two 64-row slots.
+    float* T = reinterpret_cast<float*>(base);  // [128][68]
+    constexpr int TS = 68;
+    const int c4 = threadIdx.x & 15, r8 = threadIdx.x >> 4;  // float4 column, first row
+    auto stage_chunk = [&](int ch) {  // TMEM columns [64 ch, 64 ch + 64) -> T (rows = TMEM lanes)
+      const int cw = min(64, BN - 64 * ch);
+      for (int c = 0; c < cw; c += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)(64 * ch + c), v);
+        float* dst = T + (warp * 32 + lane) * TS + c;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+    };
+    const int nch = (BN + 63) / 64;
     bool last = ok;
     if (p.splits > 1) {
-      if (ok) {  // CTA-uniform: every lane of every warp runs the warp-collective TMEM loads
-        float* Wz = p.Y + (int64_t)blockIdx.z * p.n * p.ldy + (int64_t)row * p.ldy + n0;
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-          float v[16];
-          tmem_ld16(trow + (uint32_t)c0, v);
-          if (row < p.n) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-              if (n0 + c0 + i < p.N) Wz[c0 + i] = v[i];
+      if (ok) {
+        float* Wz = p.Y + (int64_t)blockIdx.z * p.n * p.ldy;
+        for (int ch = 0; ch < nch; ++ch) {
+          stage_chunk(ch);
+          __syncthreads();
+          const int col = n0 + 64 * ch + 4 * c4;
+          if (4 * c4 < BN - 64 * ch && col < p.N) {
+            for (int k = 0; k < 16; ++k) {
+              const int rr = r8 + 8 * k;
+              const int64_t row_g = m0 + rr;
+              if (row_g < p.n)
+                *reinterpret_cast<float4*>(Wz + row_g * p.ldy + col) = *reinterpret_cast<const float4*>(T + rr * TS + 4 * c4);
+            }
           }
+          __syncthreads();
         }
       }
       __threadfence();
@@ -277,53 +300,75 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       last = ok && arrived_last;
     }
     if (last) {
-      const int rr = p.e.r;
+      const int rr_r = p.e.r;
       const bool dots = p.e.P1 || p.e.P2;
-      float d1 = 0.f, d2 = 0.f;
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        float v[16];
-        tmem_ld16(trow + (uint32_t)c0, v);
-        if (row < p.n) {
-          const int64_t base_idx = (int64_t)row * p.ldy + n0 + c0;
-          if (p.splits > 1) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              float y = 0.f;
-              for (int z = 0; z < p.splits; ++z)
-                y += (z == (int)blockIdx.z) ? v[i] : __ldcg(p.Y + (int64_t)z * p.n * p.ldy + base_idx + i);
-              v[i] = y;
+      for (int ch = 0; ch < nch; ++ch) {
+        stage_chunk(ch);
+        __syncthreads();
+        const int col = n0 + 64 * ch + 4 * c4;
+        float d1[2] = {0.f, 0.f}, d2[2] = {0.f, 0.f};  // per 64-row slot
+        if (4 * c4 < BN - 64 * ch && col < p.N) {
+          for (int k = 0; k < 16; ++k) {
+            const int rr = r8 + 8 * k;
+            const int64_t row_g = m0 + rr;
+            if (row_g >= p.n) continue;
+            const int64_t idx = row_g * p.ldy + col;
+            float4 y = *reinterpret_cast<const float4*>(T + rr * TS + 4 * c4);
+            if (p.splits > 1) {
+              float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+              for (int z = 0; z < p.splits; ++z) {
+                const float4 v = (z == (int)blockIdx.z)
+                                     ? y
+                                     : __ldcg(reinterpret_cast<const float4*>(p.Y + (int64_t)z * p.n * p.ldy + idx));
+                acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+              }
+              y = acc;
             }
-          }
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            if (n0 + c0 + i >= p.N) continue;
-            const int64_t idx = base_idx + i;
-            float y = v[i];
-            if (p.e.P1) d1 += p.e.P1[idx] * y;
-            if (p.e.P2) d2 += p.e.P2[idx] * y;
-            if (p.e.X2) y += p.e.c * p.e.X2[idx];
-            p.e.Y[idx] = y;
+            if (p.e.P1) {
+              const float4 q = *reinterpret_cast<const float4*>(p.e.P1 + idx);
+              d1[rr >> 6] += q.x * y.x + q.y * y.y + q.z * y.z + q.w * y.w;
+            }
+            if (p.e.P2) {
+              const float4 q = *reinterpret_cast<const float4*>(p.e.P2 + idx);
+              d2[rr >> 6] += q.x * y.x + q.y * y.y + q.z * y.z + q.w * y.w;
+            }
+            if (p.e.X2) {
+              const float4 q = *reinterpret_cast<const float4*>(p.e.X2 + idx);
+              y.x += p.e.c * q.x; y.y += p.e.c * q.y; y.z += p.e.c * q.z; y.w += p.e.c * q.w;
+            }
+            *reinterpret_cast<float4*>(p.e.Y + idx) = y;
           }
         }
-        if (dots && ((n0 + c0 + 16) % rr == 0 || c0 + 16 >= BN)) {
-          // end of restart j = (n0 + c0) / r inside this tile: the partials of its two 64-row
-          // slots (warps 0-1 and 2-3), summed in a fixed order
-          d1 = warp_sum(d1);
-          d2 = warp_sum(d2);
-          if (lane == 0) { s_red[warp][0] = d1; s_red[warp][1] = d2; }
+        if (dots) {
+          // partials of each restart in this chunk (r divides 64) and slot, summed over the
+          // threads of its columns in thread order
+          __syncthreads();  // every thread is done with T
+          float* red = T;   // [128][4]
+          red[4 * threadIdx.x + 0] = d1[0];
+          red[4 * threadIdx.x + 1] = d2[0];
+          red[4 * threadIdx.x + 2] = d1[1];
+          red[4 * threadIdx.x + 3] = d2[1];
           __syncthreads();
-          const int j = (n0 + c0) / rr;
-          if (threadIdx.x < 2 && j < p.e.b) {
-            const int64_t slot = 2 * (int64_t)blockIdx.y + threadIdx.x;
-            if (slot * 64 < p.n) {
+          const int cw = min(64, BN - 64 * ch);
+          const int nres = cw / rr_r;  // restarts in this chunk
+          if ((int)threadIdx.x < 2 * nres) {
+            const int jl = threadIdx.x >> 1, slot_l = threadIdx.x & 1;
+            float s1 = 0.f, s2 = 0.f;
+            for (int t = 0; t < 128; ++t) {
+              if ((4 * (t & 15)) / rr_r != jl) continue;
+              s1 += red[4 * t + 2 * slot_l];
+              s2 += red[4 * t + 2 * slot_l + 1];
+            }
+            const int j = (n0 + 64 * ch) / rr_r + jl;
+            const int64_t slot = 2 * (int64_t)blockIdx.y + slot_l;
+            if (j < p.e.b && slot * 64 < p.n) {
               double* q = p.e.part + (slot * p.e.b + j) * kNQ + p.e.q0;
-              q[0] = (double)(s_red[2 * threadIdx.x][0] + s_red[2 * threadIdx.x + 1][0]);
-              q[1] = (double)(s_red[2 * threadIdx.x][1] + s_red[2 * threadIdx.x + 1][1]);
+              q[0] = (double)s1;
+              q[1] = (double)s2;
             }
           }
-          __syncthreads();
-          d1 = d2 = 0.f;
         }
+        __syncthreads();  // T free for the next chunk
       }
     }
   }

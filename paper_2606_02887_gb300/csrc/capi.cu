@@ -91,9 +91,9 @@ struct snmf_ctx {
   void* xl = nullptr;
   int xparts = 2;                // BF16 product: X as hi + lo parts (2) or rounded to BF16 (1)
   unsigned* tcount = nullptr;    // BF16 product: arrival counters of the fused split-K epilogue
-  // the fused split-K epilogue reads the slices row by row per thread (uncoalesced); measured
-  // slower than the separate finish pass at n = 8192, N = 512 (331 against 245 us), so off
-  int fuse_epilogue = 0;
+  // the split-K reduction and epilogue fused into the BF16 product (1) or the separate finish
+  // pass (0)
+  int fuse_epilogue = 1;
   long long budget = 2000000000LL;
   __nv_bfloat16* mlp_w = nullptr;  // learned controller weights (BF16)
   float* rec_feat = nullptr;       // record mode dataset
@@ -176,10 +176,11 @@ TcEpilogue tc_epilogue(snmf_ctx* h, void* Y, double c, const void* X2, const voi
   TcEpilogue e;
   if (!h->tcount || !h->fuse_epilogue) return e;
   if (P1 || P2) {
+    // the partials are reduced per 64-column chunk of a tile: r must divide 64 and the tile width
     TcPlan pl;
     const ProdTune* tn = h->tuned ? &h->tune.cfg : nullptr;
     if (tc_plan(h->n, h->N, &pl, tn, h->xparts) < 0) tc_plan(h->n, h->N, &pl, nullptr, h->xparts);
-    if (h->r % 16 != 0 || pl.BN % h->r != 0) return e;
+    if (h->r > 64 || 64 % h->r != 0 || h->r % 4 != 0 || pl.BN % h->r != 0) return e;
   }
   e.fused = 1;
   e.Y = (float*)Y;
