@@ -244,7 +244,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       }
     }
   }
-  if (p.e.fused) {
+  if (p.e.fused && (p.ldy & 3) == 0) {  // 16-byte row groups (the launcher guarantees ldy % 4 == 0)
     // The accumulator leaves TMEM in 64-column chunks through a shared-memory tile (the ring is
     // free once the accumulator is complete), so every global access below is a coalesced
     // 16-byte access along a row.  Split K: every slice publishes its partial tile; the last

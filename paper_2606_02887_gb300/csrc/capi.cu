@@ -174,7 +174,8 @@ Dims dims(const snmf_ctx* h) {
 TcEpilogue tc_epilogue(snmf_ctx* h, void* Y, double c, const void* X2, const void* P1, const void* P2,
                        double* part) {
   TcEpilogue e;
-  if (!h->tcount || !h->fuse_epilogue) return e;
+  // the fused epilogue moves 16-byte groups along rows: the row pitch N must be a multiple of 4
+  if (!h->tcount || !h->fuse_epilogue || h->N % 4 != 0) return e;
   if (P1 || P2) {
     // the partials are reduced per 64-column chunk of a tile: r must divide 64 and the tile width
     TcPlan pl;

@@ -68,6 +68,9 @@ class snmf_stats(C.Structure):
 
 
 _lib = None
+# Inputs a handle borrows (a device A in the working precision must outlive the handle): held
+# here from snmf_create until snmf_destroy, so a caller's temporary cannot be freed under it.
+_BORROWED = {}
 
 
 def load_library(path: str = LIB_PATH):
@@ -203,6 +206,7 @@ def snmf_create(matrix, r: int, options: snmf_options | None = None, stream=None
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     st = lib.snmf_create(C.byref(h), C.byref(m), int(r), C.byref(opt), s)
     _check(lib, None, st)
+    _BORROWED[h.value] = _keep
     return h
 
 
@@ -373,7 +377,10 @@ def snmf_tuned_config(h) -> dict:
 
 def snmf_destroy(h):
     lib = load_library()
-    return lib.snmf_destroy(h)
+    st = lib.snmf_destroy(h)
+    if h is not None:
+        _BORROWED.pop(getattr(h, "value", h), None)
+    return st
 
 
 def snmf_last_error(h=None) -> str:
