@@ -212,12 +212,14 @@ def run_reference(args):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch, from the ncu captures summarised
-# in profiles/ (k_gemm_tc_dense8192_N512.md, k_rowgemm_dstep_dense8192_N512.md,
-# k_bgemm_tc_uneven256.md); keys: (workload, precision, r, batch, kernel), values: (bytes,
-# the tuned tile shapes of the capture, which the run must share).  Other configurations,
-# and runs tuned to other tiles, report null.
+# in profiles/ (k_gemm_tc_dense8192_N512.md, k_rowfuse_dstep_dense8192_N512.md,
+# k_bgemm_tc_uneven256.md); keys: (workload, precision, r, batch, kernel, row-kernel body or
+# X parts), values: (bytes, the tuned tile shapes of the capture, which the run must share).
+# Other configurations, and runs tuned to other tiles, report null.
 PROFILED_TRAFFIC = {
     ("uneven", "bf16", None, None, "product"): (875.5e6, {}),
+    ("dense8192", "bf16", 64, 8, "dstep", 2): (51.4e6, {"row_bm": 128}),
+    ("dense8192", "bf16", 64, 8, "product", 2): (274.1e6, {"splits": 4, "bn": 128}),
 }
 
 

@@ -8,12 +8,12 @@
 // A_hi B_hi + A_hi B_lo + A_lo B_hi (three MMAs per K step, the lo x lo term of relative size
 // 2^-22 dropped), so the row products carry about FP32 accuracy.
 //
-// CTA: 128 rows of restart blockIdx.y, 256 threads.  Thread (warp w, lane l) owns row
-// 32 (w % 4) + l and columns 32 (w / 4) .. 32 (w / 4) + 31: the TMEM lane quadrant of warp w is
-// w % 4, so each thread reads its own accumulator row.  Operand tiles in shared memory are
-// K-major with the 128-byte swizzle (two 32-column atoms per 64-column row; 16-byte chunk c of
-// row m stored at chunk c ^ (m % 8)), written from registers by the threads; one elected
-// thread issues the MMAs and commits them to an mbarrier that the CTA waits on (bounded).
+// CTA: 128 rows of restart blockIdx.y, 256 threads.  Operand tiles in shared memory are K-major
+// with the 128-byte swizzle (two 32-column atoms per 64-column row; 16-byte chunk c of row m
+// stored at chunk c ^ (m % 8)), written from registers by the threads; one elected thread issues
+// the MMAs and commits them to an mbarrier that the CTA waits on (bounded).  Global memory is
+// accessed in a coalesced mapping, the accumulator read from TMEM row-wise and passed through
+// shared memory (see the thread mappings below).
 #include <math.h>
 
 #include "common.cuh"
@@ -229,6 +229,47 @@ __device__ __forceinline__ void block_partials(const RowArgs& a, const float (&d
   }
 }
 
+// Thread mappings.  Elementwise work and every global access use the coalesced mapping: thread
+// t owns float4 column c4 = t % 16 (columns 4 c4 .. 4 c4 + 3) of rows t / 16 + 16 k, k < 8, so 16
+// threads read a 256-byte row segment together.  The accumulator leaves TMEM row-wise (warp w
+// reads lanes 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31) into a staging tile T with the
+// operand's swizzled layout, placed in the lo-part region of the operand tile, which the tensor
+// cores no longer read once the product has completed.
+constexpr int CM_ROWS = 8;  // rows per thread in the coalesced mapping
+
+__device__ __forceinline__ float4 ld_sw(const unsigned char* part, int m, int k) {
+  return *reinterpret_cast<const float4*>(part + sw_chunk(m, k, TR));
+}
+
+// TMEM accumulator columns [col, col + 64) -> T (swizzled like the operand tile)
+__device__ __forceinline__ void stage_acc(uint32_t tacc, int col, unsigned char* T, int mrow, int c0) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float v[16];
+    tmem_ld16(tacc + (uint32_t)(col + c0 + 16 * h), v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      *reinterpret_cast<float4*>(T + sw_chunk(mrow, c0 + 16 * h + 4 * q, TR)) =
+          make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  }
+}
+
+// Set-up shared by both kernels: barrier, TMEM (128 columns), G parts.
+__device__ __forceinline__ void tc_setup(uint64_t* bar, uint32_t* tmem_slot, int* s_bad, const float* G,
+                                         const TcTile& t) {
+  if (threadIdx.x == 0) {
+    *s_bad = 0;
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  load_gram_parts(G, t);
+}
+
 // ---------------------------------------------------------------------------------------
 // D step: q0 <g(Z), D>, q1 ||D||^2, q2 f(Z) - f(X), q4 <D G, D>; others zero.
 // ---------------------------------------------------------------------------------------
@@ -248,37 +289,28 @@ __global__ void __launch_bounds__(256, 2) k_rowtc_dstep(RowArgs a, int* err) {
   if (live) {
     const TcTile t = carve(tsm_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mrow = 32 * (warp & 3) + lane;        // row within the tile (TMEM lane)
-    const int c0 = 32 * (warp >> 2);                 // first of the thread's 32 columns
-    const int64_t i = (int64_t)blockIdx.x * TR + mrow;
-    const bool rv = i < a.n;
-    const int64_t off = i * a.ld + (int64_t)j * RC + c0;
+    const int mrow = 32 * (warp & 3) + lane, c0 = 32 * (warp >> 2);  // TMEM row mapping
+    const int c4 = threadIdx.x & 15, rw = threadIdx.x >> 4;            // coalesced mapping
+    const int64_t row_base = (int64_t)blockIdx.x * TR;
+    const int64_t colg = (int64_t)j * RC + 4 * c4;
     const float* X = (const float*)a.X;
     const float* g = (const float*)a.g_in;
     const float* B = (const float*)a.B;
     float* gZo = (float*)a.gZout;
     const float inv_rho = (float)(1.0 / cj.rho);
     const float alpha = (float)cj.alpha;
-    if (threadIdx.x == 0) {
-      s_bad = 0;
-      mbar_init(&bar, 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                   "r"(128));
-      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    load_gram_parts((const float*)a.G + (int64_t)j * RC * RC, t);
-    // Z tile: Z = Proj[X - g / rho] of the thread's 32 elements, hi / lo parts
+    tc_setup(&bar, &tmem_slot, &s_bad, (const float*)a.G + (int64_t)j * RC * RC, t);
+    // Z tile: Z = Proj[X - g / rho], hi / lo parts
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int k = 0; k < CM_ROWS; ++k) {
+      const int m = rw + 16 * k;
+      const int64_t i = row_base + m;
       float4 x4 = make_float4(0.f, 0.f, 0.f, 0.f), g4 = x4;
-      if (rv) {
-        x4 = ld4(X + off + 4 * c);
-        g4 = ld4(g + off + 4 * c);
+      if (i < a.n) {
+        x4 = ld4(X + i * a.ld + colg);
+        g4 = ld4(g + i * a.ld + colg);
       }
-      put4(t.ah, t.al, sw_chunk(mrow, c0 + 4 * c, TR), zstep1(x4.x, g4.x, inv_rho), zstep1(x4.y, g4.y, inv_rho),
+      put4(t.ah, t.al, sw_chunk(m, 4 * c4, TR), zstep1(x4.x, g4.x, inv_rho), zstep1(x4.y, g4.y, inv_rho),
            zstep1(x4.z, g4.z, inv_rho), zstep1(x4.w, g4.w, inv_rho));
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -287,57 +319,64 @@ __global__ void __launch_bounds__(256, 2) k_rowtc_dstep(RowArgs a, int* err) {
     const uint32_t tmem = tmem_slot;
     const uint32_t tacc = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     run_product(t, tmem, &bar);  // Z G -> columns 0 .. 63
-    float4 b4[8];  // B of the thread's elements, in flight during the product
+    float4 b4[CM_ROWS];  // B of the thread's elements, in flight during the product
 #pragma unroll
-    for (int c = 0; c < 8; ++c) b4[c] = rv ? ld4(B + off + 4 * c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < CM_ROWS; ++k) {
+      const int64_t i = row_base + rw + 16 * k;
+      b4[k] = i < a.n ? ld4(B + i * a.ld + colg) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     int issued = 1;  // products committed to `bar` (the drain waits for the last one)
     bool ok = wait_product(&bar, 0, &s_bad, err);
-    float d[32];
+    float d[CM_ROWS][4];
     if (ok) {
+      stage_acc(tacc, 0, t.al, mrow, c0);  // Z G -> T (the lo part of Z is no longer read)
+      __syncthreads();
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float acc[16];
-        tmem_ld16(tacc + (uint32_t)(c0 + 16 * h), acc);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int cc = 4 * h + c;  // float4 index within the thread's 32 columns
-          float4 x4 = make_float4(0.f, 0.f, 0.f, 0.f), g4 = x4;
-          if (rv) {
-            x4 = ld4(X + off + 4 * cc);
-            g4 = ld4(g + off + 4 * cc);
-          }
-          const float xs[4] = {x4.x, x4.y, x4.z, x4.w}, gs[4] = {g4.x, g4.y, g4.z, g4.w};
-          const float bs[4] = {b4[cc].x, b4[cc].y, b4[cc].z, b4[cc].w};
-          float gz[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float z = zstep1(xs[q], gs[q], inv_rho);
-            gz[q] = acc[4 * c + q] - bs[q];
-            const float dv = rv ? dir1(z, gz[q], alpha) : 0.f;
-            if (rv) {
-              dq[0] += gz[q] * dv;
-              dq[1] += dv * dv;
-              dq[2] += 0.5f * (z - xs[q]) * (gz[q] + gs[q]);
-            }
-            d[4 * cc + q] = dv;
-          }
-          if (rv) st4(gZo + off + 4 * cc, make_float4(gz[0], gz[1], gz[2], gz[3]));
-          // D into the operand tile (the tensor cores are done with Z: the product completed)
-          put4(t.ah, t.al, sw_chunk(mrow, c0 + 4 * cc, TR), d[4 * cc], d[4 * cc + 1], d[4 * cc + 2], d[4 * cc + 3]);
+      for (int k = 0; k < CM_ROWS; ++k) {
+        const int m = rw + 16 * k;
+        const int64_t i = row_base + m;
+        const bool rv = i < a.n;
+        const float4 acc = ld_sw(t.al, m, 4 * c4);
+        float4 x4 = make_float4(0.f, 0.f, 0.f, 0.f), g4 = x4;
+        if (rv) {
+          x4 = ld4(X + i * a.ld + colg);
+          g4 = ld4(g + i * a.ld + colg);
         }
+        const float xs[4] = {x4.x, x4.y, x4.z, x4.w}, gs[4] = {g4.x, g4.y, g4.z, g4.w};
+        const float as[4] = {acc.x, acc.y, acc.z, acc.w};
+        const float bs[4] = {b4[k].x, b4[k].y, b4[k].z, b4[k].w};
+        float gz[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float z = zstep1(xs[q], gs[q], inv_rho);
+          gz[q] = as[q] - bs[q];
+          const float dv = rv ? dir1(z, gz[q], alpha) : 0.f;
+          if (rv) {
+            dq[0] += gz[q] * dv;
+            dq[1] += dv * dv;
+            dq[2] += 0.5f * (z - xs[q]) * (gz[q] + gs[q]);
+          }
+          d[k][q] = dv;
+        }
+        if (rv) st4(gZo + i * a.ld + colg, make_float4(gz[0], gz[1], gz[2], gz[3]));
+        // D into the operand tile: the same chunk this thread just read (T in the lo part)
+        put4(t.ah, t.al, sw_chunk(m, 4 * c4, TR), d[k][0], d[k][1], d[k][2], d[k][3]);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       run_product(t, tmem + 64, &bar);  // D G -> columns 64 .. 127
       issued = 2;
       ok = wait_product(&bar, 1, &s_bad, err);
       if (ok) {
+        stage_acc(tacc, 64, t.al, mrow, c0);  // D G -> T
+        __syncthreads();
         float qq = 0.f;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float dg[16];
-          tmem_ld16(tacc + 64 + (uint32_t)(c0 + 16 * h), dg);
-#pragma unroll
-          for (int q = 0; q < 16; ++q) qq = fmaf(dg[q], d[16 * h + q], qq);
+        for (int k = 0; k < CM_ROWS; ++k) {
+          const float4 dg = ld_sw(t.al, rw + 16 * k, 4 * c4);
+          qq = fmaf(dg.x, d[k][0], qq);
+          qq = fmaf(dg.y, d[k][1], qq);
+          qq = fmaf(dg.z, d[k][2], qq);
+          qq = fmaf(dg.w, d[k][3], qq);
         }
         dq[4] = qq;
       }
@@ -370,11 +409,10 @@ __global__ void __launch_bounds__(256, 2) k_rowtc_update(RowArgs a, int* err) {
   if (live) {
     const TcTile t = carve(tsm_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mrow = 32 * (warp & 3) + lane;
-    const int c0 = 32 * (warp >> 2);
-    const int64_t i = (int64_t)blockIdx.x * TR + mrow;
-    const bool rv = i < a.n;
-    const int64_t off = i * a.ld + (int64_t)j * RC + c0;
+    const int mrow = 32 * (warp & 3) + lane, c0 = 32 * (warp >> 2);
+    const int c4 = threadIdx.x & 15, rw = threadIdx.x >> 4;
+    const int64_t row_base = (int64_t)blockIdx.x * TR;
+    const int64_t colg = (int64_t)j * RC + 4 * c4;
     float* X = (float*)a.Xout;  // in place: X_k in, X_{k+1} out
     float* g = (float*)a.gout;  // in place: g(X_k) in, g(X_{k+1}) out
     const float* gZ = (const float*)a.gZold;
@@ -382,25 +420,17 @@ __global__ void __launch_bounds__(256, 2) k_rowtc_update(RowArgs a, int* err) {
     const float inv_rho = (float)(1.0 / cj.rho);
     const float alpha = (float)cj.alpha;
     const float pb = (float)cj.phibeta;
-    if (threadIdx.x == 0) {
-      s_bad = 0;
-      mbar_init(&bar, 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                   "r"(128));
-      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    load_gram_parts((const float*)a.G + (int64_t)j * RC * RC, t);
+    tc_setup(&bar, &tmem_slot, &s_bad, (const float*)a.G + (int64_t)j * RC * RC, t);
     // X' tile: X' = Proj[Z + phi beta D] with Z, D recomputed from X, g, g(Z)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int k = 0; k < CM_ROWS; ++k) {
+      const int m = rw + 16 * k;
+      const int64_t i = row_base + m;
       float4 x4 = make_float4(0.f, 0.f, 0.f, 0.f), g4 = x4, z4 = x4;
-      if (rv) {
-        x4 = ld4(X + off + 4 * c);
-        g4 = ld4(g + off + 4 * c);
-        z4 = ld4(gZ + off + 4 * c);
+      if (i < a.n) {
+        x4 = ld4(X + i * a.ld + colg);
+        g4 = ld4(g + i * a.ld + colg);
+        z4 = ld4(gZ + i * a.ld + colg);
       }
       const float xs[4] = {x4.x, x4.y, x4.z, x4.w}, gs[4] = {g4.x, g4.y, g4.z, g4.w};
       const float zs[4] = {z4.x, z4.y, z4.z, z4.w};
@@ -410,7 +440,7 @@ __global__ void __launch_bounds__(256, 2) k_rowtc_update(RowArgs a, int* err) {
         const float z = zstep1(xs[q], gs[q], inv_rho);
         xn[q] = upd1(z, dir1(z, zs[q], alpha), pb);
       }
-      put4(t.ah, t.al, sw_chunk(mrow, c0 + 4 * c, TR), xn[0], xn[1], xn[2], xn[3]);
+      put4(t.ah, t.al, sw_chunk(m, 4 * c4, TR), xn[0], xn[1], xn[2], xn[3]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -418,44 +448,48 @@ __global__ void __launch_bounds__(256, 2) k_rowtc_update(RowArgs a, int* err) {
     const uint32_t tmem = tmem_slot;
     const uint32_t tacc = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     run_product(t, tmem, &bar);  // X' G -> columns 0 .. 63
-    float4 b4[8];
+    float4 b4[CM_ROWS];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) b4[c] = rv ? ld4(B + off + 4 * c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < CM_ROWS; ++k) {
+      const int64_t i = row_base + rw + 16 * k;
+      b4[k] = i < a.n ? ld4(B + i * a.ld + colg) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const bool ok = wait_product(&bar, 0, &s_bad, err);
     if (ok) {
+      stage_acc(tacc, 0, t.al, mrow, c0);  // X' G -> T
+      __syncthreads();
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float acc[16];
-        tmem_ld16(tacc + (uint32_t)(c0 + 16 * h), acc);
+      for (int k = 0; k < CM_ROWS; ++k) {
+        const int m = rw + 16 * k;
+        const int64_t i = row_base + m;
+        if (i >= a.n) continue;
+        const int64_t off = i * a.ld + colg;
+        const float4 acc = ld_sw(t.al, m, 4 * c4);
+        const float4 x4 = ld4(X + off), g4 = ld4(g + off), z4 = ld4(gZ + off);
+        const float xs[4] = {x4.x, x4.y, x4.z, x4.w}, gs[4] = {g4.x, g4.y, g4.z, g4.w};
+        const float zs[4] = {z4.x, z4.y, z4.z, z4.w};
+        const float as[4] = {acc.x, acc.y, acc.z, acc.w};
+        const float bs[4] = {b4[k].x, b4[k].y, b4[k].z, b4[k].w};
+        float xo[4], go[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int cc = 4 * h + c;
-          if (!rv) continue;
-          const float4 x4 = ld4(X + off + 4 * cc), g4 = ld4(g + off + 4 * cc), z4 = ld4(gZ + off + 4 * cc);
-          const float xs[4] = {x4.x, x4.y, x4.z, x4.w}, gs[4] = {g4.x, g4.y, g4.z, g4.w};
-          const float zs[4] = {z4.x, z4.y, z4.z, z4.w};
-          const float bs[4] = {b4[cc].x, b4[cc].y, b4[cc].z, b4[cc].w};
-          float xo[4], go[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float z = zstep1(xs[q], gs[q], inv_rho);
-            const float xn = upd1(z, dir1(z, zs[q], alpha), pb);
-            const float gn = acc[4 * c + q] - bs[q];
-            const float pgv = xn > 0.f ? gn : (gn < 0.f ? gn : 0.f);
-            dq[0] += pgv * pgv;
-            dq[1] += 0.5f * (gn - bs[q]) * xn;
-            const float sv = xn - xs[q], yv = gn - gs[q];
-            dq[2] += sv * sv;
-            dq[3] += sv * yv;
-            dq[4] += yv * yv;
-            dq[5] += 0.5f * (xn - z) * (gn + zs[q]);
-            if (xn == 0.f) dq[6] += 1.f;
-            xo[q] = xn;
-            go[q] = gn;
-          }
-          st4(X + off + 4 * cc, make_float4(xo[0], xo[1], xo[2], xo[3]));
-          st4(g + off + 4 * cc, make_float4(go[0], go[1], go[2], go[3]));
+        for (int q = 0; q < 4; ++q) {
+          const float z = zstep1(xs[q], gs[q], inv_rho);
+          const float xn = upd1(z, dir1(z, zs[q], alpha), pb);
+          const float gn = as[q] - bs[q];
+          const float pgv = xn > 0.f ? gn : (gn < 0.f ? gn : 0.f);
+          dq[0] += pgv * pgv;
+          dq[1] += 0.5f * (gn - bs[q]) * xn;
+          const float sv = xn - xs[q], yv = gn - gs[q];
+          dq[2] += sv * sv;
+          dq[3] += sv * yv;
+          dq[4] += yv * yv;
+          dq[5] += 0.5f * (xn - z) * (gn + zs[q]);
+          if (xn == 0.f) dq[6] += 1.f;
+          xo[q] = xn;
+          go[q] = gn;
         }
+        st4(X + off, make_float4(xo[0], xo[1], xo[2], xo[3]));
+        st4(g + off, make_float4(go[0], go[1], go[2], go[3]));
       }
     }
     if (s_bad && threadIdx.x == 0) mbar_wait(&bar, 0, kDrain);
