@@ -738,9 +738,11 @@ def main():
         # the library reports which row-kernel body runs and the arrays each launch moves
         sc = S.snmf_step_config(h)
         body = {0: "k_rowgemm (general)", 1: "k_rowtile (shared-memory tile body)",
-                2: "k_rowfuse (Z and D recomputed, not stored)"}[sc["body"]]
-        names = {"dstep": ("k_rowfuse_dstep" if sc["body"] == 2 else "k_rowgemm<OP_ZSTEP, EPI_DIR>"),
-                 "update": ("k_rowfuse_update" if sc["body"] == 2 else "k_rowgemm<OP_UPD, EPI_GRAD>")}
+                2: "k_rowfuse (Z and D recomputed, not stored; row products on CUDA cores)",
+                3: "k_rowtc (Z and D recomputed, not stored; row products on tcgen05, TF32 hi + lo)"}[sc["body"]]
+        prefix = {2: "k_rowfuse", 3: "k_rowtc"}.get(sc["body"])
+        names = {"dstep": (prefix + "_dstep" if prefix else "k_rowgemm<OP_ZSTEP, EPI_DIR>"),
+                 "update": (prefix + "_update" if prefix else "k_rowgemm<OP_UPD, EPI_GRAD>")}
         for name, ms_k, nbytes in (("dstep", ms_d, sc["dstep_bytes"]), ("update", ms_u, sc["update_bytes"])):
             gb = nbytes / (ms_k * 1e-3) / 1e9
             kernels[name] = {"bound": "hbm", "kernel": names[name], "body": body,
