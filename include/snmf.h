@@ -291,6 +291,36 @@ SNMF_API snmf_status snmf_get_factors(snmf_handle h, void* W, void* Ht);
 SNMF_API snmf_status snmf_apply(snmf_handle h, const void* X, void* Y, int cols, double* xax);
 
 /*
+ * Checkpoint and exact restart (no counterpart in the paper).  snmf_get_state copies the
+ * per-restart scalar state of the last solve (iteration count, projected gradient at the start
+ * pg0, last H-block projected gradient, counters, and the rest of the FP64 control record) into
+ * `blob` (host) with a version header; blob == NULL only reports the size in *size.
+ * snmf_set_state imports such a blob (same n, r, batch and formulation, same library version)
+ * for the next snmf_solve, which then continues from it: give that solve the factors the
+ * earlier solve returned (W, Ht in/out as usual); its iteration count continues and max_iter
+ * bounds the total.  In the penalty and naive forms every block restarts its BB memory and
+ * nonmonotone reference, so a solve of k outer iterations, exported, and a resumed solve of m more
+ * reproduce a solve of k + m iterations bit for bit.  Restarts that had met the tolerance stay
+ * stopped.  set_state(h, NULL, 0) drops an imported state.
+ * Errors: SNMF_ERR_ARG (buffer too small, foreign or mismatched blob), SNMF_ERR_STATE (no solve
+ * yet, dense batch handle).
+ */
+SNMF_API snmf_status snmf_get_state(snmf_handle h, void* blob, int64_t capacity, int64_t* size);
+SNMF_API snmf_status snmf_set_state(snmf_handle h, const void* blob, int64_t size);
+
+/*
+ * Per-iteration statistics of the last solve (no counterpart in the paper): the device keeps a
+ * ring of the last 256 outer iterations per restart (penalty and naive forms; written by the
+ * control step at the start of every W block).  Copies, per restart j, up to `capacity`
+ * records out[j][t][8] = {outer iteration, ||P grad|| / ||P grad_0||, ||P grad||, last alpha,
+ * last beta, line searches without an accepted trial (cumulative), learned-step proposals
+ * accepted (cumulative), active flag}, oldest first; unused records are -1.  *count: records
+ * per restart written.  The ring is not cleared between solves.
+ */
+SNMF_API snmf_status snmf_stats_ring(snmf_handle h, double* out, int capacity, int32_t* count);
+#define SNMF_RING_VALUES 8
+
+/*
  * Measurement utility (no counterpart in the paper): time `iters` back-to-back
  * A*X products of the handle's factor shape (n x r*batch) on the handle's stream
  * with CUDA events.  *ms_product: mean time of the whole product (kernel and

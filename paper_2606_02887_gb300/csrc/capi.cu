@@ -6,6 +6,7 @@
 // state of Algorithm 1 lives on the device (snmf::Ctl); the host reads one flag every
 // few replays to stop when every restart has converged.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -113,6 +114,10 @@ struct snmf_ctx {
   bool have_result = false;
   int ax_count = 0;
   BatchCtx* bt = nullptr;
+  // per-iteration statistics ring (device) and an imported solver state for an exact restart
+  double* ring = nullptr;
+  int ring_cap = 256;
+  std::vector<Ctl> resume;   // from snmf_set_state: the next solve continues from this state
   // autotuned product configuration (tuned: 1 measured here, 2 from the cache)
   TuneEntry tune{};
   int tuned = 0;          // SNMF_DENSE_BATCH handle: the uneven-batch engine
@@ -159,6 +164,8 @@ Params make_params(const snmf_ctx* h) {
   P.rec_count = h->rec_count;
   P.rec_cap = h->rec_cap;
   P.nr = h->n * (int64_t)h->r;
+  P.ring = h->ring;
+  P.ring_cap = h->ring_cap;
   return P;
 }
 
@@ -800,6 +807,8 @@ snmf_status alloc_buffers(snmf_ctx* h) {
   CK(cudaMalloc(&h->counters, (16384 + 4096) * sizeof(unsigned)));  // Gram tiles, then restarts
   CK(cudaMemsetAsync(h->counters, 0, (16384 + 4096) * sizeof(unsigned), h->s));
   CK(cudaMalloc(&h->dsc, 4096 * sizeof(double)));
+  CK(cudaMalloc(&h->ring, (size_t)h->b * h->ring_cap * kRingVals * sizeof(double)));
+  CK(cudaMemsetAsync(h->ring, 0, (size_t)h->b * h->ring_cap * kRingVals * sizeof(double), h->s));
   CK(cudaMallocHost(&h->h_flag, sizeof(int)));
   return SNMF_OK;
 }
@@ -1120,7 +1129,9 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
   h->lam = o.lambda_sym >= 0.0 ? o.lambda_sym : 0.01 * std::sqrt(h->normA2);
   if (o.formulation == SNMF_NAIVE) h->lam = 0.0;  // the naive variant has no penalty term
   if (o.autotune) {
+    nvtxRangePushA("snmf_create: autotune");
     const snmf_status ts = autotune_product(h);
+    nvtxRangePop();
     if (ts != SNMF_OK) return bail(ts);
   }
   *out = h;
@@ -1327,13 +1338,21 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
     if (Ht && !naive) CK(cudaMemcpyAsync(h->buf[B_HT], Ht, fbytes, kin, h->s));
     else CK(cudaMemcpyAsync(h->buf[B_HT], h->buf[B_W], fbytes, cudaMemcpyDeviceToDevice, h->s));
   }
-  // control state: restarts active; second array = "all live" view for final passes
+  // control state: restarts active; second array = "all live" view for final passes.  An
+  // imported state (snmf_set_state) replaces the first array: its restarts continue with their
+  // iteration counts, pg0 and last H-block projected gradient (the penalty blocks restart their
+  // BB memory and nonmonotone reference at every block, so nothing else carries over).
+  const bool resume = !h->resume.empty();
   h->h_ctl.assign(2 * h->b, Ctl{});
   for (int j = 0; j < 2 * h->b; ++j) {
     h->h_ctl[j].active = 1;
     h->h_ctl[j].lam = h->lam;
     h->h_ctl[j].rho = 1.0;
     h->h_ctl[j].mlp_mult = 1.0;
+  }
+  if (resume) {
+    for (int j = 0; j < h->b; ++j) h->h_ctl[j] = h->resume[j];
+    h->resume.clear();
   }
   CK(cudaMemcpyAsync(h->ctl, h->h_ctl.data(), 2 * h->b * sizeof(Ctl), cudaMemcpyHostToDevice, h->s));
   static const int one = 1, zero = 0;
@@ -1362,10 +1381,17 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
     h->exec_form = form;
   }
   int64_t launches = W ? 0 : 1;
-  CK(cudaGraphLaunch(h->exec[0], h->s));
-  launches += h->nodes[0];
+  nvtxRangePushA("snmf_solve: start");
+  if (!resume) {  // a resumed solve already holds the start's statistics
+    CK(cudaGraphLaunch(h->exec[0], h->s));
+    launches += h->nodes[0];
+  }
+  nvtxRangePop();
+  nvtxRangePushA("snmf_solve: iterations");
   int done = 0, launched = 0, chunk = 1;
-  const int maxit = h->opt.max_iter;
+  int done_before = 0;  // outer iterations of an imported state
+  for (int j = 0; j < h->b; ++j) done_before = std::max(done_before, resume ? h->h_ctl[j].iters : 0);
+  const int maxit = std::max(0, h->opt.max_iter - (h->opt.formulation == SNMF_DIRECT ? 0 : done_before));
   while (launched < maxit) {
     const int m = std::min(chunk, maxit - launched);
     for (int t = 0; t < m; ++t) CK(cudaGraphLaunch(h->exec[1], h->s));
@@ -1376,8 +1402,11 @@ static snmf_status solve_impl(snmf_ctx* h, bool host, void* W, void* Ht, snmf_st
     chunk = std::min(chunk * 2, 8);
   }
   (void)done;
+  nvtxRangePop();
   launches += (int64_t)h->nodes[1] * launched;
+  nvtxRangePushA("snmf_solve: final evaluation");
   CK(cudaGraphLaunch(h->exec[2], h->s));
+  nvtxRangePop();
   launches += h->nodes[2];
   if (W) CK(cudaMemcpyAsync(W, h->buf[B_W], fbytes, kout, h->s));
   if (pen && Ht) CK(cudaMemcpyAsync(Ht, h->buf[B_HT], fbytes, kout, h->s));
@@ -1615,6 +1644,83 @@ snmf_status snmf_step_config(snmf_handle h, int32_t* body, int32_t* rows_per_cta
   return SNMF_OK;
 }
 
+namespace {
+constexpr uint32_t kStateMagic = 0x534E4D46u;  // "SNMF"
+constexpr uint32_t kStateVersion = 1;
+struct StateHeader {
+  uint32_t magic, version, ctl_bytes, formulation;
+  int32_t batch, r;
+  int64_t n;
+};
+}  // namespace
+
+snmf_status snmf_get_state(snmf_handle h, void* blob, int64_t capacity, int64_t* size) {
+  if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
+  const int64_t need = (int64_t)sizeof(StateHeader) + (int64_t)h->b * (int64_t)sizeof(Ctl);
+  if (size) *size = need;
+  if (!blob) return SNMF_OK;  // size query
+  if (capacity < need) return fail(h, SNMF_ERR_ARG, "state buffer too small");
+  if (!h->have_result) return fail(h, SNMF_ERR_STATE, "no solve has run on this handle");
+  StateHeader hd{kStateMagic, kStateVersion, (uint32_t)sizeof(Ctl), (uint32_t)h->opt.formulation, h->b, h->r, h->n};
+  std::memcpy(blob, &hd, sizeof(hd));
+  std::memcpy(static_cast<unsigned char*>(blob) + sizeof(hd), h->h_ctl.data(), (size_t)h->b * sizeof(Ctl));
+  return SNMF_OK;
+}
+
+snmf_status snmf_set_state(snmf_handle h, const void* blob, int64_t size) {
+  if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
+  if (!blob) {
+    h->resume.clear();
+    return SNMF_OK;
+  }
+  StateHeader hd{};
+  if (size < (int64_t)sizeof(hd)) return fail(h, SNMF_ERR_ARG, "state blob too small");
+  std::memcpy(&hd, blob, sizeof(hd));
+  if (hd.magic != kStateMagic || hd.version != kStateVersion || hd.ctl_bytes != sizeof(Ctl))
+    return fail(h, SNMF_ERR_ARG, "not a state blob of this library version");
+  if (hd.batch != h->b || hd.r != h->r || hd.n != h->n || (int)hd.formulation != h->opt.formulation)
+    return fail(h, SNMF_ERR_ARG, "state of another problem shape or formulation");
+  if (size < (int64_t)sizeof(hd) + (int64_t)h->b * (int64_t)sizeof(Ctl)) return fail(h, SNMF_ERR_ARG, "state truncated");
+  h->resume.resize(h->b);
+  std::memcpy(h->resume.data(), static_cast<const unsigned char*>(blob) + sizeof(hd), (size_t)h->b * sizeof(Ctl));
+  for (auto& c : h->resume) {
+    // a restart that had stopped at the tolerance stays stopped; the others continue
+    const bool conv = c.pg0 == 0.0 || c.pg <= h->opt.tol * c.pg0;
+    c.active = (!conv && !c.nan_seen) ? 1 : 0;
+  }
+  return SNMF_OK;
+}
+
+snmf_status snmf_stats_ring(snmf_handle h, double* out, int capacity, int32_t* count) {
+  if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
+  if (!out || capacity < 1) return fail(h, SNMF_ERR_ARG, "bad ring arguments");
+  const int cap = std::min(capacity, h->ring_cap);
+  std::vector<double> buf((size_t)h->b * h->ring_cap * kRingVals);
+  CK(cudaMemcpyAsync(buf.data(), h->ring, buf.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  int kept = 0;
+  for (int j = 0; j < h->b; ++j) {
+    const int iters = j < (int)h->h_ctl.size() ? h->h_ctl[j].iters : 0;
+    const int have = std::min(std::min(iters + 1, h->ring_cap), cap);  // records 0 .. iters
+    for (int t = 0; t < cap; ++t) {
+      double* dst = out + ((int64_t)j * cap + t) * kRingVals;
+      if (t < have) {
+        const int it = iters + 1 - have + t;
+        const double* src = buf.data() + ((int64_t)j * h->ring_cap + (it % h->ring_cap)) * kRingVals;
+        std::memcpy(dst, src, kRingVals * sizeof(double));
+      } else {
+        for (int v = 0; v < kRingVals; ++v) dst[v] = -1.0;
+      }
+    }
+    kept = std::max(kept, have);
+  }
+  if (count) *count = kept;
+  return SNMF_OK;
+}
+
 snmf_status snmf_set_timeout(snmf_handle h, int64_t cycles) {
   if (!h) return SNMF_ERR_STATE;
   if (cycles < 0) return fail(h, SNMF_ERR_ARG, "cycles must be >= 0");
@@ -1661,7 +1767,7 @@ snmf_status snmf_destroy(snmf_handle h) {
   for (void* p : h->buf) cudaFree(p);
   cudaFree(h->ws);
   double* parts[] = {h->prow, h->pax, h->pax2, h->pax3, h->pax4, h->pclip, h->gpart, h->G64fix,
-                     h->G64p, h->dsc};
+                     h->G64p, h->dsc, h->ring};
   for (double* p : parts) cudaFree(p);
   cudaFree(h->GT);
   cudaFree(h->ctl);

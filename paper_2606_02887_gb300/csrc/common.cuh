@@ -94,7 +94,13 @@ struct Params {
   int* rec_count;
   int rec_cap;
   int64_t nr;        // entries per restart (n * r), for the active-set feature
+  double* ring;      // per-iteration statistics: ring[j][slot][kRingVals] (NULL: off)
+  int ring_cap;      // slots per restart
 };
+
+// Values of one statistics record (penalty and naive forms: written at the start of every W block,
+// i.e. once per outer iteration, for the state after the previous iteration).
+constexpr int kRingVals = 8;  // iteration, pg / pg0, pg, alpha, beta, ls_fail, ctl proposals accepted, active
 
 // ---------------------------------------------------------------------------
 // device helpers

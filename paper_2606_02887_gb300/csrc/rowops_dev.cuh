@@ -217,6 +217,17 @@ __device__ void pen_start_body(Ctl& c, const double* prow, int nrow, int b, int 
     const double joint = sqrt(pg2 + c.pgH2);
     c.pg = joint;
     if (c.iters == 0) c.pg0 = joint;
+    if (P.ring && P.ring_cap > 0) {  // statistics of the state reached by the last outer iteration
+      double* rec = P.ring + ((int64_t)j * P.ring_cap + (c.iters % P.ring_cap)) * kRingVals;
+      rec[0] = (double)c.iters;
+      rec[1] = c.pg0 > 0.0 ? joint / c.pg0 : 0.0;
+      rec[2] = joint;
+      rec[3] = c.alpha;
+      rec[4] = c.beta;
+      rec[5] = (double)c.ls_fail;
+      rec[6] = (double)c.mlp_accept;
+      rec[7] = (double)c.active;
+    }
     else if (joint <= P.tol * c.pg0 || c.iters >= P.max_iter) { c.active = 0; return; }
     if (!isfinite(joint)) { c.nan_seen = 1; c.active = 0; return; }
   } else {

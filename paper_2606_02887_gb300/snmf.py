@@ -30,7 +30,9 @@ EXPORTED = (
     "snmf_apply", "snmf_profile_ax", "snmf_apply_dense_noalloc", "snmf_controller_data",
     "snmf_mlp_train", "snmf_tuned_config", "snmf_tuned_tiles", "snmf_profile_steps", "snmf_destroy", "snmf_last_error",
     "snmf_mlp_eval", "snmf_set_timeout", "snmf_step_config", "snmf_svd_init",
+    "snmf_get_state", "snmf_set_state", "snmf_stats_ring",
 )
+SNMF_RING_VALUES = 8
 NOALLOC_SCRATCH_BYTES = 64 << 20
 NOALLOC_PARTIAL_BYTES = 4 << 20
 NOALLOC_MAX_SLICE_PAIR_BYTES = NOALLOC_SCRATCH_BYTES - NOALLOC_PARTIAL_BYTES
@@ -105,6 +107,9 @@ def load_library(path: str = LIB_PATH):
     lib.snmf_mlp_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
     lib.snmf_set_timeout.argtypes = [H, C.c_int64]
     lib.snmf_svd_init.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_uint64]
+    lib.snmf_get_state.argtypes = [H, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
+    lib.snmf_set_state.argtypes = [H, C.c_void_p, C.c_int64]
+    lib.snmf_stats_ring.argtypes = [H, C.c_void_p, C.c_int, C.POINTER(C.c_int32)]
     lib.snmf_step_config.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_int64)]
     lib.snmf_destroy.argtypes = [H]
@@ -225,6 +230,34 @@ def snmf_svd_init(h, W, Ht=None, oversample: int = 10, power_iters: int = 2, see
     """SVD start |U E^1/2| (Sec. 4.1 guideline (4)) into device tensors W (and Ht)."""
     lib = load_library()
     return _check(lib, h, lib.snmf_svd_init(h, _ptr(W), _ptr(Ht), int(oversample), int(power_iters), int(seed)))
+
+
+def snmf_get_state(h) -> bytes:
+    """The last solve's per-restart scalar state (for snmf_set_state)."""
+    lib = load_library()
+    size = C.c_int64()
+    _check(lib, h, lib.snmf_get_state(h, None, 0, C.byref(size)))
+    buf = (C.c_ubyte * size.value)()
+    _check(lib, h, lib.snmf_get_state(h, buf, size.value, C.byref(size)))
+    return bytes(buf)
+
+
+def snmf_set_state(h, blob):
+    """Continue the next solve from a state of snmf_get_state (None drops it)."""
+    lib = load_library()
+    if blob is None:
+        return _check(lib, h, lib.snmf_set_state(h, None, 0))
+    buf = (C.c_ubyte * len(blob)).from_buffer_copy(blob)
+    return _check(lib, h, lib.snmf_set_state(h, buf, len(blob)))
+
+
+def snmf_stats_ring(h, batch: int, capacity: int = 256):
+    """Per-restart statistics records [batch, capacity, 8] of the last solve (see snmf.h)."""
+    lib = load_library()
+    out = np.zeros((batch, capacity, SNMF_RING_VALUES), dtype=np.float64)
+    cnt = C.c_int32()
+    _check(lib, h, lib.snmf_stats_ring(h, out.ctypes.data, int(capacity), C.byref(cnt)))
+    return out, cnt.value
 
 
 def snmf_solve(h, W=None, Ht=None):
