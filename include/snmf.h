@@ -456,6 +456,45 @@ SNMF_API snmf_status snmf_mlp_eval(const float* weights, const float* feats, int
  */
 SNMF_API snmf_status snmf_set_timeout(snmf_handle h, int64_t cycles);
 
+/*
+ * Similarity graph of data points for Graph-SNMPBB (Sec. 2.2 builds it on a similarity graph;
+ * the recipe is the clustering workload's; no counterpart entry point in the paper).
+ *   X            device, n x d row-major FP32 points
+ *   k            neighbours per point (1 <= k <= 32, k < n): the k nearest other points by
+ *                squared Euclidean distance (FP32), ties to the lower index
+ *   sigma_rank   1 <= sigma_rank <= k: s_i = distance to the sigma_rank-th neighbour;
+ *                S_ij = exp(-d_ij^2 / (s_i s_j)) on the kNN pairs, symmetrised as max(S, S^T)
+ *   rowptr       device, n + 1 int32, out; colidx, a_hat: device, capacity entries, out: the CSR
+ *                matrix A^ = D^-1/2 S D^-1/2 (d_i = sum_j S_ij), columns ascending per row
+ *   s_values     device, capacity entries, out (may be NULL): S on the same pattern
+ *   degree       device, n FP32, out (may be NULL): d_i
+ *   capacity     entries available; 2 n k always suffices.  *nnz (host) receives the count;
+ *                a count above capacity returns SNMF_ERR_ARG with *nnz set.
+ * Work runs on `stream`; the call returns when it is done.  Allocates device scratch.
+ * Errors: SNMF_ERR_ARG, SNMF_ERR_OOM, SNMF_ERR_CUDA.
+ */
+SNMF_API snmf_status snmf_knn_graph(const float* X, int64_t n, int d, int k, int sigma_rank, int32_t* rowptr,
+                                    int32_t* colidx, float* a_hat, float* s_values, float* degree,
+                                    int64_t capacity, int64_t* nnz, void* stream);
+
+/*
+ * Cluster labels of the last solve's restart `restart` (the reading of the clustering
+ * experiments: point i belongs to argmax_c H[c][i], i.e. the largest entry of row i of Ht; W in
+ * the direct and naive forms; ties to the lowest c).  labels: device, n int32, out.
+ */
+SNMF_API snmf_status snmf_cluster_assign(snmf_handle h, int restart, int32_t* labels);
+
+/*
+ * Clustering scores (Sec. 4 reports accuracy and ARI): the contingency table of two labelings
+ * (device int32 arrays of n labels in [0, k_true) and [0, k_pred), k_true k_pred <= 4096) on the
+ * device; from it the adjusted Rand index of Hubert and Arabie and the accuracy of the best
+ * one-to-one matching of predicted to true labels (Hungarian method) on the host.  table
+ * (host, k_true x k_pred), ari, accuracy: outputs, each may be NULL.
+ * Errors: SNMF_ERR_ARG (label out of range, sizes), SNMF_ERR_OOM, SNMF_ERR_CUDA.
+ */
+SNMF_API snmf_status snmf_cluster_scores(const int32_t* truth, const int32_t* pred, int64_t n, int k_true,
+                                         int k_pred, int64_t* table, double* ari, double* accuracy, void* stream);
+
 /* Release every resource of the handle.  NULL is accepted. */
 SNMF_API snmf_status snmf_destroy(snmf_handle h);
 

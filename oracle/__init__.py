@@ -37,3 +37,4 @@ from .snmpbb import (  # noqa: F401
 from .philox import philox4x32, philox_uniform, philox_gaussian  # noqa: F401
 from .lai import lai_sketch  # noqa: F401
 from . import mlp  # noqa: F401
+from . import knn  # noqa: F401

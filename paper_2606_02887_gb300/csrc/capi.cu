@@ -1721,6 +1721,19 @@ snmf_status snmf_stats_ring(snmf_handle h, double* out, int capacity, int32_t* c
   return SNMF_OK;
 }
 
+snmf_status snmf_cluster_assign(snmf_handle h, int restart, int32_t* labels) {
+  if (!h) return SNMF_ERR_STATE;
+  if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
+  if (!labels || restart < 0 || restart >= h->b) return fail(h, SNMF_ERR_ARG, "bad cluster_assign arguments");
+  if (!h->have_result) return fail(h, SNMF_ERR_STATE, "no solve has run on this handle");
+  // the paper's reading: cluster of point i = argmax over the columns of its H row
+  const void* F = h->buf[h->opt.formulation == SNMF_PENALTY ? B_HT : B_W];
+  launch_assign(h->tdtype, F, h->n, h->N, (int64_t)restart * h->r, h->r, labels, h->s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->s));
+  return SNMF_OK;
+}
+
 snmf_status snmf_set_timeout(snmf_handle h, int64_t cycles) {
   if (!h) return SNMF_ERR_STATE;
   if (cycles < 0) return fail(h, SNMF_ERR_ARG, "cycles must be >= 0");

@@ -183,6 +183,9 @@ int launch_ax_finish_impl(int tdtype, const Dims& d, void* Y, const void* ws, in
                           double c, const void* X2, const void* P1, const void* P2,
                           double* part, int q0, const int* run_flag, cudaStream_t s, int dots_after = 0);
 
+// label_i = argmax_c F[i, col0 + c], c < r (ties: lowest c) (knn.cu)
+void launch_assign(int tdtype, const void* F, int64_t n, int64_t ld, int64_t col0, int r, int32_t* lab, cudaStream_t s);
+
 // The paper's normalized Laplacian L = I - D^-1/2 A D^-1/2 (Sec. 2.2) of a dense (FP64/FP32)
 // or CSR A: s[i] = d_i^-1/2 (0 where d_i <= 0, d_i the FP64 row sum) and out = the entries of
 // -D^-1/2 A D^-1/2 in the factor type (dense: n x n with leading dimension n; CSR: the values

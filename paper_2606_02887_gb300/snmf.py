@@ -31,6 +31,7 @@ EXPORTED = (
     "snmf_mlp_train", "snmf_tuned_config", "snmf_tuned_tiles", "snmf_profile_steps", "snmf_destroy", "snmf_last_error",
     "snmf_mlp_eval", "snmf_set_timeout", "snmf_step_config", "snmf_svd_init",
     "snmf_get_state", "snmf_set_state", "snmf_stats_ring",
+    "snmf_knn_graph", "snmf_cluster_assign", "snmf_cluster_scores",
 )
 SNMF_RING_VALUES = 8
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -110,6 +111,11 @@ def load_library(path: str = LIB_PATH):
     lib.snmf_get_state.argtypes = [H, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
     lib.snmf_set_state.argtypes = [H, C.c_void_p, C.c_int64]
     lib.snmf_stats_ring.argtypes = [H, C.c_void_p, C.c_int, C.POINTER(C.c_int32)]
+    lib.snmf_knn_graph.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]
+    lib.snmf_cluster_assign.argtypes = [H, C.c_int, C.c_void_p]
+    lib.snmf_cluster_scores.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p,
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]
     lib.snmf_step_config.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_int64)]
     lib.snmf_destroy.argtypes = [H]
@@ -258,6 +264,49 @@ def snmf_stats_ring(h, batch: int, capacity: int = 256):
     cnt = C.c_int32()
     _check(lib, h, lib.snmf_stats_ring(h, out.ctypes.data, int(capacity), C.byref(cnt)))
     return out, cnt.value
+
+
+def snmf_knn_graph(X, k: int = 10, sigma_rank: int = 7, stream=None):
+    """kNN similarity graph of device points X (n x d float32): returns (rowptr, colidx, A^ values,
+    S values, degrees) as device tensors (see include/snmf.h)."""
+    import torch
+    lib = load_library()
+    if not _is_cuda(X) or X.dim() != 2 or X.dtype != torch.float32 or not X.is_contiguous():
+        raise SnmfError(SNMF_ERR_ARG, "X must be a contiguous n x d float32 CUDA tensor")
+    n, d = X.shape
+    cap = 2 * n * k
+    rp = torch.empty(n + 1, dtype=torch.int32, device=X.device)
+    ci = torch.empty(cap, dtype=torch.int32, device=X.device)
+    ah = torch.empty(cap, dtype=torch.float32, device=X.device)
+    sv = torch.empty(cap, dtype=torch.float32, device=X.device)
+    dg = torch.empty(n, dtype=torch.float32, device=X.device)
+    nnz = C.c_int64()
+    s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib, None, lib.snmf_knn_graph(_ptr(X), n, d, int(k), int(sigma_rank), _ptr(rp), _ptr(ci), _ptr(ah),
+                                         _ptr(sv), _ptr(dg), cap, C.byref(nnz), s))
+    m = nnz.value
+    return rp, ci[:m], ah[:m], sv[:m], dg
+
+
+def snmf_cluster_assign(h, restart: int, n: int):
+    """Cluster labels (argmax of the H row) of a restart of the last solve, as a device tensor."""
+    import torch
+    lib = load_library()
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    _check(lib, h, lib.snmf_cluster_assign(h, int(restart), _ptr(lab)))
+    return lab
+
+
+def snmf_cluster_scores(truth, pred, k_true: int, k_pred: int, stream=None):
+    """(contingency table, ARI, matched accuracy) of two device int32 labelings."""
+    lib = load_library()
+    n = int(truth.shape[0])
+    table = np.zeros((k_true, k_pred), dtype=np.int64)
+    ari, acc = C.c_double(), C.c_double()
+    s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib, None, lib.snmf_cluster_scores(_ptr(truth), _ptr(pred), n, int(k_true), int(k_pred),
+                                              table.ctypes.data, C.byref(ari), C.byref(acc), s))
+    return table, ari.value, acc.value
 
 
 def snmf_solve(h, W=None, Ht=None):

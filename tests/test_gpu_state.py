@@ -78,7 +78,7 @@ def test_state_blob_checks():
         with pytest.raises(S.SnmfError):
             S.snmf_set_state(h2, blob)                           # another rank
         with pytest.raises(S.SnmfError):
-            S.snmf_set_state(h, b"\\x00" * len(blob))             # not a state blob
+            S.snmf_set_state(h, bytes(len(blob)))                    # not a state blob
         with pytest.raises(S.SnmfError):
             S.snmf_set_state(h, blob[:-8])                       # truncated
         S.snmf_set_state(h, blob)

@@ -278,6 +278,38 @@ def test_naive_variant_planted_fixed_point_and_block_monotone():
             prevF = s["F"]
 
 
+def test_knn_graph_on_points_of_a_line():
+    """Points 0, 1, 3, 7, 15 on a line (gaps double): every point's neighbours and squared
+    distances are known in closed form; S is symmetric, S_ij = exp(-d^2 / (s_i s_j)) on kNN
+    pairs, the degrees are the row sums of S and A^ = D^-1/2 S D^-1/2."""
+    X = np.array([[0.0], [1.0], [3.0], [7.0], [15.0]])
+    nbr, d2, S, deg, A_hat = O.knn.knn_graph(X, 2, 1)
+    assert nbr.tolist() == [[1, 2], [0, 2], [1, 0], [2, 1], [3, 2]]
+    assert d2.tolist() == [[1, 9], [1, 4], [4, 9], [16, 36], [64, 144]]
+    s = np.sqrt(d2[:, 0])  # sigma_rank = 1: distance to the nearest neighbour
+    assert S[0, 1] == pytest.approx(math.exp(-1.0 / (s[0] * s[1])))
+    assert S[3, 4] == pytest.approx(math.exp(-64.0 / (s[4] * s[3])))  # only 4 -> 3 is a kNN pair
+    assert np.allclose(S, S.T) and S[0, 3] == 0.0 and np.all(np.diag(S) == 0.0)
+    assert np.allclose(deg, S.sum(1))
+    assert np.allclose(A_hat, S / np.sqrt(np.outer(deg, deg)))
+
+
+def test_ari_and_accuracy_worked_example():
+    """truth [0,0,0,1,1,1], pred [0,0,1,1,2,2]: table [[2,1,0],[0,1,2]]; by hand: index
+    C(2,2) + C(2,2) = 2, row term C(3,2) + C(3,2) = 6, column term 3 C(2,2) = 3, C(6,2) = 15,
+    expected 6 * 3 / 15 = 1.2, max (6 + 3) / 2 = 4.5, ARI = 0.8 / 3.3; best matching 0->0,
+    1->2 gives accuracy 4/6.  Identical partitions up to relabelling score 1 and 1."""
+    T = O.knn.contingency([0, 0, 0, 1, 1, 1], [0, 0, 1, 1, 2, 2], 2, 3)
+    assert T.tolist() == [[2, 1, 0], [0, 1, 2]]
+    assert O.knn.adjusted_rand_index(T) == pytest.approx(0.8 / 3.3, rel=1e-14)
+    assert O.knn.matched_accuracy(T) == pytest.approx(4.0 / 6.0)
+    g = np.random.default_rng(5)
+    truth = g.integers(0, 4, 200)
+    perm = np.array([2, 0, 3, 1])
+    T2 = O.knn.contingency(truth, perm[truth], 4, 4)
+    assert O.knn.adjusted_rand_index(T2) == pytest.approx(1.0) and O.knn.matched_accuracy(T2) == 1.0
+
+
 def test_max_memory_reference():
     A, W = _small_problem(30, 3, seed=41)
     opts = O.Options(formulation="direct", memory=3, max_iter=12, tol=0.0)

@@ -8,6 +8,7 @@ from .generators import (  # noqa: F401
     planted_dense,
     uniform_init,
     gmm_knn_graph,
+    gmm_points,
     chung_lu_csr,
     uneven_batch,
     Csr,

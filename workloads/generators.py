@@ -65,6 +65,17 @@ def uniform_init(n: int, cols: int, upper: float, seed: int) -> np.ndarray:
     return g.random((n, cols)) * upper
 
 
+def gmm_points(n: int, d: int, comps: int, seed: int):
+    """The Gaussian-mixture points of gmm_knn_graph (same seeded draws): ``comps`` equally
+    weighted components in R^d, means ~ N(0, 4 I), unit covariance.  Returns (X float32 n x d,
+    labels)."""
+    g = np.random.default_rng(seed)
+    labels = g.integers(0, comps, size=n)
+    means = g.normal(0.0, 2.0, size=(comps, d))
+    X = (means[labels] + g.normal(size=(n, d))).astype(np.float32)
+    return X, labels
+
+
 def gmm_knn_graph(n: int = 20000, d: int = 64, comps: int = 20, k: int = 10,
                   sigma_rank: int = 7, seed: int = 3000, chunk: int = 2048):
     """k-nearest-neighbour Gaussian similarity graph of a Gaussian mixture.
