@@ -471,7 +471,8 @@ SNMF_API snmf_status snmf_set_timeout(snmf_handle h, int64_t cycles);
  *   capacity     entries available; 2 n k always suffices.  *nnz (host) receives the count;
  *                a count above capacity returns SNMF_ERR_ARG with *nnz set.
  * Work runs on `stream`; the call returns when it is done.  Allocates device scratch.
- * Errors: SNMF_ERR_ARG, SNMF_ERR_OOM, SNMF_ERR_CUDA.
+ * Errors: SNMF_ERR_ARG, SNMF_ERR_OOM, SNMF_ERR_CUDA; SNMF_ERR_NUMERIC when a distance is not
+ * finite or a scale s_i is zero (more than sigma_rank - 1 copies of a point), with no output.
  */
 SNMF_API snmf_status snmf_knn_graph(const float* X, int64_t n, int d, int k, int sigma_rank, int32_t* rowptr,
                                     int32_t* colidx, float* a_hat, float* s_values, float* degree,
@@ -486,7 +487,8 @@ SNMF_API snmf_status snmf_cluster_assign(snmf_handle h, int restart, int32_t* la
 
 /*
  * Clustering scores (Sec. 4 reports accuracy and ARI): the contingency table of two labelings
- * (device int32 arrays of n labels in [0, k_true) and [0, k_pred), k_true k_pred <= 4096) on the
+ * (device int32 arrays of n >= 2 labels in [0, k_true) and [0, k_pred); k_true, k_pred <= 512 and
+ * k_true k_pred <= 4096) on the
  * device; from it the adjusted Rand index of Hubert and Arabie and the accuracy of the best
  * one-to-one matching of predicted to true labels (Hungarian method) on the host.  table
  * (host, k_true x k_pred), ari, accuracy: outputs, each may be NULL.

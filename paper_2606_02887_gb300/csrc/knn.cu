@@ -29,11 +29,13 @@ constexpr int CB = 64;  // candidates staged per round
 constexpr int KMAX = 32;
 
 // Top-K (K = compile-time bound, k <= K at run time) by squared distance, candidates in
-// increasing index order; a candidate replaces an entry only when strictly closer, so equal
-// distances keep the lower index first.
+// increasing index order; a candidate replaces an entry only when strictly closer (or the entry
+// is still empty), so equal distances keep the lower index first and every slot ends up holding
+// a valid index (k < n).  A non-finite distance counts as +inf and raises *bad.
 template <int K>
 __global__ void __launch_bounds__(QB) k_knn(const float* __restrict__ X, int64_t n, int d, int k,
-                                            int32_t* __restrict__ nbr, float* __restrict__ nd2) {
+                                            int32_t* __restrict__ nbr, float* __restrict__ nd2,
+                                            int* __restrict__ bad) {
   extern __shared__ float ksm[];
   const int ds = d + 1;  // odd row stride: conflict-free per-thread rows
   float* Qs = ksm;
@@ -72,10 +74,14 @@ __global__ void __launch_bounds__(QB) k_knn(const float* __restrict__ X, int64_t
           acc = fmaf(df, df, acc);
         }
         float v = acc;
+        if (!isfinite(v)) {
+          v = INFINITY;
+          atomicOr(bad, 1);
+        }
         int32_t vi = (int32_t)j;
 #pragma unroll
         for (int t = 0; t < K; ++t) {
-          if (t < k && v < kd[t]) {
+          if (t < k && (v < kd[t] || (v == kd[t] && vi < ki[t]))) {
             const float tv = kd[t];
             const int32_t ti = ki[t];
             kd[t] = v;
@@ -99,14 +105,17 @@ __global__ void __launch_bounds__(QB) k_knn(const float* __restrict__ X, int64_t
 
 // scale s_i, directed similarities, in-degree counts
 __global__ void k_knn_sim(const int32_t* __restrict__ nbr, const float* __restrict__ nd2, int64_t n, int k,
-                          int sigma_rank, float* __restrict__ sval, int32_t* __restrict__ cnt) {
+                          int sigma_rank, float* __restrict__ sval, int32_t* __restrict__ cnt,
+                          int* __restrict__ bad) {
   const int64_t total = n * k;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / k;
     const int32_t j = nbr[e];
     const float si = sqrtf(nd2[i * k + sigma_rank - 1]);
     const float sj = sqrtf(nd2[(int64_t)j * k + sigma_rank - 1]);
-    sval[e] = expf(-nd2[e] / (si * sj));
+    const float v = expf(-nd2[e] / (si * sj));
+    if (!(si * sj > 0.f) || !isfinite(v)) atomicOr(bad, 1);  // zero scale: duplicate points
+    sval[e] = v;
     atomicAdd(&cnt[j], 1);  // the reverse entry (j, i)
   }
 }
@@ -243,10 +252,10 @@ __global__ void k_assign(const T* __restrict__ F, int64_t n, int64_t ld, int64_t
 }
 
 template <int K>
-void launch_knn(const float* X, int64_t n, int d, int k, int32_t* nbr, float* nd2, cudaStream_t s) {
+void launch_knn(const float* X, int64_t n, int d, int k, int32_t* nbr, float* nd2, int* bad, cudaStream_t s) {
   const size_t smem = (size_t)(QB + CB) * (d + 1) * sizeof(float);
   cudaFuncSetAttribute(k_knn<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_knn<K><<<(unsigned)((n + QB - 1) / QB), QB, smem, s>>>(X, n, d, k, nbr, nd2);
+  k_knn<K><<<(unsigned)((n + QB - 1) / QB), QB, smem, s>>>(X, n, d, k, nbr, nd2, bad);
 }
 
 // Best one-to-one matching maximising the matched count: the Hungarian method with potentials
@@ -309,7 +318,9 @@ extern "C" snmf_status snmf_knn_graph(const float* X, int64_t n, int d, int k, i
   int32_t *nbr = nullptr, *cnt = nullptr, *off = nullptr, *fill = nullptr, *ecol = nullptr, *cntu = nullptr;
   float *nd2 = nullptr, *sval = nullptr, *eval = nullptr, *sv = nullptr, *dg = nullptr;
   uint8_t* erep = nullptr;
+  int* bad = nullptr;
   auto cleanup = [&] {
+    cudaFree(bad);
     cudaFree(nbr); cudaFree(cnt); cudaFree(off); cudaFree(fill); cudaFree(ecol); cudaFree(cntu); cudaFree(erep);
     cudaFree(nd2); cudaFree(sval); cudaFree(eval); cudaFree(sv); cudaFree(dg);
   };
@@ -331,21 +342,26 @@ extern "C" snmf_status snmf_knn_graph(const float* X, int64_t n, int d, int k, i
   KCK(cudaMalloc(&sv, 2 * nk * sizeof(float)));
   KCK(cudaMalloc(&dg, n * sizeof(float)));
   KCK(cudaMalloc(&erep, 2 * nk));
+  KCK(cudaMalloc(&bad, sizeof(int)));
+  KCK(cudaMemsetAsync(bad, 0, sizeof(int), s));
   KCK(cudaMemsetAsync(cnt, 0, n * sizeof(int32_t), s));
   KCK(cudaMemsetAsync(fill, 0, n * sizeof(int32_t), s));
-  if (k <= 16) launch_knn<16>(X, n, d, k, nbr, nd2, s);
-  else launch_knn<32>(X, n, d, k, nbr, nd2, s);
+  if (k <= 16) launch_knn<16>(X, n, d, k, nbr, nd2, bad, s);
+  else launch_knn<32>(X, n, d, k, nbr, nd2, bad, s);
   const int g = (int)std::min<int64_t>((nk + 255) / 256, 152 * 16);
-  k_knn_sim<<<g, 256, 0, s>>>(nbr, nd2, n, k, sigma_rank, sval, cnt);
+  k_knn_sim<<<g, 256, 0, s>>>(nbr, nd2, n, k, sigma_rank, sval, cnt, bad);
   k_scan<<<1, 1024, 0, s>>>(cnt, n, k, off);  // row slots: k own + in-degree
   k_knn_fill<<<g, 256, 0, s>>>(nbr, sval, n, k, off, fill, ecol, eval);
   const int rb = (int)((n + 7) / 8);
   k_knn_dedupe<<<rb, 256, 0, s>>>(off, ecol, eval, n, 0, erep, cntu, nullptr, nullptr, nullptr);
   k_scan<<<1, 1024, 0, s>>>(cntu, n, 0, rowptr);
   int32_t total = 0;
+  int hbad = 0;
   KCK(cudaMemcpyAsync(&total, rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  KCK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   KCK(cudaStreamSynchronize(s));
   *nnz = total;
+  if (hbad) { cleanup(); return SNMF_ERR_NUMERIC; }
   if (total > capacity) { cleanup(); return SNMF_ERR_ARG; }
   k_knn_dedupe<<<rb, 256, 0, s>>>(off, ecol, eval, n, 1, erep, cntu, rowptr, colidx, sv);
   k_knn_degree<<<rb, 256, 0, s>>>(rowptr, sv, n, dg);
@@ -361,7 +377,9 @@ extern "C" snmf_status snmf_knn_graph(const float* X, int64_t n, int d, int k, i
 
 extern "C" snmf_status snmf_cluster_scores(const int32_t* truth, const int32_t* pred, int64_t n, int k_true,
                                            int k_pred, int64_t* table, double* ari, double* accuracy, void* stream) {
-  if (!truth || !pred || n < 1 || k_true < 1 || k_pred < 1 || (int64_t)k_true * k_pred > 4096) return SNMF_ERR_ARG;
+  if (!truth || !pred || n < 2 || k_true < 1 || k_pred < 1 || k_true > 512 || k_pred > 512 ||
+      (int64_t)k_true * k_pred > 4096)
+    return SNMF_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long* dt = nullptr;
   int* bad = nullptr;

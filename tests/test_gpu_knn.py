@@ -134,3 +134,15 @@ def test_graph_clustering_end_to_end():
     assert abs(ari - OK.adjusted_rand_index(To)) < 1e-12
     assert abs(acc - OK.matched_accuracy(To)) < 1e-12
     assert acc > 0.9 and ari > 0.8
+
+
+def test_knn_graph_rejects_duplicate_points_and_nan():
+    import torch
+    X, _ = gmm_points(64, 4, 2, seed=9)
+    Xd = torch.tensor(np.repeat(X[:8], 8, axis=0), device="cuda:0")  # 8 copies of each point
+    with pytest.raises(S.SnmfError):
+        S.snmf_knn_graph(Xd, k=10, sigma_rank=7)  # s_i = 0
+    Xn = X.copy()
+    Xn[5, 2] = np.nan
+    with pytest.raises(S.SnmfError):
+        S.snmf_knn_graph(torch.tensor(Xn, device="cuda:0"), k=10, sigma_rank=7)
