@@ -314,7 +314,9 @@ SNMF_API snmf_status snmf_set_state(snmf_handle h, const void* blob, int64_t siz
  * control step at the start of every W block).  Copies, per restart j, up to `capacity`
  * records out[j][t][8] = {outer iteration, ||P grad|| / ||P grad_0||, ||P grad||, last alpha,
  * last beta, line searches without an accepted trial (cumulative), learned-step proposals
- * accepted (cumulative), active flag}, oldest first; unused records are -1.  *count: records
+ * accepted (cumulative), 1 while the restart goes on and 0 on the record where it stopped (the
+ * tolerance or the iteration limit was met, or the gradient was not finite)}, oldest first;
+ * unused records are -1.  *count: records
  * per restart written.  The ring is not cleared between solves.
  */
 SNMF_API snmf_status snmf_stats_ring(snmf_handle h, double* out, int capacity, int32_t* count);

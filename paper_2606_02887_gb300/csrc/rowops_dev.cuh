@@ -217,6 +217,8 @@ __device__ void pen_start_body(Ctl& c, const double* prow, int nrow, int b, int 
     const double joint = sqrt(pg2 + c.pgH2);
     c.pg = joint;
     if (c.iters == 0) c.pg0 = joint;
+    const bool stop = c.iters > 0 && (joint <= P.tol * c.pg0 || c.iters >= P.max_iter);
+    const bool bad = !stop && !isfinite(joint);
     if (P.ring && P.ring_cap > 0) {  // statistics of the state reached by the last outer iteration
       double* rec = P.ring + ((int64_t)j * P.ring_cap + (c.iters % P.ring_cap)) * kRingVals;
       rec[0] = (double)c.iters;
@@ -226,10 +228,10 @@ __device__ void pen_start_body(Ctl& c, const double* prow, int nrow, int b, int 
       rec[4] = c.beta;
       rec[5] = (double)c.ls_fail;
       rec[6] = (double)c.mlp_accept;
-      rec[7] = (double)c.active;
+      rec[7] = (stop || bad) ? 0.0 : 1.0;  // 1: the restart goes on
     }
-    else if (joint <= P.tol * c.pg0 || c.iters >= P.max_iter) { c.active = 0; return; }
-    if (!isfinite(joint)) { c.nan_seen = 1; c.active = 0; return; }
+    if (stop) { c.active = 0; return; }
+    if (bad) { c.nan_seen = 1; c.active = 0; return; }
   } else {
     if (first) { c.pgH2 = pg2; return; }  // solve initialisation: H gradient at start
   }

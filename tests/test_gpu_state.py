@@ -60,6 +60,35 @@ def test_resume_reproduces_the_continuous_solve(prec, form):
         assert ring[j, 0, 1] == pytest.approx(1.0, rel=1e-12)
         assert np.all(ring[j, :cnt, 1] > 0) and ring[j, cnt - 1, 1] < ring[j, 0, 1]
         assert np.all(ring[j, cnt:, 0] == -1.0)
+        assert np.all(ring[j, :cnt - 1, 7] == 1.0) and ring[j, cnt - 1, 7] == 0.0  # stopped at the limit
+
+
+def test_ring_marks_the_tolerance_stop():
+    """A restart that meets the tolerance stops there: iteration count below the limit, its
+    last ring record carries the stop flag and the relative gradient at or under tol."""
+    import torch
+    dev = torch.device("cuda:0")
+    A, _ = planted_dense(300, 6, 0.01, seed=31)
+    At = torch.tensor(A, device=dev)
+    tol = 1e-3
+    o = S.snmf_default_options(precision=S.SNMF_F64, batch=2, max_iter=2000, tol=tol)
+    h = S.snmf_create(S.dense_matrix(At), 6, o)
+    try:
+        W = torch.tensor(np.concatenate([uniform_init(300, 6, math.sqrt(A.mean() / 6), seed=32 + j)
+                                         for j in range(2)], 1), device=dev)
+        st, stats = S.snmf_solve(h, W, W.clone())
+        per = S.snmf_restart_stats(h, 2)
+        ring, cnt = S.snmf_stats_ring(h, 2)
+    finally:
+        S.snmf_destroy(h)
+    assert st == S.SNMF_OK and stats["converged"] == 1
+    for j in range(2):
+        it = int(per["iters"][j])
+        assert 0 < it < 2000
+        c = min(it + 1, 256)
+        last = ring[j, c - 1]
+        assert last[0] == it and last[7] == 0.0 and last[1] <= tol
+        assert np.all(ring[j, :c - 1, 7] == 1.0) and np.all(ring[j, :c - 1, 1] > tol)
 
 
 def test_state_blob_checks():
