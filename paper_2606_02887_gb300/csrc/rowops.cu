@@ -430,6 +430,20 @@ __global__ void k_ctl_final_pen(Ctl* __restrict__ ctl, const double* __restrict_
   const int j = blockIdx.x;
   const int64_t o = (int64_t)j * r * r;
   final_pen_body(ctl[j], pax, nax, prow, nrow, GW + o, GH + o, WH + o, b, j, r, P.normA2, sh);
+  // A restart still active here stopped on the iteration limit: the control step that would
+  // have recorded its last state never ran, so its ring record is written from the final point.
+  Ctl& c = ctl[j];
+  if (threadIdx.x == 0 && P.ring && P.ring_cap > 0 && c.active && !c.nan_seen) {
+    double* rec = P.ring + ((int64_t)j * P.ring_cap + (c.iters % P.ring_cap)) * kRingVals;
+    rec[0] = (double)c.iters;
+    rec[1] = c.fin_pg;
+    rec[2] = c.fin_pg * c.pg0;
+    rec[3] = c.alpha;
+    rec[4] = c.beta;
+    rec[5] = (double)c.ls_fail;
+    rec[6] = (double)c.mlp_accept;
+    rec[7] = 0.0;
+  }
 }
 
 // final per-restart stats (direct)
