@@ -351,8 +351,10 @@ SNMF_API snmf_status snmf_profile_steps(snmf_handle h, int iters, double* ms_dst
  * (Z and D stored; D step 6 arrays, 7 with the learned step's second direction, update 8),
  * 1 the shared-memory tile body (same traffic), 2 the recomputing kernels (Z and D not stored:
  * D step 4 arrays, update 6), 3 the recomputing kernels with their row products on the tensor
- * cores (tcgen05 TF32 with hi / lo operand parts; r = 64, chosen by the autotuner when faster).
- * *rows_per_cta: rows of one CTA.  Any pointer may be NULL.
+ * cores (tcgen05 TF32 with hi / lo operand parts; r = 64, chosen by the autotuner when faster),
+ * 4 the same arithmetic as persistent kernels (one CTA per SM over 128-row tiles, inputs streamed
+ * by TMA into shared slots while the previous tile computes; same traffic as 2 and 3).
+ * *rows_per_cta: rows of one tile.  Any pointer may be NULL.
  */
 SNMF_API snmf_status snmf_step_config(snmf_handle h, int32_t* body, int32_t* rows_per_cta, int64_t* dstep_bytes,
                                       int64_t* update_bytes);

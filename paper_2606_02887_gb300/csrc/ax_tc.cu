@@ -669,6 +669,19 @@ bool make_map(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int
 
 int tc_last_status() { return g_last_cu; }
 
+bool make_map_f32_tile(CUtensorMap* m, const void* base, int64_t cols, int64_t rows, int64_t ld) {
+  EncodeFn enc = get_encode();
+  if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15) || (ld * 4) % 16 || cols > ld) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {32, 128};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int64_t tc_ld(int64_t n) { return (n + 63) / 64 * 64; }
 
 void launch_to_bf16(int src_dtype, const void* A, int64_t n, int64_t lda, void* A16, cudaStream_t s) {

@@ -4,6 +4,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "tune.cuh"
@@ -34,6 +35,10 @@ struct TcEpilogue {
   int b = 1;
 };
 
+// FP32 tensor map of a row-major matrix (rows x cols, row pitch ld elements) for tiles of
+// 128 rows x 32 columns with the 128-byte swizzle; false when it cannot be encoded (base not
+// 16-byte aligned, pitch not a multiple of 16 bytes, no encoder).
+bool make_map_f32_tile(CUtensorMap* m, const void* base, int64_t cols, int64_t rows, int64_t ld);
 // Leading dimension (elements) of the BF16 copy of A and of the transposed X parts.
 int64_t tc_ld(int64_t n);
 // diagnostics of the last launch_ax_tc failure: CUresult of the encoder, or 10000 + cudaError_t

@@ -61,7 +61,7 @@ struct snmf_ctx {
   double normL = 0.0;  // ||L||_2 (power method), enters rho of graph-regularised blocks
   int use_tile = 0;    // row kernels through the shared-memory tile body (r <= 32)
   int use_fuse = 0;    // D step and update through rowfuse.cu (FP32, r in {16, 32, 64}, no Z / D stored)
-  int row_tc = 0;      // with use_fuse: the row products on the tensor cores (rowtc.cu, r = 64; tuned)
+  int row_tc = 0;      // with use_fuse: row products on the tensor cores, 1 rowtc.cu, 2 rowtma.cu (r = 64; tuned)
   int row_bm = 0;      // general row kernel, FP32: rows per CTA (0: built-in choice; autotuned)
   AxArgs L{};
   int32_t* L_rowptr = nullptr;
@@ -335,12 +335,14 @@ snmf_status time_steps(snmf_ctx* h, int iters, double* ms_dstep, double* ms_upda
   au.ctl_mode = CTL_UPD_W;
   au.Zin = h->buf[B_Z]; au.Din = h->buf[B_D]; au.Din2 = h->buf[B_AD];
   auto dstep = [&] {
-    if (h->use_fuse && h->row_tc) launch_rowtc_dstep(ad, h->dev_err, h->s);
+    if (h->use_fuse && h->row_tc == 2 && launch_rowtma_dstep(ad, h->dev_err, h->s)) {
+    } else if (h->use_fuse && h->row_tc) launch_rowtc_dstep(ad, h->dev_err, h->s);
     else if (h->use_fuse) launch_rowfuse_dstep(ad, h->row_bm, nc, h->s);
     else launch_rowgemm(td, OP_ZSTEP, EPI_DIR, ad, h->s, nc);
   };
   auto update = [&] {
-    if (h->use_fuse && h->row_tc) launch_rowtc_update(au, h->dev_err, h->s);
+    if (h->use_fuse && h->row_tc == 2 && launch_rowtma_update(au, h->dev_err, h->s)) {
+    } else if (h->use_fuse && h->row_tc) launch_rowtc_update(au, h->dev_err, h->s);
     else if (h->use_fuse) launch_rowfuse_update(au, h->row_bm, nc, h->s);
     else launch_rowgemm(td, OP_UPD, EPI_GRAD, au, h->s);
   };
@@ -388,8 +390,10 @@ snmf_status autotune_product(snmf_ctx* h) {
       h->row_bm = e.cfg.row_bm;
       if (!h->use_tile) h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, h->row_bm);
     }
-    h->row_tc = (tune_rows && h->use_fuse && e.cfg.row_tc == 1 &&
-                 rowtc_supported(h->tdtype, h->r, h->opt.step_controller == 1 ? 2 : 1)) ? 1 : 0;
+    const int tnc = h->opt.step_controller == 1 ? 2 : 1;
+    h->row_tc = 0;
+    if (tune_rows && h->use_fuse && e.cfg.row_tc == 1 && rowtc_supported(h->tdtype, h->r, tnc)) h->row_tc = 1;
+    if (tune_rows && h->use_fuse && e.cfg.row_tc == 2 && rowtma_supported(h->tdtype, h->r, tnc, h->N)) h->row_tc = 2;
     return SNMF_OK;
   }
   std::vector<ProdTune> cand;
@@ -476,9 +480,15 @@ snmf_status autotune_product(snmf_ctx* h) {
     h->row_bm = bbm;
     if (!h->use_tile) h->nrow = rowgemm_slots(dims(h), h->tdtype, 0, bbm);
     h->tune.cfg.row_bm = bbm;
-    // the tensor-core row products (r = 64), kept when faster than the best CUDA-core height
-    if (h->use_fuse && rowtc_supported(h->tdtype, h->r, h->opt.step_controller == 1 ? 2 : 1)) {
-      h->row_tc = 1;
+    // the tensor-core row products (r = 64): per-CTA tiles (1) and the persistent TMA
+    // pipeline (2), each kept when faster than the best so far and free of device errors
+    const int tnc = h->opt.step_controller == 1 ? 2 : 1;
+    h->row_tc = 0;
+    for (int kind = 1; kind <= 2 && h->use_fuse; ++kind) {
+      if (kind == 1 && !rowtc_supported(h->tdtype, h->r, tnc)) continue;
+      if (kind == 2 && !rowtma_supported(h->tdtype, h->r, tnc, h->N)) continue;
+      const int prev = h->row_tc;
+      h->row_tc = kind;
       double md = 0.0, mu = 0.0;
       const snmf_status st = time_steps(h, 5, &md, &mu);
       if (st != SNMF_OK) return st;
@@ -486,12 +496,14 @@ snmf_status autotune_product(snmf_ctx* h) {
       CK(cudaMemcpy(&derr2, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
       if (derr2) {
         CK(cudaMemset(h->dev_err, 0, sizeof(int)));
-        h->row_tc = 0;
-      } else if (!(md + mu < bt)) {
-        h->row_tc = 0;
+        h->row_tc = prev;
+      } else if (md + mu < bt) {
+        bt = md + mu;
+      } else {
+        h->row_tc = prev;
       }
-      h->tune.cfg.row_tc = h->row_tc;
     }
+    h->tune.cfg.row_tc = h->row_tc;
   }
   tune_store(h->opt.tune_cache, dev, key, h->tune);
   return SNMF_OK;
@@ -542,13 +554,15 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P, bool nai
       RowArgs a = row_base(h, &P);
       a.X = X; a.g_in = h->buf[B_G]; a.B = h->buf[B_B]; a.gZout = h->buf[B_GZ];
       a.ctl_mode = CTL_LS;
-      if (h->row_tc) launch_rowtc_dstep(a, h->dev_err, h->s);
+      if (h->row_tc == 2 && launch_rowtma_dstep(a, h->dev_err, h->s)) {
+      } else if (h->row_tc) launch_rowtc_dstep(a, h->dev_err, h->s);
       else launch_rowfuse_dstep(a, h->row_bm, nc, h->s);
       RowArgs u = row_base(h, &P);
       u.Xout = X; u.gout = h->buf[B_G]; u.gZold = h->buf[B_GZ]; u.B = h->buf[B_B];
       u.ctl_mode = is_w ? (naive && k == K - 1 ? CTL_UPD_W_LAST_NAIVE : CTL_UPD_W)
                         : (k == K - 1 ? CTL_UPD_H_LAST : CTL_UPD_H);
-      if (h->row_tc) launch_rowtc_update(u, h->dev_err, h->s);
+      if (h->row_tc == 2 && launch_rowtma_update(u, h->dev_err, h->s)) {
+      } else if (h->row_tc) launch_rowtc_update(u, h->dev_err, h->s);
       else launch_rowfuse_update(u, h->row_bm, nc, h->s);
     }
     return;
@@ -1625,7 +1639,7 @@ snmf_status snmf_step_config(snmf_handle h, int32_t* body, int32_t* rows_per_cta
   int kind = 0, rows = 0;
   int64_t bd = 0, bu = 0;
   if (h->use_fuse) {
-    kind = h->row_tc ? 3 : 2;
+    kind = h->row_tc == 2 ? 4 : (h->row_tc ? 3 : 2);
     rows = h->row_tc ? 128 : rowfuse_bm(h->r, h->row_bm);
     bd = 4 * fb;  // X, g, B in; g(Z) out
     bu = 6 * fb;  // X, g, g(Z), B in; X', g(X') out

@@ -67,6 +67,13 @@ void launch_rowfuse_update(const RowArgs& a, int bm, int nc, cudaStream_t s);
 bool rowtc_supported(int tdtype, int r, int nc);
 void launch_rowtc_dstep(const RowArgs& a, int* err, cudaStream_t s);
 void launch_rowtc_update(const RowArgs& a, int* err, cudaStream_t s);
+// The same pair as persistent warp-specialised kernels (rowtma.cu: one CTA per SM over 128-row
+// tiles, inputs streamed by TMA into shared slots, outputs stored by TMA).  ld: the factor
+// arrays' row pitch (a multiple of 4).  false when the tensor maps cannot be encoded (nothing
+// launched).
+bool rowtma_supported(int tdtype, int r, int nc, int64_t ld);
+bool launch_rowtma_dstep(const RowArgs& a, int* err, cudaStream_t s);
+bool launch_rowtma_update(const RowArgs& a, int* err, cudaStream_t s);
 
 void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pair, int npairs,
                  double* gpart, int nchunks, const Ctl* ctl, const int* run, double* G64, void* GT,
