@@ -359,17 +359,22 @@ __device__ void pen_upd_body(Ctl& c, const double* prow, int nrow, int b, int j,
   else alpha_bb = (P.bb == 0) ? ss / sy : sy / yy;
   alpha_bb = fmin(P.alpha_max, fmax(P.alpha_min, alpha_bb));
   if (nc > 1) {
+    // The features feed an FP32 network, so they are formed in FP32 from the FP64 sums (the
+    // FP64 units of this GPU are slow, and this runs on one warp at the end of the launch).
     float phi[kMlpIn];
-    const double rho = c.rho;
-    const double bb1 = sy > 0.0 ? ss / sy : 1.0 / rho;
-    const double bb2 = (sy > 0.0 && yy > 0.0) ? sy / yy : 1.0 / rho;
-    const double pg = sqrt(pg2);
+    const float rho = (float)c.rho;
+    const float ssf = (float)ss, syf = (float)sy, yyf = (float)yy;
+    const float bb1r = syf > 0.f ? ssf * rho / syf : 1.f;  // BB1 rho, BB2 rho (1 without curvature)
+    const float bb2r = (syf > 0.f && yyf > 0.f) ? syf * rho / yyf : 1.f;
+    const float pgf = sqrtf((float)pg2);
     const double dec = f_old - f_new;
-    phi[0] = (float)log(fmin(fmax(bb1 * rho, 1e-6), 1e6));
-    phi[1] = (float)log(fmin(fmax(bb2 * rho, 1e-6), 1e6));
-    phi[2] = (float)(c.pg_prev > 0.0 ? fmin(pg / c.pg_prev, 10.0) : 1.0);
-    phi[3] = (float)fmin(fmax(dec / fmax(fabs(c.last_dec), 1e-300), -10.0), 10.0);
-    phi[4] = (float)(zeros / (double)P.nr);
+    const float prev = (float)c.pg_prev;
+    phi[0] = logf(fminf(fmaxf(bb1r, 1e-6f), 1e6f));
+    phi[1] = logf(fminf(fmaxf(bb2r, 1e-6f), 1e6f));
+    phi[2] = prev > 0.f ? fminf(pgf / prev, 10.f) : 1.f;
+    phi[3] = fminf(fmaxf((float)dec / fmaxf(fabsf((float)c.last_dec), 1e-37f), -10.f), 10.f);
+    phi[4] = (float)zeros / (float)P.nr;
+    const double pg = (double)pgf;
     float mult = 1.f;
     if (nc == 2 || nc == 3) mult = mlp_multiplier(P.mlp_w, phi);  // all lanes
     if ((threadIdx.x & 31) == 0) {

@@ -11,8 +11,8 @@
 // are freed at the warps' votes, so it issues the TMA loads of the next tiles into a ring of
 // four 32 KB shared slots (two 128 x 32 boxes each, 128-byte swizzle: the K-major layout of the
 // UMMA operand tiles) as soon as a slot frees, one full-barrier per slot, and it issues the TMA
-// stores; thread 0, in another warp, issues the MMAs.  A tile's statistics are summed over the warps (fixed order) by warp 0 after the
-// next named-barrier vote; a CTA takes one arrival ticket per run of consecutive tiles of a
+// stores; thread 0, in another warp, issues the MMAs.  A tile's statistics are summed over the
+// warps (fixed order) by warp 0 after the next named-barrier vote; a CTA takes one arrival ticket per run of consecutive tiles of a
 // restart, and runs the control step of each restart whose last run it completed after its
 // tile range.  A restart's control scalars are read once per run.
 // Row products on tcgen05 kind::tf32 with TF32 hi + lo parts (three MMAs per K step).
@@ -47,9 +47,9 @@ constexpr uint32_t DYN_BYTES = OFF_SLOT + NSLOT * SLOT + 1024;  // + alignment s
 constexpr int NCWARP = 16;  // warps (all compute)
 constexpr int NCOMP = NCWARP * 32;
 constexpr int NTHR = NCOMP;
-constexpr int kMaxTodo = 32;
+constexpr int kMaxTodo = 32;  // runs of one CTA's tile range (the launcher checks the range length)
 constexpr uint32_t kTmemCols = 512;  // two products of three 64-column accumulators (D step)
-constexpr uint32_t kProd2 = 256;     // TMEM column of the D step's second product  // runs of one CTA's tile range (the launcher checks the range length)
+constexpr uint32_t kProd2 = 256;     // TMEM column of the D step's second product
 constexpr long long kBudget = 2000000000LL;  // clock64 cycles of one wait
 constexpr long long kDrain = 2000000000LL;   // of one wait on the error path
 
@@ -151,7 +151,7 @@ __device__ __forceinline__ bool restart_live(const RowArgs& a, int j) {
   return a.ctl[j].active && !(a.run && *a.run == 0);
 }
 
-// Producer state of thread 0: the next load (tile ct, array ca, ring index q) and the busy slots.
+// Producer state of thread 32: the next load (tile ct, array ca, ring index q) and the busy slots.
 struct Loader {
   int ct, ca, q, lj;
   bool llive;
