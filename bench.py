@@ -220,6 +220,10 @@ PROFILED_TRAFFIC = {
     ("uneven", "bf16", None, None, "product"): (875.5e6, {}),
     ("dense8192", "bf16", 64, 8, "dstep", 2): (51.4e6, {"row_bm": 128}),
     ("dense8192", "bf16", 64, 8, "product", 2): (274.1e6, {"splits": 4, "bn": 128}),
+    ("dense8192", "bf16", 64, 8, "dstep", 3): (51.03e6, {}),
+    ("dense8192", "bf16", 64, 8, "update", 3): (68.16e6, {}),
+    ("dense8192", "bf16", 64, 8, "dstep", 4): (51.10e6, {}),
+    ("dense8192", "bf16", 64, 8, "update", 4): (68.78e6, {}),
 }
 
 
@@ -739,10 +743,13 @@ def main():
         sc = S.snmf_step_config(h)
         body = {0: "k_rowgemm (general)", 1: "k_rowtile (shared-memory tile body)",
                 2: "k_rowfuse (Z and D recomputed, not stored; row products on CUDA cores)",
-                3: "k_rowtc (Z and D recomputed, not stored; row products on tcgen05, TF32 hi + lo)"}[sc["body"]]
+                3: "k_rowtc (Z and D recomputed, not stored; row products on tcgen05, TF32 hi + lo)",
+                4: "k_rowtma (as k_rowtc, persistent: one CTA per SM, inputs streamed by TMA)"}[sc["body"]]
         prefix = {2: "k_rowfuse", 3: "k_rowtc"}.get(sc["body"])
         names = {"dstep": (prefix + "_dstep" if prefix else "k_rowgemm<OP_ZSTEP, EPI_DIR>"),
                  "update": (prefix + "_update" if prefix else "k_rowgemm<OP_UPD, EPI_GRAD>")}
+        if sc["body"] == 4:
+            names = {"dstep": "k_rowtma<0> (D step)", "update": "k_rowtma<1> (update)"}
         for name, ms_k, nbytes in (("dstep", ms_d, sc["dstep_bytes"]), ("update", ms_u, sc["update_bytes"])):
             gb = nbytes / (ms_k * 1e-3) / 1e9
             kernels[name] = {"bound": "hbm", "kernel": names[name], "body": body,
