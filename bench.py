@@ -831,25 +831,29 @@ def main():
             "this_run": {"iters": [int(x) for x in per["iters"]], "residual": [float(x) for x in per["residual"]],
                          "residual_true_A": res_true, "pg_rel_max": float(np.max(per["pg_rel"]))}}
         if ctl:
-            # the same batched BF16 solve with the plain BB step: separates the controller's
-            # share of the gain from batching and storage precision
-            ob = S.snmf_default_options(precision=prec, formulation=form, batch=args.batch, max_iter=args.max_iter,
-                                        tol=args.tol, nonmonotone_M=10, autotune=args.autotune,
-                                        tune_cache=args.tune_cache, step_controller=0, x_parts=args.x_parts)
-            hb = S.snmf_create(S.dense_matrix(A), args.r, ob, stream=stream)
-            bt = []
-            for k in range(2):
-                W.copy_(W0)
-                H.copy_(W0)
-                stb, sb = S.snmf_solve(hb, W, H if form == S.SNMF_PENALTY else None)
-                bt.append(sb["seconds"])
-            pb = S.snmf_restart_stats(hb, args.batch)
-            S.snmf_destroy(hb)
-            compare["batched_plain_bb_same_precision"] = {
-                "s": bt[-1], "iters": [int(x) for x in pb["iters"]],
-                "residual": [float(x) for x in pb["residual"]], "pg_rel_max": float(np.max(pb["pg_rel"])),
-                "controller_gain": bt[-1] / (ms_max / 1e3),
-                "note": "device time of one solve (CUDA events in the library), second of two runs"}
+            # the same batched solve with the plain BB step (separates the controller's share of
+            # the gain from batching and storage precision), and with the learned step in mode 1
+            # (every rejected proposal falls back to the plain BB step; two directions per step)
+            for name, mode in (("batched_plain_bb_same_precision", 0), ("learned_with_bb_fallback_mode1", 1)):
+                ob = S.snmf_default_options(precision=prec, formulation=form, batch=args.batch,
+                                            max_iter=args.max_iter, tol=args.tol, nonmonotone_M=10,
+                                            autotune=args.autotune, tune_cache=args.tune_cache, step_controller=mode,
+                                            x_parts=args.x_parts)
+                hb = S.snmf_create(S.dense_matrix(A), args.r, ob, stream=stream,
+                                   mlp_weights=weights if mode else None)
+                bt = []
+                for k in range(2):
+                    W.copy_(W0)
+                    H.copy_(W0)
+                    stb, sb = S.snmf_solve(hb, W, H if form == S.SNMF_PENALTY else None)
+                    bt.append(sb["seconds"])
+                pb = S.snmf_restart_stats(hb, args.batch)
+                S.snmf_destroy(hb)
+                compare[name] = {
+                    "s": bt[-1], "status": int(stb), "iters": [int(x) for x in pb["iters"]],
+                    "residual": [float(x) for x in pb["residual"]], "pg_rel_max": float(np.max(pb["pg_rel"])),
+                    "value_over_this": bt[-1] / (ms_max / 1e3),
+                    "note": "device time of one solve (CUDA events in the library), second of two runs"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -25,52 +25,70 @@ namespace {
 
 inline int cdivi(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
-template <typename T>
+// NT: output columns per tile (32 for N <= 32, else 64); RS rows staged per round with the next
+// round's loads in flight.
+template <typename T, int NT, int RS>
 __global__ void __launch_bounds__(256)
 k_utx(const T* __restrict__ U, int k, const T* __restrict__ X, int64_t n, int N, int64_t ldx,
       int64_t chunk, T* __restrict__ part, const double* __restrict__ lam, T* __restrict__ M,
       unsigned* __restrict__ counters, const int* run) {
-  const int lt = blockIdx.y, ct = blockIdx.z;  // 64x64 tile of the k x N output
+  constexpr int MC = NT / 16;        // micro tile columns
+  constexpr int LU = RS * 64 / 256;  // staged U values per thread
+  constexpr int LX = RS * NT / 256;  // staged X values per thread
+  const int lt = blockIdx.y, ct = blockIdx.z;  // 64 x NT tile of the k x N output
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t i_begin = (int64_t)blockIdx.x * chunk, i_end = min(n, i_begin + chunk);
-  __shared__ T Us[32][64 + 1];
-  __shared__ T Xs[32][64 + 1];
+  __shared__ T Us[RS][64 + 1];
+  __shared__ T Xs[RS][NT + 1];
   __shared__ unsigned ticket;
-  T acc[4][4];
+  T acc[4][MC];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
+    for (int c = 0; c < MC; ++c) acc[a][c] = T(0);
   const bool skip = run && *run == 0;
-  const int l0 = lt * 64, c0 = ct * 64;
+  const int l0 = lt * 64, c0 = ct * NT;
   if (!skip) {
-    for (int64_t i0 = i_begin; i0 < i_end; i0 += 32) {
-      T uv[8], xv[8];
+    T uv[LU], xv[LX];
+    auto fetch = [&](int64_t i0) {
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
+      for (int m = 0; m < LU; ++m) {
         const int e = threadIdx.x + 256 * m, rr = e >> 6, cc = e & 63;
         const int64_t i = i0 + rr;
         uv[m] = (i < i_end && l0 + cc < k) ? U[i * k + l0 + cc] : T(0);
-        xv[m] = (i < i_end && c0 + cc < N) ? X[i * ldx + c0 + cc] : T(0);
       }
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
+      for (int m = 0; m < LX; ++m) {
+        const int e = threadIdx.x + 256 * m, rr = e / NT, cc = e % NT;
+        const int64_t i = i0 + rr;
+        xv[m] = (i < i_end && c0 + cc < N) ? X[i * ldx + c0 + cc] : T(0);
+      }
+    };
+    if (i_begin < i_end) fetch(i_begin);
+    for (int64_t i0 = i_begin; i0 < i_end; i0 += RS) {
+#pragma unroll
+      for (int m = 0; m < LU; ++m) {
         const int e = threadIdx.x + 256 * m;
         Us[e >> 6][e & 63] = uv[m];
-        Xs[e >> 6][e & 63] = xv[m];
+      }
+#pragma unroll
+      for (int m = 0; m < LX; ++m) {
+        const int e = threadIdx.x + 256 * m;
+        Xs[e / NT][e % NT] = xv[m];
       }
       __syncthreads();
+      if (i0 + RS < i_end) fetch(i0 + RS);  // the next round's loads fly during this one
 #pragma unroll 8
-      for (int rr = 0; rr < 32; ++rr) {
-        T ua[4], xb[4];
+      for (int rr = 0; rr < RS; ++rr) {
+        T ua[4], xb[MC];
 #pragma unroll
         for (int a = 0; a < 4; ++a) ua[a] = Us[rr][ty + 16 * a];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) xb[c] = Xs[rr][tx + 16 * c];
+        for (int c = 0; c < MC; ++c) xb[c] = Xs[rr][tx + 16 * c];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc[a][c] = fma(ua[a], xb[c], acc[a][c]);
+          for (int c = 0; c < MC; ++c) acc[a][c] = fma(ua[a], xb[c], acc[a][c]);
       }
       __syncthreads();
     }
@@ -82,7 +100,7 @@ k_utx(const T* __restrict__ U, int k, const T* __restrict__ X, int64_t n, int N,
     const int l = l0 + ty + 16 * a;
     if (l >= k) continue;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < MC; ++c) {
       const int col = c0 + tx + 16 * c;
       if (col < N) out[(int64_t)l * N + col] = acc[a][c];
     }
@@ -93,73 +111,97 @@ k_utx(const T* __restrict__ U, int k, const T* __restrict__ X, int64_t n, int N,
   if (threadIdx.x == 0) ticket = atomicAdd(&counters[tile_id], 1u);
   __syncthreads();
   if (ticket != gridDim.x - 1) return;
-  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-    const int l = l0 + (e >> 6), col = c0 + (e & 63);
-    if (l >= k || col >= N) continue;
-    T s = T(0);
-    for (int c = 0; c < (int)gridDim.x; ++c) s += __ldcg(part + (int64_t)c * kn + (int64_t)l * N + col);
-    M[(int64_t)l * N + col] = s * (T)lam[l];
+  // last CTA of the tile: each thread sums its NE entries over the chunks in chunk order,
+  // several chunks' loads in flight
+  constexpr int NE = 64 * NT / 256;
+  constexpr int UF = NE >= 16 ? 2 : 4;
+  int64_t off[NE];
+  bool ok[NE];
+  T sacc[NE];
+#pragma unroll
+  for (int u = 0; u < NE; ++u) {
+    const int e = threadIdx.x + 256 * u;
+    const int l = l0 + e / NT, col = c0 + e % NT;
+    ok[u] = l < k && col < N;
+    off[u] = ok[u] ? (int64_t)l * N + col : 0;
+    sacc[u] = T(0);
   }
+#pragma unroll UF
+  for (int c = 0; c < (int)gridDim.x; ++c) {
+    T v[NE];
+#pragma unroll
+    for (int u = 0; u < NE; ++u) v[u] = ok[u] ? __ldcg(part + (int64_t)c * kn + off[u]) : T(0);
+#pragma unroll
+    for (int u = 0; u < NE; ++u) sacc[u] += v[u];
+  }
+#pragma unroll
+  for (int u = 0; u < NE; ++u)
+    if (ok[u]) M[off[u]] = sacc[u] * (T)lam[l0 + (threadIdx.x + 256 * u) / NT];
   if (threadIdx.x == 0) counters[tile_id] = 0u;
 }
 
-template <typename T>
+// BR rows x NC columns per CTA (32 x 64, or 64 x 32 for m <= 32), K staged in chunks of 32.
+template <typename T, int BR, int NC>
 __global__ void __launch_bounds__(256)
 k_rowmul(const T* __restrict__ In, int64_t ldi, int K, const T* __restrict__ Mm, int m, int64_t n,
          T* __restrict__ Out, int64_t ldo, const int* run) {
+  constexpr int PR = BR / 16, QC = NC / 16;  // rows and columns per thread
+  constexpr int LI = BR * 32 / 256, LM = 32 * NC / 256;
   if (run && *run == 0) return;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t row0 = (int64_t)blockIdx.x * 32;
-  const int col0 = blockIdx.y * 64;
-  __shared__ T Is[32][33];
-  __shared__ T Ms[32][65];
-  T acc[2][4];
+  const int64_t row0 = (int64_t)blockIdx.x * BR;
+  const int col0 = blockIdx.y * NC;
+  __shared__ T Is[BR][33];
+  __shared__ T Ms[32][NC + 1];
+  T acc[PR][QC];
 #pragma unroll
-  for (int p = 0; p < 2; ++p)
+  for (int p = 0; p < PR; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
+    for (int q = 0; q < QC; ++q) acc[p][q] = T(0);
   for (int k0 = 0; k0 < K; k0 += 32) {
-    T iv[4], mv[8];
+    T iv[LI], mv[LM];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < LI; ++u) {
       const int e = threadIdx.x + 256 * u, rr = e >> 5, kk = e & 31;
       const int64_t i = row0 + rr;
       iv[u] = (i < n && k0 + kk < K) ? In[i * ldi + k0 + kk] : T(0);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = threadIdx.x + 256 * u, kk = e >> 6, cc = e & 63;
+    for (int u = 0; u < LM; ++u) {
+      const int e = threadIdx.x + 256 * u, kk = e / NC, cc = e % NC;
       mv[u] = (k0 + kk < K && col0 + cc < m) ? Mm[(int64_t)(k0 + kk) * m + col0 + cc] : T(0);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < LI; ++u) {
       const int e = threadIdx.x + 256 * u;
       Is[e >> 5][e & 31] = iv[u];
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < LM; ++u) {
       const int e = threadIdx.x + 256 * u;
-      Ms[e >> 6][e & 63] = mv[u];
+      Ms[e / NC][e % NC] = mv[u];
     }
     __syncthreads();
 #pragma unroll 8
     for (int kk = 0; kk < 32; ++kk) {
-      const T a0 = Is[ty][kk], a1 = Is[ty + 16][kk];
+      T a[PR];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int p = 0; p < PR; ++p) a[p] = Is[ty + 16 * p][kk];
+#pragma unroll
+      for (int q = 0; q < QC; ++q) {
         const T mq = Ms[kk][tx + 16 * q];
-        acc[0][q] = fma(a0, mq, acc[0][q]);
-        acc[1][q] = fma(a1, mq, acc[1][q]);
+#pragma unroll
+        for (int p = 0; p < PR; ++p) acc[p][q] = fma(a[p], mq, acc[p][q]);
       }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < PR; ++p) {
     const int64_t i = row0 + ty + 16 * p;
     if (i >= n) continue;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < QC; ++q) {
       const int c = col0 + tx + 16 * q;
       if (c < m) Out[i * ldo + c] = acc[p][q];
     }
@@ -337,24 +379,35 @@ int ck(cudaError_t e, std::string& msg, const char* what) {
 
 void launch_rowmul(int tdtype, const void* In, int64_t ldi, int K, const void* M, int m, int64_t n, void* Out,
                    int64_t ldo, const int* run, cudaStream_t s) {
-  dim3 grid(cdivi(n, 32), cdivi(m, 64));
-  if (tdtype == 0)
-    k_rowmul<double><<<grid, 256, 0, s>>>((const double*)In, ldi, K, (const double*)M, m, n, (double*)Out, ldo, run);
-  else
-    k_rowmul<float><<<grid, 256, 0, s>>>((const float*)In, ldi, K, (const float*)M, m, n, (float*)Out, ldo, run);
+#define RM_ARGS(T) (const T*)In, ldi, K, (const T*)M, m, n, (T*)Out, ldo, run
+  if (m <= 32) {  // narrow output: 64 rows x 32 columns per CTA, no masked half
+    dim3 grid(cdivi(n, 64), 1);
+    if (tdtype == 0) k_rowmul<double, 64, 32><<<grid, 256, 0, s>>>(RM_ARGS(double));
+    else k_rowmul<float, 64, 32><<<grid, 256, 0, s>>>(RM_ARGS(float));
+  } else {
+    dim3 grid(cdivi(n, 32), cdivi(m, 64));
+    if (tdtype == 0) k_rowmul<double, 32, 64><<<grid, 256, 0, s>>>(RM_ARGS(double));
+    else k_rowmul<float, 32, 64><<<grid, 256, 0, s>>>(RM_ARGS(float));
+  }
+#undef RM_ARGS
 }
 
 int lai_apply(const LaiOp& op, int tdtype, const Dims& d, const void* X, void* Y, double c, const void* X2,
               const void* P1, const void* P2, double* part, const int* run, cudaStream_t s) {
   const int N = d.N;
   const int64_t chunk = (d.n + op.nchunks - 1) / op.nchunks;
-  dim3 g1(op.nchunks, cdivi(op.k, 64), cdivi(N, 64));
-  if (tdtype == 0)
-    k_utx<double><<<g1, 256, 0, s>>>((const double*)op.U, op.k, (const double*)X, d.n, N, d.ld, chunk,
-                                     (double*)op.xpart, op.lam, (double*)op.M, op.counters, run);
-  else
-    k_utx<float><<<g1, 256, 0, s>>>((const float*)op.U, op.k, (const float*)X, d.n, N, d.ld, chunk,
-                                    (float*)op.xpart, op.lam, (float*)op.M, op.counters, run);
+  const bool narrow = N <= 32;
+  dim3 g1(op.nchunks, cdivi(op.k, 64), narrow ? 1 : cdivi(N, 64));
+#define UTX_ARGS(T) (const T*)op.U, op.k, (const T*)X, d.n, N, d.ld, chunk, (T*)op.xpart, op.lam, (T*)op.M, \
+                    op.counters, run
+  if (tdtype == 0) {
+    if (narrow) k_utx<double, 32, 32><<<g1, 256, 0, s>>>(UTX_ARGS(double));
+    else k_utx<double, 64, 32><<<g1, 256, 0, s>>>(UTX_ARGS(double));
+  } else {
+    if (narrow) k_utx<float, 32, 64><<<g1, 256, 0, s>>>(UTX_ARGS(float));
+    else k_utx<float, 64, 32><<<g1, 256, 0, s>>>(UTX_ARGS(float));
+  }
+#undef UTX_ARGS
   launch_rowmul(tdtype, op.U, op.k, op.k, op.M, N, d.n, Y, d.ld, run, s);
   return launch_ax_finish_impl(tdtype, d, Y, nullptr, 1, c, X2, P1, P2, part, 0, run, s);
 }

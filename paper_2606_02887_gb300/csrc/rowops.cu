@@ -20,15 +20,16 @@ namespace snmf {
 
 namespace {
 
-template <typename T>
+template <typename T, int TW, int RS>
 __global__ void __launch_bounds__(256)
 k_gram(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, int b, int64_t ld,
        int64_t chunk, int ntile, double* __restrict__ gpart, int pair, int npairs,
        const Ctl* __restrict__ ctl, const int* run, double* __restrict__ G64, T* __restrict__ GT,
        int tpair, double lam_shift, unsigned* __restrict__ counters, Ctl* __restrict__ rho_ctl,
        int rho_iters, double rho_scale, double rho_shift) {
-  gram_body<T>(X, Y, n, r, b, ld, chunk, ntile, gpart, pair, npairs, ctl, run, G64, GT, tpair, lam_shift,
-               counters, rho_ctl, rho_iters, rho_scale, rho_shift, blockIdx.x, gridDim.x, blockIdx.y);
+  gram_body<T, TW, RS>(X, Y, n, r, b, ld, chunk, ntile, gpart, pair, npairs, ctl, run, G64, GT, tpair,
+                       lam_shift, counters, rho_ctl, rho_iters, rho_scale, rho_shift, blockIdx.x, gridDim.x,
+                       blockIdx.y);
 }
 
 template <typename T, int OP, int EPI, int BM, int NC>
@@ -468,17 +469,23 @@ void launch_gram(int tdtype, const void* X, const void* Y, const Dims& d, int pa
                  double* gpart, int nchunks, const Ctl* ctl, const int* run, double* G64, void* GT,
                  int tpair, double lam_shift, unsigned* counters, cudaStream_t s, Ctl* rho_ctl,
                  int rho_iters, double rho_scale, double rho_shift) {
-  const int ntile = (d.r + 63) / 64;
+  // r <= 32: one 32 x 32 tile per restart (a 64-wide tile would compute 4x the entries)
+  const bool narrow = d.r <= 32;
+  const int ntile = narrow ? 1 : (d.r + 63) / 64;
   const int64_t chunk = (d.n + nchunks - 1) / nchunks;
   dim3 grid(nchunks, d.b * ntile * ntile);
-  if (tdtype == 0)
-    k_gram<double><<<grid, 256, 0, s>>>((const double*)X, (const double*)Y, d.n, d.r, d.b, d.ld, chunk,
-                                        ntile, gpart, pair, npairs, ctl, run, G64, (double*)GT, tpair,
-                                        lam_shift, counters, nullptr, 0, 1.0, 0.0);
-  else
-    k_gram<float><<<grid, 256, 0, s>>>((const float*)X, (const float*)Y, d.n, d.r, d.b, d.ld, chunk,
-                                       ntile, gpart, pair, npairs, ctl, run, G64, (float*)GT, tpair,
-                                       lam_shift, counters, rho_ctl, rho_iters, rho_scale, rho_shift);
+#define GRAM_ARGS(T) (const T*)X, (const T*)Y, d.n, d.r, d.b, d.ld, chunk, ntile, gpart, pair, npairs, ctl, run, \
+                     G64, (T*)GT, tpair, lam_shift, counters
+  if (tdtype == 0) {
+    if (narrow) k_gram<double, 32, 32><<<grid, 256, 0, s>>>(GRAM_ARGS(double), nullptr, 0, 1.0, 0.0);
+    else k_gram<double, 64, 32><<<grid, 256, 0, s>>>(GRAM_ARGS(double), nullptr, 0, 1.0, 0.0);
+  } else {
+    if (narrow)
+      k_gram<float, 32, 64><<<grid, 256, 0, s>>>(GRAM_ARGS(float), rho_ctl, rho_iters, rho_scale, rho_shift);
+    else
+      k_gram<float, 64, 32><<<grid, 256, 0, s>>>(GRAM_ARGS(float), rho_ctl, rho_iters, rho_scale, rho_shift);
+  }
+#undef GRAM_ARGS
 }
 
 static int rowgemm_bm(const Dims& d, int tdtype) {

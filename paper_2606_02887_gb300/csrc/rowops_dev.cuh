@@ -454,68 +454,77 @@ __device__ void fused_control(int mode, Ctl& c, const double* part, int nslots, 
 
 
 // ------------------------------------------------------------------------------
-// Gram X_j^T Y_j per restart j.  CTA (chunk, tile): a 64x64 output tile over a chunk of
-// rows (16x16 threads, 4x4 micro tiles), FP64 partial written to gpart.  The last CTA of
-// each tile (arrival counter) sums the partials in chunk order and writes G64 (and the
-// factor-type copy with lam_shift * I on the diagonal when pair == tpair): a fixed-order,
-// deterministic two-stage reduction in one launch.
+// Gram X_j^T Y_j per restart j.  CTA (chunk, tile): a TW x TW output tile over a chunk of
+// rows (16x16 threads, TW/16 x TW/16 micro tiles; TW = 64, or 32 for r <= 32), RS rows staged
+// per round with the next round's loads in flight, X staged once when X and Y are the same
+// slice; FP64 partial written to gpart.  The last CTA of each tile (arrival counter) sums the
+// partials in chunk order and writes G64 (and the factor-type copy with lam_shift * I on the
+// diagonal when pair == tpair): a fixed-order, deterministic two-stage reduction in one launch.
 // ------------------------------------------------------------------------------
 // CTA coordinates are arguments: `cidx` of `nch` row chunks, `jt` = restart * ntile^2 + tile.
-template <typename T>
+template <typename T, int TW = 64, int RS = 32>
 __device__ __forceinline__ void
 gram_body(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, int b, int64_t ld,
           int64_t chunk, int ntile, double* __restrict__ gpart, int pair, int npairs,
           const Ctl* __restrict__ ctl, const int* run, double* __restrict__ G64, T* __restrict__ GT,
           int tpair, double lam_shift, unsigned* __restrict__ counters, Ctl* __restrict__ rho_ctl,
           int rho_iters, double rho_scale, double rho_shift, int cidx, int nch, int jt) {
+  constexpr int MT = TW / 16;             // micro tile
+  constexpr int LD = RS * TW / 256;       // staged values per thread and operand
+  static_assert(RS * TW % 256 == 0, "staging split over 256 threads");
   const int j = jt / (ntile * ntile);
   const int t = jt % (ntile * ntile);
   const int ti = t / ntile, tj = t % ntile;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t i_begin = (int64_t)cidx * chunk;
   const int64_t i_end = min(n, i_begin + chunk);
-  constexpr int RS = 32;  // rows staged per round
-  __shared__ T Xs[RS][64 + 1];
-  __shared__ T Ys[RS][64 + 1];
+  __shared__ T Xs[RS][TW + 1];
+  __shared__ T Ys[RS][TW + 1];
   __shared__ unsigned ticket;
-  T acc[4][4];
+  T acc[MT][MT];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < MT; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
+    for (int c = 0; c < MT; ++c) acc[a][c] = T(0);
   const bool skip = (run && *run == 0) || (ctl && !ctl[j].active);
   if (!skip) {
-    const int64_t cx = (int64_t)j * r + ti * 64;
-    const int64_t cy = (int64_t)j * r + tj * 64;
-    const int wx = min(64, r - ti * 64), wy = min(64, r - tj * 64);
-    for (int64_t i0 = i_begin; i0 < i_end; i0 += RS) {
-      T xv_[RS * 64 / 256], yv_[RS * 64 / 256];
+    const int64_t cx = (int64_t)j * r + ti * TW;
+    const int64_t cy = (int64_t)j * r + tj * TW;
+    const int wx = min(TW, r - ti * TW), wy = min(TW, r - tj * TW);
+    const bool same = (X == Y) && (ti == tj);  // X^T X on a diagonal tile: one operand
+    T xv_[LD], yv_[LD];
+    auto fetch = [&](int64_t i0) {
 #pragma unroll
-      for (int m = 0; m < RS * 64 / 256; ++m) {
+      for (int m = 0; m < LD; ++m) {
         const int e = threadIdx.x + 256 * m;
-        const int rr = e >> 6, cc = e & 63;
+        const int rr = e / TW, cc = e % TW;
         const int64_t i = i0 + rr;
         xv_[m] = (i < i_end && cc < wx) ? X[i * ld + cx + cc] : T(0);
-        yv_[m] = (i < i_end && cc < wy) ? Y[i * ld + cy + cc] : T(0);
+        if (!same) yv_[m] = (i < i_end && cc < wy) ? Y[i * ld + cy + cc] : T(0);
       }
+    };
+    if (i_begin < i_end) fetch(i_begin);
+    for (int64_t i0 = i_begin; i0 < i_end; i0 += RS) {
 #pragma unroll
-      for (int m = 0; m < RS * 64 / 256; ++m) {
+      for (int m = 0; m < LD; ++m) {
         const int e = threadIdx.x + 256 * m;
-        Xs[e >> 6][e & 63] = xv_[m];
-        Ys[e >> 6][e & 63] = yv_[m];
+        Xs[e / TW][e % TW] = xv_[m];
+        if (!same) Ys[e / TW][e % TW] = yv_[m];
       }
       __syncthreads();
+      if (i0 + RS < i_end) fetch(i0 + RS);  // the next round's loads fly during this one
+      const T(*Yr)[TW + 1] = same ? Xs : Ys;
 #pragma unroll 8
       for (int rr = 0; rr < RS; ++rr) {
-        T xa[4], yb[4];
+        T xa[MT], yb[MT];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) xa[a] = Xs[rr][ty + 16 * a];
+        for (int a = 0; a < MT; ++a) xa[a] = Xs[rr][ty + 16 * a];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) yb[c] = Ys[rr][tx + 16 * c];
+        for (int c = 0; c < MT; ++c) yb[c] = Yr[rr][tx + 16 * c];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < MT; ++a)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc[a][c] = fma(xa[a], yb[c], acc[a][c]);
+          for (int c = 0; c < MT; ++c) acc[a][c] = fma(xa[a], yb[c], acc[a][c]);
       }
       __syncthreads();
     }
@@ -526,12 +535,12 @@ gram_body(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, in
   T* gp = reinterpret_cast<T*>(gpart);  // chunk partials in the working type
   T* out = gp + (int64_t)cidx * slab + tile_base;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int p = ti * 64 + ty + 16 * a;
+  for (int a = 0; a < MT; ++a) {
+    const int p = ti * TW + ty + 16 * a;
     if (p >= r) continue;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int q = tj * 64 + tx + 16 * c;
+    for (int c = 0; c < MT; ++c) {
+      const int q = tj * TW + tx + 16 * c;
       if (q < r) out[(int64_t)p * r + q] = acc[a][c];
     }
   }
@@ -542,33 +551,35 @@ gram_body(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int r, in
   __syncthreads();
   if (ticket == nch - 1) {
     // last CTA of this tile: fixed-order sum over the chunks
-    // each thread owns 16 tile entries and sums them over the chunks in chunk order, with
-    // the 16 loads of a chunk (and the next chunk's) in flight together
+    // each thread owns NE tile entries and sums them over the chunks in chunk order, with
+    // the loads of several chunks in flight together
     // nch: chunks of this tile
-    int64_t off_[16];
-    bool ok_[16];
-    T sacc[16];
+    constexpr int NE = TW * TW / 256;
+    constexpr int UF = NE >= 16 ? 2 : 4;  // chunks in flight (registers: NE loads each)
+    int64_t off_[NE];
+    bool ok_[NE];
+    T sacc[NE];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
+    for (int u = 0; u < NE; ++u) {
       const int e = threadIdx.x + 256 * u;
-      const int p = ti * 64 + (e >> 6), q = tj * 64 + (e & 63);
+      const int p = ti * TW + e / TW, q = tj * TW + e % TW;
       ok_[u] = (p < r && q < r);
       off_[u] = tile_base + (int64_t)(ok_[u] ? p : 0) * r + (ok_[u] ? q : 0);
       sacc[u] = T(0);
     }
-#pragma unroll 2
+#pragma unroll UF
     for (int c = 0; c < nch; ++c) {
-      T v[16];
+      T v[NE];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) v[u] = ok_[u] ? __ldcg(gp + (int64_t)c * slab + off_[u]) : T(0);
+      for (int u = 0; u < NE; ++u) v[u] = ok_[u] ? __ldcg(gp + (int64_t)c * slab + off_[u]) : T(0);
 #pragma unroll
-      for (int u = 0; u < 16; ++u) sacc[u] += v[u];
+      for (int u = 0; u < NE; ++u) sacc[u] += v[u];
     }
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
+    for (int u = 0; u < NE; ++u) {
       if (!ok_[u]) continue;
       const int e = threadIdx.x + 256 * u;
-      const int p = ti * 64 + (e >> 6), q = tj * 64 + (e & 63);
+      const int p = ti * TW + e / TW, q = tj * TW + e % TW;
       G64[off_[u]] = (double)sacc[u];
       if (GT && pair == tpair) GT[(int64_t)j * rr2 + (int64_t)p * r + q] = sacc[u] + (p == q ? (T)lam_shift : T(0));
     }

@@ -52,7 +52,10 @@ def test_lai_penalty_solve_matches_oracle_fp64():
     opts = O.Options(max_iter=6, tol=0.0, memory=10, objective="closed", lambda_sym=0.01 * np.linalg.norm(A))
     Wo, Ho, _ = O.snmpbb_penalty(O.LaiOperator(Uo, lo), W0, W0, opts)
     W, H, _, _, _ = gpu_solve(A, W0, r, W0, lai=(k, p, q, seed), max_iter=6, tol=0.0)
-    assert rel(W, Wo) <= 1e-8 and rel(H, Ho) <= 1e-8, (rel(W, Wo), rel(H, Ho))
+    # the sketch reproduces the oracle's operator to about 2e-14 (CholeskyQR and the Jacobi
+    # eigensolver against numpy's); the iterates measure <= 6e-13 over these 6 iterations, and
+    # the oracle moves its W by the size of a perturbation of U (1e-12 -> 1.1e-12 after 6)
+    assert rel(W, Wo) <= 1e-11 and rel(H, Ho) <= 1e-11, (rel(W, Wo), rel(H, Ho))
 
 
 def test_lai_sketch_csr_fp32_power_law():

@@ -66,6 +66,23 @@ def rounding_envelope(run, key, n_iter, seeds=3, u=2.0 ** -53):
     return out
 
 
+MEASURED_FACTOR = 20.0
+
+
+def start_divergence(run, W0, n_iter, seeds=3, eps=1e-15):
+    """Measured (not modelled) sensitivity of the iteration: the oracle's own divergence, at
+    each iteration, between its run from W0 and runs from W0 perturbed by eps relative (max
+    over seeds, then the running max over iterations).  `run(W)` returns the oracle's trace."""
+    base = run(W0)
+    out = np.zeros(n_iter)
+    for seed in range(seeds):
+        g = np.random.default_rng(100 + seed)
+        tr = run(W0 * (1.0 + eps * g.standard_normal(W0.shape)))
+        for k in range(n_iter):
+            out[k] = max(out[k], rel(tr[k]["W"], base[k]["W"]), rel(tr[k]["Ht"], base[k]["Ht"]))
+    return np.maximum.accumulate(out)
+
+
 def iter_tol(envelope, k):
     """Bar at iteration k: 1e-10, widened to 10x the oracle's own rounding
     envelope where the iteration's conditioning does not allow 1e-10."""
@@ -94,6 +111,9 @@ def test_penalty_fp64_iterates_match_oracle(cfg1, oracle_pen50):
     opts = O.Options(formulation="penalty", memory=10, max_iter=50, tol=0.0, objective="closed")
     env = rounding_envelope(lambda: O.snmpbb_penalty(A, W0, W0, opts, keep_iterates=True)[2]["trace"],
                             "W", 50)
+    # second, measured bar: a small multiple of the oracle's divergence from starts perturbed by
+    # 1e-15 (measured GPU / divergence: 0.5-1.7 through iteration 28, at most about 12 at 40-46)
+    div = start_divergence(lambda W: O.snmpbb_penalty(A, W, W, opts, keep_iterates=True)[2]["trace"], W0, 50)
     errs = []
     for k in range(1, 51):
         W, H, st, stats, _ = gpu_solve(A, W0, 10, W0, max_iter=k, tol=0.0, nonmonotone_M=10)
@@ -101,6 +121,7 @@ def test_penalty_fp64_iterates_match_oracle(cfg1, oracle_pen50):
         e = max(rel(W, rec["W"]), rel(H, rec["Ht"]))
         errs.append(e)
         assert e <= iter_tol(env, k), (k, e, env[k - 1])
+        assert e <= max(ITER_TOL, MEASURED_FACTOR * div[k - 1]), (k, e, div[k - 1])
         assert stats["iters"] == k
     print("penalty M=10 gpu-vs-oracle:", " ".join(f"{k}:{e:.1e}/{env[k-1]:.1e}" for k, e in enumerate(errs, 1)))
     # where the conditioning allows it (envelope well below 1e-10) the 1e-10 bar holds
