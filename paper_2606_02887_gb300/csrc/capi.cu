@@ -541,7 +541,8 @@ void pen_block(snmf_ctx* h, int xv, int xf, bool is_w, const Params& P, bool nai
     a.X = X; a.B = h->buf[B_B]; a.LX = gr ? h->buf[B_LX] : nullptr;
     a.gout = h->buf[B_G];
     a.ctl_mode = is_w ? CTL_START_W : CTL_START_H;
-    launch_rowgemm(td, OP_LOAD, EPI_GRAD, a, h->s);
+    if (h->use_fuse && h->row_tc && !gr) launch_rowtc_grad(a, h->dev_err, h->s);  // X G on tcgen05
+    else launch_rowgemm(td, OP_LOAD, EPI_GRAD, a, h->s);
   }
   launch_any_active(h->ctl, h->b, h->run, nullptr, h->s);
   const int K = h->opt.inner_iters;

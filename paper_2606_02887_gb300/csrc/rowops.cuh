@@ -67,6 +67,10 @@ void launch_rowfuse_update(const RowArgs& a, int bm, int nc, cudaStream_t s);
 bool rowtc_supported(int tdtype, int r, int nc);
 void launch_rowtc_dstep(const RowArgs& a, int* err, cudaStream_t s);
 void launch_rowtc_update(const RowArgs& a, int* err, cudaStream_t s);
+// Block-start gradient of the same FP32, r = 64 blocks (no graph term): g = X G - B into
+// RowArgs gout from X, B; the block-start control step (ctl_mode) in the last CTA of each
+// restart, over ceil(n / 128) partial slots.
+void launch_rowtc_grad(const RowArgs& a, int* err, cudaStream_t s);
 // The same pair as persistent warp-specialised kernels (rowtma.cu: one CTA per SM over 128-row
 // tiles, inputs streamed by TMA into shared slots, outputs stored by TMA).  ld: the factor
 // arrays' row pitch (a multiple of 4).  false when the tensor maps cannot be encoded (nothing

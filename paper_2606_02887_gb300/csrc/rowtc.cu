@@ -500,6 +500,90 @@ __global__ void __launch_bounds__(256, 2) k_rowtc_update(RowArgs a, int* err) {
   block_partials(a, dq, j, blockIdx.x, gridDim.x, shq, &ticket);
 }
 
+// ---------------------------------------------------------------------------------------
+// Block-start gradient: g = X G - B written to gout; q0 ||P grad f(X)||^2, q1 1/2 <g - B, X>,
+// q6 zero entries of X; others zero.  The last CTA of each restart runs the block-start
+// control step (ctl_mode).
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 2) k_rowtc_grad(RowArgs a, int* err) {
+  extern __shared__ unsigned char tsm_raw[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_bad;
+  __shared__ float shq[8][8];
+  __shared__ unsigned ticket;
+  const int j = blockIdx.y;
+  const Ctl& cj = a.ctl[j];
+  const bool live = cj.active && !(a.run && *a.run == 0);
+  float dq[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) dq[m] = 0.f;
+  if (live) {
+    const TcTile t = carve(tsm_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mrow = 32 * (warp & 3) + lane, c0 = 32 * (warp >> 2);
+    const int c4 = threadIdx.x & 15, rw = threadIdx.x >> 4;
+    const int64_t row_base = (int64_t)blockIdx.x * TR;
+    const int64_t colg = (int64_t)j * RC + 4 * c4;
+    const float* X = (const float*)a.X;
+    const float* B = (const float*)a.B;
+    float* g = (float*)a.gout;
+    tc_setup(&bar, &tmem_slot, &s_bad, (const float*)a.G + (int64_t)j * RC * RC, t);
+#pragma unroll
+    for (int k = 0; k < CM_ROWS; ++k) {
+      const int m = rw + 16 * k;
+      const int64_t i = row_base + m;
+      const float4 x4 = i < a.n ? ld4(X + i * a.ld + colg) : make_float4(0.f, 0.f, 0.f, 0.f);
+      put4(t.ah, t.al, sw_chunk(m, 4 * c4, TR), x4.x, x4.y, x4.z, x4.w);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t tacc = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    run_product(t, tmem, &bar);  // X G -> columns 0 .. 63
+    float4 b4[CM_ROWS];
+#pragma unroll
+    for (int k = 0; k < CM_ROWS; ++k) {
+      const int64_t i = row_base + rw + 16 * k;
+      b4[k] = i < a.n ? ld4(B + i * a.ld + colg) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const bool ok = wait_product(&bar, 0, &s_bad, err);
+    if (ok) {
+      stage_acc(tacc, 0, t.al, mrow, c0);  // X G -> T
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < CM_ROWS; ++k) {
+        const int m = rw + 16 * k;
+        const int64_t i = row_base + m;
+        if (i >= a.n) continue;
+        const int64_t off = i * a.ld + colg;
+        const float4 acc = ld_sw(t.al, m, 4 * c4);
+        const float4 x4 = ld4(X + off);
+        const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+        const float as[4] = {acc.x, acc.y, acc.z, acc.w};
+        const float bs[4] = {b4[k].x, b4[k].y, b4[k].z, b4[k].w};
+        float go[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float gv = as[q] - bs[q];
+          const float pgv = xs[q] > 0.f ? gv : (gv < 0.f ? gv : 0.f);
+          dq[0] += pgv * pgv;
+          dq[1] += 0.5f * (gv - bs[q]) * xs[q];
+          if (xs[q] == 0.f) dq[6] += 1.f;
+          go[q] = gv;
+        }
+        st4(g + off, make_float4(go[0], go[1], go[2], go[3]));
+      }
+    }
+    if (s_bad && threadIdx.x == 0) mbar_wait(&bar, 0, kDrain);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+  }
+  block_partials(a, dq, j, blockIdx.x, gridDim.x, shq, &ticket);
+}
+
 }  // namespace
 
 bool rowtc_supported(int tdtype, int r, int nc) { return tdtype == 1 && r == RC && nc == 1; }
@@ -512,6 +596,16 @@ void launch_rowtc_dstep(const RowArgs& a, int* err, cudaStream_t s) {
   }
   dim3 grid((unsigned)((a.n + TR - 1) / TR), (unsigned)a.b);
   k_rowtc_dstep<<<grid, 256, SMEM_BYTES, s>>>(a, err);
+}
+
+void launch_rowtc_grad(const RowArgs& a, int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_rowtc_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    attr = true;
+  }
+  dim3 grid((unsigned)((a.n + TR - 1) / TR), (unsigned)a.b);
+  k_rowtc_grad<<<grid, 256, SMEM_BYTES, s>>>(a, err);
 }
 
 void launch_rowtc_update(const RowArgs& a, int* err, cudaStream_t s) {
