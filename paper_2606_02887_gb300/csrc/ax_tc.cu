@@ -124,7 +124,9 @@ struct TcParams {
   int stages;
   int k_iters;        // BK-steps per split
   int tmem_cols;      // power of two >= BN, >= 32
-  int xparts;         // 2: X as hi + lo BF16 parts (two MMAs per K step), 1: hi only
+  int xparts;         // 2: X as hi + lo BF16 parts, 1: hi only
+  int comb;           // xparts 2 and 2 BN <= 256: one MMA of N = 2 BN per K step over the
+                      // contiguous Xh | Xl tiles, A Xh and A Xl in TMEM columns [0, BN), [BN, 2 BN)
   int splits;         // K slices (gridDim.z)
   float* Y;           // unfused: output base (split z writes Y + z * n * ldy); fused: the slices
   int64_t ldy;
@@ -197,7 +199,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     s_issued = it;
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    const uint32_t idesc = idesc_bf16(BM, BN);
+    const uint32_t idesc = idesc_bf16(BM, p.comb ? 2 * BN : BN);
     int it = 0;
     for (; it < p.k_iters; ++it) {
       const int s = it % p.stages;
@@ -209,8 +211,13 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         const uint64_t da = sdesc(sa + kk * 32);
-        mma_bf16(tmem, da, sdesc(sh + kk * 32), idesc, (it > 0 || kk > 0) ? 1u : 0u);
-        if (p.xparts == 2) mma_bf16(tmem, da, sdesc(sl + kk * 32), idesc, 1u);
+        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+        if (p.comb) {  // B = the 2 BN rows of Xh then Xl (one operand, one read of A)
+          mma_bf16(tmem, da, sdesc(sh + kk * 32), idesc, acc);
+        } else {
+          mma_bf16(tmem, da, sdesc(sh + kk * 32), idesc, acc);
+          if (p.xparts == 2) mma_bf16(tmem, da, sdesc(sl + kk * 32), idesc, 1u);
+        }
       }
       mma_commit(&empty[s]);
     }
@@ -231,11 +238,21 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   const bool ok = !s_fail;
   const int row = m0 + warp * 32 + lane;
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  // 16 accumulator columns (with the combined MMA: the A Xh and A Xl halves added)
+  auto acc16 = [&](uint32_t col, float* v) {
+    tmem_ld16(trow + col, v);
+    if (p.comb) {
+      float t[16];
+      tmem_ld16(trow + col + (uint32_t)BN, t);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] += t[i];
+    }
+  };
   if (ok && !p.e.fused) {
     float* Yz = p.Y + (int64_t)blockIdx.z * p.n * p.ldy;
     for (int c0 = 0; c0 < BN; c0 += 16) {
       float v[16];
-      tmem_ld16(trow + (uint32_t)c0, v);
+      acc16((uint32_t)c0, v);
       if (row < p.n) {
         float* yr = Yz + (int64_t)row * p.ldy + n0 + c0;
 #pragma unroll
@@ -258,7 +275,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       const int cw = min(64, BN - 64 * ch);
       for (int c = 0; c < cw; c += 16) {
         float v[16];
-        tmem_ld16(trow + (uint32_t)(64 * ch + c), v);
+        acc16((uint32_t)(64 * ch + c), v);
         float* dst = T + (warp * 32 + lane) * TS + c;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -786,8 +803,10 @@ int launch_tc_impl(const void* A16, int64_t n, const float* X, int N, int64_t ld
   p.BN = pl.BN;
   p.stages = pl.stages;
   p.k_iters = pl.k_iters;
-  p.tmem_cols = pl.tmem_cols;
   p.xparts = xparts;
+  p.comb = xparts == 2 && 2 * pl.BN <= 256;
+  p.tmem_cols = pl.tmem_cols;
+  while (p.comb && p.tmem_cols < 2 * pl.BN) p.tmem_cols *= 2;
   p.splits = pl.splits;
   p.Y = pl.splits > 1 ? ws : Y;
   p.ldy = ldx;
