@@ -136,6 +136,195 @@ struct TcParams {
   TcEpilogue e;       // fused epilogue (e.fused = 1)
 };
 
+// Fused epilogue of one 128 x BN output tile (K slice z), run by 128 threads te = 0 .. 127;
+// q is the TMEM lane quadrant of the thread's warp, so the thread drains accumulator row
+// 32 q + (te & 31) from trow.  The accumulator leaves TMEM in 64-column chunks through the
+// shared tile T [128][kEpiTS], so every global access below is a coalesced 16-byte access
+// along a row.  Split K: every slice publishes its partial tile; the last slice of the tile to
+// arrive (arrival counter) sums the slices in slice order (the result does not depend on the
+// arrival order) and runs the epilogue: Y = sum (+ c X2) and the per-restart partials
+// <P1, A X>, <P2, A X> of the tile's two 64-row slots.  A thread reads all 16 of its rows of
+// an operand before it uses them, so those reads are in flight together.  A group whose
+// waits ran out (ok = false) publishes nothing but still takes its ticket, so the counter
+// returns to zero for the next launch.  `sync` is a barrier over exactly these 128 threads.
+constexpr int kEpiTS = 68;
+
+template <typename Sync>
+__device__ __forceinline__ void fused_tile_epilogue(const TcParams& p, float* T, uint32_t trow, int q, int te,
+                                                    int n0, int m0, int z, unsigned tile, bool ok,
+                                                    unsigned* s_ticket, Sync sync) {
+  const int BN = p.BN;
+  const int lane = te & 31;
+  const int c4 = te & 15, r8 = te >> 4;  // float4 column, first row
+  // 16 accumulator columns (with the combined MMA: the A Xh and A Xl halves added)
+  auto acc16 = [&](uint32_t col, float* v) {
+    tmem_ld16(trow + col, v);
+    if (p.comb) {
+      float t2[16];
+      tmem_ld16(trow + col + (uint32_t)BN, t2);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] += t2[k];
+    }
+  };
+  auto stage_chunk = [&](int ch) {  // TMEM columns [64 ch, 64 ch + 64) -> T (rows = TMEM lanes)
+    const int cw = min(64, BN - 64 * ch);
+    for (int c = 0; c < cw; c += 16) {
+      float v[16];
+      acc16((uint32_t)(64 * ch + c), v);
+      float* dst = T + (q * 32 + lane) * kEpiTS + c;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        *reinterpret_cast<float4*>(dst + 4 * k) = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+  };
+  const int nch = (BN + 63) / 64;
+  bool last = ok;
+  if (p.splits > 1) {
+    if (ok) {
+      float* Wz = p.Y + (int64_t)z * p.n * p.ldy;
+      for (int ch = 0; ch < nch; ++ch) {
+        stage_chunk(ch);
+        sync();
+        const int col = n0 + 64 * ch + 4 * c4;
+        if (4 * c4 < BN - 64 * ch && col < p.N) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int rr = r8 + 8 * k;
+            const int64_t row_g = m0 + rr;
+            if (row_g < p.n)
+              *reinterpret_cast<float4*>(Wz + row_g * p.ldy + col) =
+                  *reinterpret_cast<const float4*>(T + rr * kEpiTS + 4 * c4);
+          }
+        }
+        sync();
+      }
+    }
+    __threadfence();
+    sync();
+    if (te == 0) *s_ticket = atomicAdd(&p.e.counters[tile], 1u);
+    sync();
+    const bool arrived_last = *s_ticket == (unsigned)(p.splits - 1);
+    if (arrived_last) {
+      __threadfence();
+      if (te == 0) p.e.counters[tile] = 0u;  // ready for the next launch
+    }
+    last = ok && arrived_last;
+  }
+  if (!last) return;
+  const bool dots = p.e.P1 || p.e.P2;
+  for (int ch = 0; ch < nch; ++ch) {
+    stage_chunk(ch);
+    sync();
+    const int col = n0 + 64 * ch + 4 * c4;
+    float d1[2] = {0.f, 0.f}, d2[2] = {0.f, 0.f};  // per 64-row slot (row rr: slot rr / 64 = k / 8)
+    if (4 * c4 < BN - 64 * ch && col < p.N) {
+      const int64_t idx0 = (int64_t)(m0 + r8) * p.ldy + col;  // row r8 + 8 k at idx0 + 8 k ldy
+      const int64_t rstep = 8 * p.ldy;
+      const int64_t rows_left = p.n - m0 - r8;  // rows r8 + 8 k < n - m0 exist
+      const int kmax = rows_left <= 0 ? 0 : (rows_left >= 121 ? 16 : (int)((rows_left + 7) / 8));
+      float4 y[16];
+      if (p.splits > 1) {
+        // the slices in slice order; this tile's own slice is the staged chunk
+#pragma unroll
+        for (int k = 0; k < 16; ++k) y[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int zz = 0; zz < p.splits; ++zz) {
+          if (zz == z) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const float4 v = *reinterpret_cast<const float4*>(T + (r8 + 8 * k) * kEpiTS + 4 * c4);
+              y[k].x += v.x; y[k].y += v.y; y[k].z += v.z; y[k].w += v.w;
+            }
+          } else {
+            const float* Sz = p.Y + (int64_t)zz * p.n * p.ldy + idx0;
+            float4 v[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+              v[k] = k < kmax ? __ldcg(reinterpret_cast<const float4*>(Sz + k * rstep)) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              y[k].x += v[k].x; y[k].y += v[k].y; y[k].z += v[k].z; y[k].w += v[k].w;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) y[k] = *reinterpret_cast<const float4*>(T + (r8 + 8 * k) * kEpiTS + 4 * c4);
+      }
+      // P1, P2 and X2 of 8 rows at a time in flight together: the dots use A X before c X2
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float4 w1[8], w2[8], w3[8];
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int kk = 8 * h + k;
+          const int64_t off = idx0 + kk * rstep;
+          w1[k] = (p.e.P1 && kk < kmax) ? *reinterpret_cast<const float4*>(p.e.P1 + off) : zero;
+          w2[k] = (p.e.P2 && kk < kmax) ? *reinterpret_cast<const float4*>(p.e.P2 + off) : zero;
+          w3[k] = (p.e.X2 && kk < kmax) ? *reinterpret_cast<const float4*>(p.e.X2 + off) : zero;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int kk = 8 * h + k;
+          if (kk < kmax) {
+            d1[h] += w1[k].x * y[kk].x + w1[k].y * y[kk].y + w1[k].z * y[kk].z + w1[k].w * y[kk].w;
+            d2[h] += w2[k].x * y[kk].x + w2[k].y * y[kk].y + w2[k].z * y[kk].z + w2[k].w * y[kk].w;
+            if (p.e.X2) {
+              y[kk].x += p.e.c * w3[k].x; y[kk].y += p.e.c * w3[k].y; y[kk].z += p.e.c * w3[k].z;
+              y[kk].w += p.e.c * w3[k].w;
+            }
+            *reinterpret_cast<float4*>(p.e.Y + idx0 + kk * rstep) = y[kk];
+          }
+        }
+      }
+    }
+    if (dots) {
+      // partials of each restart in this chunk (r divides 64, r % 4 == 0: restart jl owns the
+      // g = r / 4 float4 columns c4 in [jl g, jl g + g)) and slot: a fixed shuffle tree over the
+      // warp's lanes of those columns and its two row groups, then the four warps in order
+      const int g = p.e.r / 4;
+      float v[4] = {d1[0], d2[0], d1[1], d2[1]};
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1)
+        if (o < g) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
+        }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) v[t] += __shfl_xor_sync(0xffffffffu, v[t], 16);
+      sync();  // every thread is done with T
+      float* red = T;  // [4 warps][16 restarts][2 slots][2 dots]
+      if (lane < 16 && c4 % g == 0) {
+        float* rw = red + (q * 16 + c4 / g) * 4;
+        rw[0] = v[0];  // slot 0: <P1, .>, <P2, .>
+        rw[1] = v[1];
+        rw[2] = v[2];  // slot 1
+        rw[3] = v[3];
+      }
+      sync();
+      const int cw = min(64, BN - 64 * ch);
+      const int nres = cw / p.e.r;  // restarts in this chunk
+      if (te < 2 * nres) {
+        const int jl = te >> 1, slot_l = te & 1;
+        float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          s1 += red[(w * 16 + jl) * 4 + 2 * slot_l];
+          s2 += red[(w * 16 + jl) * 4 + 2 * slot_l + 1];
+        }
+        const int j = (n0 + 64 * ch) / p.e.r + jl;
+        const int64_t slot = 2 * (int64_t)(m0 / BM) + slot_l;
+        if (j < p.e.b && slot * 64 < p.n) {
+          double* qq = p.e.part + (slot * p.e.b + j) * kNQ + p.e.q0;
+          qq[0] = (double)s1;
+          qq[1] = (double)s2;
+        }
+      }
+    }
+    sync();  // T free for the next chunk
+  }
+}
+
 __global__ void __launch_bounds__(128, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapXh,
           const __grid_constant__ CUtensorMap mapXl, TcParams p) {
@@ -153,7 +342,6 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
   __shared__ int s_fail, s_issued, s_consumed;
   __shared__ unsigned s_ticket;
-  __shared__ float s_red[4][2];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN;
@@ -261,134 +449,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       }
     }
   }
-  if (p.e.fused && (p.ldy & 3) == 0) {  // 16-byte row groups (the launcher guarantees ldy % 4 == 0)
-    // The accumulator leaves TMEM in 64-column chunks through a shared-memory tile (the ring is
-    // free once the accumulator is complete), so every global access below is a coalesced
-    // 16-byte access along a row.  Split K: every slice publishes its partial tile; the last
-    // slice of the tile to arrive (arrival counter) sums the slices in slice order (the result
-    // does not depend on the arrival order) and runs the epilogue: Y = sum (+ c X2), and the
-    // per-restart partials <P1, A X>, <P2, A X> of the tile's two 64-row slots.
-    float* T = reinterpret_cast<float*>(base);  // [128][68]
-    constexpr int TS = 68;
-    const int c4 = threadIdx.x & 15, r8 = threadIdx.x >> 4;  // float4 column, first row
-    auto stage_chunk = [&](int ch) {  // TMEM columns [64 ch, 64 ch + 64) -> T (rows = TMEM lanes)
-      const int cw = min(64, BN - 64 * ch);
-      for (int c = 0; c < cw; c += 16) {
-        float v[16];
-        acc16((uint32_t)(64 * ch + c), v);
-        float* dst = T + (warp * 32 + lane) * TS + c;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      }
-    };
-    const int nch = (BN + 63) / 64;
-    bool last = ok;
-    if (p.splits > 1) {
-      if (ok) {
-        float* Wz = p.Y + (int64_t)blockIdx.z * p.n * p.ldy;
-        for (int ch = 0; ch < nch; ++ch) {
-          stage_chunk(ch);
-          __syncthreads();
-          const int col = n0 + 64 * ch + 4 * c4;
-          if (4 * c4 < BN - 64 * ch && col < p.N) {
-            for (int k = 0; k < 16; ++k) {
-              const int rr = r8 + 8 * k;
-              const int64_t row_g = m0 + rr;
-              if (row_g < p.n)
-                *reinterpret_cast<float4*>(Wz + row_g * p.ldy + col) = *reinterpret_cast<const float4*>(T + rr * TS + 4 * c4);
-            }
-          }
-          __syncthreads();
-        }
-      }
-      __threadfence();
-      __syncthreads();
-      // a CTA whose waits ran out still arrives (its slice is not valid, the call reports the
-      // error), so the counter returns to zero for the next launch in every case
-      const unsigned tile = blockIdx.y * gridDim.x + blockIdx.x;
-      if (threadIdx.x == 0) s_ticket = atomicAdd(&p.e.counters[tile], 1u);
-      __syncthreads();
-      const bool arrived_last = s_ticket == (unsigned)(p.splits - 1);
-      if (arrived_last) {
-        __threadfence();
-        if (threadIdx.x == 0) p.e.counters[tile] = 0u;  // ready for the next launch
-      }
-      last = ok && arrived_last;
-    }
-    if (last) {
-      const int rr_r = p.e.r;
-      const bool dots = p.e.P1 || p.e.P2;
-      for (int ch = 0; ch < nch; ++ch) {
-        stage_chunk(ch);
-        __syncthreads();
-        const int col = n0 + 64 * ch + 4 * c4;
-        float d1[2] = {0.f, 0.f}, d2[2] = {0.f, 0.f};  // per 64-row slot
-        if (4 * c4 < BN - 64 * ch && col < p.N) {
-          for (int k = 0; k < 16; ++k) {
-            const int rr = r8 + 8 * k;
-            const int64_t row_g = m0 + rr;
-            if (row_g >= p.n) continue;
-            const int64_t idx = row_g * p.ldy + col;
-            float4 y = *reinterpret_cast<const float4*>(T + rr * TS + 4 * c4);
-            if (p.splits > 1) {
-              float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-              for (int z = 0; z < p.splits; ++z) {
-                const float4 v = (z == (int)blockIdx.z)
-                                     ? y
-                                     : __ldcg(reinterpret_cast<const float4*>(p.Y + (int64_t)z * p.n * p.ldy + idx));
-                acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
-              }
-              y = acc;
-            }
-            if (p.e.P1) {
-              const float4 q = *reinterpret_cast<const float4*>(p.e.P1 + idx);
-              d1[rr >> 6] += q.x * y.x + q.y * y.y + q.z * y.z + q.w * y.w;
-            }
-            if (p.e.P2) {
-              const float4 q = *reinterpret_cast<const float4*>(p.e.P2 + idx);
-              d2[rr >> 6] += q.x * y.x + q.y * y.y + q.z * y.z + q.w * y.w;
-            }
-            if (p.e.X2) {
-              const float4 q = *reinterpret_cast<const float4*>(p.e.X2 + idx);
-              y.x += p.e.c * q.x; y.y += p.e.c * q.y; y.z += p.e.c * q.z; y.w += p.e.c * q.w;
-            }
-            *reinterpret_cast<float4*>(p.e.Y + idx) = y;
-          }
-        }
-        if (dots) {
-          // partials of each restart in this chunk (r divides 64) and slot, summed over the
-          // threads of its columns in thread order
-          __syncthreads();  // every thread is done with T
-          float* red = T;   // [128][4]
-          red[4 * threadIdx.x + 0] = d1[0];
-          red[4 * threadIdx.x + 1] = d2[0];
-          red[4 * threadIdx.x + 2] = d1[1];
-          red[4 * threadIdx.x + 3] = d2[1];
-          __syncthreads();
-          const int cw = min(64, BN - 64 * ch);
-          const int nres = cw / rr_r;  // restarts in this chunk
-          if ((int)threadIdx.x < 2 * nres) {
-            const int jl = threadIdx.x >> 1, slot_l = threadIdx.x & 1;
-            float s1 = 0.f, s2 = 0.f;
-            for (int t = 0; t < 128; ++t) {
-              if ((4 * (t & 15)) / rr_r != jl) continue;
-              s1 += red[4 * t + 2 * slot_l];
-              s2 += red[4 * t + 2 * slot_l + 1];
-            }
-            const int j = (n0 + 64 * ch) / rr_r + jl;
-            const int64_t slot = 2 * (int64_t)blockIdx.y + slot_l;
-            if (j < p.e.b && slot * 64 < p.n) {
-              double* q = p.e.part + (slot * p.e.b + j) * kNQ + p.e.q0;
-              q[0] = (double)s1;
-              q[1] = (double)s2;
-            }
-          }
-        }
-        __syncthreads();  // T free for the next chunk
-      }
-    }
-  }
+  if (p.e.fused && (p.ldy & 3) == 0)  // 16-byte row groups (the launcher guarantees ldy % 4 == 0)
+    // the ring is free once the accumulator is complete: it holds the epilogue tile
+    fused_tile_epilogue(p, reinterpret_cast<float*>(base), trow, warp, (int)threadIdx.x, n0, m0, (int)blockIdx.z,
+                        blockIdx.y * gridDim.x + blockIdx.x, ok, &s_ticket, [] { __syncthreads(); });
   __syncthreads();  // s_fail from the epilogue visible
   if (s_fail && threadIdx.x == 0) {
     // error path: drain with its own generous budget (a short wait budget that ran out

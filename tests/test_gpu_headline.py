@@ -184,11 +184,18 @@ def test_tile_body_single_problem_follows_oracle(tile_problem, prec):
     (2048, 512, dict(splits=8, stages=4, per_sm=1, bn=64)),
     (4096, 256, dict(splits=6, stages=2, per_sm=1, bn=256)),
     (1000, 192, dict(splits=2, stages=2, per_sm=2, bn=64)),
+    # fused epilogue (r divides 64): a deeper ring at one CTA per SM, 8 slices over n = 4096, a
+    # single slice, 256-column tiles over a ragged n with the last slice shorter
+    (2048, 512, dict(splits=4, stages=3, per_sm=1, bn=128)),
+    (4096, 512, dict(splits=8, stages=3, per_sm=1, bn=128)),
+    (2048, 256, dict(splits=1, stages=5, per_sm=1, bn=64)),
+    (1000, 256, dict(splits=3, stages=2, per_sm=1, bn=256)),
 ])
 def test_tuned_product_tiles_match_emulated_operands(tmp_path, n, cols, cfg):
     """Products with tile shapes the autotuner can choose (64/128/256-column tiles, 1 or 2
-    CTAs per SM, 2 to 8 K slices), forced through the tuning cache, against the exact
-    emulation of the stored BF16 operands (same bar as the built-in configuration)."""
+    CTAs per SM, 1 to 8 K slices, with and without the fused epilogue), forced through the
+    tuning cache, against the exact emulation of the stored BF16 operands (same bar as the
+    built-in configuration)."""
     import torch
     dev = torch.device("cuda:0")
     g = np.random.default_rng(n + cols + cfg["splits"])
