@@ -65,6 +65,9 @@ def parse():
     p.add_argument("--cpu-iters", type=int, default=10, help="oracle outer iterations timed for cpu_baseline")
     p.add_argument("--x-parts", type=int, default=2, choices=[1, 2],
                    help="BF16 product: X as hi + lo BF16 parts (2) or rounded to BF16 (1)")
+    p.add_argument("--sym-half", type=int, default=1, choices=[0, 1],
+                   help="BF16 dense: keep only the 128 x 128 tiles of A on and above the diagonal "
+                        "(default; the products are bitwise those of full storage)")
     return p.parse_args()
 
 
@@ -213,13 +216,15 @@ def run_reference(args):
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch, from the ncu captures summarised
 # in profiles/ (k_gemm_tc_dense8192_N512.md, k_rowfuse_dstep_dense8192_N512.md,
-# k_bgemm_tc_uneven256.md); keys: (workload, precision, r, batch, kernel, row-kernel body or
-# X parts), values: (bytes, the tuned tile shapes of the capture, which the run must share).
-# Other configurations, and runs tuned to other tiles, report null.
+# k_rowtc_dense8192_N512.md, k_rowtma_dense8192_N512.md, k_bgemm_tc_uneven256.md); keys:
+# (workload, precision, r, batch, kernel, row-kernel body or X parts; "dense8192-sym": A held
+# as its upper tiles), values: (bytes, the tuned tile shapes of the capture, which the run must
+# share).  Other configurations, and runs tuned to other tiles, report null.
 PROFILED_TRAFFIC = {
     ("uneven", "bf16", None, None, "product"): (875.5e6, {}),
     ("dense8192", "bf16", 64, 8, "dstep", 2): (51.4e6, {"row_bm": 128}),
-    ("dense8192", "bf16", 64, 8, "product", 2): (274.1e6, {"splits": 4, "bn": 128}),
+    ("dense8192", "bf16", 64, 8, "product", 2): (274.31e6, {"splits": 4, "bn": 128}),
+    ("dense8192-sym", "bf16", 64, 8, "product", 2): (213.78e6, {"splits": 4, "bn": 128}),
     ("dense8192", "bf16", 64, 8, "dstep", 3): (51.03e6, {}),
     ("dense8192", "bf16", 64, 8, "update", 3): (68.16e6, {}),
     ("dense8192", "bf16", 64, 8, "dstep", 4): (51.10e6, {}),
@@ -637,7 +642,8 @@ def main():
     ctl = 3 if weights is not None else 0  # lean learned step
     opts = S.snmf_default_options(precision=prec, formulation=form, batch=args.batch, max_iter=args.max_iter,
                                   tol=args.tol, nonmonotone_M=10, autotune=args.autotune,
-                                  tune_cache=args.tune_cache, step_controller=ctl, x_parts=args.x_parts)
+                                  tune_cache=args.tune_cache, step_controller=ctl, x_parts=args.x_parts,
+                                  sym_half=args.sym_half if args.precision == "bf16" else 0)
     stream = torch.cuda.current_stream(dev)
     h = S.snmf_create(S.dense_matrix(A), args.r, opts, stream=stream, mlp_weights=weights)
     tuning = None
@@ -647,6 +653,8 @@ def main():
         except S.SnmfError:  # no candidate fitted this shape: built-in configuration
             tuning = {"tuned": False}
     a_bytes = A.numel() * {"bf16": 2, "fp8": 1}.get(args.precision, A.element_size())
+    if args.sym_half and args.precision == "bf16":
+        a_bytes = args.n * (args.n + 1) // 2 * 2  # the triangle on and above the diagonal
     flush = None if a_bytes > 2 * L2_BYTES else torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def step():
@@ -687,7 +695,9 @@ def main():
     n, N = args.n, args.r * args.batch
     esz = 8 if args.precision == "f64" else 4
     a_esz = {"bf16": 2, "fp8": 1}.get(args.precision, esz)
-    alg_bytes = n * n * a_esz + 2 * n * N * esz
+    sym = bool(args.sym_half and args.precision == "bf16")
+    # symmetric-half storage: A's algorithmic bytes are the triangle on and above the diagonal
+    alg_bytes = (n * (n + 1) // 2 if sym else n * n) * a_esz + 2 * n * N * esz
     flops = 2.0 * n * n * N
     peaks, peak_kind = measured_peaks()
     sm_mhz = clk.get("sm_mhz") or SM_MAX_MHZ_NOMINAL
@@ -705,7 +715,7 @@ def main():
                 "alg_bytes_per_launch": alg_bytes, "flops_per_launch": flops,
                 "ms_per_launch": ms_kern, "ms_per_product_with_epilogue": ms_prod}
     elif args.precision == "bf16":
-        workload_key = "dense8192" if args.n == 8192 else None
+        workload_key = "dense8192" + ("-sym" if sym else "") if args.n == 8192 else None
         # the method's flops 2 n^2 N; the tensor pipes execute x_parts times that (X as hi + lo
         # BF16 parts takes two MMA passes)
         tflops = flops / (ms_kern * 1e-3) / 1e12
@@ -714,7 +724,8 @@ def main():
         tensor_bound = intensity > ridge
         roof = {"bound": "tensor" if tensor_bound else "hbm",
                 "kernel": "k_split_x + k_gemm_tc (tcgen05 BF16, X as %s, split-K reduced and epilogue fused "
-                          "in the kernel)" % ("hi+lo BF16 parts" if args.x_parts == 2 else "one BF16 part"),
+                          "in the kernel%s)" % ("hi+lo BF16 parts" if args.x_parts == 2 else "one BF16 part",
+                                               "; A as its upper 128 x 128 tiles" if sym else ""),
                 "achieved": tflops if tensor_bound else aw_gbs,
                 "peak": peaks["bf16_tflops"] if tensor_bound else peaks["hbm_gbs"],
                 "unit": "TFLOP/s" if tensor_bound else "GB/s",
@@ -838,7 +849,8 @@ def main():
                 ob = S.snmf_default_options(precision=prec, formulation=form, batch=args.batch,
                                             max_iter=args.max_iter, tol=args.tol, nonmonotone_M=10,
                                             autotune=args.autotune, tune_cache=args.tune_cache, step_controller=mode,
-                                            x_parts=args.x_parts)
+                                            x_parts=args.x_parts,
+                                            sym_half=args.sym_half if args.precision == "bf16" else 0)
                 hb = S.snmf_create(S.dense_matrix(A), args.r, ob, stream=stream,
                                    mlp_weights=weights if mode else None)
                 bt = []
@@ -874,6 +886,8 @@ def main():
                 "config": {"workload": workload_name(args), "n": args.n, "r": args.r, "batch": args.batch,
                            "precision": args.precision, "formulation": args.formulation, "tol": args.tol,
                            "max_iter": args.max_iter, "controller": "learned" if ctl else "plain BB",
+                           "a_storage": "upper 128 x 128 tiles (symmetric half)" if args.sym_half and
+                           args.precision == "bf16" else "full",
                            "l2": ("inputs larger than L2 (A = %.0f MB)" % (a_bytes / 2**20)) if flush is None
                            else "L2 flushed between timed steps (256 MB write)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

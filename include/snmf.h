@@ -165,6 +165,12 @@ typedef struct {
                               is BF16 either way.  No counterpart in the paper.                */
   const char* tune_cache;  /* JSON file of tuned configurations keyed by device name and SM
                               count (read before timing, updated after); NULL: this process only */
+  int32_t sym_half;        /* SNMF_BF16 dense A: 1 = keep only the 128 x 128 tiles of A on and
+                              above the diagonal (A is symmetric, Sec. 1.2; the lower triangle
+                              is not read): about half the bytes of A in HBM and per product.
+                              The tensor-core product reads a tile below the diagonal as the
+                              transpose of its stored mirror.  Default 0.  No counterpart in
+                              the paper.                                                       */
 } snmf_options;
 
 /* Per-solve statistics (best restart = lowest objective). */

@@ -27,7 +27,9 @@ __device__ __forceinline__ double ld_a(const double* p) { return *p; }
 // TA: stored type of A (T, or BF16 read into FP32 registers: the FP32-accumulated product
 // of the stored BF16 operator, used where the tensor-core accumulation is not accurate
 // enough, i.e. the closed-form objective of the final evaluation)
-template <typename T, typename TA = T>
+// SYM: A holds the upper 128 x 128 tiles of the symmetric matrix (sym_tile, lda = tiles a side);
+// entry (r, k) below the diagonal tiles is entry (k, r) of the stored mirror tile.
+template <typename T, typename TA = T, bool SYM = false>
 __global__ void __launch_bounds__(256)
 k_gemm_dense(const TA* __restrict__ A, int64_t lda, const T* __restrict__ X, int64_t ld,
              T* __restrict__ Y, int64_t n, int cols, int64_t kchunk, const int* run) {
@@ -61,7 +63,15 @@ k_gemm_dense(const TA* __restrict__ A, int64_t lda, const T* __restrict__ X, int
     for (int m = 0; m < 4; ++m) {
       int64_t r = row0 + la_r + 16 * m;
       int64_t k = k0 + la_c;
-      ra[m] = (r < n && k < k_end) ? (T)ld_a(A + r * lda + k) : T(0);
+      const TA* pa;
+      if constexpr (SYM) {
+        const int64_t ta = r >> 7, tb = k >> 7;
+        pa = ta <= tb ? A + (sym_tile(ta, tb, lda) << 14) + ((r & 127) << 7) + (k & 127)
+                      : A + (sym_tile(tb, ta, lda) << 14) + ((k & 127) << 7) + (r & 127);
+      } else {
+        pa = A + r * lda + k;
+      }
+      ra[m] = (r < n && k < k_end) ? (T)ld_a(pa) : T(0);
       int c = col0 + lx_c + 16 * m;
       int64_t kr = k0 + lx_r;
       rx[m] = (kr < k_end && c < cols) ? X[kr * ld + c] : T(0);
@@ -233,7 +243,11 @@ int launch_ax(const AxArgs& a, int tdtype, int64_t n, int cols, int64_t ld, cons
     kchunk = (kchunk + BK - 1) / BK * BK;
     dim3 grid(gx, gy, splits);
     void* out = splits > 1 ? ws : Y;
-    if (a.a_dtype == 2)
+    if (a.a_dtype == 2 && a.sym)
+      k_gemm_dense<float, __nv_bfloat16, true><<<grid, 256, 0, s>>>((const __nv_bfloat16*)a.A, a.lda,
+                                                                    (const float*)X, ld, (float*)out, n, cols,
+                                                                    kchunk, run);
+    else if (a.a_dtype == 2)
       k_gemm_dense<float, __nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16*)a.A, a.lda, (const float*)X,
                                                               ld, (float*)out, n, cols, kchunk, run);
     else if (tdtype == 0)

@@ -87,6 +87,19 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
+// shared-memory matrix descriptor: MN-major, 128-byte swizzle.  Each 8-row group along K holds
+// 64 consecutive M elements per 128-byte row (one TMA box of 64 x 64 BF16 lands as 8 such
+// groups, 1024 B apart); the second 64-wide M block is the next box, mn_stride bytes further.
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t mn_stride) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);        // start address
+  d |= (uint64_t)((mn_stride >> 4) & 0x3FFF) << 16;  // leading byte offset: next 64-wide M block
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row K group
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)2 << 61;                          // SWIZZLE_128B
+  return d;
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -134,6 +147,9 @@ struct TcParams {
   long long budget;   // clock64 budget per wait
   const int* run;     // device run flag of a solve (NULL: always run); 0 = stopped, skip the launch
   TcEpilogue e;       // fused epilogue (e.fused = 1)
+  int sym;            // A held as its upper 128 x 128 tiles (sym_tile); mapA then has 64 x 128 boxes
+                      // of a tile's columns, mapAt 64 x 64 boxes of a tile's rows (transposed use)
+  int64_t nt;         // tiles per side of the symmetric storage
 };
 
 // Fused epilogue of one 128 x BN output tile (K slice z), run by 128 threads te = 0 .. 127;
@@ -327,7 +343,7 @@ __device__ __forceinline__ void fused_tile_epilogue(const TcParams& p, float* T,
 
 __global__ void __launch_bounds__(128, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapXh,
-          const __grid_constant__ CUtensorMap mapXl, TcParams p) {
+          const __grid_constant__ CUtensorMap mapXl, const __grid_constant__ CUtensorMap mapAt, TcParams p) {
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte aligned ring: [stage][A 128x64 | Xh BNx64 | Xl BNx64] (bf16)
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -380,7 +396,23 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       unsigned char* st = base + (size_t)s * stage_bytes;
       mbar_expect_tx(&full[s], stage_bytes);
       const int kx = kbase + it * BK;
-      tma_load_2d(st, &mapA, &full[s], kx, m0);
+      if (!p.sym) {
+        tma_load_2d(st, &mapA, &full[s], kx, m0);
+      } else {
+        // K block kx of row block m0 / 128: columns of the stored tile on or above the
+        // diagonal, else rows kx .. kx + 63 of the stored mirror tile, as two 64-column boxes
+        const int64_t i = m0 / BM, kb = kx / 128;
+        const int hh = (kx / BK) & 1;
+        if (kx >= p.n)  // beyond A (a short last slice): a box past the store, zero filled
+          tma_load_2d(st, &mapA, &full[s], 0, (int)(p.nt * (p.nt + 1) / 2 * 128));
+        else if (kb >= i)
+          tma_load_2d(st, &mapA, &full[s], 64 * hh, (int)(sym_tile(i, kb, p.nt) * 128));
+        else {
+          const int y = (int)(sym_tile(kb, i, p.nt) * 128) + 64 * hh;
+          tma_load_2d(st, &mapAt, &full[s], 0, y);
+          tma_load_2d(st + a_bytes / 2, &mapAt, &full[s], 64, y);
+        }
+      }
       tma_load_2d(st + a_bytes, &mapXh, &full[s], kx, n0);
       if (p.xparts == 2) tma_load_2d(st + a_bytes + b_bytes, &mapXl, &full[s], kx, n0);
     }
@@ -396,15 +428,19 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sa = smem_u32(base + (size_t)s * stage_bytes);
       const uint32_t sh = sa + a_bytes, sl = sa + a_bytes + b_bytes;
+      // symmetric storage below the diagonal: A is the transposed mirror tile (MN-major)
+      const int kx = kbase + it * BK;
+      const bool tr = p.sym && kx < p.n && kx / 128 < m0 / BM;
+      const uint32_t id = tr ? (idesc | (1u << 15)) : idesc;  // bit 15: A is MN-major
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint64_t da = sdesc(sa + kk * 32);
+        const uint64_t da = tr ? sdesc_mn(sa + kk * 2048, a_bytes / 2) : sdesc(sa + kk * 32);
         const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
         if (p.comb) {  // B = the 2 BN rows of Xh then Xl (one operand, one read of A)
-          mma_bf16(tmem, da, sdesc(sh + kk * 32), idesc, acc);
+          mma_bf16(tmem, da, sdesc(sh + kk * 32), id, acc);
         } else {
-          mma_bf16(tmem, da, sdesc(sh + kk * 32), idesc, acc);
-          if (p.xparts == 2) mma_bf16(tmem, da, sdesc(sl + kk * 32), idesc, 1u);
+          mma_bf16(tmem, da, sdesc(sh + kk * 32), id, acc);
+          if (p.xparts == 2) mma_bf16(tmem, da, sdesc(sl + kk * 32), id, 1u);
         }
       }
       mma_commit(&empty[s]);
@@ -504,6 +540,60 @@ __global__ void k_to_bf16(const TS* __restrict__ A, int64_t n, int64_t lda, __nv
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / ldk, k = e % ldk;
     A16[e] = __float2bfloat16_rn(k < n ? (float)A[i * lda + k] : 0.0f);
+  }
+}
+
+// A (source type, lda) -> its upper 128 x 128 tiles in BF16, one CTA per tile of the grid
+// (blockIdx.x = column tile b, blockIdx.y = row tile a; a > b does nothing): tile (a, b) at
+// sym_tile(a, b, nt) * 128 * 128, row-major, zero beyond n.  Rounding as k_to_bf16.
+template <typename TS>
+__global__ void k_to_bf16_sym(const TS* __restrict__ A, int64_t n, int64_t lda, __nv_bfloat16* __restrict__ out,
+                              int64_t nt) {
+  const int64_t a = blockIdx.y, b = blockIdx.x;
+  if (a > b) return;
+  __nv_bfloat16* T = out + sym_tile(a, b, nt) * 16384;
+  for (int e = threadIdx.x; e < 16384; e += blockDim.x) {
+    const int64_t i = a * 128 + (e >> 7), k = b * 128 + (e & 127);
+    T[e] = __float2bfloat16_rn(i < n && k < n ? (float)A[i * lda + k] : 0.0f);
+  }
+}
+
+// sum of squares and sum of the symmetric matrix held as its upper tiles: tiles strided over
+// the CTAs, a tile above the diagonal counted twice (FP64 partial per block)
+__global__ void k_sums_bf16_sym(const __nv_bfloat16* __restrict__ A, int64_t nt, double* __restrict__ part) {
+  __shared__ double sh2[32], sh1[32];
+  const int64_t ntiles = nt * (nt + 1) / 2;
+  double s2 = 0.0, s1 = 0.0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // row tile a of tile t: the last a whose diagonal tile index is <= t
+    const double q = 2.0 * (double)nt + 1.0;
+    int64_t a = (int64_t)((q - sqrt(q * q - 8.0 * (double)t)) / 2.0);
+    if (a < 0) a = 0;
+    if (a > nt - 1) a = nt - 1;
+    while (a > 0 && sym_tile(a, a, nt) > t) --a;
+    while (a + 1 < nt && sym_tile(a + 1, a + 1, nt) <= t) ++a;
+    const double w = sym_tile(a, a, nt) == t ? 1.0 : 2.0;
+    double t2 = 0.0, t1 = 0.0;
+    for (int e = threadIdx.x; e < 16384; e += blockDim.x) {
+      const double v = (double)__bfloat162float(A[t * 16384 + e]);
+      t2 += v * v;
+      t1 += v;
+    }
+    s2 += w * t2;
+    s1 += w * t1;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { sh2[wid] = s2; sh1[wid] = s1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a2 = 0.0, a1 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a2 += sh2[w]; a1 += sh1[w]; }
+    part[2 * blockIdx.x] = a2;
+    part[2 * blockIdx.x + 1] = a1;
   }
 }
 
@@ -774,6 +864,23 @@ void launch_to_bf16(int src_dtype, const void* A, int64_t n, int64_t lda, void* 
     k_to_bf16<float><<<blocks, 256, 0, s>>>((const float*)A, n, lda, (__nv_bfloat16*)A16, ldk);
 }
 
+void launch_to_bf16_sym(int src_dtype, const void* A, int64_t n, int64_t lda, void* A16s, cudaStream_t s) {
+  const int64_t nt = (n + 127) / 128;
+  dim3 grid((unsigned)nt, (unsigned)nt);
+  if (src_dtype == 0)
+    k_to_bf16_sym<double><<<grid, 256, 0, s>>>((const double*)A, n, lda, (__nv_bfloat16*)A16s, nt);
+  else
+    k_to_bf16_sym<float><<<grid, 256, 0, s>>>((const float*)A, n, lda, (__nv_bfloat16*)A16s, nt);
+}
+
+int launch_sums_bf16_sym(const void* A16s, int64_t n, double* part, cudaStream_t s) {
+  const int64_t nt = (n + 127) / 128;
+  const int64_t ntiles = nt * (nt + 1) / 2;
+  const int blocks = (int)(ntiles < 1024 ? ntiles : 1024);
+  k_sums_bf16_sym<<<blocks, 256, 0, s>>>((const __nv_bfloat16*)A16s, nt, part);
+  return blocks;
+}
+
 int launch_sums_bf16(const void* A16, int64_t elems, double* part, cudaStream_t s) {
   const int blocks = (int)((elems + 255) / 256 < 1024 ? (elems + 255) / 256 : 1024);
   k_sums_bf16<<<blocks, 256, 0, s>>>((const __nv_bfloat16*)A16, elems, part);
@@ -836,7 +943,7 @@ namespace {
 // Shared launcher of k_gemm_tc: fused epilogue when epi != NULL && epi->fused.
 int launch_tc_impl(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl, int xparts,
                    float* Y, float* ws, size_t ws_elems, int* err, long long budget, const TcEpilogue* epi,
-                   const int* run, cudaStream_t s, const ProdTune* tune) {
+                   const int* run, cudaStream_t s, const ProdTune* tune, int sym) {
   TcPlan pl;
   if (tc_plan(n, N, &pl, tune, xparts) < 0) tc_plan(n, N, &pl, nullptr, xparts);
   const int64_t ldk = tc_ld(n);
@@ -848,10 +955,19 @@ int launch_tc_impl(const void* A16, int64_t n, const float* X, int N, int64_t ld
   dim3 sg((unsigned)((ldk + 31) / 32), (unsigned)((N + 31) / 32));
   k_split_x<<<sg, 256, 0, s>>>(X, n, N, ldx, (__nv_bfloat16*)xh, xparts == 2 ? (__nv_bfloat16*)xl : nullptr,
                                ldk);
-  CUtensorMap ma, mh, ml;
-  if (!make_map(&ma, A16, ldk, n, ldk, BM) || !make_map(&mh, xh, ldk, N, ldk, pl.BN) ||
-      !make_map(&ml, xparts == 2 ? xl : xh, ldk, N, ldk, pl.BN))
+  CUtensorMap ma, mh, ml, mt;
+  const int64_t nt = (n + 127) / 128;
+  if (sym) {
+    // the upper tiles as one (tiles x 128) x 128 array: 64-column boxes of a tile's 128 rows
+    // (K-major use) and 64 x 64 boxes of its rows (the mirror's MN-major use)
+    if (!make_map(&ma, A16, 128, sym_tiles(n) * 128, 128, BM) || !make_map(&mt, A16, 128, sym_tiles(n) * 128, 128, 64))
+      return -1;
+  } else if (!make_map(&ma, A16, ldk, n, ldk, BM)) {
     return -1;
+  }
+  if (!make_map(&mh, xh, ldk, N, ldk, pl.BN) || !make_map(&ml, xparts == 2 ? xl : xh, ldk, N, ldk, pl.BN))
+    return -1;
+  if (!sym) mt = ma;
   static bool attr_done = false;
   if (!attr_done) {
     // the plan never asks for more than ~206 KB; static shared memory comes on top
@@ -878,8 +994,10 @@ int launch_tc_impl(const void* A16, int64_t n, const float* X, int N, int64_t ld
   p.budget = budget;
   p.run = run;
   if (epi && epi->fused) p.e = *epi;
+  p.sym = sym;
+  p.nt = nt;
   dim3 grid(pl.tiles_n, pl.tiles_m, pl.splits);
-  k_gemm_tc<<<grid, 128, pl.smem, s>>>(ma, mh, ml, p);
+  k_gemm_tc<<<grid, 128, pl.smem, s>>>(ma, mh, ml, mt, p);
   const cudaError_t le = cudaPeekAtLastError();
   if (le != cudaSuccess) { g_last_cu = 10000 + (int)le; return -2; }
   return (epi && epi->fused) ? 0 : pl.splits;
@@ -889,15 +1007,16 @@ int launch_tc_impl(const void* A16, int64_t n, const float* X, int N, int64_t ld
 
 int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
                  float* Y, float* ws, size_t ws_elems, int* err, long long budget, cudaStream_t s,
-                 const ProdTune* tune, int xparts) {
+                 const ProdTune* tune, int xparts, int sym) {
   return launch_tc_impl(A16, n, X, N, ldx, xh, xl, xparts, Y, ws, ws_elems, err, budget, nullptr, nullptr, s,
-                        tune);
+                        tune, sym);
 }
 
 int launch_ax_tc_fused(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
                        int xparts, float* ws, size_t ws_elems, int* err, long long budget, const TcEpilogue& epi,
-                       const int* run, cudaStream_t s, const ProdTune* tune) {
-  return launch_tc_impl(A16, n, X, N, ldx, xh, xl, xparts, epi.Y, ws, ws_elems, err, budget, &epi, run, s, tune);
+                       const int* run, cudaStream_t s, const ProdTune* tune, int sym) {
+  return launch_tc_impl(A16, n, X, N, ldx, xh, xl, xparts, epi.Y, ws, ws_elems, err, budget, &epi, run, s, tune,
+                        sym);
 }
 
 int tc_tiles(int64_t n, int N, const ProdTune* tune, int xparts) {

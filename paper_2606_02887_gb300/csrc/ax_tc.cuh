@@ -7,6 +7,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "common.cuh"
 #include "tune.cuh"
 
 namespace snmf {
@@ -48,6 +49,12 @@ int tc_last_status();
 int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune = nullptr, int xparts = 2);
 // FP64 partial sums of squares / sums of a BF16 array into part[2*block]; returns blocks.
 int launch_sums_bf16(const void* A16, int64_t elems, double* part, cudaStream_t s);
+// The same sums over the whole symmetric matrix held as its upper tiles (the tiles above the
+// diagonal count twice); returns blocks.
+int launch_sums_bf16_sym(const void* A16s, int64_t n, double* part, cudaStream_t s);
+// A (n x n, dtype 0 f64 / 1 f32, lda; only the tiles on and above the diagonal are read)
+// -> its upper tiles in BF16 (sym_tiles(n) x 128 x 128)
+void launch_to_bf16_sym(int src_dtype, const void* A, int64_t n, int64_t lda, void* A16s, cudaStream_t s);
 // A (n x n, dtype 0 f64 / 1 f32, lda) -> A16 (n x tc_ld(n) BF16, zero-padded columns)
 void launch_to_bf16(int src_dtype, const void* A, int64_t n, int64_t lda, void* A16, cudaStream_t s);
 // Y = A16 (Xh + Xl) with X (n x N FP32, ld ldx) split into BF16 parts in xh, xl (each
@@ -56,15 +63,15 @@ void launch_to_bf16(int src_dtype, const void* A, int64_t n, int64_t lda, void* 
 // of splits (1 = Y written directly), or -1 when the tensor maps cannot be encoded.
 int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
                  float* Y, float* ws, size_t ws_elems, int* err, long long budget, cudaStream_t s,
-                 const ProdTune* tune = nullptr, int xparts = 2);
+                 const ProdTune* tune = nullptr, int xparts = 2, int sym = 0);
 // The same product with the epilogue fused (see TcEpilogue) and X seen as xparts BF16 parts
 // (2: hi + lo, 1: X rounded to BF16, one MMA pass).  The slices of a split K go to ws.  Returns
 // 0 when the product and epilogue are complete in Y, or < 0 as launch_ax_tc.  xl may be NULL
 // when xparts == 1.  run: a solve's device run flag (NULL: always); when it reads 0 the launch
-// does nothing.
+// does nothing.  sym = 1: A16 holds the upper tiles of A (sym_tile) instead of n x tc_ld(n).
 int launch_ax_tc_fused(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
                        int xparts, float* ws, size_t ws_elems, int* err, long long budget, const TcEpilogue& epi,
-                       const int* run, cudaStream_t s, const ProdTune* tune = nullptr);
+                       const int* run, cudaStream_t s, const ProdTune* tune = nullptr, int sym = 0);
 // Output tiles of the product's plan (counters a fused launch needs).
 int tc_tiles(int64_t n, int N, const ProdTune* tune = nullptr, int xparts = 2);
 

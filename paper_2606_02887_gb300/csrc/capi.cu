@@ -216,7 +216,8 @@ int product_kernel(snmf_ctx* h, const AxArgs& op, const void* X, void* Y, const 
   if (op.kind == AX_DENSE && op.a_dtype == 2 && !op.accurate) {
     if (epi && epi->fused) {
       const int rc = launch_ax_tc_fused(op.A, h->n, (const float*)X, h->N, h->N, h->xh, h->xl, h->xparts,
-                                        (float*)h->ws, h->ws_elems, h->dev_err, h->budget, *epi, run, h->s, tn);
+                                        (float*)h->ws, h->ws_elems, h->dev_err, h->budget, *epi, run, h->s, tn,
+                                        op.sym);
       if (rc < 0) {
         h->tc_fail = tc_last_status();
         return 1;
@@ -224,7 +225,7 @@ int product_kernel(snmf_ctx* h, const AxArgs& op, const void* X, void* Y, const 
       return 0;
     }
     const int sp = launch_ax_tc(op.A, h->n, (const float*)X, h->N, h->N, h->xh, h->xl, (float*)Y,
-                                (float*)h->ws, h->ws_elems, h->dev_err, h->budget, h->s, tn, h->xparts);
+                                (float*)h->ws, h->ws_elems, h->dev_err, h->budget, h->s, tn, h->xparts, op.sym);
     if (sp < 1) {
       h->tc_fail = tc_last_status();
       return 1;
@@ -374,6 +375,7 @@ snmf_status autotune_product(snmf_ctx* h) {
   if (h->kind != AX_DENSE) return SNMF_OK;
   static const char* dtn[4] = {"f64", "f32", "bf16", "fp8"};
   const std::string key = std::string("dense/") + dtn[h->A.a_dtype] + (h->A.a_dtype == 2 && h->xparts == 1 ? "x1" : "") +
+                          (h->A.sym ? "s" : "") +
                           "/n" + std::to_string(h->n) + "/r" + std::to_string(h->r) + "/N" + std::to_string(h->N);
   const std::string dev = tune_device_key();
   TuneEntry e;
@@ -859,7 +861,8 @@ snmf_status validate_options(const snmf_options& o) {
       !(o.alpha_min > 0.0 && o.alpha_min < o.alpha_max) || !(o.beta_shrink > 0.0 && o.beta_shrink < 1.0) ||
       !(o.tol >= 0.0) || !(o.direct_rho_factor > 0.0))
     return SNMF_ERR_ARG;
-  if (!valid_enum(o.step_controller, 0, 3) || !valid_enum(o.x_parts, 0, 2)) return SNMF_ERR_ARG;
+  if (!valid_enum(o.step_controller, 0, 3) || !valid_enum(o.x_parts, 0, 2) || !valid_enum(o.sym_half, 0, 1))
+    return SNMF_ERR_ARG;
   if ((o.step_controller == 1 || o.step_controller == 3) && !o.mlp_weights) return SNMF_ERR_ARG;
   return SNMF_OK;
 }
@@ -903,6 +906,7 @@ void snmf_default_options(snmf_options* o) {
   o->autotune = 0;
   o->x_parts = 0;
   o->tune_cache = nullptr;
+  o->sym_half = 0;
 }
 
 snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const snmf_options* opt,
@@ -947,6 +951,8 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
     if (o.precision == SNMF_BF16 || o.precision == SNMF_FP8)
       return fail(nullptr, SNMF_ERR_ARG, "CSR supports F64/F32 precision");
   }
+  if (o.sym_half && (Am->kind != SNMF_DENSE || o.precision != SNMF_BF16))
+    return fail(nullptr, SNMF_ERR_ARG, "symmetric-half storage needs a dense A in SNMF_BF16 precision");
   if (o.step_controller && (o.formulation != SNMF_PENALTY || r > 64))
     return fail(nullptr, SNMF_ERR_ARG, "the step controller needs the penalty form and r <= 64");
   if (o.formulation == SNMF_NAIVE && o.step_controller)
@@ -1028,15 +1034,22 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
       src = staging;
     }
     const int64_t ldk = tc_ld(n);
-    CKC(cudaMalloc(&h->A_owned, (size_t)n * ldk * 2));
-    launch_to_bf16(src_dt, src, n, Am->ld, h->A_owned, h->s);
+    if (o.sym_half) {
+      // the upper 128 x 128 tiles only (A symmetric): lda = tiles a side
+      CKC(cudaMalloc(&h->A_owned, (size_t)sym_tiles(n) * 128 * 128 * 2));
+      launch_to_bf16_sym(src_dt, src, n, Am->ld, h->A_owned, h->s);
+    } else {
+      CKC(cudaMalloc(&h->A_owned, (size_t)n * ldk * 2));
+      launch_to_bf16(src_dt, src, n, Am->ld, h->A_owned, h->s);
+    }
     if (staging) {
       CKC(cudaStreamSynchronize(h->s));
       cudaFree(staging);
     }
     h->A.A = h->A_owned;
-    h->A.lda = ldk;
+    h->A.lda = o.sym_half ? (n + 127) / 128 : ldk;
     h->A.a_dtype = 2;
+    h->A.sym = o.sym_half;
     h->A.kind = AX_DENSE;
   } else if (h->kind == AX_DENSE) {
     // working copy of A in the factor type unless it can be borrowed
@@ -1129,7 +1142,8 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
     const int nb = launch_fp8_sums(h->A.A, n, h->A.a_scale, h->dsc + 16, h->s);  // ||A~||^2 of the stored values
     launch_sum_pairs(h->dsc + 16, nb, h->dsc, h->s);
   } else if (h->kind == AX_DENSE && h->A.a_dtype == 2) {
-    const int nb = launch_sums_bf16(h->A.A, n * h->A.lda, h->dsc + 16, h->s);  // ||A~||^2 of the stored values
+    const int nb = h->A.sym ? launch_sums_bf16_sym(h->A.A, n, h->dsc + 16, h->s)
+                            : launch_sums_bf16(h->A.A, n * h->A.lda, h->dsc + 16, h->s);  // ||A~||^2 of the stored values
     launch_sum_pairs(h->dsc + 16, nb, h->dsc, h->s);
   } else if (h->kind == AX_DENSE)
     launch_matrix_sums(AX_DENSE, h->tdtype, h->A.A, n, h->A.lda, 0, h->dsc + 16, h->dsc, h->s);

@@ -152,6 +152,19 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // Product kinds of the A*X operator
 enum AxKind { AX_DENSE = 0, AX_CSR = 1 };
 
+// Symmetric-half storage of a dense BF16 A (Sec. 1.2: A is symmetric): only the 128 x 128
+// tiles (a, b) with a <= b of the tile grid (nt = ceil(n / 128) tiles a side) are stored, each
+// tile row-major with a pitch of 128 elements and zero beyond n, tile (a, b) at element offset
+// sym_tile(a, b, nt) * 128 * 128 (the upper tile rows one after another).  A_ij for a tile
+// below the diagonal is the transpose of the stored tile (b, a).
+__host__ __device__ inline int64_t sym_tile(int64_t a, int64_t b, int64_t nt) {
+  return a * (2 * nt - a + 1) / 2 + (b - a);
+}
+__host__ __device__ inline int64_t sym_tiles(int64_t n) {
+  const int64_t nt = (n + 127) / 128;
+  return nt * (nt + 1) / 2;
+}
+
 struct AxArgs {
   // dense
   const void* A; int64_t lda; int a_dtype;  // a_dtype: 0 f64, 1 f32, 2 bf16, 3 fp8(e4m3) + scales
@@ -160,6 +173,7 @@ struct AxArgs {
   const int32_t* rowptr; const int32_t* colidx; const void* vals; int v_dtype;
   int kind;
   int accurate;  // BF16 dense: FP32 CUDA-core accumulation instead of the tensor-core product
+  int sym;       // BF16 dense: A holds the upper tiles of the symmetric matrix (sym_tile)
 };
 
 // Y = A X (raw product, T = double/float), n x cols, ld = leading dimension of X and Y.

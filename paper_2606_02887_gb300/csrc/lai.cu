@@ -420,7 +420,7 @@ static int sketch_product(const AxArgs& A, int td, int64_t n, int cols, const vo
   int splits;
   if (A.kind == AX_DENSE && A.a_dtype == 2) {
     splits = launch_ax_tc(A.A, n, (const float*)X, cols, cols, xh, xl, (float*)Y, (float*)ws, ws_elems, err,
-                          2000000000LL, s);
+                          2000000000LL, s, nullptr, 2, A.sym);
     if (splits < 1) return -1;
   } else {
     splits = launch_ax(A, td, n, cols, cols, X, Y, ws, ws_elems, nullptr, s);

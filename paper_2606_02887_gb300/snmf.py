@@ -56,7 +56,8 @@ class snmf_options(C.Structure):
                 ("alpha_max", C.c_double), ("beta_shrink", C.c_double), ("tol", C.c_double),
                 ("direct_rho_factor", C.c_double), ("init_scale", C.c_double), ("seed", C.c_uint64),
                 ("mlp_weights", C.c_void_p), ("timeout_cycles", C.c_int64),
-                ("autotune", C.c_int32), ("x_parts", C.c_int32), ("tune_cache", C.c_char_p)]
+                ("autotune", C.c_int32), ("x_parts", C.c_int32), ("tune_cache", C.c_char_p),
+                ("sym_half", C.c_int32)]
 
 
 class snmf_stats(C.Structure):

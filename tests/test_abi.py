@@ -36,12 +36,13 @@ def test_struct_layouts_match_header(lib):
     # sizes fixed by the header's field order (LP64)
     assert C.sizeof(S.snmf_matrix) == 4 * 4 + 3 * 8 + 3 * 8 + 2 * 4 + 8
     assert C.sizeof(S.snmf_stats) == 6 * 4 + 4 * 8 + 8 + 4 * 4
-    assert C.sizeof(S.snmf_options) == 10 * 4 + 10 * 8 + 8 + 8 + 8 + 2 * 4 + 8
+    # ... tune_cache, then sym_half and the tail padding to 8 bytes
+    assert C.sizeof(S.snmf_options) == 10 * 4 + 10 * 8 + 8 + 8 + 8 + 2 * 4 + 8 + 4 + 4
 
 
 def test_default_options(lib):
     o = S.snmf_default_options()
-    assert o.formulation == S.SNMF_PENALTY and o.precision == S.SNMF_F32
+    assert o.formulation == S.SNMF_PENALTY and o.precision == S.SNMF_F32 and o.sym_half == 0
     assert o.batch == 1 and o.nonmonotone_M == 10 and o.max_ls == 20 and o.inner_iters == 5
     assert o.theta == 1e-3 and o.phi == 1.7 and o.tol == 1e-4 and o.lambda_sym < 0
     assert o.alpha_min == 1e-10 and o.alpha_max == 1e10 and o.direct_rho_factor == 3.0
