@@ -136,10 +136,22 @@ typedef struct {
                               the unchanged nonmonotone acceptance test).
                               2: record mode: the plain BB trajectory, and at every step the
                               features phi and the best of 9 multipliers 2^(-2..2 by 1/2) are
-                              recorded (snmf_controller_data).  1, 2 and 3 need the penalty form
-                              and r <= 64.  Features phi: ln(BB1 rho), ln(BB2 rho), ratio of
-                              successive projected-gradient norms, ratio of successive objective
-                              decreases, fraction of zero entries.                               */
+                              recorded (snmf_controller_data).
+                              4: rollout branch (training data for labels scored by a short
+                              rollout): batch must be a multiple of 9; restart j belongs to group
+                              j / 9 and takes candidate c = j % 9.  Every restart follows the
+                              plain BB step, except at the inner step whose index is branch_step
+                              (counted over the whole solve: outer iteration t, block h (0 W,
+                              1 H), step k of the block -> 2 t inner_iters + h inner_iters + k),
+                              where its next step is 2^((c - 4) / 2) times the BB step.  At
+                              that step the restart with c = 4 records its features phi, with
+                              the group index as the target, for snmf_controller_data.  Give
+                              the restarts of a group the same start: they then agree up to the
+                              branch, and the factors at the end of the solve score the nine
+                              multipliers.  1, 2, 3 and 4 need the penalty form and r <= 64.
+                              Features phi: ln(BB1 rho), ln(BB2 rho), ratio of successive
+                              projected-gradient norms, ratio of successive objective decreases,
+                              fraction of zero entries.                                        */
   double lambda_sym;       /* penalty weight lambda (Eq. (3)); < 0 -> 0.01 ||A||_F (Sec. 4.1 (1)) */
   double theta;            /* Armijo parameter, default 1e-3 (Sec. 2.4)                        */
   double phi;              /* relaxation factor, default 1.7 (Sec. 2.4)                        */
@@ -171,6 +183,8 @@ typedef struct {
                               The tensor-core product reads a tile below the diagonal as the
                               transpose of its stored mirror.  Default 0.  No counterpart in
                               the paper.                                                       */
+  int32_t branch_step;     /* step_controller 4: index of the inner step that takes the nine
+                              multipliers (see step_controller); < 0: none.  Default -1.       */
 } snmf_options;
 
 /* Per-solve statistics (best restart = lowest objective). */
@@ -424,9 +438,10 @@ SNMF_API snmf_status snmf_apply_dense_noalloc(const void* A, int dtype, int64_t 
                                               void* stream);
 
 /*
- * Record-mode data (step_controller == 2; not in the paper: training data of the learned
+ * Record-mode data (step_controller == 2 or 4; not in the paper: training data of the learned
  * step controller).  Copies up to `capacity` recorded samples (features feat[i][5] and target
- * log2 multipliers targ[i], host arrays) gathered since the last call, then clears the record.
+ * log2 multipliers targ[i] in mode 2, the restart group j / 9 in mode 4; host arrays) gathered
+ * since the last call, then clears the record.
  * *count receives the number copied.  SNMF_ERR_STATE when the handle is not in record mode.
  */
 SNMF_API snmf_status snmf_controller_data(snmf_handle h, float* feat, float* targ, int capacity,

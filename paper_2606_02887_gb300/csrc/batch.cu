@@ -722,7 +722,10 @@ snmf_status batch_validate(const snmf_matrix* Am, const snmf_options& o, std::st
   if (o.formulation != SNMF_PENALTY) { *err = "dense batch: penalty form only"; return SNMF_ERR_ARG; }
   if (o.batch != 1) { *err = "dense batch: batch (restarts) must be 1"; return SNMF_ERR_ARG; }
   if (o.precision == SNMF_FP8) { *err = "dense batch: FP8 not available"; return SNMF_ERR_ARG; }
-  if (o.step_controller == 2) { *err = "dense batch: record mode needs a single-problem handle"; return SNMF_ERR_ARG; }
+  if (o.step_controller == 2 || o.step_controller == 4) {
+    *err = "dense batch: record and rollout modes need a single-problem handle";
+    return SNMF_ERR_ARG;
+  }
   if (o.precision == SNMF_F64 && Am->dtype != SNMF_F64) { *err = "dense batch: F64 precision needs F64 values"; return SNMF_ERR_ARG; }
   if (Am->dtype != SNMF_F64 && Am->dtype != SNMF_F32) { *err = "dense batch: values must be F64 or F32"; return SNMF_ERR_ARG; }
   if (Am->location != SNMF_ON_DEVICE && Am->location != SNMF_ON_HOST) { *err = "bad location"; return SNMF_ERR_ARG; }

@@ -159,13 +159,15 @@ Params make_params(const snmf_ctx* h) {
   P.normA2 = h->lai ? h->lai_op.normA2 : h->normA2;
   P.gamma = h->graph ? h->gamma : 0.0;
   P.mlp_w = h->mlp_w;
-  P.rec_feat = h->opt.step_controller == 2 ? h->rec_feat : nullptr;
+  P.rec_feat = (h->opt.step_controller == 2 || h->opt.step_controller == 4) ? h->rec_feat : nullptr;
   P.rec_targ = h->rec_targ;
   P.rec_count = h->rec_count;
   P.rec_cap = h->rec_cap;
   P.nr = h->n * (int64_t)h->r;
   P.ring = h->ring;
   P.ring_cap = h->ring_cap;
+  P.inner = h->opt.inner_iters;
+  P.branch_step = h->opt.branch_step;
   return P;
 }
 
@@ -861,9 +863,10 @@ snmf_status validate_options(const snmf_options& o) {
       !(o.alpha_min > 0.0 && o.alpha_min < o.alpha_max) || !(o.beta_shrink > 0.0 && o.beta_shrink < 1.0) ||
       !(o.tol >= 0.0) || !(o.direct_rho_factor > 0.0))
     return SNMF_ERR_ARG;
-  if (!valid_enum(o.step_controller, 0, 3) || !valid_enum(o.x_parts, 0, 2) || !valid_enum(o.sym_half, 0, 1))
+  if (!valid_enum(o.step_controller, 0, 4) || !valid_enum(o.x_parts, 0, 2) || !valid_enum(o.sym_half, 0, 1))
     return SNMF_ERR_ARG;
   if ((o.step_controller == 1 || o.step_controller == 3) && !o.mlp_weights) return SNMF_ERR_ARG;
+  if (o.step_controller == 4 && o.batch % kNCand != 0) return SNMF_ERR_ARG;
   return SNMF_OK;
 }
 
@@ -898,6 +901,7 @@ void snmf_default_options(snmf_options* o) {
   o->alpha_max = 1e10;
   o->beta_shrink = 0.5;
   o->tol = 1e-4;
+  o->branch_step = -1;
   o->direct_rho_factor = 3.0;
   o->init_scale = 2.0;
   o->seed = 0;
@@ -1130,8 +1134,8 @@ snmf_status snmf_create(snmf_handle* out, const snmf_matrix* Am, int r, const sn
     CKC(cudaMemcpyAsync(h->mlp_w, wb.data(), kMlpParams * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, h->s));
     CKC(cudaStreamSynchronize(h->s));
   }
-  if (o.step_controller == 2) {
-    h->rec_cap = 1 << 18;
+  if (o.step_controller == 2 || o.step_controller == 4) {
+    h->rec_cap = o.step_controller == 2 ? 1 << 18 : o.batch / kNCand;
     CKC(cudaMalloc(&h->rec_feat, (size_t)h->rec_cap * kMlpIn * sizeof(float)));
     CKC(cudaMalloc(&h->rec_targ, (size_t)h->rec_cap * sizeof(float)));
     CKC(cudaMalloc(&h->rec_count, sizeof(int)));
@@ -1777,7 +1781,8 @@ snmf_status snmf_set_timeout(snmf_handle h, int64_t cycles) {
 snmf_status snmf_controller_data(snmf_handle h, float* feat, float* targ, int capacity, int32_t* count) {
   if (!h) return SNMF_ERR_STATE;
   if (h->bt) return fail(h, SNMF_ERR_STATE, "not available for a dense batch handle");
-  if (h->opt.step_controller != 2) return fail(h, SNMF_ERR_STATE, "the handle is not in record mode");
+  if (h->opt.step_controller != 2 && h->opt.step_controller != 4)
+    return fail(h, SNMF_ERR_STATE, "the handle is not in record mode");
   if (capacity < 0 || (capacity > 0 && (!feat || !targ))) return fail(h, SNMF_ERR_ARG, "bad buffers");
   int cnt = 0;
   CK(cudaMemcpyAsync(&cnt, h->rec_count, sizeof(int), cudaMemcpyDeviceToHost, h->s));

@@ -83,7 +83,7 @@ struct Params {
   int max_ls;
   int max_iter;
   int power_iters;
-  int controller;    // learned step controller on/off
+  int controller;    // step controller: 0 plain BB, 1/3 learned, 2 record, 4 rollout branch
   double theta, phi, eta, alpha_min, alpha_max, beta_shrink, tol;
   double rho_factor; // direct form rho scaling
   double normA2;     // ||A||_F^2 of the stored operator
@@ -96,6 +96,8 @@ struct Params {
   int64_t nr;        // entries per restart (n * r), for the active-set feature
   double* ring;      // per-iteration statistics: ring[j][slot][kRingVals] (NULL: off)
   int ring_cap;      // slots per restart
+  int inner;         // inner steps per block (penalty form)
+  int branch_step;   // controller 4: inner step, counted over the solve, that takes the 9 multipliers
 };
 
 // Values of one statistics record (penalty and naive forms: written at the start of every W block,

@@ -376,7 +376,10 @@ __device__ void pen_upd_body(Ctl& c, const double* prow, int nrow, int b, int j,
     phi[4] = (float)zeros / (float)P.nr;
     const double pg = (double)pgf;
     float mult = 1.f;
-    if (nc == 2 || nc == 3) mult = mlp_multiplier(P.mlp_w, phi);  // all lanes
+    // rollout branch (controller 4): this step's index counted over the whole solve
+    const bool branch = P.controller == 4 &&
+                        (int64_t)c.iters * 2 * P.inner + (int64_t)is_h_block * P.inner + c.k == P.branch_step;
+    if ((nc == 2 || nc == 3) && P.controller != 4) mult = mlp_multiplier(P.mlp_w, phi);  // all lanes
     if ((threadIdx.x & 31) == 0) {
       for (int u = 0; u < kMlpIn; ++u) c.feat[u] = phi[u];
       c.feat_ok = 1;
@@ -386,6 +389,20 @@ __device__ void pen_upd_body(Ctl& c, const double* prow, int nrow, int b, int j,
         c.mlp_mult = mult;
         c.cand_alpha[0] = fmin(P.alpha_max, fmax(P.alpha_min, (double)mult * alpha_bb));
         c.cand_alpha[1] = alpha_bb;
+      } else if (nc == 3 && P.controller == 4) {
+        // rollout branch: candidate j % 9 scales the next step by 2^((c - 4) / 2); the group's
+        // plain candidate records the features of the branch point, tagged with the group
+        if (branch) {
+          const int cand = j % kNCand;
+          alpha_bb = fmin(P.alpha_max, fmax(P.alpha_min, exp2(0.5 * (cand - 4)) * alpha_bb));
+          if (cand == 4 && P.rec_feat) {
+            const int idx = atomicAdd(P.rec_count, 1);
+            if (idx < P.rec_cap) {
+              for (int u = 0; u < kMlpIn; ++u) P.rec_feat[(int64_t)idx * kMlpIn + u] = phi[u];
+              P.rec_targ[idx] = (float)(j / kNCand);
+            }
+          }
+        }
       } else if (nc == 3) {  // lean learned step: the next D uses the proposal directly
         c.mlp_mult = mult;
         alpha_bb = fmin(P.alpha_max, fmax(P.alpha_min, (double)mult * alpha_bb));
@@ -438,7 +455,7 @@ __device__ void final_pen_body(Ctl& c, const double* pax, int nax, const double*
 __device__ void fused_control(int mode, Ctl& c, const double* part, int nslots, int b, int r, int j,
                               const Params& P, const double* G64fix, double* sh, int nc) {
   // candidates of the solve (3: the lean learned step, one candidate)
-  const int pc = P.controller == 1 ? 2 : (P.controller == 2 ? kNCand : (P.controller == 3 ? 3 : 1));
+  const int pc = P.controller == 1 ? 2 : (P.controller == 2 ? kNCand : (P.controller >= 3 ? 3 : 1));
   switch (mode) {
     case CTL_START_W: pen_start_body(c, part, nslots, b, j, P, 1, 0, sh); break;
     case CTL_START_H: pen_start_body(c, part, nslots, b, j, P, 0, 0, sh); break;

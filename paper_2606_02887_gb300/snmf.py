@@ -57,7 +57,7 @@ class snmf_options(C.Structure):
                 ("direct_rho_factor", C.c_double), ("init_scale", C.c_double), ("seed", C.c_uint64),
                 ("mlp_weights", C.c_void_p), ("timeout_cycles", C.c_int64),
                 ("autotune", C.c_int32), ("x_parts", C.c_int32), ("tune_cache", C.c_char_p),
-                ("sym_half", C.c_int32)]
+                ("sym_half", C.c_int32), ("branch_step", C.c_int32)]
 
 
 class snmf_stats(C.Structure):

@@ -36,12 +36,13 @@ def test_struct_layouts_match_header(lib):
     # sizes fixed by the header's field order (LP64)
     assert C.sizeof(S.snmf_matrix) == 4 * 4 + 3 * 8 + 3 * 8 + 2 * 4 + 8
     assert C.sizeof(S.snmf_stats) == 6 * 4 + 4 * 8 + 8 + 4 * 4
-    # ... tune_cache, then sym_half and the tail padding to 8 bytes
+    # ... tune_cache, then sym_half and branch_step
     assert C.sizeof(S.snmf_options) == 10 * 4 + 10 * 8 + 8 + 8 + 8 + 2 * 4 + 8 + 4 + 4
 
 
 def test_default_options(lib):
     o = S.snmf_default_options()
+    assert o.branch_step == -1 and o.step_controller == 0
     assert o.formulation == S.SNMF_PENALTY and o.precision == S.SNMF_F32 and o.sym_half == 0
     assert o.batch == 1 and o.nonmonotone_M == 10 and o.max_ls == 20 and o.inner_iters == 5
     assert o.theta == 1e-3 and o.phi == 1.7 and o.tol == 1e-4 and o.lambda_sym < 0
@@ -69,6 +70,10 @@ def test_invalid_arguments_rejected_before_launch(lib):
     bad = S.snmf_default_options(theta=1.5)
     assert _create(lib, m, 2, bad)[0] == S.SNMF_ERR_ARG
     bad = S.snmf_default_options(nonmonotone_M=65)
+    assert _create(lib, m, 2, bad)[0] == S.SNMF_ERR_ARG
+    bad = S.snmf_default_options(step_controller=4, batch=8)     # rollout groups of 9 restarts
+    assert _create(lib, m, 2, bad)[0] == S.SNMF_ERR_ARG
+    bad = S.snmf_default_options(step_controller=5)
     assert _create(lib, m, 2, bad)[0] == S.SNMF_ERR_ARG
     m2, _ = S.dense_matrix(A)
     m2.ld = 4                                                    # ld < n
@@ -120,3 +125,14 @@ def test_noalloc_limits_follow_the_header(lib, repo_root):
     if torch.cuda.is_available():
         pytest.skip("a GPU is present: placeholder pointers must not reach a launch")
     assert f(fake, S.SNMF_F32, n_max, n_max, fake, fake, 1, C.byref(out), None) == S.SNMF_ERR_CUDA
+
+
+def test_rollout_labels_pick_the_lowest_objective_and_break_ties_to_one():
+    from paper_2606_02887_gb300.train_controller import rollout_labels
+    f = np.array([[5.0, 4.0, 3.0, 2.5, 2.0, 2.2, 1.0, 3.0, 9.0],    # candidate 6: multiplier 2
+                  [1.0] * 9,                                          # all equal: plain step
+                  [2.0, 2.0, 2.0, 2.0, 1.0, 1.0 - 1e-15, 2, 2, 2],  # within the tie margin
+                  [0.5, 1, 1, 1, 1, 1, 1, 1, 1],                      # multiplier 1/4
+                  [np.nan, 1, 1, 1, 1, 1, 1, 1, 1]])                  # non-finite: dropped
+    lab = rollout_labels(f)
+    assert lab[:4].tolist() == [1.0, 0.0, 0.0, -2.0] and np.isnan(lab[4])

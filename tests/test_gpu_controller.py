@@ -79,12 +79,65 @@ def test_record_mode_produces_labelled_states():
     assert np.all((f[:, 4] >= 0) & (f[:, 4] <= 1))
 
 
+def test_rollout_branch_mode():
+    """Controller 4: the restarts of a group share a start and agree up to the branch step;
+    there, candidate c scales the step by 2^((c - 4) / 2).  Candidate 4 (multiplier 1) is the
+    plain BB trajectory bit for bit, the other candidates leave it, a branch step past the end
+    of the solve changes nothing, and each group records one feature vector at the branch."""
+    import torch
+    dev = torch.device("cuda:0")
+    n, r, m = 300, 6, 2
+    A, _ = planted_dense(n, r, seed=821, rel_noise=0.01)
+    starts = [uniform_init(n, r, math.sqrt(A.mean() / r), 822 + q) for q in range(m)]
+    W0 = np.concatenate([starts[q] for q in range(m) for _ in range(9)], 1)
+    At = torch.tensor(A, dtype=torch.float32, device=dev)
+
+    def run(controller, branch, max_iter):
+        o = S.snmf_default_options(precision=S.SNMF_F32, batch=9 * m, step_controller=controller,
+                                   branch_step=branch, max_iter=max_iter, tol=0.0, nonmonotone_M=10)
+        h = S.snmf_create(S.dense_matrix(At), r, o)
+        try:
+            Wt = torch.tensor(W0, dtype=torch.float32, device=dev)
+            Ht = Wt.clone()
+            S.snmf_solve(h, Wt, Ht)
+            f, grp = S.snmf_controller_data(h, capacity=4 * m) if controller == 4 else (None, None)
+            fin = S.snmf_restart_stats(h, 9 * m)["f"]
+        finally:
+            S.snmf_destroy(h)
+        return Wt.cpu().numpy(), Ht.cpu().numpy(), f, grp, fin
+
+    K = 5
+    t, blk, k = 2, 1, 1
+    branch = 2 * t * K + blk * K + k
+    Wp, Hp, _, _, fp = run(0, -1, t + 2)
+    Wb, Hb, f, grp, fb = run(4, branch, t + 2)
+    Wn, Hn, fn, _, _ = run(4, 2 * (t + 2) * K, t + 2)        # branch after the last step
+    assert np.array_equal(Wn, Wp) and np.array_equal(Hn, Hp) and len(fn) == 0
+    cols = lambda j: slice(j * r, (j + 1) * r)
+    for q in range(m):
+        j4 = 9 * q + 4
+        assert np.array_equal(Wb[:, cols(j4)], Wp[:, cols(j4)]) and np.array_equal(Hb[:, cols(j4)], Hp[:, cols(j4)])
+        for c in range(9):
+            j = 9 * q + c
+            assert rel(Wp[:, cols(j)], Wp[:, cols(j4)]) <= 1e-5   # one start per group
+            if c % 2 == 1:  # 2^(+-1/2), 2^(+-3/2): no backtracking of the plain step gives these
+                assert not np.array_equal(Wb[:, cols(j)], Wp[:, cols(j)]), (q, c)
+    assert sorted(grp.astype(int).tolist()) == list(range(m))
+    assert np.all(np.isfinite(f)) and np.all((f[:, 4] >= 0) & (f[:, 4] <= 1))
+    from paper_2606_02887_gb300.train_controller import rollout_labels
+    lab = rollout_labels(fb.reshape(m, 9))
+    assert np.all(np.isfinite(lab)) and set(lab.tolist()) <= set(np.arange(-2, 2.01, 0.5))
+
+
 @pytest.mark.parametrize("mode", [1, 3])
 def test_learned_controller_gain_over_plain_bb(mode):
     """Held-out planted problems (seeds disjoint from the training set), batched restarts:
     with the trained controller every restart must still reach the tolerance, the best
-    restart's residual must be within 1e-3 of the plain method's, and the test reports the
-    gain in outer iterations and device time over the plain BB step."""
+    restart's residual must be within 1e-3 of the plain method's, and the outer iterations
+    summed over the set must stay within 5% of the plain BB step's (controllers trained on
+    other label sets took 60% to 4.7x more).  The test reports the change in outer iterations
+    and device time; the network's inference makes a step slower, so equal iterations cost
+    more device time than plain BB."""
     from paper_2606_02887_gb300.train_controller import WEIGHTS_PATH, load_weights
     if not os.path.exists(WEIGHTS_PATH):
         pytest.skip("no trained controller weights")
@@ -108,3 +161,4 @@ def test_learned_controller_gain_over_plain_bb(mode):
         t_learn += sl["seconds"]
     print(f"learned controller (mode {mode}): outer iterations {it_learn:.0f} vs plain {it_plain:.0f} "
           f"({100 * (1 - it_learn / it_plain):+.1f}%), device time {t_learn:.3f} s vs {t_plain:.3f} s")
+    assert it_learn <= 1.05 * it_plain, (it_learn, it_plain)
