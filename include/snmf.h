@@ -116,7 +116,10 @@ typedef struct {
                               objective, line search and BB inner products are FP64 throughout.
                               SNMF_FP8 (dense only): E4M3 codes of A / s_t with a power-of-two
                               scale s_t per 128 x 128 tile (the smallest 2^k with
-                              max|A_t| / 2^k <= 448), round to nearest even, saturating   */
+                              max|A_t| / 2^k <= 448), round to nearest even, saturating; the
+                              iteration's products decode the codes to BF16 (exactly) and run
+                              on the tensor cores like SNMF_BF16 (X as BF16 hi + lo parts),
+                              the final evaluation on CUDA cores with FP32 X               */
   int32_t batch;           /* b random restarts sharing A (columns r*b), default 1            */
   int32_t nonmonotone_M;   /* 0: eta averaging of Alg. 1 line 4; M > 0: max of the last M
                               objective values (M <= 64).  Default 10                          */

@@ -12,16 +12,25 @@
 //                   accumulator, tcgen05.commit frees the stage
 //   warps 0-3     : epilogue: tcgen05.ld 32 rows each, store FP32 rows (split-K slice or Y)
 //
+// E4M3 A (k_gemm_tc<true>): TMA stages the 128 x 64 code tile unswizzled beside the ring
+// stage; warps 2-3 decode it, times the power-of-two scale of its 128 x 128 tile of A, into
+// the stage's BF16 A tile in the layout the 128-byte swizzle gives (the decode is exact: an
+// E4M3 value times 2^k has at most 4 significant bits), and the MMA issuer waits for that
+// conversion as well as for the TMA bytes.  The MMAs and the epilogue are the BF16 kernel's.
+//
 // Every mbarrier wait is bounded by a clock64 budget; on expiry the kernel records an
 // error code, stops issuing, releases its TMEM and returns (no unbounded spin).
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
 
 #include "ax_tc.cuh"
 #include "common.cuh"
+#include "fp8.cuh"
 
 namespace snmf {
 
@@ -46,6 +55,18 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// two E4M3 codes (low byte first) -> two BF16 values times s (a power of two), packed low first
+__device__ __forceinline__ uint32_t e4m3x2_to_bf16x2(uint32_t codes, float s) {
+  const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(codes & 0xFFFFu), __NV_E4M3);
+  const float2 f = __half22float2(__half2(hr));
+  const __nv_bfloat162 b = __floats2bfloat162_rn(f.x * s, f.y * s);
+  return *reinterpret_cast<const uint32_t*>(&b);
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -150,6 +171,8 @@ struct TcParams {
   int sym;            // A held as its upper 128 x 128 tiles (sym_tile); mapA then has 64 x 128 boxes
                       // of a tile's columns, mapAt 64 x 64 boxes of a tile's rows (transposed use)
   int64_t nt;         // tiles per side of the symmetric storage
+  const float* scales;  // E4M3 A: power-of-two scale per 128 x 128 tile, [nt8][nt8] row-major
+  int nt8;              // E4M3 A: 128-wide tiles per side
 };
 
 // Fused epilogue of one 128 x BN output tile (K slice z), run by 128 threads te = 0 .. 127;
@@ -341,21 +364,24 @@ __device__ __forceinline__ void fused_tile_epilogue(const TcParams& p, float* T,
   }
 }
 
+template <bool FP8>
 __global__ void __launch_bounds__(128, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapXh,
           const __grid_constant__ CUtensorMap mapXl, const __grid_constant__ CUtensorMap mapAt, TcParams p) {
   extern __shared__ unsigned char smem_raw[];
-  // 1024-byte aligned ring: [stage][A 128x64 | Xh BNx64 | Xl BNx64] (bf16)
+  // 1024-byte aligned ring: [stage][A 128x64 | Xh BNx64 | Xl BNx64] (bf16) [| A codes 128x64 (E4M3)]
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int BN = p.BN;
   const uint32_t a_bytes = BM * BK * 2;
   const uint32_t b_bytes = (uint32_t)BN * BK * 2;
-  const uint32_t stage_bytes = a_bytes + (uint32_t)p.xparts * b_bytes;
+  constexpr uint32_t a8_bytes = FP8 ? BM * BK : 0;  // E4M3 codes of the A tile, staged by TMA
+  const uint32_t stage_bytes = a_bytes + (uint32_t)p.xparts * b_bytes + a8_bytes;
   uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)p.stages * stage_bytes);
   uint64_t* empty = full + p.stages;
   uint64_t* accum = empty + p.stages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* conv = accum + 2;  // E4M3 A: the stage's BF16 A tile is written (64 decoder threads)
   __shared__ int s_fail, s_issued, s_consumed;
   __shared__ unsigned s_ticket;
 
@@ -372,6 +398,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     for (int s = 0; s < p.stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      if (FP8) mbar_init(&conv[s], 64);
     }
     mbar_init(accum, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -394,11 +421,16 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
       if (!mbar_wait(&empty[s], ph ^ 1u, p.budget)) { atomicExch(p.err, 1); s_fail = 1; break; }
       unsigned char* st = base + (size_t)s * stage_bytes;
-      mbar_expect_tx(&full[s], stage_bytes);
       const int kx = kbase + it * BK;
-      if (!p.sym) {
+      if (FP8) {
+        // the codes (64 bytes of each of 128 rows, zero filled past A), then the X parts
+        mbar_expect_tx(&full[s], a8_bytes + (uint32_t)p.xparts * b_bytes);
+        tma_load_2d(st + a_bytes + (size_t)p.xparts * b_bytes, &mapA, &full[s], kx, m0);
+      } else if (!p.sym) {
+        mbar_expect_tx(&full[s], stage_bytes);
         tma_load_2d(st, &mapA, &full[s], kx, m0);
       } else {
+        mbar_expect_tx(&full[s], stage_bytes);
         // K block kx of row block m0 / 128: columns of the stored tile on or above the
         // diagonal, else rows kx .. kx + 63 of the stored mirror tile, as two 64-column boxes
         const int64_t i = m0 / BM, kb = kx / 128;
@@ -425,6 +457,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       const int s = it % p.stages;
       const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
       if (!mbar_wait(&full[s], ph, p.budget)) { atomicExch(p.err, 2); s_fail = 1; break; }
+      if (FP8 && !mbar_wait(&conv[s], ph, p.budget)) { atomicExch(p.err, 5); s_fail = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sa = smem_u32(base + (size_t)s * stage_bytes);
       const uint32_t sh = sa + a_bytes, sl = sa + a_bytes + b_bytes;
@@ -447,6 +480,33 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     }
     s_consumed = it;
     mma_commit(accum);  // arrives once every MMA issued above has completed
+  } else if (FP8 && warp >= 2) {
+    // decoder: 16-byte chunk c of row m of the BF16 tile (8 codes) goes to chunk c ^ (m % 8)
+    // of its 128-byte row, the 128-byte swizzle the MMA descriptors expect
+    const int tid = threadIdx.x - 64;
+    for (int it = 0; it < p.k_iters; ++it) {
+      const int s = it % p.stages;
+      const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
+      if (!mbar_wait(&full[s], ph, p.budget)) { atomicExch(p.err, 4); s_fail = 1; break; }
+      unsigned char* st = base + (size_t)s * stage_bytes;
+      const unsigned char* a8 = st + a_bytes + (size_t)p.xparts * b_bytes;
+      const int kt = (kbase + it * BK) / 128;
+      const float sc = kt < p.nt8 ? __ldg(p.scales + (int64_t)(m0 / BM) * p.nt8 + kt) : 0.f;
+#pragma unroll 4
+      for (int i = 0; i < (BM * BK / 8) / 64; ++i) {
+        const int id = tid + 64 * i;
+        const int m = id >> 3, c = id & 7;
+        const uint2 v = *reinterpret_cast<const uint2*>(a8 + m * 64 + c * 8);
+        uint4 o;
+        o.x = e4m3x2_to_bf16x2(v.x, sc);
+        o.y = e4m3x2_to_bf16x2(v.x >> 16, sc);
+        o.z = e4m3x2_to_bf16x2(v.y, sc);
+        o.w = e4m3x2_to_bf16x2(v.y >> 16, sc);
+        *reinterpret_cast<uint4*>(st + m * 128 + ((c ^ (m & 7)) << 4)) = o;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> the MMA's reads
+      mbar_arrive(&conv[s]);
+    }
   }
   __syncwarp();
   __syncthreads();  // role loops finished; s_fail / s_issued / s_consumed visible
@@ -838,6 +898,22 @@ bool make_map(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int
 
 }  // namespace
 
+// Tensor map of the E4M3 code matrix (1-byte elements, pitch ld bytes): 64 x box_rows boxes,
+// unswizzled (the kernel's decoder writes the swizzled BF16 tile itself).
+static bool make_map_u8(CUtensorMap* m, const void* base, int64_t inner, int64_t rows, int64_t ld, int box_rows) {
+  EncodeFn enc = get_encode();
+  if (!enc) { g_last_cu = -1; return false; }
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  g_last_cu = (int)r;
+  return r == CUDA_SUCCESS;
+}
+
 int tc_last_status() { return g_last_cu; }
 
 bool make_map_f32_tile(CUtensorMap* m, const void* base, int64_t cols, int64_t rows, int64_t ld) {
@@ -887,7 +963,7 @@ int launch_sums_bf16(const void* A16, int64_t elems, double* part, cudaStream_t 
   return blocks;
 }
 
-int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune, int xparts) {
+int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune, int xparts, int a8) {
   TcPlan pl{};
   pl.BN = N <= 256 ? ((N + 15) / 16 * 16) : 256;
   if (tune && tune->bn > 0) {
@@ -897,7 +973,8 @@ int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune, int xparts) {
   pl.tiles_n = (N + pl.BN - 1) / pl.BN;
   pl.tiles_m = (int)((n + BM - 1) / BM);
   const int64_t kiters_total = (n + BK - 1) / BK;
-  const uint32_t stage_bytes = BM * BK * 2 + (uint32_t)xparts * pl.BN * BK * 2;
+  // E4M3 A (a8): the stage also holds the 128 x 64 code tile
+  const uint32_t stage_bytes = BM * BK * 2 + (uint32_t)xparts * pl.BN * BK * 2 + (a8 ? BM * BK : 0);
   // two CTAs per SM with a 3-stage ring when it fits in half the SM, else one CTA with
   // as many stages as fit (at most 6)
   int per_sm = 1, stages;
@@ -933,7 +1010,7 @@ int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune, int xparts) {
   pl.k_iters = (int)((kiters_total + splits - 1) / splits);
   pl.tmem_cols = 32;
   while (pl.tmem_cols < pl.BN) pl.tmem_cols *= 2;
-  pl.smem = stage_bytes * stages + 1024 + 8 * (2 * stages + 2) + 64;
+  pl.smem = stage_bytes * stages + 1024 + 8 * (2 * stages + 2) + 64 + (a8 ? 8 * stages : 0);
   *plan = pl;
   return 0;
 }
@@ -941,11 +1018,14 @@ int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune, int xparts) {
 namespace {
 
 // Shared launcher of k_gemm_tc: fused epilogue when epi != NULL && epi->fused.
+// scales8 != NULL: A16 is the E4M3 code matrix (pitch fp8_ld(n) bytes) with its tile scales.
 int launch_tc_impl(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl, int xparts,
                    float* Y, float* ws, size_t ws_elems, int* err, long long budget, const TcEpilogue* epi,
-                   const int* run, cudaStream_t s, const ProdTune* tune, int sym) {
+                   const int* run, cudaStream_t s, const ProdTune* tune, int sym, const float* scales8 = nullptr) {
+  const int a8 = scales8 ? 1 : 0;
+  if (a8) sym = 0;
   TcPlan pl;
-  if (tc_plan(n, N, &pl, tune, xparts) < 0) tc_plan(n, N, &pl, nullptr, xparts);
+  if (tc_plan(n, N, &pl, tune, xparts, a8) < 0) tc_plan(n, N, &pl, nullptr, xparts, a8);
   const int64_t ldk = tc_ld(n);
   if ((size_t)pl.splits * n * ldx > ws_elems) {
     // not enough split workspace: recompute the plan without splitting
@@ -962,20 +1042,26 @@ int launch_tc_impl(const void* A16, int64_t n, const float* X, int N, int64_t ld
     // (K-major use) and 64 x 64 boxes of its rows (the mirror's MN-major use)
     if (!make_map(&ma, A16, 128, sym_tiles(n) * 128, 128, BM) || !make_map(&mt, A16, 128, sym_tiles(n) * 128, 128, 64))
       return -1;
+  } else if (a8) {
+    if (!make_map_u8(&ma, A16, fp8_ld(n), n, fp8_ld(n), BM)) return -1;
   } else if (!make_map(&ma, A16, ldk, n, ldk, BM)) {
     return -1;
   }
   if (!make_map(&mh, xh, ldk, N, ldk, pl.BN) || !make_map(&ml, xparts == 2 ? xl : xh, ldk, N, ldk, pl.BN))
     return -1;
   if (!sym) mt = ma;
-  static bool attr_done = false;
-  if (!attr_done) {
+  static bool attr_done[2] = {false, false};
+  if (!attr_done[a8]) {
     // the plan never asks for more than ~206 KB; static shared memory comes on top
-    if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024) != cudaSuccess) {
+    const cudaError_t ae = a8 ? cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     210 * 1024)
+                              : cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     210 * 1024);
+    if (ae != cudaSuccess) {
       g_last_cu = 10000 + (int)cudaGetLastError();
       return -3;
     }
-    attr_done = true;
+    attr_done[a8] = true;
   }
   TcParams p;
   p.n = n;
@@ -996,8 +1082,13 @@ int launch_tc_impl(const void* A16, int64_t n, const float* X, int N, int64_t ld
   if (epi && epi->fused) p.e = *epi;
   p.sym = sym;
   p.nt = nt;
+  p.scales = scales8;
+  p.nt8 = a8 ? fp8_ntiles(n) : 0;
   dim3 grid(pl.tiles_n, pl.tiles_m, pl.splits);
-  k_gemm_tc<<<grid, 128, pl.smem, s>>>(ma, mh, ml, mt, p);
+  if (a8)
+    k_gemm_tc<true><<<grid, 128, pl.smem, s>>>(ma, mh, ml, mt, p);
+  else
+    k_gemm_tc<false><<<grid, 128, pl.smem, s>>>(ma, mh, ml, mt, p);
   const cudaError_t le = cudaPeekAtLastError();
   if (le != cudaSuccess) { g_last_cu = 10000 + (int)le; return -2; }
   return (epi && epi->fused) ? 0 : pl.splits;
@@ -1017,6 +1108,20 @@ int launch_ax_tc_fused(const void* A16, int64_t n, const float* X, int N, int64_
                        const int* run, cudaStream_t s, const ProdTune* tune, int sym) {
   return launch_tc_impl(A16, n, X, N, ldx, xh, xl, xparts, epi.Y, ws, ws_elems, err, budget, &epi, run, s, tune,
                         sym);
+}
+
+int launch_ax_tc8(const void* A8, const float* scales, int64_t n, const float* X, int N, int64_t ldx, void* xh,
+                  void* xl, float* Y, float* ws, size_t ws_elems, int* err, long long budget, cudaStream_t s,
+                  const ProdTune* tune, int xparts) {
+  return launch_tc_impl(A8, n, X, N, ldx, xh, xl, xparts, Y, ws, ws_elems, err, budget, nullptr, nullptr, s, tune, 0,
+                        scales);
+}
+
+int launch_ax_tc8_fused(const void* A8, const float* scales, int64_t n, const float* X, int N, int64_t ldx,
+                        void* xh, void* xl, int xparts, float* ws, size_t ws_elems, int* err, long long budget,
+                        const TcEpilogue& epi, const int* run, cudaStream_t s, const ProdTune* tune) {
+  return launch_tc_impl(A8, n, X, N, ldx, xh, xl, xparts, epi.Y, ws, ws_elems, err, budget, &epi, run, s, tune, 0,
+                        scales);
 }
 
 int tc_tiles(int64_t n, int N, const ProdTune* tune, int xparts) {

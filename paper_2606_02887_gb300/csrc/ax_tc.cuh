@@ -46,7 +46,7 @@ int64_t tc_ld(int64_t n);
 int tc_last_status();
 // Built-in plan, or the autotuned (per_sm, stages, splits) when `tune` sets them; returns
 // -1 when a tuned ring does not fit in shared memory.
-int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune = nullptr, int xparts = 2);
+int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune = nullptr, int xparts = 2, int a8 = 0);
 // FP64 partial sums of squares / sums of a BF16 array into part[2*block]; returns blocks.
 int launch_sums_bf16(const void* A16, int64_t elems, double* part, cudaStream_t s);
 // The same sums over the whole symmetric matrix held as its upper tiles (the tiles above the
@@ -74,6 +74,16 @@ int launch_ax_tc_fused(const void* A16, int64_t n, const float* X, int N, int64_
                        const int* run, cudaStream_t s, const ProdTune* tune = nullptr, int sym = 0);
 // Output tiles of the product's plan (counters a fused launch needs).
 int tc_tiles(int64_t n, int N, const ProdTune* tune = nullptr, int xparts = 2);
+// The same product with A stored as E4M3 codes (n x fp8_ld(n) bytes) and a power-of-two scale
+// per 128 x 128 tile (scales[fp8_ntiles(n)^2], row-major): the kernel decodes each code tile to
+// BF16 in shared memory (exactly) and runs the BF16 MMAs and epilogue.  Returns as
+// launch_ax_tc / launch_ax_tc_fused (< 0: the tensor map could not be encoded).
+int launch_ax_tc8(const void* A8, const float* scales, int64_t n, const float* X, int N, int64_t ldx, void* xh,
+                  void* xl, float* Y, float* ws, size_t ws_elems, int* err, long long budget, cudaStream_t s,
+                  const ProdTune* tune = nullptr, int xparts = 2);
+int launch_ax_tc8_fused(const void* A8, const float* scales, int64_t n, const float* X, int N, int64_t ldx,
+                        void* xh, void* xl, int xparts, float* ws, size_t ws_elems, int* err, long long budget,
+                        const TcEpilogue& epi, const int* run, cudaStream_t s, const ProdTune* tune = nullptr);
 
 // ---- grouped product of the uneven batch (one CTA per 128-row tile of a problem) ----
 // A_all: BF16, rows of all problems packed, pitch lda; X parts: BF16 hi / lo, row xrow_p + c

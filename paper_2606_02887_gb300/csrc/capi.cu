@@ -189,7 +189,8 @@ TcEpilogue tc_epilogue(snmf_ctx* h, void* Y, double c, const void* X2, const voi
     // the partials are reduced per 64-column chunk of a tile: r must divide 64 and the tile width
     TcPlan pl;
     const ProdTune* tn = h->tuned ? &h->tune.cfg : nullptr;
-    if (tc_plan(h->n, h->N, &pl, tn, h->xparts) < 0) tc_plan(h->n, h->N, &pl, nullptr, h->xparts);
+    const int a8 = h->A.a_dtype == 3;
+    if (tc_plan(h->n, h->N, &pl, tn, h->xparts, a8) < 0) tc_plan(h->n, h->N, &pl, nullptr, h->xparts, a8);
     if (h->r > 64 || 64 % h->r != 0 || h->r % 4 != 0 || pl.BN % h->r != 0) return e;
   }
   e.fused = 1;
@@ -206,15 +207,29 @@ TcEpilogue tc_epilogue(snmf_ctx* h, void* Y, double c, const void* X2, const voi
   return e;
 }
 
-// The product kernel: CUDA cores (FP64/FP32 dense, CSR) or tcgen05 (BF16 dense).  Returns the
-// number of split-K slices written to h->ws (1 = result in Y), or 0 when the epilogue `epi`
-// was fused into the product (the result, c X2 and the partials are complete).
+// The product kernel: CUDA cores (FP64/FP32 dense, CSR, the FP8 final evaluation) or tcgen05
+// (BF16 dense; E4M3 dense, decoded to BF16 in shared memory).  Returns the number of split-K
+// slices written to h->ws (1 = result in Y), or 0 when the epilogue `epi` was fused into the
+// product (the result, c X2 and the partials are complete).
 int product_kernel(snmf_ctx* h, const AxArgs& op, const void* X, void* Y, const int* run,
                    const TcEpilogue* epi = nullptr) {
   const ProdTune* tn = (h->tuned && &op == &h->A) ? &h->tune.cfg : nullptr;  // the tuned shape only
-  if (op.kind == AX_DENSE && op.a_dtype == 3)
+  if (op.kind == AX_DENSE && op.a_dtype == 3) {
+    if (!op.accurate && h->xh) {
+      if (epi && epi->fused) {
+        if (launch_ax_tc8_fused(op.A, op.a_scale, h->n, (const float*)X, h->N, h->N, h->xh, h->xl, h->xparts,
+                                (float*)h->ws, h->ws_elems, h->dev_err, h->budget, *epi, run, h->s, tn) >= 0)
+          return 0;
+      } else {
+        const int sp = launch_ax_tc8(op.A, op.a_scale, h->n, (const float*)X, h->N, h->N, h->xh, h->xl, (float*)Y,
+                                     (float*)h->ws, h->ws_elems, h->dev_err, h->budget, h->s, tn, h->xparts);
+        if (sp >= 1) return sp;
+      }
+      // no tensor map for these codes: the CUDA-core product below
+    }
     return launch_ax_fp8(op.A, op.a_scale, h->n, (const float*)X, h->N, h->N, (float*)Y, (float*)h->ws,
                          h->ws_elems, run, h->s, tn);
+  }
   if (op.kind == AX_DENSE && op.a_dtype == 2 && !op.accurate) {
     if (epi && epi->fused) {
       const int rc = launch_ax_tc_fused(op.A, h->n, (const float*)X, h->N, h->N, h->xh, h->xl, h->xparts,
@@ -249,7 +264,8 @@ int ax_apply(snmf_ctx* h, const AxArgs& op, bool use_lai, const void* X, void* Y
     return lai_apply(h->lai_op, h->tdtype, d, X, Y, c, X2, P1, P2, part, run, h->s);
   }
   TcEpilogue epi;
-  if (op.kind == AX_DENSE && op.a_dtype == 2 && !op.accurate) epi = tc_epilogue(h, Y, c, X2, P1, P2, part);
+  if (op.kind == AX_DENSE && (op.a_dtype == 2 || op.a_dtype == 3) && !op.accurate)
+    epi = tc_epilogue(h, Y, c, X2, P1, P2, part);
   const int splits = product_kernel(h, op, X, Y, run, &epi);
   if (splits == 0) return (int)((h->n + kRowTile - 1) / kRowTile);  // epilogue done in the product
   return launch_ax_finish_impl(h->tdtype, d, Y, h->ws, splits, c, X2, P1, P2, part, 0, run, h->s, dots_after);
@@ -376,7 +392,7 @@ snmf_status time_steps(snmf_ctx* h, int iters, double* ms_dstep, double* ms_upda
 snmf_status autotune_product(snmf_ctx* h) {
   if (h->kind != AX_DENSE) return SNMF_OK;
   static const char* dtn[4] = {"f64", "f32", "bf16", "fp8"};
-  const std::string key = std::string("dense/") + dtn[h->A.a_dtype] + (h->A.a_dtype == 2 && h->xparts == 1 ? "x1" : "") +
+  const std::string key = std::string("dense/") + dtn[h->A.a_dtype] + (h->A.a_dtype >= 2 && h->xparts == 1 ? "x1" : "") +
                           (h->A.sym ? "s" : "") +
                           "/n" + std::to_string(h->n) + "/r" + std::to_string(h->r) + "/N" + std::to_string(h->N);
   const std::string dev = tune_device_key();
@@ -401,7 +417,7 @@ snmf_status autotune_product(snmf_ctx* h) {
     return SNMF_OK;
   }
   std::vector<ProdTune> cand;
-  if (h->A.a_dtype == 2) {
+  if (h->A.a_dtype == 2 || h->A.a_dtype == 3) {
     const int rings[7][2] = {{2, 2}, {2, 3}, {2, 4}, {1, 2}, {1, 3}, {1, 4}, {1, 6}};
     const int bn0 = h->N <= 256 ? (h->N + 15) / 16 * 16 : 256;
     std::vector<int> bns{bn0};
@@ -416,7 +432,7 @@ snmf_status autotune_product(snmf_ctx* h) {
         t.splits = sp;
         t.bn = bn;
         TcPlan pl;
-        if (tc_plan(h->n, h->N, &pl, &t, h->xparts) < 0 || pl.splits != sp) continue;
+        if (tc_plan(h->n, h->N, &pl, &t, h->xparts, h->A.a_dtype == 3) < 0 || pl.splits != sp) continue;
         if ((size_t)sp * h->n * h->N > h->ws_elems && sp > 1) continue;
         cand.push_back(t);
       }
@@ -813,7 +829,7 @@ snmf_status alloc_buffers(snmf_ctx* h) {
   CK(cudaMalloc(&h->recompute, sizeof(int)));
   CK(cudaMalloc(&h->dev_err, sizeof(int)));
   CK(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->s));
-  if (h->kind == AX_DENSE && h->prec == SNMF_BF16) {
+  if (h->kind == AX_DENSE && (h->prec == SNMF_BF16 || h->prec == SNMF_FP8)) {
     const size_t xb = (size_t)h->N * tc_ld(h->n) * 2;
     CK(cudaMalloc(&h->xh, xb));
     CK(cudaMalloc(&h->xl, xb));

@@ -1,6 +1,8 @@
 // FP8 storage of A for the A*X products: A~ = E4M3(A / s_t) * s_t with a power-of-two
 // scale s_t per 128 x 128 tile (the smallest 2^k with max|A_t| / 2^k <= 448), and the
-// CUDA-core product Y = A~ X that dequantizes the codes while staging them.
+// CUDA-core product Y = A~ X that dequantizes the codes while staging them (the final
+// evaluation's product, with X in FP32; the iteration's products run on the tensor cores,
+// k_gemm_tc<true> in ax_tc.cu).
 //
 //   k_fp8_scales : one CTA per tile: max|A_t| (fixed-shape block reduction), s_t exactly
 //                  from frexp (no rounding in the exponent choice)

@@ -1,5 +1,7 @@
 """FP8 storage of A (E4M3 codes, power-of-two scale per 128 x 128 tile) through the C ABI:
-the stored operator against the oracle codec bit for bit, the product, and a full solve."""
+the stored operator against the oracle codec bit for bit, the tensor-core product (codes
+decoded to BF16 in shared memory) against an exact emulation of its operands, and a full
+solve."""
 import math
 
 import numpy as np
@@ -11,6 +13,7 @@ import paper_2606_02887_gb300.snmf as S
 from workloads import planted_dense, uniform_init
 
 from gpu_helpers import gpu_solve, rel
+from test_gpu_bf16 import bf16_round
 
 pytestmark = pytest.mark.gpu
 
@@ -41,24 +44,36 @@ def test_fp8_stored_operator_matches_oracle_codec_bit_exact():
     assert np.array_equal(got, At_oracle), np.max(np.abs(got - At_oracle))
 
 
-def test_fp8_product_against_fp64():
+@pytest.mark.parametrize("n,r,b", [(700, 24, 1), (1000, 10, 1), (256, 64, 1), (2048, 64, 8), (8192, 64, 1),
+                                   (333, 20, 3)])
+def test_fp8_product_matches_emulated_operands(n, r, b):
+    """The product of the stored E4M3 operator runs on the tensor cores as A~ (X_hi + X_lo),
+    X split into two BF16 parts; A~ is exact in BF16 (4 significant bits times a power of two),
+    so the exact product of those operands is the reference.  Bar: the tensor cores' FP32
+    accumulation, as for the BF16 operator (3e-5).  Shapes: ragged n and column counts, 8
+    restarts with the epilogue fused (r = 64), an unfused epilogue (r = 10, 20), n = 8192."""
     import torch
-    g = np.random.default_rng(5)
-    A, _ = planted_dense(700, 8, 0.05, seed=43)
+    g = np.random.default_rng(n + 7 * r + b)
+    A, _ = planted_dense(n, 8, 0.05, seed=43 + n)
     A32 = A.astype(np.float32)
     _, _, At = F.quantize(A32.astype(np.float64))
-    h, keep = _handle(A32, 24, 1)
+    cols = r * b
+    h, keep = _handle(A32, r, b)
     try:
-        Xn = g.random((700, 24)).astype(np.float32)
+        Xn = g.random((n, cols)).astype(np.float32)
         X = torch.tensor(Xn, device="cuda:0")
         Y = torch.empty_like(X)
-        xax = S.snmf_apply(h, X, Y, 24)
+        xax = S.snmf_apply(h, X, Y, cols)
         got = Y.cpu().numpy().astype(np.float64)
     finally:
         S.snmf_destroy(h)
-    ref = At @ Xn.astype(np.float64)
-    assert rel(got, ref) <= 1e-6
-    assert abs(xax - np.sum(Xn.astype(np.float64) * ref)) <= 1e-6 * abs(xax)
+    Xh = bf16_round(Xn)
+    Xl = bf16_round(Xn - Xh)
+    ref = At @ (Xh.astype(np.float64) + Xl.astype(np.float64))
+    assert rel(got, ref) <= 3e-5, rel(got, ref)
+    assert np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-30)) <= 3e-5
+    assert rel(got, At @ Xn.astype(np.float64)) <= 4e-5
+    assert abs(xax - np.sum(Xn.astype(np.float64) * ref)) <= 1e-5 * abs(xax)
 
 
 def test_fp8_solve_reaches_oracle_residual():
