@@ -136,3 +136,20 @@ def test_rollout_labels_pick_the_lowest_objective_and_break_ties_to_one():
                   [np.nan, 1, 1, 1, 1, 1, 1, 1, 1]])                  # non-finite: dropped
     lab = rollout_labels(f)
     assert lab[:4].tolist() == [1.0, 0.0, 0.0, -2.0] and np.isnan(lab[4])
+
+
+def test_rollout_targets_score_by_objective_or_projected_gradient():
+    from paper_2606_02887_gb300.train_controller import rollout_targets
+    feats = np.arange(15, dtype=np.float32).reshape(3, 5)
+    fv = np.array([[3.0, 2, 1, 2, 2, 2, 2, 2, 2],       # objective: multiplier 2^-1
+                   [1.0] * 9,
+                   [np.inf, 1, 1, 1, 1, 1, 1, 1, 1]])     # dropped
+    pv = np.array([[1.0, 1, 1, 1, 1, 1, 1, 1, 0.5],     # projected gradient: multiplier 4
+                   [1.0, 1, 1, 1, 1, 0.9, 1, 1, 1],      # 10% better: kept at margin 0.05 only
+                   [1.0] * 9])
+    f, t = rollout_targets(feats, fv, pv, score="f")
+    assert f.shape == (2, 5) and t.tolist() == [-1.0, 0.0] and np.array_equal(f, feats[:2])
+    f, t = rollout_targets(feats, fv, pv, score="pg", margin=0.05)
+    assert t.tolist() == [2.0, 0.5, 0.0]
+    f, t = rollout_targets(feats, fv, pv, score="pg", margin=0.2)
+    assert t.tolist() == [2.0, 0.0, 0.0]
