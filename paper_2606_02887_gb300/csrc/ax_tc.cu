@@ -12,11 +12,12 @@
 //                   accumulator, tcgen05.commit frees the stage
 //   warps 0-3     : epilogue: tcgen05.ld 32 rows each, store FP32 rows (split-K slice or Y)
 //
-// E4M3 A (k_gemm_tc<true>): TMA stages the 128 x 64 code tile unswizzled beside the ring
-// stage; warps 2-3 decode it, times the power-of-two scale of its 128 x 128 tile of A, into
-// the stage's BF16 A tile in the layout the 128-byte swizzle gives (the decode is exact: an
-// E4M3 value times 2^k has at most 4 significant bits), and the MMA issuer waits for that
-// conversion as well as for the TMA bytes.  The MMAs and the epilogue are the BF16 kernel's.
+// E4M3 A (k_gemm_tc<true>): a ring stage holds the 128 x 64 code tile (unswizzled) and the X
+// parts; warps 2-3 decode the codes, times the power-of-two scale of their 128 x 128 tile of
+// A, into one of two BF16 A buffers outside the ring, in the layout the 128-byte swizzle gives
+// (the decode is exact: an E4M3 value times 2^k has at most 4 significant bits).  The MMA
+// issuer waits for the stage's TMA bytes and for the decoded buffer, and frees the buffer with
+// a commit.  The MMAs and the epilogue are the BF16 kernel's.
 //
 // Every mbarrier wait is bounded by a clock64 budget; on expiry the kernel records an
 // error code, stops issuing, releases its TMEM and returns (no unbounded spin).
@@ -369,19 +370,23 @@ __global__ void __launch_bounds__(128, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapXh,
           const __grid_constant__ CUtensorMap mapXl, const __grid_constant__ CUtensorMap mapAt, TcParams p) {
   extern __shared__ unsigned char smem_raw[];
-  // 1024-byte aligned ring: [stage][A 128x64 | Xh BNx64 | Xl BNx64] (bf16) [| A codes 128x64 (E4M3)]
+  // 1024-byte aligned ring: [stage][A 128x64 | Xh BNx64 | Xl BNx64] (bf16); E4M3 A:
+  // [A buffer 0 | A buffer 1] (bf16, decoded) then the ring [stage][codes 128x64 | Xh | Xl]
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int BN = p.BN;
   const uint32_t a_bytes = BM * BK * 2;
   const uint32_t b_bytes = (uint32_t)BN * BK * 2;
-  constexpr uint32_t a8_bytes = FP8 ? BM * BK : 0;  // E4M3 codes of the A tile, staged by TMA
-  const uint32_t stage_bytes = a_bytes + (uint32_t)p.xparts * b_bytes + a8_bytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)p.stages * stage_bytes);
+  constexpr uint32_t a8_bytes = BM * BK;               // E4M3 codes of the A tile, staged by TMA
+  const uint32_t xoff = FP8 ? a8_bytes : a_bytes;      // offset of the X parts in a stage
+  const uint32_t stage_bytes = xoff + (uint32_t)p.xparts * b_bytes;
+  unsigned char* ring = base + (FP8 ? 2 * a_bytes : 0);
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)p.stages * stage_bytes);
   uint64_t* empty = full + p.stages;
   uint64_t* accum = empty + p.stages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
-  uint64_t* conv = accum + 2;  // E4M3 A: the stage's BF16 A tile is written (64 decoder threads)
+  uint64_t* conv = accum + 2;   // E4M3 A [2]: A buffer decoded (64 decoder threads arrive)
+  uint64_t* afree = accum + 4;  // E4M3 A [2]: A buffer read by its MMAs (commit)
   __shared__ int s_fail, s_issued, s_consumed;
   __shared__ unsigned s_ticket;
 
@@ -398,7 +403,12 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     for (int s = 0; s < p.stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      if (FP8) mbar_init(&conv[s], 64);
+    }
+    if (FP8) {
+      for (int j = 0; j < 2; ++j) {
+        mbar_init(&conv[j], 64);
+        mbar_init(&afree[j], 1);
+      }
     }
     mbar_init(accum, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -420,12 +430,12 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       const int s = it % p.stages;
       const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
       if (!mbar_wait(&empty[s], ph ^ 1u, p.budget)) { atomicExch(p.err, 1); s_fail = 1; break; }
-      unsigned char* st = base + (size_t)s * stage_bytes;
+      unsigned char* st = ring + (size_t)s * stage_bytes;
       const int kx = kbase + it * BK;
       if (FP8) {
         // the codes (64 bytes of each of 128 rows, zero filled past A), then the X parts
-        mbar_expect_tx(&full[s], a8_bytes + (uint32_t)p.xparts * b_bytes);
-        tma_load_2d(st + a_bytes + (size_t)p.xparts * b_bytes, &mapA, &full[s], kx, m0);
+        mbar_expect_tx(&full[s], stage_bytes);
+        tma_load_2d(st, &mapA, &full[s], kx, m0);
       } else if (!p.sym) {
         mbar_expect_tx(&full[s], stage_bytes);
         tma_load_2d(st, &mapA, &full[s], kx, m0);
@@ -445,8 +455,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
           tma_load_2d(st + a_bytes / 2, &mapAt, &full[s], 64, y);
         }
       }
-      tma_load_2d(st + a_bytes, &mapXh, &full[s], kx, n0);
-      if (p.xparts == 2) tma_load_2d(st + a_bytes + b_bytes, &mapXl, &full[s], kx, n0);
+      tma_load_2d(st + xoff, &mapXh, &full[s], kx, n0);
+      if (p.xparts == 2) tma_load_2d(st + xoff + b_bytes, &mapXl, &full[s], kx, n0);
     }
     s_issued = it;
   } else if (warp == 1 && lane == 0) {
@@ -457,10 +467,15 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       const int s = it % p.stages;
       const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
       if (!mbar_wait(&full[s], ph, p.budget)) { atomicExch(p.err, 2); s_fail = 1; break; }
-      if (FP8 && !mbar_wait(&conv[s], ph, p.budget)) { atomicExch(p.err, 5); s_fail = 1; break; }
+      if (FP8 && !mbar_wait(&conv[it & 1], (uint32_t)(it >> 1) & 1u, p.budget)) {
+        atomicExch(p.err, 5);
+        s_fail = 1;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = smem_u32(base + (size_t)s * stage_bytes);
-      const uint32_t sh = sa + a_bytes, sl = sa + a_bytes + b_bytes;
+      const uint32_t st_u = smem_u32(ring + (size_t)s * stage_bytes);
+      const uint32_t sa = FP8 ? smem_u32(base + (size_t)(it & 1) * a_bytes) : st_u;
+      const uint32_t sh = st_u + xoff, sl = st_u + xoff + b_bytes;
       // symmetric storage below the diagonal: A is the transposed mirror tile (MN-major)
       const int kx = kbase + it * BK;
       const bool tr = p.sym && kx < p.n && kx / 128 < m0 / BM;
@@ -477,6 +492,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         }
       }
       mma_commit(&empty[s]);
+      if (FP8) mma_commit(&afree[it & 1]);  // the A buffer may be decoded into again
     }
     s_consumed = it;
     mma_commit(accum);  // arrives once every MMA issued above has completed
@@ -488,8 +504,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       const int s = it % p.stages;
       const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
       if (!mbar_wait(&full[s], ph, p.budget)) { atomicExch(p.err, 4); s_fail = 1; break; }
-      unsigned char* st = base + (size_t)s * stage_bytes;
-      const unsigned char* a8 = st + a_bytes + (size_t)p.xparts * b_bytes;
+      // buffer it % 2, once the MMAs of its previous use (iteration it - 2) have completed
+      if (!mbar_wait(&afree[it & 1], ((uint32_t)(it >> 1) & 1u) ^ 1u, p.budget)) {
+        atomicExch(p.err, 6);
+        s_fail = 1;
+        break;
+      }
+      unsigned char* abuf = base + (size_t)(it & 1) * a_bytes;
+      const unsigned char* a8 = ring + (size_t)s * stage_bytes;
       const int kt = (kbase + it * BK) / 128;
       const float sc = kt < p.nt8 ? __ldg(p.scales + (int64_t)(m0 / BM) * p.nt8 + kt) : 0.f;
 #pragma unroll 4
@@ -502,10 +524,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         o.y = e4m3x2_to_bf16x2(v.x >> 16, sc);
         o.z = e4m3x2_to_bf16x2(v.y, sc);
         o.w = e4m3x2_to_bf16x2(v.y >> 16, sc);
-        *reinterpret_cast<uint4*>(st + m * 128 + ((c ^ (m & 7)) << 4)) = o;
+        *reinterpret_cast<uint4*>(abuf + m * 128 + ((c ^ (m & 7)) << 4)) = o;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> the MMA's reads
-      mbar_arrive(&conv[s]);
+      mbar_arrive(&conv[it & 1]);
     }
   }
   __syncwarp();
@@ -973,16 +995,18 @@ int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune, int xparts, in
   pl.tiles_n = (N + pl.BN - 1) / pl.BN;
   pl.tiles_m = (int)((n + BM - 1) / BM);
   const int64_t kiters_total = (n + BK - 1) / BK;
-  // E4M3 A (a8): the stage also holds the 128 x 64 code tile
-  const uint32_t stage_bytes = BM * BK * 2 + (uint32_t)xparts * pl.BN * BK * 2 + (a8 ? BM * BK : 0);
+  // E4M3 A (a8): a stage holds the 128 x 64 code tile instead of the BF16 A tile, and the two
+  // decoded BF16 A buffers sit outside the ring
+  const uint32_t stage_bytes = (a8 ? BM * BK : BM * BK * 2) + (uint32_t)xparts * pl.BN * BK * 2;
+  const uint32_t fixed = a8 ? 2 * BM * BK * 2 : 0;
   // two CTAs per SM with a 3-stage ring when it fits in half the SM, else one CTA with
   // as many stages as fit (at most 6)
   int per_sm = 1, stages;
-  if (3 * stage_bytes + 4096 <= 110 * 1024) {
+  if (3 * stage_bytes + fixed + 4096 <= 110 * 1024) {
     per_sm = 2;
     stages = 3;
   } else {
-    stages = (int)((200 * 1024) / stage_bytes);
+    stages = (int)((200 * 1024 - fixed) / stage_bytes);
     if (stages > 6) stages = 6;
     if (stages < 2) stages = 2;
   }
@@ -990,7 +1014,7 @@ int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune, int xparts, in
     per_sm = tune->per_sm;
     stages = tune->stages;
     const size_t cap = per_sm == 2 ? 110 * 1024 : 206 * 1024;
-    if ((size_t)stage_bytes * stages + 4096 > cap || stages < 2) return -1;
+    if ((size_t)stage_bytes * stages + fixed + 4096 > cap || stages < 2) return -1;
   }
   pl.stages = stages;
   const int tiles = pl.tiles_n * pl.tiles_m;
@@ -1010,7 +1034,7 @@ int tc_plan(int64_t n, int N, TcPlan* plan, const ProdTune* tune, int xparts, in
   pl.k_iters = (int)((kiters_total + splits - 1) / splits);
   pl.tmem_cols = 32;
   while (pl.tmem_cols < pl.BN) pl.tmem_cols *= 2;
-  pl.smem = stage_bytes * stages + 1024 + 8 * (2 * stages + 2) + 64 + (a8 ? 8 * stages : 0);
+  pl.smem = fixed + stage_bytes * stages + 1024 + 8 * (2 * stages + 2) + 64 + (a8 ? 32 : 0);
   *plan = pl;
   return 0;
 }
