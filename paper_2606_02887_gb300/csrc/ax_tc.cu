@@ -1148,12 +1148,6 @@ int launch_ax_tc8_fused(const void* A8, const float* scales, int64_t n, const fl
                         scales);
 }
 
-int tc_tiles(int64_t n, int N, const ProdTune* tune, int xparts) {
-  TcPlan pl;
-  if (tc_plan(n, N, &pl, tune, xparts) < 0) tc_plan(n, N, &pl, nullptr, xparts);
-  return pl.tiles_n * pl.tiles_m;
-}
-
 void launch_bsplit_x(const TcItem* items, int nitems, const int* cnt, const float* X, void* xh, void* xl,
                      int64_t lda, const void* ctl, size_t ctl_stride, size_t active_off, const int* run,
                      cudaStream_t s) {

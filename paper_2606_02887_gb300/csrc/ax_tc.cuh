@@ -72,8 +72,6 @@ int launch_ax_tc(const void* A16, int64_t n, const float* X, int N, int64_t ldx,
 int launch_ax_tc_fused(const void* A16, int64_t n, const float* X, int N, int64_t ldx, void* xh, void* xl,
                        int xparts, float* ws, size_t ws_elems, int* err, long long budget, const TcEpilogue& epi,
                        const int* run, cudaStream_t s, const ProdTune* tune = nullptr, int sym = 0);
-// Output tiles of the product's plan (counters a fused launch needs).
-int tc_tiles(int64_t n, int N, const ProdTune* tune = nullptr, int xparts = 2);
 // The same product with A stored as E4M3 codes (n x fp8_ld(n) bytes) and a power-of-two scale
 // per 128 x 128 tile (scales[fp8_ntiles(n)^2], row-major): the kernel decodes each code tile to
 // BF16 in shared memory (exactly) and runs the BF16 MMAs and epilogue.  Returns as

@@ -1159,13 +1159,6 @@ snmf_status batch_profile_ax(BatchCtx* b, int iters, double* ms, std::string* er
   return SNMF_OK;
 }
 
-int64_t batch_product_bytes(const BatchCtx* b) {
-  const int64_t asz = b->a_dtype == 0 ? 8 : (b->a_dtype == 2 ? 2 : 4);
-  int64_t t = 0;
-  for (const BProb& q : b->hp) t += q.n * q.n * asz + 2 * q.n * q.r * (int64_t)b->esz;
-  return t;
-}
-
 snmf_status batch_get_factors(BatchCtx* b, void* W, void* Ht, std::string* err) {
   if (!b->have_result) { *err = "no solve has run"; return SNMF_ERR_STATE; }
   const size_t fbytes = (size_t)b->xtot * b->esz;

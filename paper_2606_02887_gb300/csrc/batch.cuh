@@ -29,9 +29,8 @@ int batch_nprob(const BatchCtx* b);
 // Budget (clock64 cycles) of the bounded device waits of the engine's tensor-core product.
 void batch_set_budget(BatchCtx* b, long long cycles);
 // Mean time (ms, CUDA events on the engine's stream) of one grouped A_p X_p product over
-// every problem, and its algorithmic bytes (sum of n_p^2 stored A bytes + X and Y).
+// every problem.
 snmf_status batch_profile_ax(BatchCtx* b, int iters, double* ms, std::string* err);
-int64_t batch_product_bytes(const BatchCtx* b);
 void batch_destroy(BatchCtx* b);
 
 }  // namespace snmf

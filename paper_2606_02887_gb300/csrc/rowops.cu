@@ -136,15 +136,10 @@ __global__ void k_rho(const double* __restrict__ G64, int r, int iters, double r
 }
 
 // ---------------------------------------------------------------------------
-// Penalty form control (Sec. 2.1): block start / line search / update.
+// Penalty form control (Sec. 2.1) as a separate launch: the line search.  The block start and
+// the update run fused into the producing row kernels (fused_control).
 // prow: row-kernel partials (q layout of EPI_GRAD / EPI_DIR), nrow slots.
 // ---------------------------------------------------------------------------
-__global__ void k_ctl_pen_start(Ctl* __restrict__ ctl, const double* __restrict__ prow, int nrow,
-                                int b, Params P, int is_w_block, int first) {
-  __shared__ double sh[32];
-  pen_start_body(ctl[blockIdx.x], prow, nrow, b, blockIdx.x, P, is_w_block, first, sh);
-}
-
 // After DIR (q: 0 gd, 1 dd, 2 f(Z)-f(X_k)) and the Gram of D (pair `dpair`):
 // line search on f(Z + beta D) - f(Z) = beta gd + beta^2/2 q with
 // q = <D^T D, H H^T> + lambda ||D||^2 + gamma <D, L D>.
@@ -154,13 +149,6 @@ __global__ void k_ctl_pen_ls(Ctl* __restrict__ ctl, const double* __restrict__ p
                              Params P, int graph) {
   __shared__ double sh[32];
   pen_ls_body(ctl[blockIdx.x], prow, nrow, pax, nax, b, r, blockIdx.x, G64fix, DtD, P, graph, sh);
-}
-
-// After UPD (q: 0 pg2, 1 f-const, 2 ss, 3 sy, 4 yy, 5 f(X')-f(Z)).
-__global__ void k_ctl_pen_upd(Ctl* __restrict__ ctl, const double* __restrict__ prow, int nrow,
-                              int b, Params P, int is_h_block, int last) {
-  __shared__ double sh[32];
-  pen_upd_body(ctl[blockIdx.x], prow, nrow, b, blockIdx.x, P, is_h_block, last, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -643,18 +631,10 @@ void launch_convert(int sdtype, int ddtype, const void* src, int64_t rows, int64
     k_convert<float, float><<<blocks, 256, 0, s>>>((const float*)src, rows, cols, lds, (float*)dst, ldd);
 }
 
-void launch_ctl_pen_start(Ctl* ctl, const double* prow, int nrow, int b, const Params& P, int is_w,
-                          int first, cudaStream_t s) {
-  k_ctl_pen_start<<<b, 32, 0, s>>>(ctl, prow, nrow, b, P, is_w, first);
-}
 void launch_ctl_pen_ls(Ctl* ctl, const double* prow, int nrow, const double* pax, int nax, int b,
                        int r, const double* G64fix, const double* DtD, const Params& P, int graph,
                        cudaStream_t s) {
   k_ctl_pen_ls<<<b, 32, 0, s>>>(ctl, prow, nrow, pax, nax, b, r, G64fix, DtD, P, graph);
-}
-void launch_ctl_pen_upd(Ctl* ctl, const double* prow, int nrow, int b, const Params& P, int is_h,
-                        int last, cudaStream_t s) {
-  k_ctl_pen_upd<<<b, 32, 0, s>>>(ctl, prow, nrow, b, P, is_h, last);
 }
 void launch_ctl_dir_init(Ctl* ctl, const double* pax, int nax, const double* prow, int nrow,
                          const double* plx, int nlx, const double* GW, int b, int r, const Params& P,

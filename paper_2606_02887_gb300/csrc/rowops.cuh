@@ -104,13 +104,9 @@ void launch_matrix_sums(int kind, int vdtype, const void* vals, int64_t n, int64
 void launch_convert(int sdtype, int ddtype, const void* src, int64_t rows, int64_t cols, int64_t lds,
                     void* dst, int64_t ldd, cudaStream_t s);
 
-void launch_ctl_pen_start(Ctl* ctl, const double* prow, int nrow, int b, const Params& P, int is_w,
-                          int first, cudaStream_t s);
 void launch_ctl_pen_ls(Ctl* ctl, const double* prow, int nrow, const double* pax, int nax, int b,
                        int r, const double* G64fix, const double* DtD, const Params& P, int graph,
                        cudaStream_t s);
-void launch_ctl_pen_upd(Ctl* ctl, const double* prow, int nrow, int b, const Params& P, int is_h,
-                        int last, cudaStream_t s);
 void launch_ctl_dir_init(Ctl* ctl, const double* pax, int nax, const double* prow, int nrow,
                          const double* plx, int nlx, const double* GW, int b, int r, const Params& P,
                          cudaStream_t s);
