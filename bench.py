@@ -704,9 +704,8 @@ def main():
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12  # TFLOP/s at max clock
     achieved_tflops = flops / (ms_kern * 1e-3) / 1e12 if ms_kern > 0 else None
     aw_gbs = alg_bytes / (ms_kern * 1e-3) / 1e9 if ms_kern > 0 else None
-    if args.precision in ("f32", "fp8"):
-        kn = "k_gemm_dense<float> (CUDA-core FFMA)" if args.precision == "f32" else \
-            "k_gemm_fp8 (E4M3 codes decoded in registers, CUDA-core FFMA)"
+    if args.precision == "f32":
+        kn = "k_gemm_dense<float> (CUDA-core FFMA)"
         roof = {"bound": "alu", "kernel": kn, "achieved": achieved_tflops,
                 "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak if achieved_tflops else None,
                 "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
@@ -714,8 +713,9 @@ def main():
                 "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "flops_per_launch": flops,
                 "ms_per_launch": ms_kern, "ms_per_product_with_epilogue": ms_prod}
-    elif args.precision == "bf16":
-        workload_key = "dense8192" + ("-sym" if sym else "") if args.n == 8192 else None
+    elif args.precision in ("bf16", "fp8"):
+        # E4M3 A: the same tcgen05 kernel with the code tiles decoded to BF16 in shared memory
+        workload_key = "dense8192" + ("-sym" if sym else "") if args.n == 8192 and args.precision == "bf16" else None
         # the method's flops 2 n^2 N; the tensor pipes execute x_parts times that (X as hi + lo
         # BF16 parts takes two MMA passes)
         tflops = flops / (ms_kern * 1e-3) / 1e12
@@ -723,8 +723,10 @@ def main():
         intensity = args.x_parts * flops / alg_bytes
         tensor_bound = intensity > ridge
         roof = {"bound": "tensor" if tensor_bound else "hbm",
-                "kernel": "k_split_x + k_gemm_tc (tcgen05 BF16, X as %s, split-K reduced and epilogue fused "
-                          "in the kernel%s)" % ("hi+lo BF16 parts" if args.x_parts == 2 else "one BF16 part",
+                "kernel": "k_split_x + %s (tcgen05 BF16, X as %s, split-K reduced and epilogue fused "
+                          "in the kernel%s)" % ("k_gemm_tc" if args.precision == "bf16" else
+                                               "k_gemm_tc<true> (E4M3 code tiles decoded to BF16 in shared memory)",
+                                               "hi+lo BF16 parts" if args.x_parts == 2 else "one BF16 part",
                                                "; A as its upper 128 x 128 tiles" if sym else ""),
                 "achieved": tflops if tensor_bound else aw_gbs,
                 "peak": peaks["bf16_tflops"] if tensor_bound else peaks["hbm_gbs"],
